@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 transfer-operator path.
+
+One step = one pass of the whole hot path over one atmosphere: the
+right-hand side (formal solve with boundaries), the Jacobi diagonal, and a
+Jacobi-preconditioned GMRES(30) solve to ||r||/||b|| < 1e-8, each iteration
+being one matrix-free apply (quadrature T, formal solver Lambda) plus the
+Arnoldi orthogonalisation.  Workload: N_s=300, N_mu=32, N_nu=101
+(1,939,200 unknowns), tau 1e-4..1e8, x in [-8,8], eps=1e-4, a=1e-3, W2=1,
+DELO-linear, FP64.
+
+Reported value: operator applies per second over the timed solves (whole job
+over all ranks).  Extra keys: solves/s, the standalone apply rate and its
+algorithmic HBM bandwidth, the roofline object, the oracle's CPU rate.
+
+Multi-GPU: independent replicas (one atmosphere per rank, no collective on
+the data path; weak scaling), timed between barriers, max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "operator applies/s & HBM GB/s; batched solves/s at resid 1e-8; p50/p99 latency"
+WORKLOAD = "slab300: Ns=300 Nmu=32 Nnu=101 (1,939,200 unknowns), line-centre tau 1e-4..1e8, x in [-8,8], " \
+           "eps=1e-4 a=1e-3 W2=1, DELO-linear; Jacobi-GMRES(30) to 1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "local_lambda", "none"])
+    ap.add_argument("--apply-reps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle
+def cpu_baseline(precond: str, budget_s: float = 20.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    same workload: one GMRES(30) restart cycle (30 applies + MGS), in a child
+    process with BLAS pinned to one thread."""
+    code = f"""
+import json, os, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import rt_workloads as W
+from oracle.transfer import Transfer
+from oracle import krylov as K
+at = W.slab300()
+tr = Transfer(at)
+b = tr.rhs_I()
+d = tr.jacobi_I()
+Minv = {{"jacobi": lambda v: v / d, "local_lambda": tr.local_lambda_I_inverse, "none": None}}[{precond!r}]
+t0 = time.perf_counter()
+x, info = K.gmres(tr.apply_I, b, M_inv=Minv, restart=30, maxit=30, tol=1e-30)
+dt = time.perf_counter() - t0
+print(json.dumps({{"applies": info.applies, "seconds": dt}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=max(120.0, 10 * budget_s))
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["applies"] / d["seconds"], "unit": "applies/s", "cores": 1, "kind": "oracle",
+            "sample": f"one GMRES(30) restart cycle of the slab300 solve ({d['applies']} applies, "
+                      f"{d['seconds']:.1f} s), numpy FP64, BLAS pinned to 1 thread"}
+
+
+def reference_main(args, rank, world):
+    """--impl reference: the oracle timed on the host cores on the same workload."""
+    if rank != 0:
+        return
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(args.precond)
+        if "value" in cb:
+            vals.append(cb["value"])
+    if not vals:
+        print(json.dumps({"impl": "reference", "unavailable": cb.get("error", "oracle failed")}))
+        return
+    v = statistics.median(vals)
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "applies/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 30 / v,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "precond": args.precond},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+    if args.impl == "reference":
+        if dist is not None:
+            import torch
+            dist.init_process_group("gloo")
+        reference_main(args, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    import rt_workloads as W
+    from paper_2110_11873_gb300 import Problem, _native
+    from paper_2110_11873_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    if dist is not None:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    lib = _native.load()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    at = W.slab300()
+    P = Problem(at)
+    N = P.N
+    stream = torch.cuda.current_stream()
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    d = torch.empty(N, dtype=torch.float64, device="cuda")
+    x = torch.empty(N, dtype=torch.float64, device="cuda")
+
+    def step():
+        P.rhs(out=b)
+        P.jacobi_diag(out=d)
+        _, info = P.solve(b, "gmres", x=x, restart=30, precond=args.precond, rtol=1e-8)
+        return info
+
+    launches0 = lib.rt_launch_count() if hasattr(lib, "rt_launch_count") else None
+    for _ in range(max(args.warmup, 3)):
+        info = step()
+    assert info.ok, info
+    barrier()
+    applies = 0
+    solves = 0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        if hasattr(lib, "rt_launch_count"):
+            launches0 = lib.rt_launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            info = step()
+            applies += info.applies
+            solves += 1
+        e1.record(stream)
+        barrier()
+        launches1 = lib.rt_launch_count() if hasattr(lib, "rt_launch_count") else None
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    cnt = torch.tensor([applies, solves], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    applies_all, solves_all = (float(v) for v in cnt.tolist())
+    value = applies_all / (ms_max / 1000.0)
+
+    # ---- standalone operator apply (the roofline unit): y = x - Lambda T J x
+    xin = torch.randn(N, dtype=torch.float64, device="cuda")
+    yout = torch.empty_like(xin)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(5):
+        P.apply(xin, out=yout)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.apply_reps):
+        flush.zero_()   # 256 MB write: evicts the 129 MB L2 between launches
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        P.apply(xin, out=yout)
+        a1.record(stream)
+        evs.append((a0, a1))
+    torch.cuda.synchronize()
+    apply_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in evs)
+    alg_bytes = 2 * N * 8
+    apply_gbs = alg_bytes / (apply_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    # ---- end to end through the public API with host buffers
+    b_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    x_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    P.rhs(out=b)
+    b_host.copy_(b)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_applies = 0
+    for _ in range(args.steps):
+        b.copy_(b_host, non_blocking=True)
+        _, info = P.solve(b, "gmres", x=x, restart=30, precond=args.precond, rtol=1e-8)
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_applies += info.applies
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = e2e_applies * world / float(te.item())
+
+    # ---- local-Lambda solve rate, for context
+    _, li = P.solve(b, "gmres", x=x, restart=30, precond="local_lambda", rtol=1e-8)
+    torch.cuda.synchronize()
+    tl0 = time.perf_counter()
+    nl = 3
+    for _ in range(nl):
+        _, li = P.solve(b, "gmres", x=x, restart=30, precond="local_lambda", rtol=1e-8)
+    torch.cuda.synchronize()
+    ll_solve_ms = (time.perf_counter() - tl0) * 1000 / nl
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precond": args.precond, "restart": 30, "rtol": 1e-8,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "Krylov basis 31 x 15.5 MB = 480 MB > 129 MB L2; standalone applies flush L2 "
+                             "with a 256 MB write between launches"},
+            "solves_per_s": solves_all / (ms_max / 1000.0),
+            "iters_per_solve": info.iters, "applies_per_solve": info.applies,
+            "apply": {"ms": apply_ms, "applies_per_s": 1000.0 / apply_ms, "alg_gbs": apply_gbs},
+            "local_lambda_solve": {"iters": li.iters, "ms": ll_solve_ms, "solves_per_s": 1000.0 / ll_solve_ms},
+            "roofline": {"kernel": "operator apply (k_moments + k_formal64)", "bound": "hbm",
+                         "achieved": apply_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": apply_gbs / hbm_peak, "traffic": None,
+                         "note": "of measured hbm_gbs; algorithmic bytes 2*N*8 per apply"},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_value, "unit": "applies/s", "h2d_bytes_per_step": N * 8,
+                    "d2h_bytes_per_step": N * 8},
+            "gpu_launches": (launches1 - launches0) if launches0 is not None else None,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(args.precond)
+        print(json.dumps(out))
+    P.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

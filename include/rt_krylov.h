@@ -1,0 +1,190 @@
+/*
+ * rt_krylov.h -- C ABI of the GB300 (sm_103a) matrix-free transfer operator and
+ * Krylov solvers for the 1D two-level-atom CRD polarized transfer problem of
+ * Benedusi, Janett, Belluzzi & Krause (2021), "Numerical solutions to linear
+ * transfer problems of polarized radiation II" (Sect. 3-4).
+ *
+ * Unknown: the I-form vector of Eq. (19), the Stokes I and Q radiation field
+ * at every height z_k, direction mu_m and frequency nu_p:
+ *
+ *     x[s][k][m][p],  s = 0 (I), 1 (Q);  k = 0..Ns-1 (top, smallest tau, to
+ *     bottom);  m = 0..Nmu-1 (mu ascending: the Nmu/2 downward directions
+ *     first);  p = 0..Nnu-1 (reduced frequency ascending);
+ *     flat index ((s*Ns + k)*Nmu + m)*Nnu + p,  length N = 2*Ns*Nmu*Nnu.
+ *
+ * Operator (Eq. 19, Algorithm 1 transposed to the I-form):
+ *     A x = x - Lambda(T(J x)),
+ *   J: sigma00_k = xi * J00_k, sigma20_k = xi * W2 * J20_k  (Eq. 11-14, xi = 1-eps)
+ *   T: S_I(k,m) = sigma00_k + T201(mu_m) sigma20_k, S_Q(k,m) = T202(mu_m) sigma20_k (Eq. 7-8)
+ *   Lambda: formal solution of Eq. (9)-(10) along every (m,p) ray with zero inflow.
+ * Right-hand side (Eq. 19): b = Lambda T c + t with c = [eps B_k, 0] and the
+ * boundary conditions after Eq. (10) (I = B(tau_Ns), Q = 0 entering at the
+ * bottom for mu > 0; nothing entering at the top).
+ *
+ * Memory: every vector argument named *_dev is caller-owned device memory on
+ * the device that was current at rt_problem_create; the library never frees
+ * it and keeps no pointer to it after the call returns.  Host arrays in
+ * rt_problem_desc are copied by rt_problem_create.  The problem owns its
+ * device workspaces (coefficient tables, Krylov basis) until
+ * rt_problem_destroy.  `stream` is a cudaStream_t (NULL = legacy default
+ * stream); all device work of a call is ordered on it.  Calls on one problem
+ * must not overlap in time (one host thread at a time, one stream at a time).
+ *
+ * Errors: every entry point returns an rt_status and never throws;
+ * rt_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef RT_KRYLOV_H
+#define RT_KRYLOV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RT_OK = 0,
+  RT_EINVAL = 1,       /* invalid argument; nothing was launched */
+  RT_ENOMEM = 2,       /* device allocation failed */
+  RT_ECUDA = 3,        /* a CUDA runtime call failed; see rt_last_error() */
+  RT_ENOTCONV = 4,     /* maxit reached: x_dev holds the last iterate */
+  RT_EBREAKDOWN = 5,   /* Krylov breakdown (zero denominator); x_dev holds the last iterate */
+  RT_ENUMERIC = 6,     /* NaN or Inf met in a residual */
+  RT_EPENDING = 7,     /* batch ticket not finished yet */
+  RT_ETIMEOUT = 8      /* a device-side bounded wait gave up */
+} rt_status;
+
+/* optical-depth convention (reading of Sect. 4.1): the tau grid is line-centre
+   optical depth (path depth at frequency p scaled by H(a,x_p)/H(a,0)) or
+   frequency-integrated optical depth (scaled by phi(x_p) = H(a,x_p)/sqrt(pi)) */
+enum { RT_TAU_LINE_CENTER = 0, RT_TAU_FREQ_INTEGRATED = 1 };
+/* angular quadrature: Gauss-Legendre per hemisphere (Nmu/2 nodes on [0,1] and
+   their mirror) or Nmu Gauss-Legendre nodes on [-1,1] (Sect. 4.1) */
+enum { RT_MU_GL_HALF = 0, RT_MU_GL_FULL = 1 };
+/* formal solver (Sect. 4.1): DELO-linear, implicit Euler, trapezoidal */
+enum { RT_FS_DELO_LINEAR = 0, RT_FS_IMPLICIT_EULER = 1, RT_FS_TRAPEZOIDAL = 2 };
+
+typedef struct {
+  int32_t Ns;              /* heights, >= 2 */
+  int32_t Nmu;             /* directions, even, >= 2, <= 256 */
+  int32_t Nnu;             /* frequencies, >= 2 */
+  const double* tau;       /* host, Ns strictly increasing optical depths (required) */
+  const double* B;         /* host, Ns Planck values, or NULL for B = 1 */
+  const double* phi;       /* host, Nnu profile values phi(x_p) = H(a,x_p)/sqrt(pi), or
+                              NULL to compute the Voigt profile internally (needs 0 < a <= 0.1);
+                              for RT_TAU_LINE_CENTER, phi at x = 0 is taken as
+                              phi_center (below) */
+  double phi_center;       /* used only when phi != NULL and tau_kind is line-centre:
+                              phi(0) = H(a,0)/sqrt(pi) */
+  double x_min, x_max;     /* uniform reduced-frequency grid, x_min < x_max */
+  double a;                /* Voigt damping (Sect. 3.1: 1e-3) */
+  double eps;              /* thermalisation parameter, 0 < eps <= 1 (Eq. 13) */
+  double W2;               /* polarizability factor on sigma^2_0 (Eq. 14: 1) */
+  int32_t tau_kind;        /* RT_TAU_* */
+  int32_t mu_quad;         /* RT_MU_* */
+  int32_t formal_solver;   /* RT_FS_* */
+  int32_t freq_norm;       /* 1: divide the trapezoidal spectral weights by their sum;
+                              0: plain trapezoid (the paper's tables) */
+} rt_problem_desc;
+
+typedef struct rt_problem rt_problem;
+
+/* Build grids, profile and coefficient tables for one atmosphere (Sect. 3.2,
+   4.1).  Device workspaces are allocated here.  RT_EINVAL for Ns < 2, odd or
+   out-of-range Nmu, Nnu < 2, eps outside (0,1], a <= 0 (or a > 0.1 with
+   phi == NULL), non-increasing tau, x_min >= x_max, unknown enums. */
+rt_status rt_problem_create(const rt_problem_desc* desc, void* stream, rt_problem** out);
+rt_status rt_problem_destroy(rt_problem* prob);
+/* N = 2*Ns*Nmu*Nnu, or -1 for NULL */
+int64_t rt_problem_size(const rt_problem* prob);
+
+/* Host copies of the discrete grids (any pointer may be NULL):
+   mu[Nmu], w_mu[Nmu] (sum 2), x[Nnu], phi[Nnu], w_nu[Nnu] (spectral weights,
+   sum 1 with freq_norm), phi_hat[Nnu] (optical-depth scale per frequency). */
+rt_status rt_problem_grids(const rt_problem* prob, double* mu, double* w_mu, double* x,
+                           double* phi, double* w_nu, double* phi_hat);
+
+/* y = x - Lambda(T(J x))   (Eq. 19; Algorithm 1).  x_dev, y_dev: N doubles,
+   distinct buffers.  FP64 throughout. */
+rt_status rt_apply(rt_problem* prob, const double* x_dev, double* y_dev, void* stream);
+
+/* Same operator with FP32 vectors and FP32 quadrature and formal solver
+   (coefficients recomputed in FP32 with the small-Delta series). */
+rt_status rt_apply_f32(rt_problem* prob, const float* x_dev, float* y_dev, void* stream);
+
+/* b = Lambda T c + t of Eq. (19): one formal solve with S_I = eps B, S_Q = 0
+   and the boundary radiation.  b_dev: N doubles. */
+rt_status rt_rhs(rt_problem* prob, double* b_dev, void* stream);
+
+/* Diagonal of Id - Lambda T J (Jacobi P = D, Sect. 2.3):
+   D_I = 1 - xi beta* w_m w_p (1 + W2 T201^2), D_Q = 1 - xi W2 beta* w_m w_p T202^2,
+   beta* the coefficient of S_k in the last formal-solver step ending at k.
+   d_dev: N doubles. */
+rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream);
+
+/* z = P^{-1} v for the local-Lambda preconditioner P = Id - Lambda* T J
+   (Lambda* the diagonal of Lambda): P^{-1} v = v + Lambda* T M^{-1} J v with
+   M_k = Id - J_k Lambda*_k T_k the 2x2 per-height block of the sigma-form
+   (Eq. 18).  This is the sigma-form block-Jacobi preconditioner of Sect. 2.3
+   carried to the I-form by the Woodbury identity.  v_dev, z_dev: N doubles. */
+rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double* z_dev, void* stream);
+
+/* ---------------------------------------------------------------- solvers */
+enum { RT_PREC_NONE = 0, RT_PREC_JACOBI = 1, RT_PREC_LOCAL_LAMBDA = 2 };
+enum { RT_X0_ZERO = 0, RT_X0_USER = 1 };
+enum { RT_ORTHO_MGS = 0, RT_ORTHO_CGS2 = 1 };
+enum { RT_PRECISION_FP64 = 0, RT_PRECISION_FP32_REFINE = 1 };
+
+typedef struct {
+  int32_t restart;       /* GMRES restart length m, 1..64 (Sect. 2.1) */
+  int32_t maxit;         /* cap on iterations (Arnoldi steps / BiCGSTAB-CGS iterations) */
+  int32_t precond;       /* RT_PREC_*, applied from the right */
+  int32_t x0_kind;       /* RT_X0_ZERO, or RT_X0_USER: x_dev holds the initial guess */
+  int32_t ortho;         /* GMRES Arnoldi: RT_ORTHO_MGS (default) or RT_ORTHO_CGS2 */
+  int32_t precision;     /* RT_PRECISION_FP64, or FP32 operator inside FP64 iterative refinement */
+  double rtol;           /* stop when ||b - A x||_2 / ||b||_2 < rtol (Sect. 4.2) */
+  double inner_rtol;     /* FP32_REFINE: relative tolerance of each inner solve (e.g. 1e-4) */
+  int32_t max_refine;    /* FP32_REFINE: cap on refinement steps */
+  double* resid_hist;    /* optional host array: relative residual estimate per iteration */
+  int32_t hist_cap;      /* its capacity */
+} rt_solver_opts;
+
+typedef struct {
+  rt_status status;
+  int32_t iters;         /* Arnoldi steps (GMRES) or full iterations (BiCGSTAB, CGS), all cycles */
+  int32_t restarts;      /* GMRES cycles */
+  int32_t applies;       /* products with A (FP64 and FP32) */
+  int32_t refine_steps;  /* FP32_REFINE outer steps */
+  int32_t hist_len;      /* entries written to resid_hist */
+  double rel_resid;      /* final ||b - A x|| / ||b||, FP64 operator */
+  double t_total_ms;     /* wall time of the call */
+} rt_solve_info;
+
+/* Fill opts with defaults: restart 30, maxit 10000, Jacobi, x0 = 0, MGS,
+   FP64, rtol 1e-8, inner_rtol 1e-4, max_refine 20, no history. */
+void rt_solver_opts_default(rt_solver_opts* opts);
+
+/* Right-preconditioned restarted GMRES(m) (Sect. 2.1; Saad & Schultz 1986).
+   b_dev, x_dev: N doubles.  Returns RT_OK when converged, RT_ENOTCONV at
+   maxit, RT_EBREAKDOWN, RT_ENUMERIC; in each case x_dev holds the iterate. */
+rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
+                         double* x_dev, rt_solve_info* info, void* stream);
+/* Right-preconditioned BiCGSTAB (Sect. 2.2; van der Vorst 1992). */
+rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
+                            double* x_dev, rt_solve_info* info, void* stream);
+/* Right-preconditioned CGS (Sect. 2.2; Sonneveld 1989). */
+rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
+                       double* x_dev, rt_solve_info* info, void* stream);
+
+/* Thread-local message describing the last error returned on this thread. */
+const char* rt_last_error(void);
+
+/* Instrumentation (the paper has no counterpart; it counts this library's
+   work): number of kernels this library has launched in the process so far.
+   A kernel node of a captured CUDA graph counts once per graph launch. */
+int64_t rt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_KRYLOV_H */

@@ -1,0 +1,178 @@
+"""Thin Python layer over the C ABI: PyTorch supplies device memory and the
+stream; every step of the computation runs in the library's kernels."""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+_DESC_FIELDS = ("Ns", "Nmu", "Nnu", "tau", "B", "x_min", "x_max", "a", "eps", "W2", "tau_kind",
+                "mu_quad", "formal_solver", "freq_norm")
+
+
+def _dptr(arr: np.ndarray):
+    return arr.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclasses.dataclass
+class SolveResult:
+    status: int
+    iters: int
+    restarts: int
+    applies: int
+    refine_steps: int
+    rel_resid: float
+    t_total_ms: float
+    history: np.ndarray
+
+    @property
+    def ok(self) -> bool:
+        return self.status == N.RT_OK
+
+    @property
+    def status_name(self) -> str:
+        return N.STATUS_NAMES.get(self.status, str(self.status))
+
+
+class Problem:
+    """One atmosphere on the current CUDA device.
+
+    ``atm`` is any object with the descriptor fields of rt_problem_desc
+    (Ns, Nmu, Nnu, tau, B, x_min, x_max, a, eps, W2, tau_kind, mu_quad,
+    formal_solver, freq_norm); ``phi`` optionally overrides the internal
+    Voigt profile (with ``phi_center`` for line-centre tau).
+    """
+
+    def __init__(self, atm, phi: Optional[np.ndarray] = None, phi_center: float = 0.0,
+                 stream: Optional[torch.cuda.Stream] = None):
+        self.lib = N.load()
+        f = {k: getattr(atm, k) for k in _DESC_FIELDS}
+        self._tau = np.ascontiguousarray(f["tau"], dtype=np.float64)
+        self._B = np.ascontiguousarray(f["B"], dtype=np.float64)
+        self._phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+        d = N.ProblemDesc()
+        d.Ns, d.Nmu, d.Nnu = int(f["Ns"]), int(f["Nmu"]), int(f["Nnu"])
+        d.tau = _dptr(self._tau)
+        d.B = _dptr(self._B)
+        d.phi = _dptr(self._phi) if self._phi is not None else None
+        d.phi_center = float(phi_center)
+        d.x_min, d.x_max = float(f["x_min"]), float(f["x_max"])
+        d.a, d.eps, d.W2 = float(f["a"]), float(f["eps"]), float(f["W2"])
+        d.tau_kind, d.mu_quad = int(f["tau_kind"]), int(f["mu_quad"])
+        d.formal_solver, d.freq_norm = int(f["formal_solver"]), int(f["freq_norm"])
+        self.desc = d
+        self.Ns, self.Nmu, self.Nnu = d.Ns, d.Nmu, d.Nnu
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = C.c_void_p()
+        N.check(self.lib.rt_problem_create(C.byref(d), _stream_handle(stream), C.byref(h)), "rt_problem_create")
+        self.handle = h
+        self.N = int(self.lib.rt_problem_size(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize(self.device)
+            self.lib.rt_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- grids
+    def grids(self):
+        out = {k: np.zeros(self.Nmu) for k in ("mu", "w_mu")}
+        out.update({k: np.zeros(self.Nnu) for k in ("x", "phi", "w_nu", "phi_hat")})
+        N.check(self.lib.rt_problem_grids(self.handle, *(_dptr(out[k]) for k in
+                                                         ("mu", "w_mu", "x", "phi", "w_nu", "phi_hat"))),
+                "rt_problem_grids")
+        return out
+
+    # ------------------------------------------------------------- operator
+    def _vec(self, x: Optional[torch.Tensor], dtype=torch.float64) -> torch.Tensor:
+        if x is None:
+            return torch.empty(self.N, dtype=dtype, device=self.device)
+        if x.dtype != dtype or x.device != self.device or not x.is_contiguous() or x.numel() != self.N:
+            raise ValueError(f"expected a contiguous {dtype} vector of {self.N} on {self.device}")
+        return x
+
+    def apply(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """y = x - Lambda(T(J x)) in FP64."""
+        x = self._vec(x)
+        y = self._vec(out)
+        N.check(self.lib.rt_apply(self.handle, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                  _stream_handle(stream)), "rt_apply")
+        return y
+
+    def apply_f32(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        x = self._vec(x, torch.float32)
+        y = self._vec(out, torch.float32)
+        N.check(self.lib.rt_apply_f32(self.handle, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                      _stream_handle(stream)), "rt_apply_f32")
+        return y
+
+    def rhs(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        b = self._vec(out)
+        N.check(self.lib.rt_rhs(self.handle, C.c_void_p(b.data_ptr()), _stream_handle(stream)), "rt_rhs")
+        return b
+
+    def jacobi_diag(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        d = self._vec(out)
+        N.check(self.lib.rt_jacobi_diag(self.handle, C.c_void_p(d.data_ptr()), _stream_handle(stream)),
+                "rt_jacobi_diag")
+        return d
+
+    def precond_local_lambda(self, v: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None):
+        v = self._vec(v)
+        z = self._vec(out)
+        N.check(self.lib.rt_precond_local_lambda(self.handle, C.c_void_p(v.data_ptr()),
+                                                 C.c_void_p(z.data_ptr()), _stream_handle(stream)),
+                "rt_precond_local_lambda")
+        return z
+
+    # --------------------------------------------------------------- solvers
+    def solve(self, b: torch.Tensor, method: str = "gmres", x: Optional[torch.Tensor] = None, *,
+              restart: int = 30, maxit: int = 10000, precond: str = "jacobi", rtol: float = 1e-8,
+              x0: bool = False, precision: str = "fp64", inner_rtol: float = 1e-4, max_refine: int = 20,
+              hist_cap: int = 0, raise_on_error: bool = True, stream=None):
+        """Solve A x = b; returns (x, SolveResult).  ``x0=True`` uses ``x`` as initial guess."""
+        b = self._vec(b)
+        x = self._vec(x) if x is not None else torch.zeros(self.N, dtype=torch.float64, device=self.device)
+        o = N.SolverOpts()
+        self.lib.rt_solver_opts_default(C.byref(o))
+        o.restart, o.maxit, o.rtol = restart, maxit, rtol
+        o.precond = {"none": N.RT_PREC_NONE, "jacobi": N.RT_PREC_JACOBI,
+                     "local_lambda": N.RT_PREC_LOCAL_LAMBDA}[precond]
+        o.x0_kind = N.RT_X0_USER if x0 else N.RT_X0_ZERO
+        o.precision = {"fp64": N.RT_PRECISION_FP64, "fp32_refine": N.RT_PRECISION_FP32_REFINE}[precision]
+        o.inner_rtol, o.max_refine = inner_rtol, max_refine
+        hist = np.zeros(max(hist_cap, 1))
+        if hist_cap:
+            o.resid_hist, o.hist_cap = _dptr(hist), hist_cap
+        info = N.SolveInfo()
+        fn = {"gmres": self.lib.rt_solve_gmres, "bicgstab": self.lib.rt_solve_bicgstab,
+              "cgs": self.lib.rt_solve_cgs}[method]
+        st = fn(self.handle, C.byref(o), C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), C.byref(info),
+                _stream_handle(stream))
+        res = SolveResult(info.status, info.iters, info.restarts, info.applies, info.refine_steps,
+                          info.rel_resid, info.t_total_ms, hist[: info.hist_len].copy())
+        if raise_on_error and st not in (N.RT_OK, N.RT_ENOTCONV, N.RT_EBREAKDOWN):
+            raise N.RTError(st, f"rt_solve_{method}")
+        return x, res

@@ -1,0 +1,143 @@
+// Internal declarations of the GB300 transfer-operator library.
+//
+// Device layout of the I-form vector (Eq. 19): x[s][k][m][p], p fastest; the
+// Nmu*Nnu rays of one height are contiguous.  Directions are stored mu
+// ascending, so m < Nh (Nh = Nmu/2) are the downward rays (mu < 0, entering at
+// the top, k = 0) and m >= Nh the upward rays (entering at the bottom).  The
+// formal-solver coefficients depend on |mu| only, indexed mm = |m - Nh + 1/2| - 1/2:
+//   mm = Nh-1-m (m < Nh),  mm = m-Nh (m >= Nh).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rt_krylov.h"
+
+namespace rt {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// launch accounting for rt_launch_count(): launches issued while a graph is
+// being captured are not counted; a graph launch counts its kernel nodes
+extern thread_local int g_capturing;
+void count_launches(long long n);
+#define RT_COUNT(n)                                  \
+  do {                                               \
+    if (!::rt::g_capturing) ::rt::count_launches(n); \
+  } while (0)
+
+#define RT_TRY_CUDA(call)                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      ::rt::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,     \
+                      __LINE__);                                                            \
+      return e_ == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;                        \
+    }                                                                                       \
+  } while (0)
+
+#define RT_TRY(expr)                 \
+  do {                               \
+    rt_status s_ = (expr);           \
+    if (s_ != RT_OK) return s_;      \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------- kernels
+// number of SMs on the device (152 on GB300), queried once per problem
+constexpr int kBlockVec = 512;          // threads per block of the vector kernels
+constexpr int kMaxPartials = 2048;      // upper bound on reduction partials per column
+constexpr int kMaxRestart = 64;
+
+// device-side state of a GMRES cycle (lives in device memory)
+struct GmresDev {
+  double H[(kMaxRestart + 1) * kMaxRestart];  // column-major (m+1) x m, rotated in place
+  double cs[kMaxRestart], sn[kMaxRestart];
+  double g[kMaxRestart + 1];
+  double y[kMaxRestart];
+  double bnorm, tol, rnorm, rel;   // ||b||, rtol, last true residual norm, rnorm/bnorm
+  int kstop;                       // steps this cycle may take (set at cycle start)
+  int kdone;                       // steps completed this cycle
+  int iters;                       // Arnoldi steps over all cycles
+  int maxit;
+  int breakdown;
+  int hist_len;
+};
+
+// device-side scalars of BiCGSTAB / CGS
+struct BicgDev {
+  double rho, rho_old, alpha, omega, beta;
+  double bnorm, tol, rel;
+  int done;        // 1 converged, 2 breakdown, 3 numeric
+  int iters;
+  int maxit;
+  int half;        // BiCGSTAB converged at the half step
+};
+
+struct Problem {
+  // sizes
+  int Ns = 0, Nmu = 0, Nnu = 0, Nh = 0;
+  int64_t nray = 0;   // Nmu*Nnu rays per Stokes parameter
+  int64_t N = 0;      // 2*Ns*nray
+  int device = 0, num_sms = 0;
+  // physics
+  double eps = 0, xi = 0, W2 = 0, a = 0;
+  int tau_kind = 0, mu_quad = 0, fs = 0, freq_norm = 0;
+  // host grids
+  std::vector<double> tau, B, mu, w_mu, x, phi, w_nu, phi_hat, t201, t202;
+  // FP64 device tables
+  double* ce = nullptr;    // [(Ns-1)][Nh][Nnu] step factor e
+  double* ca = nullptr;    // ... alpha (coefficient of the upwind S)
+  double* cb = nullptr;    // ... beta  (coefficient of S at the new node)
+  double* wray = nullptr;  // [Nmu][Nnu] hat-w_m * hat-w_p
+  double* t201d = nullptr; // [Nmu]
+  double* t202d = nullptr; // [Nmu]
+  double* Bd = nullptr;    // [Ns]
+  double* Minv = nullptr;  // [Ns][4] inverse of the 2x2 local blocks M_k (row-major)
+  double* S = nullptr;     // [2][Ns][Nmu] source-function scratch
+  double* S2 = nullptr;    // second source-function scratch
+  // FP32 device tables
+  float* dtau32 = nullptr;  // [Ns-1] tau_{k+1} - tau_k
+  float* r32 = nullptr;     // [Nh][Nnu] phi_hat_p / |mu|
+  float* wray32 = nullptr;
+  float* t201f = nullptr;
+  float* t202f = nullptr;
+  float* S32 = nullptr;     // [2][Ns][Nmu]
+  // solver workspace (allocated on first use)
+  int ws_restart = 0;
+  double* V = nullptr;        // (restart+1) vectors of N
+  double* work = nullptr;     // 8 work vectors of N
+  double* dinv = nullptr;     // N, Jacobi inverse diagonal
+  float* work32 = nullptr;    // 2 vectors of N (FP32 operator)
+  double* partials = nullptr; // 2 x kMaxPartials x 8
+  GmresDev* gm = nullptr;
+  BicgDev* bc = nullptr;
+  double* hist = nullptr;     // device history
+  int hist_cap_dev = 0;
+  int vec_grid = 0;           // blocks of the reduction kernels
+};
+
+// operator entry points used by the solvers (all enqueue on `st`)
+enum ApplyMode { AM_PLAIN = 0, AM_JACOBI = 1, AM_LOCAL_LAMBDA = 2 };
+// kstop/step: inside a captured GMRES cycle the kernels of Arnoldi step
+// `step` return at once when step >= *kstop (NULL: always run)
+rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st,
+                     const int* kstop = nullptr, int step = 0);
+rt_status op_apply32(Problem* P, const float* x, float* y, int mode, cudaStream_t st);
+rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cudaStream_t st,
+                           const int* kstop = nullptr, int step = 0);
+rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st);
+rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st);
+rt_status op_rhs(Problem* P, double* b, cudaStream_t st);
+void release_graphs(Problem* P);
+
+}  // namespace rt
+
+struct rt_problem {
+  rt::Problem P;
+};

@@ -1,0 +1,1020 @@
+// Krylov solvers on the device (Sect. 2 of the paper): restarted GMRES(m)
+// with modified Gram-Schmidt Arnoldi and Givens rotations, BiCGSTAB and CGS,
+// all right-preconditioned, plus FP32-operator iterative refinement.
+//
+// Design:
+//  * every reduction is deterministic: a fixed grid writes one partial per
+//    block, and the consumer sums the partials in a fixed order (each block
+//    of the consumer kernel redundantly, so no extra launch is needed);
+//  * all scalars (Hessenberg matrix, rotations, alpha/omega/rho) stay in
+//    device memory and are updated by single-thread kernels, so a whole
+//    GMRES restart cycle (m Arnoldi steps, the least-squares solve, the
+//    update of x and the true residual) is one CUDA graph launch followed by
+//    one host read of the convergence state;
+//  * a step index baked into each kernel of the cycle graph is compared with
+//    the device counter `kstop`: once the residual estimate passes the
+//    tolerance the remaining kernels of the cycle return at once.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "rt_common.cuh"
+
+namespace rt {
+
+namespace {
+
+constexpr int kVecThreads = kBlockVec;
+constexpr int kWorkVecs = 9;
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block sum in a fixed order; result valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = wsum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// sum of G partials in a fixed order (lane-strided, then a fixed shuffle tree);
+// every thread of the calling warp gets the result
+__device__ __forceinline__ double sum_partials_warp(const double* __restrict__ part, int G) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < G; i += 32) s += part[i];
+  return wsum(s);
+}
+
+// broadcast of sum_partials to the whole block
+__device__ __forceinline__ double block_partials(const double* __restrict__ part, int G) {
+  __shared__ double bc;
+  if (threadIdx.x < 32) {
+    const double s = sum_partials_warp(part, G);
+    if (threadIdx.x == 0) bc = s;
+  }
+  __syncthreads();
+  const double v = bc;
+  __syncthreads();
+  return v;
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void __launch_bounds__(kVecThreads) k_dot(const double* __restrict__ a, const double* __restrict__ b,
+                                                     int64_t N, double* __restrict__ part, const int* kstop, int step) {
+  if (kstop && step >= *kstop) return;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(a[i], b[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// two dot products at once: part[0..G) = <a,b>, part[G..2G) = <c,d>
+__global__ void __launch_bounds__(kVecThreads) k_dot2(const double* __restrict__ a, const double* __restrict__ b,
+                                                      const double* __restrict__ c, const double* __restrict__ d,
+                                                      int64_t N, double* __restrict__ part, const int* done) {
+  if (done && *done) return;
+  double s = 0.0, t = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    s = fma(a[i], b[i], s);
+    t = fma(c[i], d[i], t);
+  }
+  s = block_sum(s);
+  t = block_sum(t);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    part[gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// MGS pass: h = sum(part_in); w -= h * vprev; partial <w, vnext> (or <w,w>)
+__global__ void __launch_bounds__(kVecThreads) k_mgs(double* __restrict__ w, const double* __restrict__ vprev,
+                                                     const double* __restrict__ vnext, int64_t N,
+                                                     const double* __restrict__ part_in, double* __restrict__ part_out,
+                                                     double* __restrict__ hslot, const int* kstop, int step) {
+  if (step >= *kstop) return;
+  const double h = block_partials(part_in, gridDim.x);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hslot = h;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = fma(-h, vprev[i], w[i]);
+    w[i] = wi;
+    s = fma(wi, vnext ? vnext[i] : wi, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part_out[blockIdx.x] = s;
+}
+
+// h_{j+1,j} = ||w||; v_{j+1} = w / h
+__global__ void __launch_bounds__(kVecThreads) k_normalize(const double* __restrict__ w, double* __restrict__ v,
+                                                           int64_t N, const double* __restrict__ part_in,
+                                                           GmresDev* gm, int m, const int* kstop, int step) {
+  if (step >= *kstop) return;
+  const double hn = sqrt(block_partials(part_in, gridDim.x));
+  if (blockIdx.x == 0 && threadIdx.x == 0) gm->H[step * (m + 1) + step + 1] = hn;
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * inv;
+}
+
+// Givens rotations on column j of the Hessenberg matrix (one thread)
+__global__ void k_givens(GmresDev* gm, int m, int j, double* hist, int hist_cap) {
+  if (j >= gm->kstop) return;
+  double* Hc = gm->H + j * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double t = gm->cs[i] * Hc[i] + gm->sn[i] * Hc[i + 1];
+    Hc[i + 1] = -gm->sn[i] * Hc[i] + gm->cs[i] * Hc[i + 1];
+    Hc[i] = t;
+  }
+  const double a = Hc[j], b = Hc[j + 1];
+  const double hn = hypot(a, b);
+  if (hn == 0.0) {
+    gm->breakdown = 1;
+    gm->kstop = j;
+    return;
+  }
+  const double c = a / hn, s = b / hn;
+  gm->cs[j] = c;
+  gm->sn[j] = s;
+  Hc[j] = hn;
+  Hc[j + 1] = 0.0;
+  gm->g[j + 1] = -s * gm->g[j];
+  gm->g[j] = c * gm->g[j];
+  gm->iters += 1;
+  gm->kdone = j + 1;
+  const double est = fabs(gm->g[j + 1]) / gm->bnorm;
+  if (hist && gm->hist_len < hist_cap) hist[gm->hist_len++] = est;
+  if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
+}
+
+// back substitution H(0:k,0:k) y = g(0:k) (one thread)
+__global__ void k_lsq(GmresDev* gm, int m) {
+  const int k = gm->kdone;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gm->g[i];
+    for (int l = i + 1; l < k; ++l) s -= gm->H[l * (m + 1) + i] * gm->y[l];
+    gm->y[i] = s / gm->H[i * (m + 1) + i];
+  }
+}
+
+// t = sum_{i<k} y_i V_i; mode 0: x += t, 1: x += dinv*t, 2: t stored for P^{-1}
+__global__ void __launch_bounds__(kVecThreads) k_combine(const double* __restrict__ V, int64_t N,
+                                                         const GmresDev* gm, double* __restrict__ x,
+                                                         const double* __restrict__ dinv, double* __restrict__ t,
+                                                         int mode) {
+  const int k = gm->kdone;
+  __shared__ double ys[kMaxRestart];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = gm->y[i];
+  __syncthreads();
+  if (k == 0) return;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s = fma(ys[i], V[(int64_t)i * N + n], s);
+    if (mode == 0) x[n] += s;
+    else if (mode == 1) x[n] = fma(dinv[n], s, x[n]);
+    else t[n] = s;
+  }
+}
+
+// x += z
+__global__ void __launch_bounds__(kVecThreads) k_axpy1(double* __restrict__ x, const double* __restrict__ z, int64_t N) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+    x[n] += z[n];
+}
+
+// r = b - Ax; partial ||r||^2
+__global__ void __launch_bounds__(kVecThreads) k_residual(const double* __restrict__ b, const double* __restrict__ Ax,
+                                                          double* __restrict__ r, int64_t N, double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[n] - Ax[n];
+    r[n] = v;
+    s = fma(v, v, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// start of a cycle: beta = ||r||, v_0 = r / beta, g = beta e_1
+__global__ void __launch_bounds__(kVecThreads) k_cycle_start(const double* __restrict__ r, double* __restrict__ v0,
+                                                             int64_t N, const double* __restrict__ part, GmresDev* gm,
+                                                             int m) {
+  const double rn = sqrt(block_partials(part, gridDim.x));
+  const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+    v0[n] = r[n] * inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    gm->rnorm = rn;
+    gm->rel = rn / gm->bnorm;
+    for (int i = 0; i <= m; ++i) gm->g[i] = 0.0;
+    gm->g[0] = rn;
+    gm->kdone = 0;
+    int left = gm->maxit - gm->iters;
+    gm->kstop = left < m ? (left > 0 ? left : 0) : m;
+    if (!(gm->rel >= gm->tol)) gm->kstop = 0;  // converged (or NaN): no steps
+  }
+}
+
+__global__ void k_set_bnorm(const double* __restrict__ part, int G, GmresDev* gm) {
+  if (threadIdx.x < 32) {
+    const double s = sum_partials_warp(part, G);
+    if (threadIdx.x == 0) gm->bnorm = sqrt(s);
+  }
+}
+
+// ---------------------------------------------------- BiCGSTAB / CGS kernels
+__device__ __forceinline__ double fin(const double* part, int G) {  // single-warp use
+  return sum_partials_warp(part, G);
+}
+
+// scalar kernels run with one warp
+__global__ void k_bc_init(BicgDev* bc, const double* part, int G) {
+  // part: [<r,r> | <rhat,r>]
+  const double rr = fin(part, G), rho = fin(part + G, G);
+  if (threadIdx.x == 0) {
+    bc->rel = sqrt(rr) / bc->bnorm;
+    bc->rho = rho;
+    bc->rho_old = 1.0;
+    bc->alpha = 1.0;
+    bc->omega = 1.0;
+    bc->beta = 0.0;
+    bc->done = !(bc->rel >= bc->tol) ? 1 : 0;
+    if (bc->rel != bc->rel) bc->done = 3;
+    if (!bc->done && rho == 0.0) bc->done = 2;
+  }
+}
+
+// alpha = rho / <rhat, v>
+__global__ void k_bc_alpha(BicgDev* bc, const double* part, int G) {
+  if (bc->done) return;
+  const double rv = fin(part, G);
+  if (threadIdx.x == 0) {
+    if (rv == 0.0) { bc->done = 2; return; }
+    bc->alpha = bc->rho / rv;
+  }
+}
+
+// ---- BiCGSTAB
+// p = r + beta (p - omega v)
+__global__ void __launch_bounds__(kVecThreads) k_bs_p(double* __restrict__ p, const double* __restrict__ r,
+                                                      const double* __restrict__ v, int64_t N, const BicgDev* bc) {
+  if (bc->done) return;
+  const double beta = bc->beta, omega = bc->omega;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+    p[n] = fma(beta, fma(-omega, v[n], p[n]), r[n]);
+}
+
+// s = r - alpha v, partial ||s||^2
+__global__ void __launch_bounds__(kVecThreads) k_bs_s(double* __restrict__ s, const double* __restrict__ r,
+                                                      const double* __restrict__ v, int64_t N, const BicgDev* bc,
+                                                      double* __restrict__ part) {
+  if (bc->done) return;
+  const double alpha = bc->alpha;
+  double acc = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const double v2 = fma(-alpha, v[n], r[n]);
+    s[n] = v2;
+    acc = fma(v2, v2, acc);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// half-step test on ||s||
+__global__ void k_bs_check_s(BicgDev* bc, const double* part, int G) {
+  if (bc->done) return;
+  const double ss = fin(part, G);
+  if (threadIdx.x == 0) {
+    const double rel = sqrt(ss) / bc->bnorm;
+    bc->iters += 1;
+    if (!(rel >= bc->tol)) {
+      bc->rel = rel;
+      bc->half = 1;
+      bc->done = (rel != rel) ? 3 : 1;
+    }
+  }
+}
+
+// omega = <t,s>/<t,t>
+__global__ void k_bs_omega(BicgDev* bc, const double* part, int G) {
+  if (bc->done) return;
+  const double ts = fin(part, G), tt = fin(part + G, G);
+  if (threadIdx.x == 0) {
+    if (tt == 0.0) { bc->done = 2; return; }
+    bc->omega = ts / tt;
+  }
+}
+
+// acc += alpha p + omega s (the half-step: acc += alpha p); r = s - omega t;
+// partials ||r||^2 and <rhat, r>
+__global__ void __launch_bounds__(kVecThreads) k_bs_update(double* __restrict__ acc, const double* __restrict__ p,
+                                                           const double* __restrict__ s, const double* __restrict__ t,
+                                                           double* __restrict__ r, const double* __restrict__ rhat,
+                                                           int64_t N, const BicgDev* bc, double* __restrict__ part) {
+  if (bc->done == 1 && bc->half) {
+    // converged on s: finish the direction update only (once)
+    if (bc->half == 1) {
+      const double alpha = bc->alpha;
+      for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        acc[n] = fma(alpha, p[n], acc[n]);
+    }
+    return;
+  }
+  if (bc->done) return;
+  const double alpha = bc->alpha, omega = bc->omega;
+  double a1 = 0.0, a2 = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    acc[n] = fma(alpha, p[n], fma(omega, s[n], acc[n]));
+    const double rn = fma(-omega, t[n], s[n]);
+    r[n] = rn;
+    a1 = fma(rn, rn, a1);
+    a2 = fma(rhat[n], rn, a2);
+  }
+  a1 = block_sum(a1);
+  a2 = block_sum(a2);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = a1;
+    part[gridDim.x + blockIdx.x] = a2;
+  }
+}
+
+__global__ void k_bs_check_r(BicgDev* bc, const double* part, int G, double* hist, int hist_cap) {
+  if (bc->done == 1 && bc->half == 1) {
+    if (threadIdx.x == 0) {
+      bc->half = 2;  // the direction update of the half step has been applied
+      if (hist && bc->iters - 1 < hist_cap) hist[bc->iters - 1] = bc->rel;
+    }
+    return;
+  }
+  if (bc->done) return;
+  const double rr = fin(part, G), rho = fin(part + G, G);
+  if (threadIdx.x == 0) {
+    bc->rel = sqrt(rr) / bc->bnorm;
+    if (hist && bc->iters - 1 < hist_cap) hist[bc->iters - 1] = bc->rel;
+    if (bc->rel != bc->rel) { bc->done = 3; return; }
+    if (!(bc->rel >= bc->tol)) { bc->done = 1; return; }
+    if (bc->omega == 0.0 || rho == 0.0) { bc->done = 2; return; }
+    bc->beta = (rho / bc->rho) * (bc->alpha / bc->omega);
+    bc->rho = rho;
+    if (bc->iters >= bc->maxit) bc->done = 4;
+  }
+}
+
+// ---- CGS
+// u = r + beta q; p = u + beta (q + beta p)
+__global__ void __launch_bounds__(kVecThreads) k_cgs_up(double* __restrict__ u, double* __restrict__ p,
+                                                        const double* __restrict__ r, const double* __restrict__ q,
+                                                        int64_t N, const BicgDev* bc) {
+  if (bc->done) return;
+  const double beta = bc->beta;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const double un = fma(beta, q[n], r[n]);
+    u[n] = un;
+    p[n] = fma(beta, fma(beta, p[n], q[n]), un);
+  }
+}
+
+// q = u - alpha vhat; w = u + q; acc += alpha w
+__global__ void __launch_bounds__(kVecThreads) k_cgs_q(double* __restrict__ q, double* __restrict__ w,
+                                                       double* __restrict__ acc, const double* __restrict__ u,
+                                                       const double* __restrict__ vh, int64_t N, const BicgDev* bc) {
+  if (bc->done) return;
+  const double alpha = bc->alpha;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const double qn = fma(-alpha, vh[n], u[n]);
+    q[n] = qn;
+    const double wn = u[n] + qn;
+    w[n] = wn;
+    acc[n] = fma(alpha, wn, acc[n]);
+  }
+}
+
+// r -= alpha qhat; partials ||r||^2, <rhat, r>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_r(double* __restrict__ r, const double* __restrict__ qh,
+                                                       const double* __restrict__ rhat, int64_t N, const BicgDev* bc,
+                                                       double* __restrict__ part) {
+  if (bc->done) return;
+  const double alpha = bc->alpha;
+  double a1 = 0.0, a2 = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const double rn = fma(-alpha, qh[n], r[n]);
+    r[n] = rn;
+    a1 = fma(rn, rn, a1);
+    a2 = fma(rhat[n], rn, a2);
+  }
+  a1 = block_sum(a1);
+  a2 = block_sum(a2);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = a1;
+    part[gridDim.x + blockIdx.x] = a2;
+  }
+}
+
+__global__ void k_cgs_check(BicgDev* bc, const double* part, int G, double* hist, int hist_cap) {
+  if (bc->done) return;
+  const double rr = fin(part, G), rho = fin(part + G, G);
+  if (threadIdx.x == 0) {
+    bc->iters += 1;
+    bc->rel = sqrt(rr) / bc->bnorm;
+    if (hist && bc->iters - 1 < hist_cap) hist[bc->iters - 1] = bc->rel;
+    if (bc->rel != bc->rel) { bc->done = 3; return; }
+    if (!(bc->rel >= bc->tol)) { bc->done = 1; return; }
+    if (rho == 0.0) { bc->done = 2; return; }
+    bc->beta = rho / bc->rho;
+    bc->rho = rho;
+    if (bc->iters >= bc->maxit) bc->done = 4;
+  }
+}
+
+// y = x * d (Jacobi scaling); used by the FP32 refinement path
+__global__ void __launch_bounds__(kVecThreads) k_mul(const double* __restrict__ x, const double* __restrict__ d,
+                                                     double* __restrict__ y, int64_t N) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+    y[n] = x[n] * d[n];
+}
+
+}  // namespace
+
+
+// ------------------------------------------------------------ workspace
+struct Workspace {
+  double* V;        // (m+1) x N
+  double* w[8];     // work vectors
+  double* part[2];  // ping-pong partial buffers
+};
+
+static rt_status ensure_workspace(Problem* P, int restart, cudaStream_t st) {
+  if (!P->vec_grid) {
+    int64_t g = (P->N + 2 * kVecThreads - 1) / (2 * kVecThreads);
+    int cap = 4 * P->num_sms;
+    if (cap > kMaxPartials) cap = kMaxPartials;
+    P->vec_grid = (int)(g < 1 ? 1 : (g > cap ? cap : g));
+  }
+  if (!P->work) RT_TRY_CUDA(cudaMalloc((void**)&P->work, (size_t)kWorkVecs * P->N * sizeof(double)));
+  if (!P->dinv) RT_TRY_CUDA(cudaMalloc((void**)&P->dinv, (size_t)P->N * sizeof(double)));
+  if (!P->partials) RT_TRY_CUDA(cudaMalloc((void**)&P->partials, (size_t)2 * 2 * kMaxPartials * sizeof(double)));
+  if (!P->gm) RT_TRY_CUDA(cudaMalloc((void**)&P->gm, sizeof(GmresDev)));
+  if (!P->bc) RT_TRY_CUDA(cudaMalloc((void**)&P->bc, sizeof(BicgDev)));
+  if (restart > P->ws_restart) {
+    release_graphs(P);  // captured graphs hold the old basis pointer
+    if (P->V) cudaFree(P->V);
+    P->V = nullptr;
+    P->ws_restart = 0;
+    RT_TRY_CUDA(cudaMalloc((void**)&P->V, (size_t)(restart + 1) * P->N * sizeof(double)));
+    P->ws_restart = restart;
+  }
+  (void)st;
+  return RT_OK;
+}
+
+static inline double* wk(Problem* P, int i) { return P->work + (size_t)i * P->N; }
+static inline double* partb(Problem* P, int i) { return P->partials + (size_t)i * 2 * kMaxPartials; }
+
+// A M^{-1} v with the chosen preconditioner and operator precision
+static rt_status apply_prec(Problem* P, const double* v, double* y, int precond, int fp32, cudaStream_t st,
+                            const int* kstop = nullptr, int step = 0) {
+  const int mode = precond == RT_PREC_JACOBI ? AM_JACOBI : precond == RT_PREC_LOCAL_LAMBDA ? AM_LOCAL_LAMBDA : AM_PLAIN;
+  if (fp32) return op_apply32_f64io(P, v, y, mode, st, kstop, step);
+  return op_apply64(P, v, y, mode, st, kstop, step);
+}
+
+// x += M^{-1} t  (t may be overwritten)
+static rt_status add_precond(Problem* P, double* x, double* t, int precond, double* tmp, cudaStream_t st) {
+  const int G = P->vec_grid;
+  if (precond == RT_PREC_NONE) {
+    k_axpy1<<<G, kVecThreads, 0, st>>>(x, t, P->N); RT_COUNT(1);
+  } else if (precond == RT_PREC_JACOBI) {
+    k_mul<<<G, kVecThreads, 0, st>>>(t, P->dinv, tmp, P->N); RT_COUNT(1);
+    k_axpy1<<<G, kVecThreads, 0, st>>>(x, tmp, P->N); RT_COUNT(1);
+  } else {
+    RT_TRY(op_precond_ll(P, t, tmp, st));
+    k_axpy1<<<G, kVecThreads, 0, st>>>(x, tmp, P->N); RT_COUNT(1);
+  }
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+// --------------------------------------------------------------- GMRES
+struct GmresGraphKey {
+  int m, precond, fp32;
+  bool operator<(const GmresGraphKey& o) const {
+    return std::tie(m, precond, fp32) < std::tie(o.m, o.precond, o.fp32);
+  }
+};
+
+struct GraphCache {
+  std::map<GmresGraphKey, cudaGraphExec_t> gmres;
+  cudaGraphExec_t bicg[2][3][2] = {};  // [method][precond][fp32]
+  std::map<cudaGraphExec_t, long long> kernels;  // kernel nodes per executable graph
+  cudaStream_t cap = nullptr;
+  ~GraphCache() {
+    for (auto& kv : gmres) cudaGraphExecDestroy(kv.second);
+    for (auto& a : bicg)
+      for (auto& b : a)
+        for (auto& c : b)
+          if (c) cudaGraphExecDestroy(c);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+static std::map<const Problem*, GraphCache*>& caches() {
+  static std::map<const Problem*, GraphCache*> c;
+  return c;
+}
+static std::mutex g_cache_mu;
+
+static GraphCache* cache_of(Problem* P) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto& c = caches();
+  auto it = c.find(P);
+  if (it != c.end()) return it->second;
+  GraphCache* g = new GraphCache();
+  c[P] = g;
+  return g;
+}
+
+void release_graphs(Problem* P) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto& c = caches();
+  auto it = c.find(P);
+  if (it != c.end()) {
+    delete it->second;
+    c.erase(it);
+  }
+}
+
+// Enqueue one restart cycle: steps 0..m-1, least squares, x update, true
+// residual and the start of the next cycle.  Vectors: x = wk(0), b = wk(1),
+// r = wk(2), w = wk(3), t = wk(4), Ax = wk(5), tmp = wk(6).
+static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStream_t st) {
+  const int G = P->vec_grid;
+  const int64_t N = P->N;
+  GmresDev* gm = P->gm;
+  const int* kstop = &gm->kstop;
+  double* w = wk(P, 3);
+  double* hist = P->hist;
+  const int hcap = P->hist_cap_dev;
+  for (int j = 0; j < m; ++j) {
+    double* vj = P->V + (size_t)j * N;
+    RT_TRY(apply_prec(P, vj, w, precond, fp32, st, kstop, j));
+    int pb = 0;
+    k_dot<<<G, kVecThreads, 0, st>>>(w, P->V, N, partb(P, pb), kstop, j); RT_COUNT(1);
+    for (int i = 0; i <= j; ++i) {
+      const double* vprev = P->V + (size_t)i * N;
+      const double* vnext = (i < j) ? P->V + (size_t)(i + 1) * N : nullptr;
+      k_mgs<<<G, kVecThreads, 0, st>>>(w, vprev, vnext, N, partb(P, pb), partb(P, pb ^ 1), &gm->H[j * (m + 1) + i],
+                                       kstop, j); RT_COUNT(1);
+      pb ^= 1;
+    }
+    k_normalize<<<G, kVecThreads, 0, st>>>(w, P->V + (size_t)(j + 1) * N, N, partb(P, pb), gm, m, kstop, j); RT_COUNT(1);
+    k_givens<<<1, 1, 0, st>>>(gm, m, j, hist, hcap); RT_COUNT(1);
+  }
+  RT_TRY_CUDA(cudaGetLastError());
+  k_lsq<<<1, 1, 0, st>>>(gm, m); RT_COUNT(1);
+  double* x = wk(P, 0);
+  double* t = wk(P, 4);
+  if (precond == RT_PREC_LOCAL_LAMBDA) {
+    k_combine<<<G, kVecThreads, 0, st>>>(P->V, N, gm, x, P->dinv, t, 2); RT_COUNT(1);
+    RT_TRY(op_precond_ll(P, t, wk(P, 6), st));
+    k_axpy1<<<G, kVecThreads, 0, st>>>(x, wk(P, 6), N); RT_COUNT(1);
+  } else {
+    k_combine<<<G, kVecThreads, 0, st>>>(P->V, N, gm, x, P->dinv, t, precond == RT_PREC_JACOBI ? 1 : 0); RT_COUNT(1);
+  }
+  RT_TRY(op_apply64(P, x, wk(P, 5), AM_PLAIN, st));
+  k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
+  k_cycle_start<<<G, kVecThreads, 0, st>>>(wk(P, 2), P->V, N, partb(P, 0), gm, m); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+template <typename F>
+static rt_status capture_graph(GraphCache* gc, F&& enqueue, cudaGraphExec_t* out) {
+  if (!gc->cap) RT_TRY_CUDA(cudaStreamCreateWithFlags(&gc->cap, cudaStreamNonBlocking));
+  RT_TRY_CUDA(cudaStreamBeginCapture(gc->cap, cudaStreamCaptureModeThreadLocal));
+  g_capturing = 1;
+  rt_status s = enqueue(gc->cap);
+  g_capturing = 0;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(gc->cap, &g);
+  if (s != RT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) {
+    set_error("graph capture failed: %s", cudaGetErrorString(e));
+    return RT_ECUDA;
+  }
+  size_t nn = 0;
+  long long nk = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+      }
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_error("graph instantiate failed: %s", cudaGetErrorString(e));
+    return RT_ECUDA;
+  }
+  gc->kernels[ex] = nk;
+  *out = ex;
+  return RT_OK;
+}
+
+static rt_status launch_graph(GraphCache* gc, cudaGraphExec_t ex, cudaStream_t st) {
+  RT_TRY_CUDA(cudaGraphLaunch(ex, st));
+  count_launches(gc->kernels[ex]);
+  return RT_OK;
+}
+
+static rt_status get_graph(Problem* P, GraphCache* gc, int m, int precond, int fp32, cudaGraphExec_t* out) {
+  GmresGraphKey key{m, precond, fp32};
+  auto it = gc->gmres.find(key);
+  if (it != gc->gmres.end()) {
+    *out = it->second;
+    return RT_OK;
+  }
+  cudaGraphExec_t ex = nullptr;
+  RT_TRY(capture_graph(gc, [&](cudaStream_t cs) { return enqueue_cycle(P, m, precond, fp32, cs); }, &ex));
+  gc->gmres[key] = ex;
+  *out = ex;
+  return RT_OK;
+}
+
+static rt_status ensure_hist(Problem* P, int cap) {
+  if (cap > P->hist_cap_dev) {
+    if (P->hist) cudaFree(P->hist);
+    P->hist = nullptr;
+    P->hist_cap_dev = 0;
+    // the graphs bake the history pointer: drop them
+    release_graphs(P);
+    RT_TRY_CUDA(cudaMalloc((void**)&P->hist, (size_t)cap * sizeof(double)));
+    P->hist_cap_dev = cap;
+  }
+  return RT_OK;
+}
+
+// Core GMRES on internal buffers: b = wk(1) given, x = wk(0) holds x0 (or
+// zero).  Returns the host copy of the final device state.
+static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, double tol, int maxit, bool x0_zero,
+                            GmresDev* hs, int* cycles, cudaStream_t st) {
+  const int G = P->vec_grid;
+  const int64_t N = P->N;
+  const int m = o->restart;
+  GmresDev init;
+  memset(&init, 0, sizeof init);
+  init.tol = tol;
+  init.maxit = maxit;
+  RT_TRY_CUDA(cudaMemcpyAsync(P->gm, &init, sizeof init, cudaMemcpyHostToDevice, st));
+  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), N, partb(P, 1), nullptr, 0); RT_COUNT(1);
+  k_set_bnorm<<<1, 32, 0, st>>>(partb(P, 1), G, P->gm); RT_COUNT(1);
+  if (x0_zero) {
+    k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), N, partb(P, 0), nullptr, 0); RT_COUNT(1);
+    k_cycle_start<<<G, kVecThreads, 0, st>>>(wk(P, 1), P->V, N, partb(P, 0), P->gm, m); RT_COUNT(1);
+  } else {
+    RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
+    k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
+    k_cycle_start<<<G, kVecThreads, 0, st>>>(wk(P, 2), P->V, N, partb(P, 0), P->gm, m); RT_COUNT(1);
+  }
+  RT_TRY_CUDA(cudaGetLastError());
+  RT_TRY_CUDA(cudaMemcpyAsync(hs, P->gm, sizeof(GmresDev), cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  *cycles = 0;
+  if (hs->bnorm == 0.0 || !(hs->rel >= tol) || hs->rel != hs->rel) return RT_OK;
+  GraphCache* gc = cache_of(P);
+  cudaGraphExec_t ex;
+  RT_TRY(get_graph(P, gc, m, o->precond, fp32, &ex));
+  for (;;) {
+    RT_TRY(launch_graph(gc, ex, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(hs, P->gm, sizeof(GmresDev), cudaMemcpyDeviceToHost, st));
+    RT_TRY_CUDA(cudaStreamSynchronize(st));
+    *cycles += 1;
+    if (hs->rel != hs->rel) return RT_OK;
+    if (!(hs->rel >= tol)) return RT_OK;
+    if (hs->iters >= maxit) return RT_OK;
+    if (hs->breakdown && hs->kdone == 0) return RT_OK;
+    if (hs->kstop == 0) return RT_OK;
+  }
+}
+
+static rt_status prepare(Problem* P, const rt_solver_opts* o, int restart, cudaStream_t st) {
+  RT_TRY(ensure_workspace(P, restart, st));
+  if (o->resid_hist && o->hist_cap > 0) RT_TRY(ensure_hist(P, o->hist_cap));
+  if (o->precond == RT_PREC_JACOBI) RT_TRY(op_jacobi_inv(P, P->dinv, st));
+  return RT_OK;
+}
+
+static rt_status check_opts(const rt_solver_opts* o, const double* b, const double* x) {
+  if (!o || !b || !x) { set_error("opts, b_dev and x_dev are required"); return RT_EINVAL; }
+  if (o->restart < 1 || o->restart > kMaxRestart) { set_error("restart must be in [1,%d]", kMaxRestart); return RT_EINVAL; }
+  if (o->maxit < 1) { set_error("maxit must be >= 1"); return RT_EINVAL; }
+  if (o->precond < RT_PREC_NONE || o->precond > RT_PREC_LOCAL_LAMBDA) { set_error("bad precond"); return RT_EINVAL; }
+  if (o->x0_kind != RT_X0_ZERO && o->x0_kind != RT_X0_USER) { set_error("bad x0_kind"); return RT_EINVAL; }
+  if (o->ortho != RT_ORTHO_MGS) { set_error("only RT_ORTHO_MGS is implemented"); return RT_EINVAL; }
+  if (o->precision != RT_PRECISION_FP64 && o->precision != RT_PRECISION_FP32_REFINE) { set_error("bad precision"); return RT_EINVAL; }
+  if (!(o->rtol > 0.0)) { set_error("rtol must be > 0"); return RT_EINVAL; }
+  return RT_OK;
+}
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static rt_status finish_info(rt_solve_info* info, rt_status s, double t0) {
+  if (info) {
+    info->status = s;
+    info->t_total_ms = now_ms() - t0;
+  }
+  return s;
+}
+
+// true relative residual of x = wk(0) against b = wk(1)
+static rt_status true_residual(Problem* P, double* rel, cudaStream_t st) {
+  const int G = P->vec_grid;
+  RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
+  k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), P->N, partb(P, 0)); RT_COUNT(1);
+  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), P->N, partb(P, 1), nullptr, 0); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  std::vector<double> h(2 * G);
+  RT_TRY_CUDA(cudaMemcpyAsync(h.data(), partb(P, 0), G * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaMemcpyAsync(h.data() + G, partb(P, 1), G * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  double rr = 0, bb = 0;
+  for (int i = 0; i < G; ++i) { rr += h[i]; bb += h[G + i]; }
+  *rel = bb > 0 ? sqrt(rr / bb) : 0.0;
+  return RT_OK;
+}
+
+static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* b, double* x, rt_solve_info* info,
+                             cudaStream_t st) {
+  const double t0 = now_ms();
+  if (info) memset(info, 0, sizeof *info);
+  RT_TRY(prepare(P, o, o->restart, st));
+  const size_t bytes = (size_t)P->N * sizeof(double);
+  RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
+  if (o->x0_kind == RT_X0_USER) RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), x, bytes, cudaMemcpyDeviceToDevice, st));
+  else RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
+  GmresDev hs;
+  int cycles = 0;
+  rt_status s = RT_OK;
+  int iters = 0, applies = 0, refine = 0;
+  double rel = 0.0;
+  if (o->precision == RT_PRECISION_FP64) {
+    RT_TRY(gmres_core(P, o, 0, o->rtol, o->maxit, o->x0_kind == RT_X0_ZERO, &hs, &cycles, st));
+    iters = hs.iters;
+    applies = hs.iters + cycles + (o->x0_kind == RT_X0_USER ? 1 : 0);
+    rel = hs.bnorm == 0.0 ? 0.0 : hs.rel;
+    if (rel != rel) s = RT_ENUMERIC;
+    else if (!(rel < o->rtol) && hs.bnorm != 0.0) s = (hs.breakdown && hs.kdone == 0) ? RT_EBREAKDOWN : RT_ENOTCONV;
+  } else {
+    // FP32 operator inside FP64 iterative refinement:
+    //   r = b - A64 x (FP64);  solve A32 d = r to inner_rtol;  x += d
+    double* xb = wk(P, 7);   // the outer iterate
+    RT_TRY_CUDA(cudaMemcpyAsync(xb, wk(P, 0), bytes, cudaMemcpyDeviceToDevice, st));
+    double* bsave = wk(P, 8);
+    RT_TRY_CUDA(cudaMemcpyAsync(bsave, wk(P, 1), bytes, cudaMemcpyDeviceToDevice, st));
+    RT_TRY(true_residual(P, &rel, st));  // r = wk(2)
+    applies += 1;
+    s = RT_ENOTCONV;
+    const int maxref = o->max_refine > 0 ? o->max_refine : 20;
+    while (refine < maxref && iters < o->maxit) {
+      if (rel != rel) { s = RT_ENUMERIC; break; }
+      if (rel < o->rtol) { s = RT_OK; break; }
+      // inner solve: b <- r, x <- 0
+      RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), wk(P, 2), bytes, cudaMemcpyDeviceToDevice, st));
+      RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
+      RT_TRY(gmres_core(P, o, 1, o->inner_rtol > 0 ? o->inner_rtol : 1e-4, o->maxit - iters, true, &hs, &cycles, st));
+      iters += hs.iters;
+      applies += hs.iters + cycles;
+      refine += 1;
+      k_axpy1<<<P->vec_grid, kVecThreads, 0, st>>>(xb, wk(P, 0), P->N); RT_COUNT(1);
+      RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), xb, bytes, cudaMemcpyDeviceToDevice, st));
+      RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), bsave, bytes, cudaMemcpyDeviceToDevice, st));
+      RT_TRY(true_residual(P, &rel, st));
+      applies += 1;
+      if (hs.iters == 0) break;
+    }
+    if (s == RT_ENOTCONV && rel < o->rtol) s = RT_OK;
+  }
+  RT_TRY_CUDA(cudaMemcpyAsync(x, o->precision == RT_PRECISION_FP64 ? wk(P, 0) : wk(P, 7), bytes,
+                              cudaMemcpyDeviceToDevice, st));
+  int hl = 0;
+  if (o->resid_hist && o->hist_cap > 0 && P->hist) {
+    hl = o->precision == RT_PRECISION_FP64 ? hs.hist_len : 0;
+    if (hl > o->hist_cap) hl = o->hist_cap;
+    if (hl) RT_TRY_CUDA(cudaMemcpyAsync(o->resid_hist, P->hist, hl * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  if (info) {
+    info->iters = iters;
+    info->restarts = cycles;
+    info->applies = applies;
+    info->refine_steps = refine;
+    info->rel_resid = rel;
+    info->hist_len = hl;
+  }
+  return finish_info(info, s, t0);
+}
+
+// ----------------------------------------------------------- BiCGSTAB / CGS
+// vectors: x0 = wk(0), b = wk(1), r = wk(2), rhat = wk(3), p = wk(4),
+// v = wk(5), s = wk(6), t = wk(7) (BiCGSTAB);  CGS: u = wk(5), q = wk(6),
+// w/vhat = wk(7) and V[0], V[1] as scratch.  acc = V[2] accumulates the
+// unpreconditioned direction sum; x = x0 + M^{-1} acc at the end.
+static rt_status enqueue_bicg_iter(Problem* P, int method, int precond, int fp32, cudaStream_t st) {
+  const int G = P->vec_grid;
+  const int64_t N = P->N;
+  BicgDev* bc = P->bc;
+  double* acc = P->V + 2 * (size_t)N;
+  double *r = wk(P, 2), *rhat = wk(P, 3), *p = wk(P, 4);
+  if (method == 0) {
+    double *v = wk(P, 5), *s = wk(P, 6), *t = wk(P, 7);
+    k_bs_p<<<G, kVecThreads, 0, st>>>(p, r, v, N, bc); RT_COUNT(1);
+    RT_TRY(apply_prec(P, p, v, precond, fp32, st));
+    k_dot<<<G, kVecThreads, 0, st>>>(rhat, v, N, partb(P, 0), &bc->done, 0); RT_COUNT(1);
+    k_bc_alpha<<<1, 32, 0, st>>>(bc, partb(P, 0), G); RT_COUNT(1);
+    k_bs_s<<<G, kVecThreads, 0, st>>>(s, r, v, N, bc, partb(P, 1)); RT_COUNT(1);
+    k_bs_check_s<<<1, 32, 0, st>>>(bc, partb(P, 1), G); RT_COUNT(1);
+    RT_TRY(apply_prec(P, s, t, precond, fp32, st));
+    k_dot2<<<G, kVecThreads, 0, st>>>(t, s, t, t, N, partb(P, 0), &bc->done); RT_COUNT(1);
+    k_bs_omega<<<1, 32, 0, st>>>(bc, partb(P, 0), G); RT_COUNT(1);
+    k_bs_update<<<G, kVecThreads, 0, st>>>(acc, p, s, t, r, rhat, N, bc, partb(P, 1)); RT_COUNT(1);
+    k_bs_check_r<<<1, 32, 0, st>>>(bc, partb(P, 1), G, P->hist, P->hist_cap_dev); RT_COUNT(1);
+  } else {
+    double *u = wk(P, 5), *q = wk(P, 6), *w = wk(P, 7);
+    double* vh = P->V;
+    double* qh = P->V + (size_t)N;
+    k_cgs_up<<<G, kVecThreads, 0, st>>>(u, p, r, q, N, bc); RT_COUNT(1);
+    RT_TRY(apply_prec(P, p, vh, precond, fp32, st));
+    k_dot<<<G, kVecThreads, 0, st>>>(rhat, vh, N, partb(P, 0), &bc->done, 0); RT_COUNT(1);
+    k_bc_alpha<<<1, 32, 0, st>>>(bc, partb(P, 0), G); RT_COUNT(1);
+    k_cgs_q<<<G, kVecThreads, 0, st>>>(q, w, acc, u, vh, N, bc); RT_COUNT(1);
+    RT_TRY(apply_prec(P, w, qh, precond, fp32, st));
+    k_cgs_r<<<G, kVecThreads, 0, st>>>(r, qh, rhat, N, bc, partb(P, 1)); RT_COUNT(1);
+    k_cgs_check<<<1, 32, 0, st>>>(bc, partb(P, 1), G, P->hist, P->hist_cap_dev); RT_COUNT(1);
+  }
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+// a kernel that skips when done: apply_prec launches operator kernels that do
+// not look at the flag, so an iteration after convergence still computes an
+// (unused) product; the graph therefore holds one iteration and the host
+// checks the flag after every launch.
+static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, const double* b, double* x,
+                            rt_solve_info* info, cudaStream_t st) {
+  const double t0 = now_ms();
+  if (info) memset(info, 0, sizeof *info);
+  if (o->precision != RT_PRECISION_FP64) {
+    set_error("BiCGSTAB/CGS support FP64 only");
+    return finish_info(info, RT_EINVAL, t0);
+  }
+  RT_TRY(prepare(P, o, 2, st));
+  const int G = P->vec_grid;
+  const int64_t N = P->N;
+  const size_t bytes = (size_t)N * sizeof(double);
+  double *x0 = wk(P, 0), *bb = wk(P, 1), *r = wk(P, 2), *rhat = wk(P, 3);
+  double* acc = P->V + 2 * (size_t)N;
+  RT_TRY_CUDA(cudaMemcpyAsync(bb, b, bytes, cudaMemcpyDeviceToDevice, st));
+  int applies = 0;
+  if (o->x0_kind == RT_X0_USER) {
+    RT_TRY_CUDA(cudaMemcpyAsync(x0, x, bytes, cudaMemcpyDeviceToDevice, st));
+    RT_TRY(op_apply64(P, x0, wk(P, 5), AM_PLAIN, st));
+    k_residual<<<G, kVecThreads, 0, st>>>(bb, wk(P, 5), r, N, partb(P, 0)); RT_COUNT(1);
+    applies = 1;
+  } else {
+    RT_TRY_CUDA(cudaMemsetAsync(x0, 0, bytes, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(r, bb, bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  RT_TRY_CUDA(cudaMemcpyAsync(rhat, r, bytes, cudaMemcpyDeviceToDevice, st));
+  for (int i = 4; i < 8; ++i) RT_TRY_CUDA(cudaMemsetAsync(wk(P, i), 0, bytes, st));
+  RT_TRY_CUDA(cudaMemsetAsync(acc, 0, bytes, st));
+  BicgDev init;
+  memset(&init, 0, sizeof init);
+  init.tol = o->rtol;
+  init.maxit = o->maxit;
+  RT_TRY_CUDA(cudaMemcpyAsync(P->bc, &init, sizeof init, cudaMemcpyHostToDevice, st));
+  // ||b||, then ||r||^2 and <rhat, r>
+  k_dot<<<G, kVecThreads, 0, st>>>(bb, bb, N, partb(P, 1), nullptr, 0); RT_COUNT(1);
+  k_dot2<<<G, kVecThreads, 0, st>>>(r, r, rhat, r, N, partb(P, 0), nullptr); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  {
+    std::vector<double> h(G);
+    RT_TRY_CUDA(cudaMemcpyAsync(h.data(), partb(P, 1), G * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RT_TRY_CUDA(cudaStreamSynchronize(st));
+    double s2 = 0;
+    for (int i = 0; i < G; ++i) s2 += h[i];
+    init.bnorm = sqrt(s2);
+    if (init.bnorm == 0.0) {
+      RT_TRY_CUDA(cudaMemsetAsync(x, 0, bytes, st));
+      RT_TRY_CUDA(cudaStreamSynchronize(st));
+      if (info) info->rel_resid = 0.0;
+      return finish_info(info, RT_OK, t0);
+    }
+    RT_TRY_CUDA(cudaMemcpyAsync(&P->bc->bnorm, &init.bnorm, sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  k_bc_init<<<1, 32, 0, st>>>(P->bc, partb(P, 0), G); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  GraphCache* gc = cache_of(P);
+  cudaGraphExec_t& ex = gc->bicg[method][o->precond][0];
+  if (!ex) {
+    const int prec = o->precond;
+    rt_status s = capture_graph(gc, [&](cudaStream_t cs) { return enqueue_bicg_iter(P, method, prec, 0, cs); }, &ex);
+    if (s != RT_OK) return finish_info(info, s, t0);
+  }
+  BicgDev hs;
+  RT_TRY_CUDA(cudaMemcpyAsync(&hs, P->bc, sizeof hs, cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  while (!hs.done) {
+    RT_TRY(launch_graph(gc, ex, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(&hs, P->bc, sizeof hs, cudaMemcpyDeviceToHost, st));
+    RT_TRY_CUDA(cudaStreamSynchronize(st));
+    applies += (hs.half ? 1 : 2);
+  }
+  // x = x0 + M^{-1} acc
+  RT_TRY(add_precond(P, x0, acc, o->precond, wk(P, 6), st));
+  RT_TRY_CUDA(cudaMemcpyAsync(x, x0, bytes, cudaMemcpyDeviceToDevice, st));
+  double rel = 0;
+  RT_TRY(true_residual(P, &rel, st));
+  int hl = 0;
+  if (o->resid_hist && o->hist_cap > 0 && P->hist) {
+    hl = hs.iters < o->hist_cap ? hs.iters : o->hist_cap;
+    if (hl) RT_TRY_CUDA(cudaMemcpyAsync(o->resid_hist, P->hist, hl * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RT_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  rt_status s = hs.done == 1 ? RT_OK : hs.done == 2 ? RT_EBREAKDOWN : hs.done == 3 ? RT_ENUMERIC : RT_ENOTCONV;
+  if (info) {
+    info->iters = hs.iters;
+    info->applies = applies;
+    info->rel_resid = rel;
+    info->hist_len = hl;
+  }
+  return finish_info(info, s, t0);
+}
+
+}  // namespace rt
+
+using namespace rt;
+
+extern "C" {
+
+void rt_solver_opts_default(rt_solver_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->restart = 30;
+  o->maxit = 10000;
+  o->precond = RT_PREC_JACOBI;
+  o->x0_kind = RT_X0_ZERO;
+  o->ortho = RT_ORTHO_MGS;
+  o->precision = RT_PRECISION_FP64;
+  o->rtol = 1e-8;
+  o->inner_rtol = 1e-4;
+  o->max_refine = 20;
+}
+
+rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,
+                         rt_solve_info* info, void* stream) {
+  clear_error();
+  if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
+  RT_TRY(check_opts(opts, b_dev, x_dev));
+  return solve_gmres(&prob->P, opts, b_dev, x_dev, info, as_stream(stream));
+}
+
+rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,
+                            rt_solve_info* info, void* stream) {
+  clear_error();
+  if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
+  RT_TRY(check_opts(opts, b_dev, x_dev));
+  return solve_bicg(&prob->P, 0, opts, b_dev, x_dev, info, as_stream(stream));
+}
+
+rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,
+                       rt_solve_info* info, void* stream) {
+  clear_error();
+  if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
+  RT_TRY(check_opts(opts, b_dev, x_dev));
+  return solve_bicg(&prob->P, 1, opts, b_dev, x_dev, info, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/rt_krylov.h; the ctypes structures match the C layout; argument
+validation runs on the host (CPU, no device work)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2110_11873_gb300 import _native as N
+from paper_2110_11873_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rt_krylov.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return N.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported_and_bound(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    out = subprocess.run(["nm", "-D", "--defined-only", N.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(rt_\w+)", out))
+    bound = {n for n, _, _ in N.SIGNATURES}
+    for n in names:
+        assert n in exported, n
+        assert n in bound, n
+        assert getattr(lib, n) is not None
+
+
+_LAYOUT_C = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "rt_krylov.h"
+#define F(T, f) printf("%s.%s %zu\n", #T, #f, offsetof(T, f))
+int main(void) {
+  printf("rt_problem_desc %zu\nrt_solver_opts %zu\nrt_solve_info %zu\n",
+         sizeof(rt_problem_desc), sizeof(rt_solver_opts), sizeof(rt_solve_info));
+  F(rt_problem_desc, tau); F(rt_problem_desc, phi_center); F(rt_problem_desc, W2);
+  F(rt_problem_desc, freq_norm);
+  F(rt_solver_opts, rtol); F(rt_solver_opts, resid_hist); F(rt_solver_opts, hist_cap);
+  F(rt_solve_info, rel_resid); F(rt_solve_info, t_total_ms);
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                               check=True).stdout.split("\n") if line)
+    structs = {"rt_problem_desc": N.ProblemDesc, "rt_solver_opts": N.SolverOpts, "rt_solve_info": N.SolveInfo}
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+    for key, val in got.items():
+        if "." in key:
+            sname, field = key.split(".")
+            assert getattr(structs[sname], field).offset == int(val), key
+
+
+def _desc(**kw):
+    tau = np.logspace(-4, 6, 10)
+    keep = [tau]
+    d = N.ProblemDesc()
+    d.Ns, d.Nmu, d.Nnu = 10, 4, 5
+    d.tau = tau.ctypes.data_as(C.POINTER(C.c_double))
+    d.x_min, d.x_max, d.a, d.eps, d.W2 = -4.0, 4.0, 1e-3, 1e-4, 1.0
+    for k, v in kw.items():
+        if k == "tau":
+            arr = np.asarray(v, dtype=np.float64)
+            keep.append(arr)
+            d.tau = arr.ctypes.data_as(C.POINTER(C.c_double))
+        else:
+            setattr(d, k, v)
+    return d, keep
+
+
+@pytest.mark.parametrize("bad", [
+    dict(Ns=1), dict(Nmu=3), dict(Nmu=0), dict(Nnu=1), dict(eps=0.0), dict(eps=1.5), dict(a=0.0),
+    dict(a=0.5), dict(x_min=4.0), dict(tau_kind=7), dict(mu_quad=5), dict(formal_solver=9),
+    dict(tau=np.r_[np.logspace(-4, 6, 9), 1.0]),
+])
+def test_invalid_descriptors_are_rejected_on_the_host(lib, bad):
+    d, keep = _desc(**bad)
+    h = C.c_void_p()
+    st = lib.rt_problem_create(C.byref(d), None, C.byref(h))
+    assert st == N.RT_EINVAL
+    assert not h.value
+    assert N.last_error()
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.rt_apply(None, None, None, None) == N.RT_EINVAL
+    assert lib.rt_problem_size(None) == -1
+    assert lib.rt_problem_destroy(None) == N.RT_OK
+    o = N.SolverOpts()
+    lib.rt_solver_opts_default(C.byref(o))
+    assert (o.restart, o.maxit, o.precond, o.rtol) == (30, 10000, N.RT_PREC_JACOBI, 1e-8)
+    info = N.SolveInfo()
+    assert lib.rt_solve_gmres(None, C.byref(o), None, None, C.byref(info), None) == N.RT_EINVAL

@@ -1,0 +1,145 @@
+"""GPU Krylov solvers against the oracle (C-ABI path).
+
+* iteration counts within +-1 of the oracle's textbook solvers (same
+  algorithm, same x0, restart length and stopping rule);
+* FP64 iterates at a forced equal number of iterations agree to 1e-10
+  relative (the two sides differ only in rounding order);
+* converged FP64 solutions satisfy ||b - A x||/||b|| < rtol with the
+  oracle's FP64 operator, and mixed-precision solutions reach the same
+  residual after refinement and lie within 1e-6 of the exact (LU) solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import rt_workloads as W
+from oracle import krylov as K
+from oracle.transfer import Transfer
+from paper_2110_11873_gb300 import _native as N
+
+from gpu_util import assert_close_scaled, problem, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def slab70():
+    at = W.slab70()
+    tr = Transfer(at)
+    return at, problem(at), tr, tr.rhs_I(), tr.exact_I()
+
+
+def _oracle_solve(tr, b, method, prec, **kw):
+    d = tr.jacobi_I()
+    Minv = {"none": None, "jacobi": lambda v: v / d, "local_lambda": tr.local_lambda_I_inverse}[prec]
+    fn = {"gmres": K.gmres, "bicgstab": K.bicgstab, "cgs": K.cgs}[method]
+    return fn(tr.apply_I, b, M_inv=Minv, **kw)
+
+
+def _true_rel(tr, b, x):
+    return np.linalg.norm(b - tr.apply_I(x)) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", ["local_lambda", "jacobi", "none"])
+def test_gmres_slab70(slab70, prec):
+    at, P, tr, b, xs = slab70
+    xg, info = P.solve(to_dev(b), "gmres", restart=30, precond=prec, rtol=1e-8)
+    assert info.ok, info
+    xo, io = _oracle_solve(tr, b, "gmres", prec, restart=30, tol=1e-8)
+    assert abs(info.iters - io.iters) <= 1, (info.iters, io.iters)
+    x = to_host(xg)
+    assert _true_rel(tr, b, x) < 1e-8
+    assert abs(info.rel_resid - _true_rel(tr, b, x)) < 1e-10
+    # same accuracy class as the oracle against the exact LU solution
+    eo = np.linalg.norm(xo - xs) / np.linalg.norm(xs)
+    eg = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+    assert eg < 5 * eo + 1e-12, (eg, eo)
+
+
+@pytest.mark.parametrize("prec,iters", [("local_lambda", 12), ("jacobi", 75)])
+def test_gmres_iterates_at_equal_iteration_count(slab70, prec, iters):
+    at, P, tr, b, xs = slab70
+    xg, info = P.solve(to_dev(b), "gmres", restart=30, precond=prec, rtol=1e-30, maxit=iters)
+    assert info.status == N.RT_ENOTCONV and info.iters == iters
+    xo, io = _oracle_solve(tr, b, "gmres", prec, restart=30, tol=1e-30, maxit=iters)
+    assert io.iters == iters
+    assert_close_scaled(to_host(xg), xo, 1e-10, f"gmres {prec} after {iters}")
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "cgs"])
+@pytest.mark.parametrize("prec", ["local_lambda", "jacobi"])
+def test_bicgstab_cgs_slab70(slab70, method, prec):
+    at, P, tr, b, xs = slab70
+    xg, info = P.solve(to_dev(b), method, precond=prec, rtol=1e-8, maxit=4000)
+    xo, io = _oracle_solve(tr, b, method, prec, tol=1e-8, maxit=4000)
+    assert io.status == K.OK
+    assert info.ok, info
+    assert abs(info.iters - io.iters) <= 1, (info.iters, io.iters)
+    assert _true_rel(tr, b, to_host(xg)) < 2e-8
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "cgs"])
+def test_bicgstab_cgs_iterates_at_equal_iteration_count(slab70, method):
+    at, P, tr, b, xs = slab70
+    xg, info = P.solve(to_dev(b), method, precond="local_lambda", rtol=1e-30, maxit=6)
+    xo, io = _oracle_solve(tr, b, method, "local_lambda", tol=1e-30, maxit=6)
+    assert info.iters == io.iters == 6
+    assert_close_scaled(to_host(xg), xo, 1e-10, method)
+
+
+def test_mixed_precision_refinement_slab70(slab70):
+    at, P, tr, b, xs = slab70
+    xg, info = P.solve(to_dev(b), "gmres", precond="local_lambda", rtol=1e-8, precision="fp32_refine",
+                       inner_rtol=1e-4)
+    assert info.ok and info.refine_steps >= 2, info
+    x = to_host(xg)
+    assert _true_rel(tr, b, x) < 1e-8
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-6
+
+
+def test_user_initial_guess_and_zero_rhs(slab70):
+    at, P, tr, b, xs = slab70
+    # the exact solution as initial guess: converged before any iteration
+    xg, info = P.solve(to_dev(b), "gmres", x=to_dev(xs), x0=True, precond="local_lambda")
+    assert info.ok and info.iters == 0 and info.applies == 1
+    # b = 0: x = 0
+    z = torch.zeros(tr.N, dtype=torch.float64, device="cuda")
+    for m in ("gmres", "bicgstab", "cgs"):
+        xg, info = P.solve(z, m, x=to_dev(xs), precond="jacobi")
+        assert info.ok and info.iters == 0 and float(xg.abs().max()) == 0.0
+
+
+def test_maxit_reached_reports_not_converged(slab70):
+    at, P, tr, b, xs = slab70
+    xg, info = P.solve(to_dev(b), "gmres", precond="jacobi", maxit=7)
+    assert info.status == N.RT_ENOTCONV and info.iters == 7
+    xg, info = P.solve(to_dev(b), "bicgstab", precond="jacobi", maxit=3)
+    assert info.status == N.RT_ENOTCONV and info.iters == 3
+
+
+def test_residual_history_is_recorded(slab70):
+    at, P, tr, b, xs = slab70
+    xg, info = P.solve(to_dev(b), "gmres", precond="local_lambda", hist_cap=200)
+    xo, io = _oracle_solve(tr, b, "gmres", "local_lambda", restart=30, tol=1e-8)
+    n = min(len(info.history), len(io.history))
+    assert n >= info.iters - 1
+    np.testing.assert_allclose(info.history[:n], io.history[:n], rtol=1e-6)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("fs", [W.FS_DELO_LINEAR, W.FS_IMPLICIT_EULER])
+def test_slab300_gmres_fp64_and_mixed(fs):
+    """The benchmark workload: 1,939,200 unknowns."""
+    at = W.slab300(formal_solver=fs)
+    P, tr = problem(at), Transfer(at)
+    b = tr.rhs_I()
+    xs = tr.exact_I()
+    xo, io = _oracle_solve(tr, b, "gmres", "local_lambda", restart=30, tol=1e-8)
+    xg, info = P.solve(to_dev(b), "gmres", precond="local_lambda", rtol=1e-8)
+    assert info.ok and abs(info.iters - io.iters) <= 1, (info.iters, io.iters)
+    assert _true_rel(tr, b, to_host(xg)) < 1e-8
+    xm, im = P.solve(to_dev(b), "gmres", precond="local_lambda", rtol=1e-8, precision="fp32_refine")
+    assert im.ok
+    x = to_host(xm)
+    assert _true_rel(tr, b, x) < 1e-8
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-6
