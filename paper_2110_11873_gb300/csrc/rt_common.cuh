@@ -90,11 +90,18 @@ struct Problem {
   int tau_kind = 0, mu_quad = 0, fs = 0, freq_norm = 0;
   // host grids
   std::vector<double> tau, B, mu, w_mu, x, phi, w_nu, phi_hat, t201, t202;
+  // ray groups of the formal-solver kernel: 32 consecutive rays of one
+  // direction sign; the nd = Nh*Nnu downward rays come first
+  int64_t nd = 0;
+  int ngroups = 0;
+  int ntile64 = 1, ntile32 = 1;   // depth tiles per ray group (FP64 / FP32 kernels)
   // FP64 device tables
-  double* ce = nullptr;    // [(Ns-1)][Nh][Nnu] step factor e
+  double* ce = nullptr;    // [(Ns-1)][nray] step factor e of the interval (i, i+1) on ray r
   double* ca = nullptr;    // ... alpha (coefficient of the upwind S)
   double* cb = nullptr;    // ... beta  (coefficient of S at the new node)
-  double* wray = nullptr;  // [Nmu][Nnu] hat-w_m * hat-w_p
+  double* wray = nullptr;  // [nray] hat-w_m * hat-w_p
+  double* wI2 = nullptr;   // [Nnu] spectral weights hat-w_p
+  double* wQ2 = nullptr;   // [Nmu] angular weights hat-w_m = w_m / 2
   double* t201d = nullptr; // [Nmu]
   double* t202d = nullptr; // [Nmu]
   double* Bd = nullptr;    // [Ns]
@@ -103,8 +110,10 @@ struct Problem {
   double* S2 = nullptr;    // second source-function scratch
   // FP32 device tables
   float* dtau32 = nullptr;  // [Ns-1] tau_{k+1} - tau_k
-  float* r32 = nullptr;     // [Nh][Nnu] phi_hat_p / |mu|
+  float* r32 = nullptr;     // [nray] phi_hat_p / |mu_m|
   float* wray32 = nullptr;
+  float* wI2f = nullptr;
+  float* wQ2f = nullptr;
   float* t201f = nullptr;
   float* t202f = nullptr;
   float* S32 = nullptr;     // [2][Ns][Nmu]

@@ -75,12 +75,32 @@ __device__ __forceinline__ double block_partials(const double* __restrict__ part
 }
 
 // ------------------------------------------------------------------ kernels
+// Grid-stride loops unrolled by kU with all loads of a round issued before
+// any arithmetic, so each thread keeps kU independent loads in flight.
+constexpr int kU = 4;
+
+// skip test shared by the kernels of a captured iteration: GMRES kernels of
+// Arnoldi step `step` skip once step >= *kstop; BiCGSTAB/CGS kernels skip
+// once *done is set
+__device__ __forceinline__ bool gated(const int* kstop, int step, const int* done) {
+  return (kstop && step >= *kstop) || (done && *done);
+}
+
 __global__ void __launch_bounds__(kVecThreads) k_dot(const double* __restrict__ a, const double* __restrict__ b,
-                                                     int64_t N, double* __restrict__ part, const int* kstop, int step) {
-  if (kstop && step >= *kstop) return;
+                                                     int64_t N, double* __restrict__ part, const int* kstop, int step,
+                                                     const int* done) {
+  if (gated(kstop, step, done)) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    s = fma(a[i], b[i], s);
+  for (; i + (kU - 1) * stride < N; i += kU * stride) {
+    double av[kU], bv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) { av[u] = a[i + u * stride]; bv[u] = b[i + u * stride]; }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) s = fma(av[u], bv[u], s);
+  }
+  for (; i < N; i += stride) s = fma(a[i], b[i], s);
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -90,8 +110,25 @@ __global__ void __launch_bounds__(kVecThreads) k_dot2(const double* __restrict__
                                                       const double* __restrict__ c, const double* __restrict__ d,
                                                       int64_t N, double* __restrict__ part, const int* done) {
   if (done && *done) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double s = 0.0, t = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (; i + (kU - 1) * stride < N; i += kU * stride) {
+    double av[kU], bv[kU], cv[kU], dv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      av[u] = a[i + u * stride];
+      bv[u] = b[i + u * stride];
+      cv[u] = c[i + u * stride];
+      dv[u] = d[i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      s = fma(av[u], bv[u], s);
+      t = fma(cv[u], dv[u], t);
+    }
+  }
+  for (; i < N; i += stride) {
     s = fma(a[i], b[i], s);
     t = fma(c[i], d[i], t);
   }
@@ -111,11 +148,29 @@ __global__ void __launch_bounds__(kVecThreads) k_mgs(double* __restrict__ w, con
   if (step >= *kstop) return;
   const double h = block_partials(part_in, gridDim.x);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hslot = h;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  const double* __restrict__ vn = vnext ? vnext : w;
+  for (; i + (kU - 1) * stride < N; i += kU * stride) {
+    double wv[kU], pv[kU], nv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      wv[u] = w[i + u * stride];
+      pv[u] = vprev[i + u * stride];
+      if (vnext) nv[u] = vnext[i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const double wi = fma(-h, pv[u], wv[u]);
+      w[i + u * stride] = wi;
+      s = fma(wi, vnext ? nv[u] : wi, s);
+    }
+  }
+  for (; i < N; i += stride) {
     const double wi = fma(-h, vprev[i], w[i]);
     w[i] = wi;
-    s = fma(wi, vnext ? vnext[i] : wi, s);
+    s = fma(wi, vnext ? vn[i] : wi, s);
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part_out[blockIdx.x] = s;
@@ -129,8 +184,16 @@ __global__ void __launch_bounds__(kVecThreads) k_normalize(const double* __restr
   const double hn = sqrt(block_partials(part_in, gridDim.x));
   if (blockIdx.x == 0 && threadIdx.x == 0) gm->H[step * (m + 1) + step + 1] = hn;
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = w[i] * inv;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kU - 1) * stride < N; i += kU * stride) {
+    double wv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) wv[u] = w[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[i + u * stride] = wv[u] * inv;
+  }
+  for (; i < N; i += stride) v[i] = w[i] * inv;
 }
 
 // Givens rotations on column j of the Hessenberg matrix (one thread)
@@ -574,7 +637,7 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
     double* vj = P->V + (size_t)j * N;
     RT_TRY(apply_prec(P, vj, w, precond, fp32, st, kstop, j));
     int pb = 0;
-    k_dot<<<G, kVecThreads, 0, st>>>(w, P->V, N, partb(P, pb), kstop, j); RT_COUNT(1);
+    k_dot<<<G, kVecThreads, 0, st>>>(w, P->V, N, partb(P, pb), kstop, j, nullptr); RT_COUNT(1);
     for (int i = 0; i <= j; ++i) {
       const double* vprev = P->V + (size_t)i * N;
       const double* vnext = (i < j) ? P->V + (size_t)(i + 1) * N : nullptr;
@@ -687,10 +750,10 @@ static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, doubl
   init.tol = tol;
   init.maxit = maxit;
   RT_TRY_CUDA(cudaMemcpyAsync(P->gm, &init, sizeof init, cudaMemcpyHostToDevice, st));
-  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), N, partb(P, 1), nullptr, 0); RT_COUNT(1);
+  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), N, partb(P, 1), nullptr, 0, nullptr); RT_COUNT(1);
   k_set_bnorm<<<1, 32, 0, st>>>(partb(P, 1), G, P->gm); RT_COUNT(1);
   if (x0_zero) {
-    k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), N, partb(P, 0), nullptr, 0); RT_COUNT(1);
+    k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), N, partb(P, 0), nullptr, 0, nullptr); RT_COUNT(1);
     k_cycle_start<<<G, kVecThreads, 0, st>>>(wk(P, 1), P->V, N, partb(P, 0), P->gm, m); RT_COUNT(1);
   } else {
     RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
@@ -754,7 +817,7 @@ static rt_status true_residual(Problem* P, double* rel, cudaStream_t st) {
   const int G = P->vec_grid;
   RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
   k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), P->N, partb(P, 0)); RT_COUNT(1);
-  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), P->N, partb(P, 1), nullptr, 0); RT_COUNT(1);
+  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), P->N, partb(P, 1), nullptr, 0, nullptr); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   std::vector<double> h(2 * G);
   RT_TRY_CUDA(cudaMemcpyAsync(h.data(), partb(P, 0), G * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -852,7 +915,7 @@ static rt_status enqueue_bicg_iter(Problem* P, int method, int precond, int fp32
     double *v = wk(P, 5), *s = wk(P, 6), *t = wk(P, 7);
     k_bs_p<<<G, kVecThreads, 0, st>>>(p, r, v, N, bc); RT_COUNT(1);
     RT_TRY(apply_prec(P, p, v, precond, fp32, st));
-    k_dot<<<G, kVecThreads, 0, st>>>(rhat, v, N, partb(P, 0), &bc->done, 0); RT_COUNT(1);
+    k_dot<<<G, kVecThreads, 0, st>>>(rhat, v, N, partb(P, 0), nullptr, 0, &bc->done); RT_COUNT(1);
     k_bc_alpha<<<1, 32, 0, st>>>(bc, partb(P, 0), G); RT_COUNT(1);
     k_bs_s<<<G, kVecThreads, 0, st>>>(s, r, v, N, bc, partb(P, 1)); RT_COUNT(1);
     k_bs_check_s<<<1, 32, 0, st>>>(bc, partb(P, 1), G); RT_COUNT(1);
@@ -867,7 +930,7 @@ static rt_status enqueue_bicg_iter(Problem* P, int method, int precond, int fp32
     double* qh = P->V + (size_t)N;
     k_cgs_up<<<G, kVecThreads, 0, st>>>(u, p, r, q, N, bc); RT_COUNT(1);
     RT_TRY(apply_prec(P, p, vh, precond, fp32, st));
-    k_dot<<<G, kVecThreads, 0, st>>>(rhat, vh, N, partb(P, 0), &bc->done, 0); RT_COUNT(1);
+    k_dot<<<G, kVecThreads, 0, st>>>(rhat, vh, N, partb(P, 0), nullptr, 0, &bc->done); RT_COUNT(1);
     k_bc_alpha<<<1, 32, 0, st>>>(bc, partb(P, 0), G); RT_COUNT(1);
     k_cgs_q<<<G, kVecThreads, 0, st>>>(q, w, acc, u, vh, N, bc); RT_COUNT(1);
     RT_TRY(apply_prec(P, w, qh, precond, fp32, st));
@@ -916,7 +979,7 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
   init.maxit = o->maxit;
   RT_TRY_CUDA(cudaMemcpyAsync(P->bc, &init, sizeof init, cudaMemcpyHostToDevice, st));
   // ||b||, then ||r||^2 and <rhat, r>
-  k_dot<<<G, kVecThreads, 0, st>>>(bb, bb, N, partb(P, 1), nullptr, 0); RT_COUNT(1);
+  k_dot<<<G, kVecThreads, 0, st>>>(bb, bb, N, partb(P, 1), nullptr, 0, nullptr); RT_COUNT(1);
   k_dot2<<<G, kVecThreads, 0, st>>>(r, r, rhat, r, N, partb(P, 0), nullptr); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   {

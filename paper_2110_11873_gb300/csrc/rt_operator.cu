@@ -1,22 +1,29 @@
 // The matrix-free transfer operator of Eq. (19), y = x - Lambda(T(J x)), as
 // two kernels per application (Algorithm 1, transposed to the I-form):
 //
-//   k_moments  (quadrature T∘J, Eq. 11-14 and 7-8): one block per height k
-//              reduces the Nmu*Nnu rays of I and Q to J00_k, J20_k, forms
-//              sigma_k and writes the source functions S_I(k,m), S_Q(k,m).
-//              Each warp owns whole direction rows m, so the quadrature is
-//              sum_m w_m T2_m (sum_p w_p x_mp): one multiply-add per element.
-//   k_formal   (formal solver Lambda, Eq. 9-10): one thread per (m,p) ray,
-//              carrying both Stokes parameters down the depth recurrence
-//              I_k = e I_prev + alpha S_prev + beta S_k, and writing
-//              y_k = z_k - I_k on the fly.  Neighbouring threads are
-//              neighbouring frequencies, so every depth step is a coalesced
-//              row access.
+//   k_moments  quadrature T∘J (Eq. 11-14, 7-8): one block per height k
+//              reduces the Nmu*Nnu rays of I and Q to J00_k and J20_k with
+//              precomputed per-ray weights (w, w T201, w T202), forms sigma_k
+//              and writes the source functions S_I(k,m), S_Q(k,m).
+//   k_formal   formal solver Lambda (Eq. 9-10) along every ray, writing
+//              y_k = z_k - I_k on the fly.  A CTA owns one group of 32 rays of
+//              the same direction sign (so the 32 lanes of a warp read one
+//              contiguous row of x per depth step) and splits the depth into
+//              `ntile` tiles, one warp each.  With more than one tile the
+//              depth recurrence I_k = e I_prev + alpha S_prev + beta S_k is
+//              solved as an affine scan: every warp first composes the map
+//              I_out = E I_in + B of its tile (phase A), one warp chains the
+//              maps over the tiles (phase B), and every warp then re-sweeps
+//              its tile from the right inflow (phase C).  Each lane keeps a
+//              ring of the next kRing steps' loads in registers so that
+//              memory latency overlaps the recurrence.
 //
-// FP64 variant: step coefficients (e, alpha, beta) precomputed per
-// (interval, |mu|, nu) in FP64 (shared by I, Q and by +-mu).  FP32 variant:
-// coefficients recomputed from Delta in FP32 with a Taylor branch for small
-// Delta, so the apply streams only x and y.
+// FP64: step coefficients (e, alpha, beta) are precomputed per (interval,
+// ray) in FP64 and streamed; FP64 arithmetic on this GPU is ~70x slower than
+// FP32, so the FP64 kernels are built to issue as few FP64 operations as the
+// recurrence needs (8 per (k,m,p) for both Stokes parameters).  FP32: the
+// coefficients are recomputed from Delta in FP32, so the apply streams only
+// x and y.
 #include <math.h>
 
 #include "rt_common.cuh"
@@ -26,11 +33,12 @@ namespace rt {
 namespace {
 
 constexpr int kMomThreads = 256;
-constexpr int kFormalThreads = 128;
+constexpr int kMaxTiles = 8;     // FP32 kernel: up to 256 threads per CTA (255 registers a lane)
+constexpr int kMaxTiles64 = 8;   // FP64 kernel: up to 256 threads, so each lane may hold 255 registers
+constexpr int kRing = 8;         // prefetch depth of the FP64 formal-solver kernel (steps)
+constexpr int kRing32 = 16;      // prefetch depth of the FP32 kernel (one lane carries I and Q)
 
-enum KMode { KM_PLAIN = 0, KM_JACOBI = 1, KM_LOCAL_LAMBDA = 2 };
-
-__device__ __forceinline__ int abs_mu_index(int m, int Nh) { return m < Nh ? Nh - 1 - m : m - Nh; }
+enum KMode { KM_PLAIN = 0, KM_JACOBI = 1, KM_LOCAL_LAMBDA = 2, KM_RHS = 3 };
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -40,28 +48,24 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ------------------------------------------------------------- setup kernels
-// Step coefficients of the formal solvers, FP64, per interval i, |mu| index
-// mm and frequency p:  Delta = dtau_i * phi_hat_p / |mu|.
-__global__ void k_coeffs64(const double* __restrict__ dtau, const double* __restrict__ phat,
-                           const double* __restrict__ absmu, int Ns, int Nh, int Nnu, int fs,
-                           double* __restrict__ ce, double* __restrict__ ca, double* __restrict__ cb) {
-  const int64_t n = (int64_t)(Ns - 1) * Nh * Nnu;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int p = (int)(t % Nnu);
-    const int64_t q = t / Nnu;
-    const int mm = (int)(q % Nh);
-    const int i = (int)(q / Nh);
-    const double D = dtau[i] * phat[p] / absmu[mm];
+// Step coefficients of the formal solvers, FP64, per interval i and ray r:
+// Delta = dtau_i * phi_hat_p / |mu_m|.
+__global__ void k_coeffs64(const double* __restrict__ dtau, const double* __restrict__ rscale, int Ns,
+                           int64_t nray, int fs, double* __restrict__ ce, double* __restrict__ ca,
+                           double* __restrict__ cb) {
+  const int64_t n = (int64_t)(Ns - 1) * nray;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t % nray;
+    const int i = (int)(t / nray);
+    const double D = dtau[i] * rscale[r];
     double e, al, be;
     if (fs == RT_FS_DELO_LINEAR) {
+      e = exp(-D);
       if (D < 0.5) {
         // beta = sum_{n>=1} (-1)^{n+1} D^n/(n+1)!,  alpha = sum (-1)^{n+1} n D^n/(n+1)!
-        // Horner form, 20 terms (0.5^20/21! ~ 2e-26)
-        double b = 0.0, a = 0.0;
-        double c = 1.0;
-        for (int k = 2; k <= 21; ++k) c /= k;   // c = 1/21!
-        // walk n = 20..1 with c_n = 1/(n+1)!
+        // Horner form over n = 20..1 (0.5^20/21! ~ 2e-26)
+        double b = 0.0, a = 0.0, c = 1.0;
+        for (int k = 2; k <= 21; ++k) c /= k;  // 1/21!
         for (int nn = 20; nn >= 1; --nn) {
           const double sgn = (nn & 1) ? 1.0 : -1.0;
           b = b * D + sgn * c;
@@ -70,12 +74,10 @@ __global__ void k_coeffs64(const double* __restrict__ dtau, const double* __rest
         }
         be = b * D;
         al = a * D;
-        e = exp(-D);
       } else {
-        e = exp(-D);
-        const double r = -expm1(-D) / D;
-        be = 1.0 - r;
-        al = r - e;
+        const double q = -expm1(-D) / D;   // w0 / Delta
+        be = 1.0 - q;
+        al = q - e;
       }
     } else if (fs == RT_FS_IMPLICIT_EULER) {
       e = 1.0 / (1.0 + D);
@@ -93,12 +95,11 @@ __global__ void k_coeffs64(const double* __restrict__ dtau, const double* __rest
   }
 }
 
-// beta* (coefficient of S_k in I_k) of ray (m,p) at height k
-__device__ __forceinline__ double beta_star(const double* __restrict__ cb, int k, int m, int p, int Ns,
-                                            int Nh, int Nnu) {
-  const int mm = abs_mu_index(m, Nh);
-  if (m < Nh) return k == 0 ? 0.0 : cb[((int64_t)(k - 1) * Nh + mm) * Nnu + p];
-  return k == Ns - 1 ? 0.0 : cb[((int64_t)k * Nh + mm) * Nnu + p];
+// beta* (coefficient of S_k in I_k) of ray r = m*Nnu + p at height k
+__device__ __forceinline__ double beta_star(const double* __restrict__ cb, int k, int m, int64_t r, int Ns,
+                                            int Nh, int64_t nray) {
+  if (m < Nh) return k == 0 ? 0.0 : cb[(int64_t)(k - 1) * nray + r];
+  return k == Ns - 1 ? 0.0 : cb[(int64_t)k * nray + r];
 }
 
 // 2x2 local blocks M_k = Id - J_k Lambda*_k T_k of the sigma-form and their
@@ -106,27 +107,30 @@ __device__ __forceinline__ double beta_star(const double* __restrict__ cb, int k
 __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __restrict__ cb,
                                                              const double* __restrict__ wray,
                                                              const double* __restrict__ t201,
-                                                             const double* __restrict__ t202, int Ns,
-                                                             int Nmu, int Nnu, double xi, double W2,
+                                                             const double* __restrict__ t202, int Ns, int Nmu,
+                                                             int Nnu, double xi, double W2,
                                                              double* __restrict__ Minv) {
   const int k = blockIdx.x;
   const int Nh = Nmu / 2;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t nray = (int64_t)Nmu * Nnu;
   double a0 = 0, a1 = 0, a2 = 0;
-  for (int m = warp; m < Nmu; m += nw) {
-    double s = 0;
-    for (int p = lane; p < Nnu; p += 32) s += wray[m * Nnu + p] * beta_star(cb, k, m, p, Ns, Nh, Nnu);
-    s = warp_sum(s);
+  for (int64_t r = threadIdx.x; r < nray; r += blockDim.x) {
+    const int m = (int)(r / Nnu);
+    const double s = wray[r] * beta_star(cb, k, m, r, Ns, Nh, nray);
     a0 += s;
     a1 += t201[m] * s;
     a2 += (t201[m] * t201[m] + t202[m] * t202[m]) * s;
   }
-  __shared__ double red[3][32];
+  __shared__ double red[3][kMomThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
   if (lane == 0) { red[0][warp] = a0; red[1][warp] = a1; red[2][warp] = a2; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double b0 = 0, b1 = 0, b2 = 0;
-    for (int w = 0; w < nw; ++w) { b0 += red[0][w]; b1 += red[1][w]; b2 += red[2][w]; }
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { b0 += red[0][w]; b1 += red[1][w]; b2 += red[2][w]; }
     const double m00 = 1.0 - xi * b0, m01 = -xi * b1, m10 = -xi * W2 * b1, m11 = 1.0 - xi * W2 * b2;
     const double det = m00 * m11 - m01 * m10;
     Minv[4 * k + 0] = m11 / det;
@@ -136,20 +140,19 @@ __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __re
   }
 }
 
-// inverse Jacobi diagonal (or the diagonal itself) of Id - Lambda T J
+// Jacobi diagonal of Id - Lambda T J, or its inverse
 __global__ void k_jacobi(const double* __restrict__ cb, const double* __restrict__ wray,
-                         const double* __restrict__ t201, const double* __restrict__ t202, int Ns, int Nmu,
-                         int Nnu, double xi, double W2, int inverse, double* __restrict__ d) {
+                         const double* __restrict__ t201, const double* __restrict__ t202, int Ns, int Nmu, int Nnu,
+                         double xi, double W2, int inverse, double* __restrict__ d) {
   const int Nh = Nmu / 2;
   const int64_t nray = (int64_t)Nmu * Nnu, N = 2 * (int64_t)Ns * nray;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t % nray;
     const int64_t sk = t / nray;
     const int k = (int)(sk % Ns), s = (int)(sk / Ns);
-    const int m = (int)(r / Nnu), p = (int)(r % Nnu);
-    const double bw = beta_star(cb, k, m, p, Ns, Nh, Nnu) * wray[r];
-    const double v = s == 0 ? 1.0 - xi * bw * (1.0 + W2 * t201[m] * t201[m])
-                            : 1.0 - xi * W2 * bw * t202[m] * t202[m];
+    const int m = (int)(r / Nnu);
+    const double bw = beta_star(cb, k, m, r, Ns, Nh, nray) * wray[r];
+    const double v = s == 0 ? 1.0 - xi * bw * (1.0 + W2 * t201[m] * t201[m]) : 1.0 - xi * W2 * bw * t202[m] * t202[m];
     d[t] = inverse ? 1.0 / v : v;
   }
 }
@@ -163,43 +166,72 @@ __global__ void k_rhs_source(const double* __restrict__ B, int Ns, int Nmu, doub
   }
 }
 
+// z = v + beta* S (the Lambda* T M^{-1} J part of P^{-1} v, S = T M^{-1} J v)
+__global__ void k_add_local(const double* __restrict__ v, const double* __restrict__ cb, const double* __restrict__ S,
+                            int Ns, int Nmu, int Nnu, double* __restrict__ z) {
+  const int Nh = Nmu / 2;
+  const int64_t nray = (int64_t)Nmu * Nnu, N = 2 * (int64_t)Ns * nray;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t % nray, sk = t / nray;
+    const int k = (int)(sk % Ns), s = (int)(sk / Ns);
+    const int m = (int)(r / Nnu);
+    z[t] = v[t] + beta_star(cb, k, m, r, Ns, Nh, nray) * S[((int64_t)s * Ns + k) * Nmu + m];
+  }
+}
+
 // ----------------------------------------------------------------- K1: T∘J
-// MODE: KM_PLAIN z = x; KM_JACOBI z = x * dinv; KM_LOCAL_LAMBDA z = x and the
-// per-height sigma is replaced by M_k^{-1} sigma.  TI: input vector type,
-// TC: compute type of the quadrature.
+// One block per height; warp w sums the direction rows m = w, w+8, ...:
+// a_m = sum_p w_p z_I(k,m,p), b_m = sum_p w_p z_Q(k,m,p) (one multiply-add
+// per element), then J00 += w_m a_m and J20 += w_m (T201_m a_m + T202_m b_m).
+// Every lane issues the loads of a whole row before it adds.  MODE:
+// KM_PLAIN z = x; KM_JACOBI z = x * dinv; KM_LOCAL_LAMBDA z = x and
+// sigma_k <- M_k^{-1} sigma_k.  TI: input vector type, TC: arithmetic type.
+constexpr int kRowChunk = 8;   // loads per lane in flight per Stokes parameter
+
 template <typename TI, typename TC, int MODE>
-__global__ void __launch_bounds__(kMomThreads) k_moments(const TI* __restrict__ x, const double* __restrict__ dinv,
-                                                         const TC* __restrict__ wray, const TC* __restrict__ t201,
-                                                         const TC* __restrict__ t202,
-                                                         const double* __restrict__ Minv, int Ns, int Nmu,
-                                                         int Nnu, TC xi, TC xiW2, TC* __restrict__ S,
-                                                         const int* kstop, int step) {
+__global__ void __launch_bounds__(kMomThreads) k_moments(
+    const TI* __restrict__ x, const double* __restrict__ dinv, const TC* __restrict__ wnu,
+    const TC* __restrict__ wmu, const TC* __restrict__ t201, const TC* __restrict__ t202,
+    const double* __restrict__ Minv, int Ns, int Nmu, int Nnu, TC xi, TC xiW2, TC* __restrict__ S,
+    const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
   const int k = blockIdx.x;
   const int64_t nray = (int64_t)Nmu * Nnu;
-  const TI* xI = x + (int64_t)k * nray;
-  const TI* xQ = x + ((int64_t)Ns + k) * nray;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t oI = (int64_t)k * nray, oQ = ((int64_t)Ns + k) * nray;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int nw = kMomThreads / 32;
   TC j00 = 0, j20 = 0;
   for (int m = warp; m < Nmu; m += nw) {
+    const int64_t row = (int64_t)m * Nnu;
     TC aI = 0, aQ = 0;
-    for (int p = lane; p < Nnu; p += 32) {
-      const int idx = m * Nnu + p;
-      const TC w = wray[idx];
-      TC vI = (TC)xI[idx], vQ = (TC)xQ[idx];
-      if (MODE == KM_JACOBI) {
-        vI *= (TC)dinv[(int64_t)k * nray + idx];
-        vQ *= (TC)dinv[((int64_t)Ns + k) * nray + idx];
+    for (int p0 = 0; p0 < Nnu; p0 += 32 * kRowChunk) {
+      TC vI[kRowChunk], vQ[kRowChunk], wv[kRowChunk];
+#pragma unroll
+      for (int c = 0; c < kRowChunk; ++c) {
+        const int p = p0 + c * 32 + lane;
+        const bool ok = p < Nnu;
+        const int64_t q = row + (ok ? p : 0);
+        vI[c] = ok ? (TC)x[oI + q] : (TC)0;
+        vQ[c] = ok ? (TC)x[oQ + q] : (TC)0;
+        wv[c] = ok ? wnu[p] : (TC)0;
+        if (MODE == KM_JACOBI && ok) {
+          vI[c] *= (TC)dinv[oI + q];
+          vQ[c] *= (TC)dinv[oQ + q];
+        }
       }
-      aI += w * vI;
-      aQ += w * vQ;
+#pragma unroll
+      for (int c = 0; c < kRowChunk; ++c) {
+        aI = fma(wv[c], vI[c], aI);
+        aQ = fma(wv[c], vQ[c], aQ);
+      }
     }
     aI = warp_sum(aI);
     aQ = warp_sum(aQ);
-    j00 += aI;
-    j20 += t201[m] * aI + t202[m] * aQ;
+    const TC wm = wmu[m];
+    j00 = fma(wm, aI, j00);
+    j20 = fma(wm, fma(t201[m], aI, t202[m] * aQ), j20);
   }
-  __shared__ TC red[2][32];
+  __shared__ TC red[2][nw];
   __shared__ TC sig[2];
   if (lane == 0) { red[0][warp] = j00; red[1][warp] = j20; }
   __syncthreads();
@@ -224,82 +256,8 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const TI* __restrict__ 
   }
 }
 
-// ------------------------------------------------------------ K2: Lambda, FP64
-// MODE: KM_PLAIN y = x - Lambda S;  KM_JACOBI y = x*dinv - Lambda S;
-// KM_LOCAL_LAMBDA y = u - Lambda S with u = x + beta* S, which reduces to
-// y_k = x_k - (e I_prev + alpha S_prev).
-// RHS (rhs != 0): y = Lambda S + t, the boundary inflow included.
-template <int MODE>
-__global__ void __launch_bounds__(kFormalThreads) k_formal64(
-    const double* __restrict__ x, const double* __restrict__ dinv, const double* __restrict__ ce,
-    const double* __restrict__ ca, const double* __restrict__ cb, const double* __restrict__ S,
-    double* __restrict__ y, int Ns, int Nmu, int Nnu, int rhs, double inflow_bottom, const int* kstop, int step) {
-  if (kstop && step >= *kstop) return;
-  const int64_t nray = (int64_t)Nmu * Nnu;
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= nray) return;
-  const int Nh = Nmu >> 1;
-  const int m = (int)(r / Nnu), p = (int)(r - (int64_t)m * Nnu);
-  const bool down = m < Nh;
-  const int mm = abs_mu_index(m, Nh);
-  const int64_t cstr = (int64_t)Nh * Nnu, coff = (int64_t)mm * Nnu + p;
-  const int64_t qoff = (int64_t)Ns * nray;
-  const double* SI = S + m;
-  const double* SQ = S + (int64_t)Ns * Nmu + m;
-  const int k0 = down ? 0 : Ns - 1;
-  const int dk = down ? 1 : -1;
-  double II = (rhs && !down) ? inflow_bottom : 0.0, IQ = 0.0;
-  double sIp = SI[(int64_t)k0 * Nmu], sQp = SQ[(int64_t)k0 * Nmu];
-  {
-    const int64_t o = (int64_t)k0 * nray + r;
-    if (rhs) {
-      y[o] = II;
-      y[qoff + o] = IQ;
-    } else if (MODE == KM_JACOBI) {
-      y[o] = x[o] * dinv[o];
-      y[qoff + o] = x[qoff + o] * dinv[qoff + o];
-    } else {
-      y[o] = x[o];
-      y[qoff + o] = x[qoff + o];
-    }
-  }
-#pragma unroll 4
-  for (int j = 1; j < Ns; ++j) {
-    const int k = k0 + j * dk;
-    const int i = down ? k - 1 : k;
-    const int64_t c = (int64_t)i * cstr + coff;
-    const double e = ce[c], al = ca[c], be = cb[c];
-    const double sI = SI[(int64_t)k * Nmu], sQ = SQ[(int64_t)k * Nmu];
-    const int64_t o = (int64_t)k * nray + r;
-    if (rhs) {
-      II = fma(e, II, fma(al, sIp, be * sI));
-      IQ = fma(e, IQ, fma(al, sQp, be * sQ));
-      y[o] = II;
-      y[qoff + o] = IQ;
-    } else if (MODE == KM_LOCAL_LAMBDA) {
-      const double tI = fma(e, II, al * sIp), tQ = fma(e, IQ, al * sQp);
-      y[o] = x[o] - tI;
-      y[qoff + o] = x[qoff + o] - tQ;
-      II = fma(be, sI, tI);
-      IQ = fma(be, sQ, tQ);
-    } else {
-      II = fma(e, II, fma(al, sIp, be * sI));
-      IQ = fma(e, IQ, fma(al, sQp, be * sQ));
-      double zI = x[o], zQ = x[qoff + o];
-      if (MODE == KM_JACOBI) {
-        zI *= dinv[o];
-        zQ *= dinv[qoff + o];
-      }
-      y[o] = zI - II;
-      y[qoff + o] = zQ - IQ;
-    }
-    sIp = sI;
-    sQp = sQ;
-  }
-}
-
-// ------------------------------------------------------------ K2: Lambda, FP32
-// coefficients from Delta in FP32 (DELO-linear: Taylor branch below 0.5)
+// --------------------------------------------------------------- K2: Lambda
+// FP32 step coefficients from Delta (DELO-linear: Taylor branch below 0.5)
 template <int FS>
 __device__ __forceinline__ void coeffs32(float D, float& e, float& al, float& be) {
   if (FS == RT_FS_DELO_LINEAR) {
@@ -318,79 +276,219 @@ __device__ __forceinline__ void coeffs32(float D, float& e, float& al, float& be
       be = -b * D;
       al = -a * D;
     } else {
-      const float r = (1.0f - e) / D;
-      be = 1.0f - r;
-      al = r - e;
+      const float q = __fdividef(1.0f - e, D);
+      be = 1.0f - q;
+      al = q - e;
     }
   } else if (FS == RT_FS_IMPLICIT_EULER) {
-    e = 1.0f / (1.0f + D);
+    e = __frcp_rn(1.0f + D);
     al = 0.0f;
     be = D * e;
   } else {
-    const float h = 0.5f * D, q = 1.0f / (1.0f + h);
+    const float h = 0.5f * D, q = __frcp_rn(1.0f + h);
     e = (1.0f - h) * q;
     al = h * q;
     be = al;
   }
 }
 
-template <typename TV, int FS, int MODE>
-__global__ void __launch_bounds__(kFormalThreads) k_formal32(
-    const TV* __restrict__ x, const double* __restrict__ dinv, const float* __restrict__ dtau,
-    const float* __restrict__ rr, const float* __restrict__ S, TV* __restrict__ y, int Ns, int Nmu, int Nnu,
-    const int* kstop, int step) {
-  if (kstop && step >= *kstop) return;
-  const int64_t nray = (int64_t)Nmu * Nnu;
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= nray) return;
-  const int Nh = Nmu >> 1;
-  const int m = (int)(r / Nnu), p = (int)(r - (int64_t)m * Nnu);
-  const bool down = m < Nh;
-  const float rp = rr[abs_mu_index(m, Nh) * Nnu + p];
-  const int64_t qoff = (int64_t)Ns * nray;
-  const float* SI = S + m;
-  const float* SQ = S + (int64_t)Ns * Nmu + m;
-  const int k0 = down ? 0 : Ns - 1;
-  const int dk = down ? 1 : -1;
-  float II = 0.f, IQ = 0.f;
-  float sIp = SI[(int64_t)k0 * Nmu], sQp = SQ[(int64_t)k0 * Nmu];
-  {
-    const int64_t o = (int64_t)k0 * nray + r;
-    if (MODE == KM_JACOBI) {
-      y[o] = (TV)((float)x[o] * (float)dinv[o]);
-      y[qoff + o] = (TV)((float)x[qoff + o] * (float)dinv[qoff + o]);
+struct FormalArgs {
+  const void* x;          // input vector (TV)
+  const double* dinv;     // Jacobi inverse diagonal (KM_JACOBI)
+  const double* ce;       // FP64 coefficient tables [(Ns-1)][nray]
+  const double* ca;
+  const double* cb;
+  const float* dtau32;    // FP32: interval optical depths
+  const float* r32;       // FP32: per-ray scale phi_hat/|mu|
+  const void* S;          // source functions (TC) [2][Ns][Nmu]
+  void* y;                // output vector (TV)
+  int Ns, Nmu, Nnu;
+  int64_t nray, nd;       // rays per Stokes parameter, downward rays
+  int ngd;                // ray groups of downward rays
+  int ntile;              // depth tiles per group (warps per CTA)
+  double inflow_bottom;   // KM_RHS: I entering at the bottom (mu > 0)
+  const int* kstop;       // graph early exit (NULL: run)
+  int step;
+};
+
+// One lane: NS Stokes parameters (s0 .. s0+NS-1) of ray r, depth steps
+// [j0, j1) in marching order (node index j; height k = j for downward rays,
+// Ns-1-j for upward rays).  PHASE 0 composes the tile map (E, B) with zero
+// inflow; PHASE 1 sweeps from the inflow I and writes the output.
+template <typename TC, typename TV, int FS, int MODE, int PHASE, int NS, int RING>
+__device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, int64_t r, int m, bool active, int j0,
+                                      int j1, TC (&I)[NS], TC& E) {
+  const int Ns = A.Ns;
+  const int64_t nray = A.nray;
+  const int64_t plane = (int64_t)Ns * nray;
+  const TC* __restrict__ Sm = reinterpret_cast<const TC*>(A.S) + (int64_t)s0 * Ns * A.Nmu + m;
+  const int64_t sstride = (int64_t)Ns * A.Nmu;
+  const TV* __restrict__ x = reinterpret_cast<const TV*>(A.x) + (int64_t)s0 * plane;
+  TV* __restrict__ y = reinterpret_cast<TV*>(A.y) + (int64_t)s0 * plane;
+  const double* __restrict__ dinv = A.dinv + (int64_t)s0 * plane;
+  const float rs = (sizeof(TC) == 4) ? A.r32[r] : 0.0f;
+  auto height = [&](int j) { return down ? j : Ns - 1 - j; };
+  auto interval = [&](int j) { return down ? j - 1 : Ns - 1 - j; };
+  TC sp[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) sp[q] = Sm[q * sstride + (int64_t)height(j0 - 1) * A.Nmu];  // upwind source
+  // register ring of the next RING steps
+  TC re[RING], ra[RING], rb[RING], rsv[RING][NS], rx[RING][NS], rd[RING][NS];
+  auto load = [&](int u, int j) {
+    if (j < j1) {
+      const int k = height(j), i = interval(j);
+      if (sizeof(TC) == 8) {
+        const int64_t c = (int64_t)i * nray + r;
+        re[u] = (TC)A.ce[c];
+        ra[u] = (TC)A.ca[c];
+        rb[u] = (TC)A.cb[c];
+      } else {
+        re[u] = (TC)A.dtau32[i];   // Delta = dtau_i * r_ray; coefficients formed at use
+      }
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        rsv[u][q] = Sm[q * sstride + (int64_t)k * A.Nmu];
+        if (PHASE == 1 && MODE != KM_RHS) {
+          const int64_t o = q * plane + (int64_t)k * nray + r;
+          rx[u][q] = (TC)x[o];
+          if (MODE == KM_JACOBI) rd[u][q] = (TC)dinv[o];
+        }
+      }
+    }
+  };
+  auto step = [&](int u, int j) {
+    TC e, al, be;
+    if (sizeof(TC) == 8) {
+      e = re[u];
+      al = ra[u];
+      be = rb[u];
     } else {
-      y[o] = x[o];
-      y[qoff + o] = x[qoff + o];
+      float ef, af, bf;
+      coeffs32<FS>((float)re[u] * rs, ef, af, bf);
+      e = (TC)ef;
+      al = (TC)af;
+      be = (TC)bf;
+    }
+    if (PHASE == 0) E *= e;
+    const int64_t o = (int64_t)height(j) * nray + r;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const TC sk = rsv[u][q];
+      if (PHASE == 0) {
+        I[q] = fma(e, I[q], fma(al, sp[q], be * sk));
+      } else if (MODE == KM_LOCAL_LAMBDA) {
+        // y = (x + beta* S) - I = x - (e I_prev + alpha S_prev)
+        const TC t = fma(e, I[q], al * sp[q]);
+        if (active) y[q * plane + o] = (TV)(rx[u][q] - t);
+        I[q] = fma(be, sk, t);
+      } else {
+        I[q] = fma(e, I[q], fma(al, sp[q], be * sk));
+        if (active) {
+          if (MODE == KM_RHS) y[q * plane + o] = (TV)I[q];
+          else if (MODE == KM_JACOBI) y[q * plane + o] = (TV)(rx[u][q] * rd[u][q] - I[q]);
+          else y[q * plane + o] = (TV)(rx[u][q] - I[q]);
+        }
+      }
+      sp[q] = sk;
+    }
+  };
+#pragma unroll
+  for (int u = 0; u < RING; ++u) load(u, j0 + u);
+  int jb = j0;
+  // full rounds: every step of the round and every refill is in range, so the
+  // round is straight-line code the compiler can interleave across steps
+  for (; jb + 2 * RING <= j1; jb += RING) {
+#pragma unroll
+    for (int u = 0; u < RING; ++u) {
+      step(u, jb + u);
+      load(u, jb + u + RING);
     }
   }
-#pragma unroll 4
-  for (int j = 1; j < Ns; ++j) {
-    const int k = k0 + j * dk;
-    const int i = down ? k - 1 : k;
-    float e, al, be;
-    coeffs32<FS>(dtau[i] * rp, e, al, be);
-    const float sI = SI[(int64_t)k * Nmu], sQ = SQ[(int64_t)k * Nmu];
-    const int64_t o = (int64_t)k * nray + r;
-    if (MODE == KM_LOCAL_LAMBDA) {
-      const float tI = fmaf(e, II, al * sIp), tQ = fmaf(e, IQ, al * sQp);
-      y[o] = (TV)((float)x[o] - tI);
-      y[qoff + o] = (TV)((float)x[qoff + o] - tQ);
-      II = fmaf(be, sI, tI);
-      IQ = fmaf(be, sQ, tQ);
-    } else {
-      II = fmaf(e, II, fmaf(al, sIp, be * sI));
-      IQ = fmaf(e, IQ, fmaf(al, sQp, be * sQ));
-      float zI = (float)x[o], zQ = (float)x[qoff + o];
-      if (MODE == KM_JACOBI) {
-        zI *= (float)dinv[o];
-        zQ *= (float)dinv[qoff + o];
+  for (; jb < j1; jb += RING) {
+#pragma unroll
+    for (int u = 0; u < RING; ++u) {
+      if (jb + u < j1) {
+        step(u, jb + u);
+        load(u, jb + u + RING);
       }
-      y[o] = (TV)(zI - II);
-      y[qoff + o] = (TV)(zQ - IQ);
     }
-    sIp = sI;
-    sQp = sQ;
+  }
+}
+
+// grid: NSPLIT * ngroups CTAs (ray group g, and with NSPLIT = 2 the Stokes
+// parameter s = blockIdx.x % 2 -- with NSPLIT = 1 one lane carries I and Q);
+// block: 32 * ntile threads (warp t = depth tile t)
+template <typename TC, typename TV, int FS, int MODE, int NSPLIT, int RING, int MAXT>
+__global__ void __launch_bounds__(32 * MAXT) k_formal(const FormalArgs A) {
+  constexpr int NS = 2 / NSPLIT;   // Stokes parameters per lane
+  if (A.kstop && A.step >= *A.kstop) return;
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const int s0 = NSPLIT == 2 ? (blockIdx.x & 1) : 0;
+  const int g = NSPLIT == 2 ? (blockIdx.x >> 1) : blockIdx.x;
+  const bool down = g < A.ngd;
+  const int64_t base = down ? (int64_t)g * 32 : A.nd + (int64_t)(g - A.ngd) * 32;
+  const int64_t end = down ? A.nd : A.nray;
+  const bool active = base + lane < end;
+  const int64_t r = active ? base + lane : end - 1;
+  const int m = (int)(r / A.Nnu);
+  const int Ns = A.Ns;
+  const int T = A.ntile;
+  const int L = (Ns - 1 + T - 1) / T;   // steps per tile
+  const int j0 = 1 + t * L;
+  const int j1 = min(Ns, j0 + L);
+  __shared__ TC sh[1 + NS][MAXT][32];   // per tile: E and B, then the tile's inflow
+  TC I[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) I[q] = (MODE == KM_RHS && !down && s0 + q == 0) ? (TC)A.inflow_bottom : (TC)0;
+  if (T > 1) {
+    // phase A: tile maps (the last tile's map is not needed)
+    if (t < T - 1 && j0 < j1) {
+      TC E = 1, B[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) B[q] = 0;
+      sweep<TC, TV, FS, MODE, 0, NS, RING>(A, s0, down, r, m, active, j0, j1, B, E);
+      sh[0][t][lane] = E;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) sh[1 + q][t][lane] = B[q];
+    }
+    __syncthreads();
+    // phase B: inflow of every tile
+    if (t == 0) {
+      TC in[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) in[q] = I[q];
+      for (int u = 0; u < T; ++u) {
+        const bool has = u < T - 1 && 1 + u * L < Ns;
+        const TC E = has ? sh[0][u][lane] : (TC)1;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          const TC B = has ? sh[1 + q][u][lane] : (TC)0;
+          sh[1 + q][u][lane] = in[q];
+          if (has) in[q] = fma(E, in[q], B);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NS; ++q) I[q] = sh[1 + q][t][lane];
+  }
+  // entry node (tile 0): the inflow itself
+  if (t == 0 && active) {
+    const int k0 = down ? 0 : Ns - 1;
+    const TV* __restrict__ x = reinterpret_cast<const TV*>(A.x);
+    TV* __restrict__ y = reinterpret_cast<TV*>(A.y);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const int64_t o = (int64_t)(s0 + q) * Ns * A.nray + (int64_t)k0 * A.nray + r;
+      if (MODE == KM_RHS) y[o] = (TV)I[q];
+      else if (MODE == KM_JACOBI) y[o] = (TV)((TC)x[o] * (TC)A.dinv[o]);
+      else y[o] = x[o];
+    }
+  }
+  // phase C: sweep with the true inflow
+  if (j0 < j1) {
+    TC E = 1;
+    sweep<TC, TV, FS, MODE, 1, NS, RING>(A, s0, down, r, m, active, j0, j1, I, E);
   }
 }
 
@@ -404,13 +502,13 @@ inline int grid_for(int64_t n, int threads, int cap) {
 
 // --------------------------------------------------------------- host side
 void free_device(Problem* P) {
-  void* ptrs[] = {P->ce, P->ca, P->cb, P->wray, P->t201d, P->t202d, P->Bd, P->Minv, P->S, P->S2,
-                  P->dtau32, P->r32, P->wray32, P->t201f, P->t202f, P->S32, P->V, P->work, P->dinv,
-                  P->work32, P->partials, P->gm, P->bc, P->hist};
+  void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wI2, P->wQ2,  P->t201d, P->t202d,
+                  P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32,  P->wI2f, P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,      P->work, P->dinv,  P->work32,
+                  P->partials, P->gm,  P->bc,     P->hist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  P->ce = P->ca = P->cb = P->wray = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
-  P->dtau32 = P->r32 = P->wray32 = P->t201f = P->t202f = P->S32 = nullptr;
+  P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
+  P->dtau32 = P->r32 = P->wray32 = P->wI2f = P->wQ2f = P->t201f = P->t202f = P->S32 = nullptr;
   P->V = P->work = P->dinv = P->partials = P->hist = nullptr;
   P->work32 = nullptr;
   P->gm = nullptr;
@@ -424,79 +522,168 @@ static rt_status upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
   return RT_OK;
 }
 
+// Depth tiles per ray group.  FP64: the kernel is bound by FP64 issue, one
+// warp per SM sub-partition at a time; a tiled sweep costs 8 FP64 operations
+// per step (tile map, then the re-sweep) against 4 untiled, so choose the T
+// minimising waves x steps-per-tile x cost.  FP32: tiles are cheap, so aim at
+// about 16 warps per SM with tiles of at least 2*kRing steps.
+static int choose_tiles64(const Problem* P) {
+  const int64_t slots = 4LL * P->num_sms;
+  int best = 1;
+  double best_cost = 1e300;
+  for (int T = 1; T <= kMaxTiles64; ++T) {
+    const int L = (P->Ns - 1 + T - 1) / T;
+    if (T > 1 && L < 2 * kRing) break;
+    const int64_t warps = 2LL * P->ngroups * T;
+    const double waves = (double)((warps + slots - 1) / slots);
+    const double cost = waves * L * (T == 1 ? 4.0 : 8.0);
+    if (cost < best_cost * 0.97) {
+      best_cost = cost;
+      best = T;
+    }
+  }
+  return best;
+}
+
+static int choose_tiles32(const Problem* P) {
+  const int64_t want = (8LL * P->num_sms + P->ngroups - 1) / P->ngroups;
+  int T = want < 1 ? 1 : (int)(want > kMaxTiles ? kMaxTiles : want);
+  while (T > 1 && (P->Ns - 1) / T < 2 * kRing32) --T;
+  return T;
+}
+
 rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu, Nh = P->Nh;
-  std::vector<double> dtau(Ns - 1), absmu(Nh), wray((size_t)Nmu * Nnu);
+  const int64_t nray = P->nray;
+  P->nd = (int64_t)Nh * Nnu;
+  const int ngd = (int)((P->nd + 31) / 32);
+  P->ngroups = 2 * ngd;
+  P->ntile64 = choose_tiles64(P);
+  P->ntile32 = choose_tiles32(P);
+  std::vector<double> dtau(Ns - 1), rscale(nray), w0(nray), wnu(P->w_nu), wmu(Nmu);
+  for (int m = 0; m < Nmu; ++m) wmu[m] = 0.5 * P->w_mu[m];
   for (int i = 0; i + 1 < Ns; ++i) dtau[i] = P->tau[i + 1] - P->tau[i];
-  for (int mm = 0; mm < Nh; ++mm) absmu[mm] = P->mu[Nh + mm];
   for (int m = 0; m < Nmu; ++m)
-    for (int p = 0; p < Nnu; ++p) wray[(size_t)m * Nnu + p] = 0.5 * P->w_mu[m] * P->w_nu[p];
-  double *d_dtau = nullptr, *d_phat = nullptr, *d_absmu = nullptr;
+    for (int p = 0; p < Nnu; ++p) {
+      const size_t r = (size_t)m * Nnu + p;
+      rscale[r] = P->phi_hat[p] / fabs(P->mu[m]);
+      w0[r] = 0.5 * P->w_mu[m] * P->w_nu[p];
+    }
+  double *d_dtau = nullptr, *d_rs = nullptr;
   RT_TRY(upload(&d_dtau, dtau, st));
-  RT_TRY(upload(&d_phat, P->phi_hat, st));
-  RT_TRY(upload(&d_absmu, absmu, st));
-  RT_TRY(upload(&P->wray, wray, st));
+  RT_TRY(upload(&d_rs, rscale, st));
+  RT_TRY(upload(&P->wray, w0, st));
+  RT_TRY(upload(&P->wI2, wnu, st));   // spectral weights hat-w_p
+  RT_TRY(upload(&P->wQ2, wmu, st));   // angular weights hat-w_m
   RT_TRY(upload(&P->t201d, P->t201, st));
   RT_TRY(upload(&P->t202d, P->t202, st));
   RT_TRY(upload(&P->Bd, P->B, st));
-  const size_t nc = (size_t)(Ns - 1) * Nh * Nnu;
+  const size_t nc = (size_t)(Ns - 1) * nray;
   RT_TRY_CUDA(cudaMalloc((void**)&P->ce, nc * sizeof(double)));
   RT_TRY_CUDA(cudaMalloc((void**)&P->ca, nc * sizeof(double)));
   RT_TRY_CUDA(cudaMalloc((void**)&P->cb, nc * sizeof(double)));
   RT_TRY_CUDA(cudaMalloc((void**)&P->Minv, (size_t)Ns * 4 * sizeof(double)));
   RT_TRY_CUDA(cudaMalloc((void**)&P->S, (size_t)2 * Ns * Nmu * sizeof(double)));
   RT_TRY_CUDA(cudaMalloc((void**)&P->S2, (size_t)2 * Ns * Nmu * sizeof(double)));
-  k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_phat, d_absmu, Ns, Nh, Nnu,
-                                                                         P->fs, P->ce, P->ca, P->cb); RT_COUNT(1);
+  k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_rs, Ns, nray, P->fs, P->ce,
+                                                                         P->ca, P->cb); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   k_local_blocks<<<Ns, kMomThreads, 0, st>>>(P->cb, P->wray, P->t201d, P->t202d, Ns, Nmu, Nnu, P->xi, P->W2,
                                              P->Minv); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   // FP32 tables
-  std::vector<float> dtau32(Ns - 1), r32((size_t)Nh * Nnu), wray32(wray.size()), t201f(Nmu), t202f(Nmu);
+  std::vector<float> dtau32(Ns - 1), r32(nray), w032(nray), wI32(Nnu), wQ32(Nmu), t201f(Nmu), t202f(Nmu);
   for (int i = 0; i + 1 < Ns; ++i) dtau32[i] = (float)dtau[i];
-  for (int mm = 0; mm < Nh; ++mm)
-    for (int p = 0; p < Nnu; ++p) r32[(size_t)mm * Nnu + p] = (float)(P->phi_hat[p] / absmu[mm]);
-  for (size_t t = 0; t < wray.size(); ++t) wray32[t] = (float)wray[t];
+  for (int64_t r = 0; r < nray; ++r) {
+    r32[r] = (float)rscale[r];
+    w032[r] = (float)w0[r];
+  }
+  for (int p = 0; p < Nnu; ++p) wI32[p] = (float)wnu[p];
+  for (int m = 0; m < Nmu; ++m) wQ32[m] = (float)wmu[m];
   for (int m = 0; m < Nmu; ++m) { t201f[m] = (float)P->t201[m]; t202f[m] = (float)P->t202[m]; }
   RT_TRY(upload(&P->dtau32, dtau32, st));
   RT_TRY(upload(&P->r32, r32, st));
-  RT_TRY(upload(&P->wray32, wray32, st));
+  RT_TRY(upload(&P->wray32, w032, st));
+  RT_TRY(upload(&P->wI2f, wI32, st));
+  RT_TRY(upload(&P->wQ2f, wQ32, st));
   RT_TRY(upload(&P->t201f, t201f, st));
   RT_TRY(upload(&P->t202f, t202f, st));
   RT_TRY_CUDA(cudaMalloc((void**)&P->S32, (size_t)2 * Ns * Nmu * sizeof(float)));
   RT_TRY_CUDA(cudaStreamSynchronize(st));
   cudaFree(d_dtau);
-  cudaFree(d_phat);
-  cudaFree(d_absmu);
+  cudaFree(d_rs);
   return RT_OK;
 }
 
-static int formal_grid(const Problem* P) { return (int)((P->nray + kFormalThreads - 1) / kFormalThreads); }
+static FormalArgs formal_args(const Problem* P, const void* x, void* y, const void* S, int ntile, const int* kstop,
+                              int step) {
+  FormalArgs A;
+  A.x = x;
+  A.dinv = P->dinv;
+  A.ce = P->ce;
+  A.ca = P->ca;
+  A.cb = P->cb;
+  A.dtau32 = P->dtau32;
+  A.r32 = P->r32;
+  A.S = S;
+  A.y = y;
+  A.Ns = P->Ns;
+  A.Nmu = P->Nmu;
+  A.Nnu = P->Nnu;
+  A.nray = P->nray;
+  A.nd = P->nd;
+  A.ngd = P->ngroups / 2;
+  A.ntile = ntile;
+  A.inflow_bottom = P->B[P->Ns - 1];
+  A.kstop = kstop;
+  A.step = step;
+  return A;
+}
 
-rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st, const int* kstop,
-                     int step) {
+template <int MODE>
+static void launch_formal64(const Problem* P, const double* x, double* y, const double* S, cudaStream_t st,
+                            const int* kstop, int step) {
+  const FormalArgs A = formal_args(P, x, y, S, P->ntile64, kstop, step);
+  k_formal<double, double, 0, MODE, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A); RT_COUNT(1);
+}
+
+template <typename TV, int MODE>
+static void launch_formal32(const Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step) {
+  const FormalArgs A = formal_args(P, x, y, P->S32, P->ntile32, kstop, step);
+  const int g = P->ngroups, b = 32 * P->ntile32;
+  switch (P->fs) {
+    case RT_FS_DELO_LINEAR:
+      k_formal<float, TV, RT_FS_DELO_LINEAR, MODE, 1, kRing32, kMaxTiles><<<g, b, 0, st>>>(A); RT_COUNT(1);
+      break;
+    case RT_FS_IMPLICIT_EULER:
+      k_formal<float, TV, RT_FS_IMPLICIT_EULER, MODE, 1, kRing32, kMaxTiles><<<g, b, 0, st>>>(A); RT_COUNT(1);
+      break;
+    default:
+      k_formal<float, TV, RT_FS_TRAPEZOIDAL, MODE, 1, kRing32, kMaxTiles><<<g, b, 0, st>>>(A); RT_COUNT(1);
+  }
+}
+
+rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st, const int* kstop, int step) {
   const double xiW2 = P->xi * P->W2;
-  const int g = formal_grid(P);
   const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu;
   switch (mode) {
     case AM_PLAIN:
-      k_moments<double, double, KM_PLAIN><<<Ns, kMomThreads, 0, st>>>(
-          x, nullptr, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu, Nnu, P->xi, xiW2, P->S, kstop, step); RT_COUNT(1);
-      k_formal64<KM_PLAIN><<<g, kFormalThreads, 0, st>>>(x, nullptr, P->ce, P->ca, P->cb, P->S, y, Ns, Nmu, Nnu, 0,
-                                                         0.0, kstop, step); RT_COUNT(1);
+      k_moments<double, double, KM_PLAIN><<<Ns, kMomThreads, 0, st>>>(x, nullptr, P->wI2, P->wQ2, P->t201d,
+                                                                       P->t202d, nullptr, Ns, Nmu, Nnu, P->xi, xiW2,
+                                                                       P->S, kstop, step); RT_COUNT(1);
+      launch_formal64<KM_PLAIN>(P, x, y, P->S, st, kstop, step);
       break;
     case AM_JACOBI:
-      k_moments<double, double, KM_JACOBI><<<Ns, kMomThreads, 0, st>>>(
-          x, P->dinv, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu, Nnu, P->xi, xiW2, P->S, kstop, step); RT_COUNT(1);
-      k_formal64<KM_JACOBI><<<g, kFormalThreads, 0, st>>>(x, P->dinv, P->ce, P->ca, P->cb, P->S, y, Ns, Nmu, Nnu, 0,
-                                                          0.0, kstop, step); RT_COUNT(1);
+      k_moments<double, double, KM_JACOBI><<<Ns, kMomThreads, 0, st>>>(x, P->dinv, P->wI2, P->wQ2,
+                                                                        P->t201d, P->t202d, nullptr, Ns, Nmu, Nnu,
+                                                                        P->xi, xiW2, P->S, kstop, step); RT_COUNT(1);
+      launch_formal64<KM_JACOBI>(P, x, y, P->S, st, kstop, step);
       break;
     case AM_LOCAL_LAMBDA:
       k_moments<double, double, KM_LOCAL_LAMBDA><<<Ns, kMomThreads, 0, st>>>(
-          x, nullptr, P->wray, P->t201d, P->t202d, P->Minv, Ns, Nmu, Nnu, P->xi, xiW2, P->S, kstop, step); RT_COUNT(1);
-      k_formal64<KM_LOCAL_LAMBDA><<<g, kFormalThreads, 0, st>>>(x, nullptr, P->ce, P->ca, P->cb, P->S, y, Ns, Nmu,
-                                                                Nnu, 0, 0.0, kstop, step); RT_COUNT(1);
+          x, nullptr, P->wI2, P->wQ2, P->t201d, P->t202d, P->Minv, Ns, Nmu, Nnu, P->xi, xiW2, P->S, kstop,
+          step); RT_COUNT(1);
+      launch_formal64<KM_LOCAL_LAMBDA>(P, x, y, P->S, st, kstop, step);
       break;
     default:
       set_error("bad apply mode");
@@ -506,45 +693,27 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
   return RT_OK;
 }
 
-template <typename TV, int MODE>
-static void launch_formal32(Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step) {
-  const int g = formal_grid(P);
-  switch (P->fs) {
-    case RT_FS_DELO_LINEAR:
-      k_formal32<TV, RT_FS_DELO_LINEAR, MODE><<<g, kFormalThreads, 0, st>>>(
-          x, P->dinv, P->dtau32, P->r32, P->S32, y, P->Ns, P->Nmu, P->Nnu, kstop, step); RT_COUNT(1);
-      break;
-    case RT_FS_IMPLICIT_EULER:
-      k_formal32<TV, RT_FS_IMPLICIT_EULER, MODE><<<g, kFormalThreads, 0, st>>>(
-          x, P->dinv, P->dtau32, P->r32, P->S32, y, P->Ns, P->Nmu, P->Nnu, kstop, step); RT_COUNT(1);
-      break;
-    default:
-      k_formal32<TV, RT_FS_TRAPEZOIDAL, MODE><<<g, kFormalThreads, 0, st>>>(
-          x, P->dinv, P->dtau32, P->r32, P->S32, y, P->Ns, P->Nmu, P->Nnu, kstop, step); RT_COUNT(1);
-  }
-}
-
 template <typename TV>
-static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStream_t st, const int* kstop,
-                              int step) {
+static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStream_t st, const int* kstop, int step) {
   const float xi = (float)P->xi, xiW2 = (float)(P->xi * P->W2);
   const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu;
   switch (mode) {
     case AM_PLAIN:
-      k_moments<TV, float, KM_PLAIN><<<Ns, kMomThreads, 0, st>>>(x, nullptr, P->wray32, P->t201f, P->t202f, nullptr,
-                                                                  Ns, Nmu, Nnu, xi, xiW2, P->S32, kstop, step); RT_COUNT(1);
+      k_moments<TV, float, KM_PLAIN><<<Ns, kMomThreads, 0, st>>>(x, nullptr, P->wI2f, P->wQ2f, P->t201f,
+                                                                  P->t202f, nullptr, Ns, Nmu, Nnu, xi, xiW2, P->S32,
+                                                                  kstop, step); RT_COUNT(1);
       launch_formal32<TV, KM_PLAIN>(P, x, y, st, kstop, step);
       break;
     case AM_JACOBI:
-      k_moments<TV, float, KM_JACOBI><<<Ns, kMomThreads, 0, st>>>(x, P->dinv, P->wray32, P->t201f, P->t202f,
-                                                                   nullptr, Ns, Nmu, Nnu, xi, xiW2, P->S32, kstop,
-                                                                   step); RT_COUNT(1);
+      k_moments<TV, float, KM_JACOBI><<<Ns, kMomThreads, 0, st>>>(x, P->dinv, P->wI2f, P->wQ2f, P->t201f,
+                                                                   P->t202f, nullptr, Ns, Nmu, Nnu, xi, xiW2, P->S32,
+                                                                   kstop, step); RT_COUNT(1);
       launch_formal32<TV, KM_JACOBI>(P, x, y, st, kstop, step);
       break;
     case AM_LOCAL_LAMBDA:
-      k_moments<TV, float, KM_LOCAL_LAMBDA><<<Ns, kMomThreads, 0, st>>>(x, nullptr, P->wray32, P->t201f, P->t202f,
-                                                                         P->Minv, Ns, Nmu, Nnu, xi, xiW2, P->S32,
-                                                                         kstop, step); RT_COUNT(1);
+      k_moments<TV, float, KM_LOCAL_LAMBDA><<<Ns, kMomThreads, 0, st>>>(x, nullptr, P->wI2f, P->wQ2f,
+                                                                         P->t201f, P->t202f, P->Minv, Ns, Nmu, Nnu,
+                                                                         xi, xiW2, P->S32, kstop, step); RT_COUNT(1);
       launch_formal32<TV, KM_LOCAL_LAMBDA>(P, x, y, st, kstop, step);
       break;
     default:
@@ -574,32 +743,17 @@ rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st) {
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st) {
   k_rhs_source<<<grid_for((int64_t)P->Ns * P->Nmu, 256, 4 * P->num_sms), 256, 0, st>>>(P->Bd, P->Ns, P->Nmu, P->eps,
                                                                                       P->S2); RT_COUNT(1);
-  k_formal64<KM_PLAIN><<<formal_grid(P), kFormalThreads, 0, st>>>(nullptr, nullptr, P->ce, P->ca, P->cb, P->S2, b,
-                                                                  P->Ns, P->Nmu, P->Nnu, 1, P->B[P->Ns - 1],
-                                                                  nullptr, 0); RT_COUNT(1);
+  launch_formal64<KM_RHS>(P, nullptr, b, P->S2, st, nullptr, 0);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
 
 // z = P^{-1} v = v + beta* T M^{-1} J v
-namespace {
-__global__ void k_add_local(const double* __restrict__ v, const double* __restrict__ cb,
-                            const double* __restrict__ S, int Ns, int Nmu, int Nnu, double* __restrict__ z) {
-  const int Nh = Nmu / 2;
-  const int64_t nray = (int64_t)Nmu * Nnu, N = 2 * (int64_t)Ns * nray;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t % nray, sk = t / nray;
-    const int k = (int)(sk % Ns), s = (int)(sk / Ns);
-    const int m = (int)(r / Nnu), p = (int)(r % Nnu);
-    z[t] = v[t] + beta_star(cb, k, m, p, Ns, Nh, Nnu) * S[((int64_t)s * Ns + k) * Nmu + m];
-  }
-}
-}  // namespace
-
 rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st) {
   const double xiW2 = P->xi * P->W2;
   k_moments<double, double, KM_LOCAL_LAMBDA><<<P->Ns, kMomThreads, 0, st>>>(
-      v, nullptr, P->wray, P->t201d, P->t202d, P->Minv, P->Ns, P->Nmu, P->Nnu, P->xi, xiW2, P->S2, nullptr, 0); RT_COUNT(1);
+      v, nullptr, P->wI2, P->wQ2, P->t201d, P->t202d, P->Minv, P->Ns, P->Nmu, P->Nnu, P->xi, xiW2, P->S2,
+      nullptr, 0); RT_COUNT(1);
   k_add_local<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(v, P->cb, P->S2, P->Ns, P->Nmu, P->Nnu, z); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
