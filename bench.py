@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "local_lambda", "none"])
     ap.add_argument("--apply-reps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-deep", action="store_true")
     return ap.parse_args()
 
 
@@ -106,10 +107,10 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- CPU oracle
-def cpu_baseline(precond: str, budget_s: float = 20.0):
+def cpu_baseline(precond: str, cycles: int = 5, budget_s: float = 20.0):
     """The oracle as it stands, single-threaded, on a bounded sample of the
-    same workload: one GMRES(30) restart cycle (30 applies + MGS), in a child
-    process with BLAS pinned to one thread."""
+    same workload: `cycles` GMRES(30) restart cycles (30 applies + MGS each),
+    in a child process with BLAS pinned to one thread."""
     code = f"""
 import json, os, sys, time
 sys.path.insert(0, {ROOT!r})
@@ -123,7 +124,7 @@ b = tr.rhs_I()
 d = tr.jacobi_I()
 Minv = {{"jacobi": lambda v: v / d, "local_lambda": tr.local_lambda_I_inverse, "none": None}}[{precond!r}]
 t0 = time.perf_counter()
-x, info = K.gmres(tr.apply_I, b, M_inv=Minv, restart=30, maxit=30, tol=1e-30)
+x, info = K.gmres(tr.apply_I, b, M_inv=Minv, restart=30, maxit={30 * cycles}, tol=1e-30)
 dt = time.perf_counter() - t0
 print(json.dumps({{"applies": info.applies, "seconds": dt}}))
 """
@@ -134,7 +135,8 @@ print(json.dumps({{"applies": info.applies, "seconds": dt}}))
         return {"error": r.stderr[-400:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": d["applies"] / d["seconds"], "unit": "applies/s", "cores": 1, "kind": "oracle",
-            "sample": f"one GMRES(30) restart cycle of the slab300 solve ({d['applies']} applies, "
+            "seconds": d["seconds"],
+            "sample": f"{cycles} GMRES(30) restart cycle(s) of the slab300 Jacobi solve ({d['applies']} applies, "
                       f"{d['seconds']:.1f} s), numpy FP64, BLAS pinned to 1 thread"}
 
 
@@ -142,21 +144,22 @@ def reference_main(args, rank, world):
     """--impl reference: the oracle timed on the host cores on the same workload."""
     if rank != 0:
         return
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
-    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.precond, cycles=1)
+    vals, secs = [], []
     cb = None
     for _ in range(args.steps):
-        cb = cpu_baseline(args.precond)
+        cb = cpu_baseline(args.precond, cycles=1)
         if "value" in cb:
             vals.append(cb["value"])
+            secs.append(cb["seconds"])
     if not vals:
         print(json.dumps({"impl": "reference", "unavailable": cb.get("error", "oracle failed")}))
         return
     v = statistics.median(vals)
     cb["value"] = v
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "applies/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 30 / v,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.median(secs),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD, "precond": args.precond},
            "cpu_baseline": cb,
@@ -246,32 +249,66 @@ def main():
     applies_all, solves_all = (float(v) for v in cnt.tolist())
     value = applies_all / (ms_max / 1000.0)
 
-    # ---- standalone operator apply (the roofline unit): y = x - Lambda T J x
-    xin = torch.randn(N, dtype=torch.float64, device="cuda")
-    yout = torch.empty_like(xin)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(5):
-        P.apply(xin, out=yout)
-    torch.cuda.synchronize()
-    evs = []
-    for _ in range(args.apply_reps):
-        flush.zero_()   # 256 MB write: evicts the 129 MB L2 between launches
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        P.apply(xin, out=yout)
-        a1.record(stream)
-        evs.append((a0, a1))
-    torch.cuda.synchronize()
-    apply_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in evs)
-    alg_bytes = 2 * N * 8
-    apply_gbs = alg_bytes / (apply_ms * 1e-3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps, flush_l2):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(reps):
+            if flush_l2:
+                flush.zero_()   # 256 MB write: evicts the 129 MB L2 before the launch
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            fn()
+            a1.record(stream)
+            evs.append((a0, a1))
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b_) for a, b_ in evs)
+
+    # ---- dominant kernel of the step: the MGS Arnoldi orthogonalisation
+    # (k_dot + (j+1) k_mgs + k_norm_out launches of rt_arnoldi_mgs), at the
+    # mean Arnoldi index j = 15 of a GMRES(30) cycle; the 17-vector basis
+    # (264 MB) is larger than L2
+    jm = 15
+    V = torch.randn((jm + 2) * N, dtype=torch.float64, device="cuda")
+    w = torch.randn(N, dtype=torch.float64, device="cuda")
+    hbuf = torch.empty(jm + 2, dtype=torch.float64, device="cuda")
+    mgs_ms = timed(lambda: P.arnoldi_mgs(V, jm, w, hbuf), 20, False)
+    mgs_bytes = (4 * jm + 7) * N * 8
+    mgs_gbs = mgs_bytes / (mgs_ms * 1e-3) / 1e9
+    del V
+
+    # ---- the operator apply y = x - Lambda T J x, FP64 and FP32, L2 flushed
+    xin = torch.randn(N, dtype=torch.float64, device="cuda")
+    yout = torch.empty_like(xin)
+    apply_ms = timed(lambda: P.apply(xin, out=yout), args.apply_reps, True)
+    x32 = xin.float()
+    y32 = torch.empty_like(x32)
+    apply32_ms = timed(lambda: P.apply_f32(x32, out=y32), args.apply_reps, True)
+    apply_gbs = 2 * N * 8 / (apply_ms * 1e-3) / 1e9
+    apply32_gbs = 2 * N * 4 / (apply32_ms * 1e-3) / 1e9
+    # the deep atmosphere (N_s=2000, N_mu=64, N_nu=201: 51.5M unknowns, 206 MB
+    # per FP32 vector), the HBM-bound case of the FP32 operator
+    deep = None
+    if not args.no_deep:
+        Pd = Problem(W.sweep(2000))
+        xd = torch.randn(Pd.N, dtype=torch.float32, device="cuda")
+        yd = torch.empty_like(xd)
+        deep_ms = timed(lambda: Pd.apply_f32(xd, out=yd), 20, True)
+        deep = {"workload": "sweep: Ns=2000 Nmu=64 Nnu=201 (51,456,000 unknowns), FP32 operator",
+                "ms": deep_ms, "alg_gbs": 2 * Pd.N * 4 / (deep_ms * 1e-3) / 1e9}
+        deep["frac_of_hbm"] = deep["alg_gbs"] / hbm_peak
+        del xd, yd
+        Pd.close()
 
     # ---- end to end through the public API with host buffers
     b_host = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -315,12 +352,15 @@ def main():
                              "with a 256 MB write between launches"},
             "solves_per_s": solves_all / (ms_max / 1000.0),
             "iters_per_solve": info.iters, "applies_per_solve": info.applies,
-            "apply": {"ms": apply_ms, "applies_per_s": 1000.0 / apply_ms, "alg_gbs": apply_gbs},
+            "apply_fp64": {"ms": apply_ms, "applies_per_s": 1000.0 / apply_ms, "alg_gbs": apply_gbs},
+            "apply_fp32": {"ms": apply32_ms, "applies_per_s": 1000.0 / apply32_ms, "alg_gbs": apply32_gbs},
+            "apply_fp32_deep": deep,
             "local_lambda_solve": {"iters": li.iters, "ms": ll_solve_ms, "solves_per_s": 1000.0 / ll_solve_ms},
-            "roofline": {"kernel": "operator apply (k_moments + k_formal64)", "bound": "hbm",
-                         "achieved": apply_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": apply_gbs / hbm_peak, "traffic": None,
-                         "note": "of measured hbm_gbs; algorithmic bytes 2*N*8 per apply"},
+            "roofline": {"kernel": "MGS Arnoldi orthogonalisation (k_dot + 16 x k_mgs + k_norm_out, j=15)",
+                         "bound": "hbm", "achieved": mgs_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": mgs_gbs / hbm_peak, "traffic": None,
+                         "note": "of measured hbm_gbs; algorithmic bytes (4j+7)*N*8 per step, "
+                                 "burst peak (kernel timed alone)"},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": "applies/s", "h2d_bytes_per_step": N * 8,
                     "d2h_bytes_per_step": N * 8},

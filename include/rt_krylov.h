@@ -129,6 +129,15 @@ rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream);
    carried to the I-form by the Woodbury identity.  v_dev, z_dev: N doubles. */
 rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double* z_dev, void* stream);
 
+/* One Arnoldi orthogonalisation step by modified Gram-Schmidt (Sect. 2.1:
+   the O(nN) nested loop of GMRES), on the problem's vector length N:
+     for i = 0..j: h_i = <w, v_i>; w -= h_i v_i;   h_{j+1} = ||w||;  v_{j+1} = w / h_{j+1}
+   V_dev: j+2 vectors of N doubles, contiguous (v_i at V_dev + i*N), v_0..v_j
+   orthonormal; v_{j+1} is written.  w_dev: N doubles, overwritten.
+   h_dev: j+2 doubles (device), receives h_0..h_{j+1}.  0 <= j < 64.
+   Reductions are deterministic (fixed block partials, fixed summation order). */
+rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* h_dev, void* stream);
+
 /* ---------------------------------------------------------------- solvers */
 enum { RT_PREC_NONE = 0, RT_PREC_JACOBI = 1, RT_PREC_LOCAL_LAMBDA = 2 };
 enum { RT_X0_ZERO = 0, RT_X0_USER = 1 };

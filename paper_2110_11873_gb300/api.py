@@ -147,6 +147,18 @@ class Problem:
                 "rt_precond_local_lambda")
         return z
 
+    def arnoldi_mgs(self, V: torch.Tensor, j: int, w: torch.Tensor, h: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+        """One MGS Arnoldi step: orthogonalise w against V[0..j], write
+        V[j+1] = w/||w||; returns h (j+2 values)."""
+        if V.dtype != torch.float64 or not V.is_contiguous() or V.numel() < (j + 2) * self.N:
+            raise ValueError("V must be a contiguous float64 tensor of at least (j+2)*N values")
+        w = self._vec(w)
+        h = torch.empty(j + 2, dtype=torch.float64, device=self.device) if h is None else h
+        N.check(self.lib.rt_arnoldi_mgs(self.handle, C.c_void_p(V.data_ptr()), int(j), C.c_void_p(w.data_ptr()),
+                                        C.c_void_p(h.data_ptr()), _stream_handle(stream)), "rt_arnoldi_mgs")
+        return h
+
     # --------------------------------------------------------------- solvers
     def solve(self, b: torch.Tensor, method: str = "gmres", x: Optional[torch.Tensor] = None, *,
               restart: int = 30, maxit: int = 10000, precond: str = "jacobi", rtol: float = 1e-8,

@@ -196,6 +196,17 @@ __global__ void __launch_bounds__(kVecThreads) k_normalize(const double* __restr
   for (; i < N; i += stride) v[i] = w[i] * inv;
 }
 
+// v = w / ||w|| with ||w|| from the partials, written to *hout
+__global__ void __launch_bounds__(kVecThreads) k_norm_out(const double* __restrict__ w, double* __restrict__ v,
+                                                          int64_t N, const double* __restrict__ part_in,
+                                                          double* __restrict__ hout) {
+  const double hn = sqrt(block_partials(part_in, gridDim.x));
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hout = hn;
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * inv;
+}
+
 // Givens rotations on column j of the Hessenberg matrix (one thread)
 __global__ void k_givens(GmresDev* gm, int m, int j, double* hist, int hist_cap) {
   if (j >= gm->kstop) return;
@@ -1054,6 +1065,32 @@ void rt_solver_opts_default(rt_solver_opts* o) {
   o->rtol = 1e-8;
   o->inner_rtol = 1e-4;
   o->max_refine = 20;
+}
+
+rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* h_dev, void* stream) {
+  clear_error();
+  if (!prob || !V_dev || !w_dev || !h_dev) { set_error("prob, V_dev, w_dev and h_dev are required"); return RT_EINVAL; }
+  if (j < 0 || j >= kMaxRestart) { set_error("j must be in [0,%d)", kMaxRestart); return RT_EINVAL; }
+  Problem* P = &prob->P;
+  cudaStream_t st = as_stream(stream);
+  RT_TRY(ensure_workspace(P, 1, st));
+  const int G = P->vec_grid;
+  const int64_t N = P->N;
+  // the kernels gate on kstop: point it at a device int that never stops them
+  int* always = reinterpret_cast<int*>(&P->gm->kstop);
+  const int big = 1 << 30;
+  RT_TRY_CUDA(cudaMemcpyAsync(always, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+  int pb = 0;
+  k_dot<<<G, kVecThreads, 0, st>>>(w_dev, V_dev, N, partb(P, pb), nullptr, 0, nullptr); RT_COUNT(1);
+  for (int i = 0; i <= j; ++i) {
+    const double* vprev = V_dev + (size_t)i * N;
+    const double* vnext = (i < j) ? V_dev + (size_t)(i + 1) * N : nullptr;
+    k_mgs<<<G, kVecThreads, 0, st>>>(w_dev, vprev, vnext, N, partb(P, pb), partb(P, pb ^ 1), h_dev + i, always, 0); RT_COUNT(1);
+    pb ^= 1;
+  }
+  k_norm_out<<<G, kVecThreads, 0, st>>>(w_dev, V_dev + (size_t)(j + 1) * N, N, partb(P, pb), h_dev + j + 1); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
 }
 
 rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,

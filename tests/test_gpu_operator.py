@@ -131,3 +131,29 @@ def test_deep_sweep_atmosphere_ns2000():
     assert_close_scaled(to_host(P.apply(to_dev(x))), tr.apply_I(x), TOL64, "sweep2000")
     y32 = to_host(P.apply_f32(to_dev(x, torch.float32)))
     assert_close_scaled(y32, tr.apply_I(x.astype(np.float32).astype(np.float64)), TOL32, "sweep2000 fp32")
+
+
+def test_arnoldi_mgs_step_against_plain_mgs():
+    """rt_arnoldi_mgs: h_i = <w, v_i>, w -= h_i v_i (i = 0..j), h_{j+1} = ||w||,
+    v_{j+1} = w / h_{j+1}, compared with the same loop in numpy."""
+    at = W.slab(37, 6, 33, 1e-4, 1e6, 6.0)
+    P = problem(at)
+    N = P.N
+    j = 5
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((N, j + 1)))
+    w0 = rng.standard_normal(N)
+    V = np.zeros((j + 2) * N)
+    V[: (j + 1) * N] = Q.T.reshape(-1)
+    Vd = to_dev(V)
+    wd = to_dev(w0)
+    h = to_host(P.arnoldi_mgs(Vd, j, wd))
+    w = w0.copy()
+    href = np.zeros(j + 2)
+    for i in range(j + 1):
+        href[i] = np.dot(w, Q[:, i])
+        w = w - href[i] * Q[:, i]
+    href[j + 1] = np.linalg.norm(w)
+    np.testing.assert_allclose(h, href, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(to_host(Vd)[(j + 1) * N:], w / href[j + 1], rtol=1e-11, atol=1e-14)
+    np.testing.assert_allclose(to_host(wd), w, rtol=1e-11, atol=1e-14)
