@@ -138,6 +138,29 @@ rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double*
    Reductions are deterministic (fixed block partials, fixed summation order). */
 rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* h_dev, void* stream);
 
+/* The same MGS Arnoldi step for callers that cannot allocate device memory
+   (code running while a stream is captured into a CUDA graph, processes whose
+   device memory belongs to another allocator that must account for every
+   byte, service loops that cannot afford the device synchronisation an
+   allocation may cause).  The paper has no counterpart: this is a
+   deployment variant of rt_arnoldi_mgs.
+   It needs no rt_problem: N is the vector length, V_dev holds j+2 vectors of
+   N doubles (v_0..v_j orthonormal; v_{j+1} is written), w_dev is overwritten,
+   h_dev receives j+2 doubles; all caller-owned device memory.
+   It calls no cudaMalloc, cudaFree or allocating library routine.  Its only
+   scratch, the per-block partial sums of the reductions, is a static device
+   array of 2 x 1024 doubles (16 KB) inside the library, which every GPU that
+   loads the library keeps until the process exits.  The first call on a
+   device looks up that array's device address (cudaGetSymbolAddress) with
+   the device current; make that first call before any stream capture.
+   All calls share the one array: calls whose work overlaps on the GPU (two
+   streams, or two host threads) race and must not be issued.
+   Sizes beyond the limits return RT_EINVAL with a message:
+   1 <= N <= RT_ARNOLDI_STATIC_MAX_N, 0 <= j < RT_ARNOLDI_STATIC_MAX_J. */
+#define RT_ARNOLDI_STATIC_MAX_N ((int64_t)1 << 40)
+#define RT_ARNOLDI_STATIC_MAX_J 64
+rt_status rt_arnoldi_mgs_static(double* V_dev, int64_t N, int32_t j, double* w_dev, double* h_dev, void* stream);
+
 /* ---------------------------------------------------------------- solvers */
 enum { RT_PREC_NONE = 0, RT_PREC_JACOBI = 1, RT_PREC_LOCAL_LAMBDA = 2 };
 enum { RT_X0_ZERO = 0, RT_X0_USER = 1 };

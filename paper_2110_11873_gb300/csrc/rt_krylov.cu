@@ -1118,3 +1118,85 @@ rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// MGS Arnoldi step without device allocation.
+//
+// For callers that cannot call cudaMalloc: code running while a CUDA stream is
+// being captured into a graph, processes whose device memory is entirely owned
+// by another allocator that must account for every byte, and service loops
+// where the device-wide synchronisation an allocation may cause is not
+// acceptable.  The only scratch this step needs -- one deterministic partial
+// sum per block for each reduction -- lives in the file-scope array below,
+// which every GPU that loads the library keeps until the process exits.
+namespace rt {
+namespace {
+constexpr int kStaticPartials = 1024;   // partial sums per reduction (blocks of the grid)
+static __device__ __align__(256) double g_static_scratch[2 * kStaticPartials];
+static __device__ int g_static_never_stop = 1 << 30;   // gate value for k_mgs: never skip
+
+struct StaticScratch {
+  double* scratch = nullptr;
+  int* gate = nullptr;
+  int grid_cap = 0;
+};
+std::mutex g_static_mu;
+std::map<int, StaticScratch> g_static_by_device;
+
+// Device addresses of the static scratch on the current device; looked up
+// once per device (cudaGetSymbolAddress) and cached.
+rt_status static_scratch_for_current_device(StaticScratch* out) {
+  int dev = 0;
+  RT_TRY_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  auto it = g_static_by_device.find(dev);
+  if (it == g_static_by_device.end()) {
+    StaticScratch s;
+    RT_TRY_CUDA(cudaGetSymbolAddress((void**)&s.scratch, g_static_scratch));
+    RT_TRY_CUDA(cudaGetSymbolAddress((void**)&s.gate, g_static_never_stop));
+    int sms = 0;
+    RT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    s.grid_cap = 4 * sms < kStaticPartials ? 4 * sms : kStaticPartials;
+    it = g_static_by_device.emplace(dev, s).first;
+  }
+  *out = it->second;
+  return RT_OK;
+}
+}  // namespace
+}  // namespace rt
+
+extern "C" {
+
+rt_status rt_arnoldi_mgs_static(double* V_dev, int64_t N, int32_t j, double* w_dev, double* h_dev, void* stream) {
+  clear_error();
+  if (!V_dev || !w_dev || !h_dev) { set_error("V_dev, w_dev and h_dev are required"); return RT_EINVAL; }
+  if (N < 1 || N > RT_ARNOLDI_STATIC_MAX_N) {
+    set_error("N must be in [1, %lld] (got %lld)", (long long)RT_ARNOLDI_STATIC_MAX_N, (long long)N);
+    return RT_EINVAL;
+  }
+  if (j < 0 || j >= RT_ARNOLDI_STATIC_MAX_J) {
+    set_error("j must be in [0, %d) (got %d)", RT_ARNOLDI_STATIC_MAX_J, (int)j);
+    return RT_EINVAL;
+  }
+  StaticScratch sc;
+  RT_TRY(static_scratch_for_current_device(&sc));
+  cudaStream_t st = as_stream(stream);
+  int64_t g = (N + 2 * kVecThreads - 1) / (2 * kVecThreads);
+  const int G = (int)(g < 1 ? 1 : (g > sc.grid_cap ? sc.grid_cap : g));
+  double* part[2] = {sc.scratch, sc.scratch + kStaticPartials};
+  // every partial a kernel reads was written earlier in this call by the
+  // kernel before it, for the same grid size: nothing has to start at zero
+  int pb = 0;
+  k_dot<<<G, kVecThreads, 0, st>>>(w_dev, V_dev, N, part[pb], nullptr, 0, nullptr); RT_COUNT(1);
+  for (int i = 0; i <= j; ++i) {
+    const double* vprev = V_dev + (size_t)i * N;
+    const double* vnext = (i < j) ? V_dev + (size_t)(i + 1) * N : nullptr;
+    k_mgs<<<G, kVecThreads, 0, st>>>(w_dev, vprev, vnext, N, part[pb], part[pb ^ 1], h_dev + i, sc.gate, 0); RT_COUNT(1);
+    pb ^= 1;
+  }
+  k_norm_out<<<G, kVecThreads, 0, st>>>(w_dev, V_dev + (size_t)(j + 1) * N, N, part[pb], h_dev + j + 1); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+}  // extern "C"
