@@ -208,6 +208,65 @@ rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const 
 rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                        double* x_dev, rt_solve_info* info, void* stream);
 
+/* ----------------------------------------------------- batching and serving
+   A server keeps many atmospheres resident on the device and solves them
+   together by restarted GMRES(m) in lock-step: every phase of an Arnoldi step
+   is one launch over all resident instances (the instances need not have the
+   same sizes), and the whole restart cycle is one CUDA graph.  A worker
+   thread admits submitted requests while a slot is free and the memory
+   budget can hold the instance (tables, Krylov basis and work vectors in one
+   device arena allocated at creation), runs cycles, and retires finished
+   instances -- copying x to host memory and returning their memory -- before
+   the next cycle, so requests that arrive while others are on the device join
+   at the next cycle boundary (continuous batching).  Each instance's
+   arithmetic depends only on its own data (deterministic reductions), so a
+   result is the same whatever else is in the batch.  The problem is the one
+   of rt_problem_create; the right-hand side is b = Lambda T c + t (rt_rhs)
+   and the initial guess 0; the stopping rule is ||b - A x|| / ||b|| < rtol
+   with the FP64 operator. */
+typedef struct {
+  int64_t mem_budget_bytes;  /* device arena for resident instances, allocated at creation */
+  int32_t max_slots;         /* instances resident at once, 1..4096 */
+  int32_t restart;           /* GMRES restart length for all instances, 1..64 */
+  int32_t precond;           /* RT_PREC_* for all instances */
+  int32_t precision;         /* RT_PRECISION_FP64, or RT_PRECISION_FP32_REFINE: FP32 operator in the
+                                Arnoldi steps, FP64 true residual at every restart (each restart is
+                                an iterative-refinement step) */
+} rt_server_opts;
+
+typedef struct rt_server rt_server;
+
+/* defaults: 8 GiB budget, 64 slots, restart 30, local-Lambda, FP64 */
+void rt_server_opts_default(rt_server_opts* opts);
+/* Create a server on the current device (the device stays the worker's). */
+rt_status rt_server_create(const rt_server_opts* opts, rt_server** out);
+/* Queue one solve.  desc as for rt_problem_create (arrays copied; Ns <= 4096);
+   opts may be NULL (rtol 1e-8, maxit 10000) -- only rtol and maxit are read.
+   *ticket identifies the request for rt_poll. */
+rt_status rt_batch_submit(rt_server* srv, const rt_problem_desc* desc, const rt_solver_opts* opts,
+                          uint64_t* ticket);
+/* RT_EPENDING while the request is queued or resident; afterwards its final
+   status (RT_OK, RT_ENOTCONV, RT_EBREAKDOWN, RT_ENUMERIC, RT_ENOMEM when the
+   instance cannot fit the budget even alone), with info filled (t_total_ms:
+   submission to completion) and, when x_host is not NULL, the N-vector
+   solution copied there.  A finished request is released by the poll that
+   reports it. */
+rt_status rt_poll(rt_server* srv, uint64_t ticket, rt_solve_info* info, double* x_host);
+typedef struct {
+  int32_t resident;          /* instances on the device now */
+  int32_t queued;            /* submitted, not yet admitted */
+  int64_t arena_in_use;      /* bytes of the budget held by resident instances */
+  int64_t arena_largest_free;/* largest contiguous free block of the budget */
+  int64_t cycles;            /* restart cycles run so far */
+  int64_t completed;         /* requests finished so far */
+} rt_server_stats;
+
+/* Snapshot of the server's state (for monitoring). */
+rt_status rt_server_stats_get(rt_server* srv, rt_server_stats* out);
+
+/* Stop the worker (queued requests are dropped) and free everything. */
+rt_status rt_server_destroy(rt_server* srv);
+
 /* Thread-local message describing the last error returned on this thread. */
 const char* rt_last_error(void);
 

@@ -51,6 +51,20 @@ class SolveInfo(C.Structure):
     ]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [
+        ("mem_budget_bytes", C.c_int64), ("max_slots", C.c_int32), ("restart", C.c_int32),
+        ("precond", C.c_int32), ("precision", C.c_int32),
+    ]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("resident", C.c_int32), ("queued", C.c_int32), ("arena_in_use", C.c_int64),
+        ("arena_largest_free", C.c_int64), ("cycles", C.c_int64), ("completed", C.c_int64),
+    ]
+
+
 # (name, restype, argtypes) for every entry point of include/rt_krylov.h
 _P = C.c_void_p
 SIGNATURES = [
@@ -69,6 +83,12 @@ SIGNATURES = [
     ("rt_solve_gmres", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),
     ("rt_solve_bicgstab", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),
     ("rt_solve_cgs", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),
+    ("rt_server_opts_default", None, [C.POINTER(ServerOpts)]),
+    ("rt_server_create", C.c_int, [C.POINTER(ServerOpts), C.POINTER(_P)]),
+    ("rt_batch_submit", C.c_int, [_P, C.POINTER(ProblemDesc), C.POINTER(SolverOpts), C.POINTER(C.c_uint64)]),
+    ("rt_poll", C.c_int, [_P, C.c_uint64, C.POINTER(SolveInfo), C.POINTER(C.c_double)]),
+    ("rt_server_stats_get", C.c_int, [_P, C.POINTER(ServerStats)]),
+    ("rt_server_destroy", C.c_int, [_P]),
     ("rt_last_error", C.c_char_p, []),
     ("rt_launch_count", C.c_int64, []),
 ]

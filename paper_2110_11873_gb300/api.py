@@ -44,6 +44,85 @@ class SolveResult:
         return N.STATUS_NAMES.get(self.status, str(self.status))
 
 
+def _desc_of(atm, keep: list, phi=None, phi_center=0.0) -> "N.ProblemDesc":
+    f = {k: getattr(atm, k) for k in _DESC_FIELDS}
+    tau = np.ascontiguousarray(f["tau"], dtype=np.float64)
+    B = np.ascontiguousarray(f["B"], dtype=np.float64)
+    keep += [tau, B]
+    d = N.ProblemDesc()
+    d.Ns, d.Nmu, d.Nnu = int(f["Ns"]), int(f["Nmu"]), int(f["Nnu"])
+    d.tau = _dptr(tau)
+    d.B = _dptr(B)
+    if phi is not None:
+        ph = np.ascontiguousarray(phi, dtype=np.float64)
+        keep.append(ph)
+        d.phi = _dptr(ph)
+    d.phi_center = float(phi_center)
+    d.x_min, d.x_max = float(f["x_min"]), float(f["x_max"])
+    d.a, d.eps, d.W2 = float(f["a"]), float(f["eps"]), float(f["W2"])
+    d.tau_kind, d.mu_quad = int(f["tau_kind"]), int(f["mu_quad"])
+    d.formal_solver, d.freq_norm = int(f["formal_solver"]), int(f["freq_norm"])
+    return d
+
+
+class Server:
+    """Batched / served solves (rt_server_*): submit atmospheres, poll results."""
+
+    def __init__(self, mem_budget_bytes: int = 8 << 30, max_slots: int = 64, restart: int = 30,
+                 precond: str = "local_lambda", precision: str = "fp64"):
+        self.lib = N.load()
+        o = N.ServerOpts()
+        self.lib.rt_server_opts_default(C.byref(o))
+        o.mem_budget_bytes, o.max_slots, o.restart = int(mem_budget_bytes), int(max_slots), int(restart)
+        o.precond = {"none": N.RT_PREC_NONE, "jacobi": N.RT_PREC_JACOBI,
+                     "local_lambda": N.RT_PREC_LOCAL_LAMBDA}[precond]
+        o.precision = {"fp64": N.RT_PRECISION_FP64, "fp32_refine": N.RT_PRECISION_FP32_REFINE}[precision]
+        h = C.c_void_p()
+        N.check(self.lib.rt_server_create(C.byref(o), C.byref(h)), "rt_server_create")
+        self.handle = h
+        self.sizes = {}
+
+    def submit(self, atm, rtol: float = 1e-8, maxit: int = 10000) -> int:
+        keep = []
+        d = _desc_of(atm, keep)
+        o = N.SolverOpts()
+        self.lib.rt_solver_opts_default(C.byref(o))
+        o.rtol, o.maxit = rtol, maxit
+        t = C.c_uint64()
+        N.check(self.lib.rt_batch_submit(self.handle, C.byref(d), C.byref(o), C.byref(t)), "rt_batch_submit")
+        self.sizes[t.value] = 2 * d.Ns * d.Nmu * d.Nnu
+        return t.value
+
+    def poll(self, ticket: int, want_x: bool = True):
+        """None while pending; else (status, SolveResult, x or None)."""
+        info = N.SolveInfo()
+        x = np.empty(self.sizes[ticket]) if want_x else None
+        st = self.lib.rt_poll(self.handle, C.c_uint64(ticket), C.byref(info),
+                              _dptr(x) if x is not None else None)
+        if st == N.RT_EPENDING:
+            return None
+        self.sizes.pop(ticket, None)
+        res = SolveResult(info.status, info.iters, info.restarts, info.applies, info.refine_steps,
+                          info.rel_resid, info.t_total_ms, np.zeros(0))
+        return st, res, x
+
+    def stats(self) -> dict:
+        st = N.ServerStats()
+        N.check(self.lib.rt_server_stats_get(self.handle, C.byref(st)), "rt_server_stats_get")
+        return {f: getattr(st, f) for f, _ in N.ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rt_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Problem:
     """One atmosphere on the current CUDA device.
 

@@ -1,0 +1,1158 @@
+// Batched uneven instances and the serving loop.
+//
+// Many atmospheres of different sizes are solved together by restarted
+// GMRES(m) in lock-step: every phase of an Arnoldi step (quadrature, formal
+// solve, each MGS pass, normalisation, Givens update) is ONE persistent
+// launch over all resident instances.  Each launch walks a device-resident
+// work list -- (instance, height) items for the quadrature, (instance, ray
+// group, Stokes) items for the formal solver, (instance, vector chunk) items
+// for the vector kernels, instances for the scalar updates -- so the grid is
+// fixed, the whole restart cycle is captured once as a CUDA graph, and
+// instances join or leave between cycles by rewriting the work lists only.
+// An instance whose residual estimate has passed its tolerance skips the
+// remaining steps of the cycle (per-instance step gate, as in the single
+// instance solver).
+//
+// The server owns one device arena (its memory budget) and a worker thread:
+// requests are admitted while a slot is free and the arena can hold the
+// instance (coefficient tables, Krylov basis and work vectors), each cycle
+// advances every resident instance, and finished instances are retired
+// (solution copied to the host, memory returned) before the next cycle.
+// Reductions are deterministic (per-chunk partials summed in a fixed order),
+// so an instance's result does not depend on what else is in the batch.
+//
+// Precision: FP64, or FP32 operator inside FP64 iterative refinement -- the
+// Arnoldi steps apply the FP32 operator, while each cycle ends with the true
+// residual b - A x from the FP64 operator, so every restart is a refinement
+// step and the stopping test is FP64.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+
+#include "rt_device.cuh"
+
+namespace rt {
+
+namespace {
+
+constexpr int kBT = 512;          // threads of the batched vector kernels
+constexpr int kFormalWarps = 4;   // warps per CTA of the batched formal solver
+constexpr int kInstThreads = 128; // threads of the per-instance scalar kernels
+enum VecId { VX = 100, VB, VR, VW, VT, VTMP };
+
+struct InstDev {
+  int Ns, Nmu, Nnu, Nh, ngd, ngroups, fs, nchunks, chunk, m;
+  int64_t nray, nd, N;
+  double xi, xiW2, inflow_bottom;
+  const double *ce, *ca, *cb, *wnu, *wmu, *t201, *t202, *Minv;
+  const float *dtau32, *r32, *wnu32, *wmu32, *t201f, *t202f;
+  double *S, *S2;
+  float* S32;
+  double *V, *x, *b, *r, *w, *t, *tmp, *dinv, *part;
+  GmresDev* gm;
+};
+
+struct InstStatus {
+  double rel;
+  int iters, kstop, kdone, breakdown;
+};
+
+struct Counts {
+  int nh, ng64, nc, ni;
+  int ng32[3], off32[3];   // FP32 formal-solver items, grouped by formal solver
+};
+
+__device__ __forceinline__ double* vec(const InstDev& I, int id) {
+  if (id < VX) return I.V + (int64_t)id * I.N;
+  switch (id) {
+    case VX: return I.x;
+    case VB: return I.b;
+    case VR: return I.r;
+    case VW: return I.w;
+    case VT: return I.t;
+    default: return I.tmp;
+  }
+}
+
+__device__ __forceinline__ bool step_gated(const InstDev& I, int step) {
+  return step >= 0 && step >= I.gm->kstop;
+}
+
+__device__ __forceinline__ double bsum(double v) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// sum of an instance's chunk partials in a fixed order, broadcast to the block
+__device__ __forceinline__ double inst_sum(const InstDev& I, int pb) {
+  __shared__ double bc;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int c = threadIdx.x; c < I.nchunks; c += 32) s += I.part[pb * I.nchunks + c];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) bc = s;
+  }
+  __syncthreads();
+  const double v = bc;
+  __syncthreads();
+  return v;
+}
+
+// ------------------------------------------------------------ operator
+template <typename TC, int MODE>
+__global__ void __launch_bounds__(kMomThreads) kb_moments(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                                          const Counts* cnt, int src, int step, int useS2) {
+  const int n = cnt->nh;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    if (step_gated(I, step)) continue;
+    const double* x = vec(I, src);
+    if (sizeof(TC) == 8) {
+      moments_height<double, double, MODE>(x, I.dinv, I.wnu, I.wmu, I.t201, I.t202, I.Minv, I.Ns, I.Nmu, I.Nnu, I.xi,
+                                           I.xiW2, useS2 ? I.S2 : I.S, it.y);
+    } else {
+      moments_height<double, float, MODE>(x, I.dinv, I.wnu32, I.wmu32, I.t201f, I.t202f, I.Minv, I.Ns, I.Nmu, I.Nnu,
+                                          (float)I.xi, (float)I.xiW2, I.S32, it.y);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TC, int FS, int MODE, int NS>
+__device__ __forceinline__ void formal_item(const InstDev& I, int g, int s0, int src, int dst) {
+  const int lane = threadIdx.x & 31;
+  FormalArgs A;
+  A.x = vec(I, src);
+  A.dinv = I.dinv;
+  A.ce = I.ce;
+  A.ca = I.ca;
+  A.cb = I.cb;
+  A.dtau32 = I.dtau32;
+  A.r32 = I.r32;
+  A.S = sizeof(TC) == 8 ? (const void*)I.S : (const void*)I.S32;
+  A.y = vec(I, dst);
+  A.Ns = I.Ns;
+  A.Nmu = I.Nmu;
+  A.Nnu = I.Nnu;
+  A.nray = I.nray;
+  A.nd = I.nd;
+  A.ngd = I.ngd;
+  A.ntile = 1;
+  A.inflow_bottom = I.inflow_bottom;
+  A.kstop = nullptr;
+  A.step = 0;
+  const bool down = g < I.ngd;
+  const int64_t base = down ? (int64_t)g * 32 : I.nd + (int64_t)(g - I.ngd) * 32;
+  const int64_t end = down ? I.nd : I.nray;
+  const bool active = base + lane < end;
+  const int64_t r = active ? base + lane : end - 1;
+  const int m = (int)(r / I.Nnu);
+  const int Ns = I.Ns;
+  TC Iv[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) Iv[q] = 0;
+  if (active) {
+    const int k0 = down ? 0 : Ns - 1;
+    const double* x = reinterpret_cast<const double*>(A.x);
+    double* y = reinterpret_cast<double*>(A.y);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const int64_t o = (int64_t)(s0 + q) * Ns * I.nray + (int64_t)k0 * I.nray + r;
+      if (MODE == KM_JACOBI) y[o] = x[o] * I.dinv[o];
+      else y[o] = x[o];
+    }
+  }
+  TC E = 1;
+  if (sizeof(TC) == 8)
+    sweep<TC, double, FS, MODE, 1, NS, kRing>(A, s0, down, r, m, active, 1, Ns, Iv, E);
+  else
+    sweep<TC, double, FS, MODE, 1, NS, kRing32>(A, s0, down, r, m, active, 1, Ns, Iv, E);
+}
+
+// FP64: items (slot, group, Stokes); FP32: items (slot, group) with both
+// Stokes parameters per lane, one launch per formal solver (FS)
+template <typename TC, int FS, int MODE>
+__global__ void __launch_bounds__(32 * kFormalWarps) kb_formal(const InstDev* __restrict__ insts,
+                                                               const int4* __restrict__ wl, const Counts* cnt,
+                                                               int src, int dst, int step) {
+  const int n = sizeof(TC) == 8 ? cnt->ng64 : cnt->ng32[FS];
+  const int off = sizeof(TC) == 8 ? 0 : cnt->off32[FS];
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
+    const int4 it = wl[off + w];
+    const InstDev& I = insts[it.x];
+    if (step_gated(I, step)) continue;
+    if (sizeof(TC) == 8) formal_item<TC, 0, MODE, 1>(I, it.y, it.z, src, dst);
+    else formal_item<TC, FS, MODE, 2>(I, it.y, 0, src, dst);
+  }
+}
+
+// ------------------------------------------------------------ vectors
+#define CHUNK_LOOP(body)                                                      \
+  {                                                                           \
+    const int64_t lo = (int64_t)it.y * I.chunk;                               \
+    const int64_t hi = lo + I.chunk < I.N ? lo + I.chunk : I.N;               \
+    for (int64_t n_ = lo + threadIdx.x; n_ < hi; n_ += blockDim.x) { body }   \
+  }
+
+__global__ void __launch_bounds__(kBT) kb_dot(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                              const Counts* cnt, int ida, int idb, int pb, int step) {
+  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    if (step_gated(I, step)) continue;
+    const double* a = vec(I, ida);
+    const double* b = vec(I, idb);
+    double s = 0.0;
+    CHUNK_LOOP(s = fma(a[n_], b[n_], s);)
+    s = bsum(s);
+    if (threadIdx.x == 0) I.part[pb * I.nchunks + it.y] = s;
+  }
+}
+
+// MGS pass i of Arnoldi step j: h = <w, v_i> (from the partials); w -= h v_i;
+// partial <w, v_{i+1}> (or <w, w> for i == j)
+__global__ void __launch_bounds__(kBT) kb_mgs(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                              const Counts* cnt, int i, int j, int pb) {
+  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    if (step_gated(I, j)) continue;
+    const double h = inst_sum(I, pb);
+    if (it.y == 0 && threadIdx.x == 0) I.gm->H[j * (I.m + 1) + i] = h;
+    double* wv = I.w;
+    const double* vp = I.V + (int64_t)i * I.N;
+    const double* vn = i < j ? I.V + (int64_t)(i + 1) * I.N : nullptr;
+    double s = 0.0;
+    CHUNK_LOOP(const double wi = fma(-h, vp[n_], wv[n_]); wv[n_] = wi; s = fma(wi, vn ? vn[n_] : wi, s);)
+    s = bsum(s);
+    if (threadIdx.x == 0) I.part[(pb ^ 1) * I.nchunks + it.y] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kBT) kb_normalize(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                                    const Counts* cnt, int j, int pb) {
+  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    if (step_gated(I, j)) continue;
+    const double hn = sqrt(inst_sum(I, pb));
+    if (it.y == 0 && threadIdx.x == 0) I.gm->H[j * (I.m + 1) + j + 1] = hn;
+    const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+    const double* wv = I.w;
+    double* v = I.V + (int64_t)(j + 1) * I.N;
+    CHUNK_LOOP(v[n_] = wv[n_] * inv;)
+  }
+}
+
+__global__ void kb_givens(const InstDev* __restrict__ insts, const int* __restrict__ wi, const Counts* cnt, int j) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt->ni) return;
+  const InstDev& I = insts[wi[q]];
+  GmresDev* gm = I.gm;
+  if (j >= gm->kstop) return;
+  const int m = I.m;
+  double* Hc = gm->H + j * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double t = gm->cs[i] * Hc[i] + gm->sn[i] * Hc[i + 1];
+    Hc[i + 1] = -gm->sn[i] * Hc[i] + gm->cs[i] * Hc[i + 1];
+    Hc[i] = t;
+  }
+  const double a = Hc[j], b = Hc[j + 1];
+  const double hn = hypot(a, b);
+  if (hn == 0.0) {
+    gm->breakdown = 1;
+    gm->kstop = j;
+    return;
+  }
+  const double c = a / hn, s = b / hn;
+  gm->cs[j] = c;
+  gm->sn[j] = s;
+  Hc[j] = hn;
+  Hc[j + 1] = 0.0;
+  gm->g[j + 1] = -s * gm->g[j];
+  gm->g[j] = c * gm->g[j];
+  gm->iters += 1;
+  gm->kdone = j + 1;
+  const double est = fabs(gm->g[j + 1]) / gm->bnorm;
+  if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
+}
+
+__global__ void kb_lsq(const InstDev* __restrict__ insts, const int* __restrict__ wi, const Counts* cnt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt->ni) return;
+  const InstDev& I = insts[wi[q]];
+  GmresDev* gm = I.gm;
+  const int k = gm->kdone, m = I.m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gm->g[i];
+    for (int l = i + 1; l < k; ++l) s -= gm->H[l * (m + 1) + i] * gm->y[l];
+    gm->y[i] = s / gm->H[i * (m + 1) + i];
+  }
+}
+
+// s = sum_{i<kdone} y_i V_i; mode 0: x += s, 1: x += dinv s, 2: t = s
+__global__ void __launch_bounds__(kBT) kb_combine(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                                  const Counts* cnt, int mode) {
+  __shared__ double ys[kMaxRestart];
+  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    const int k = I.gm->kdone;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = I.gm->y[i];
+    __syncthreads();
+    CHUNK_LOOP(double s = 0.0; for (int i = 0; i < k; ++i) s = fma(ys[i], I.V[(int64_t)i * I.N + n_], s);
+               if (mode == 0) I.x[n_] += s; else if (mode == 1) I.x[n_] = fma(I.dinv[n_], s, I.x[n_]);
+               else I.t[n_] = s;)
+    __syncthreads();
+  }
+}
+
+// x += t + beta* S2 (P^{-1} t with S2 = T M^{-1} J t)
+__global__ void __launch_bounds__(kBT) kb_add_local(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                                    const Counts* cnt) {
+  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    CHUNK_LOOP(const int64_t rr = n_ % I.nray; const int64_t sk = n_ / I.nray; const int k = (int)(sk % I.Ns);
+               const int s = (int)(sk / I.Ns); const int m = (int)(rr / I.Nnu);
+               I.x[n_] += I.t[n_] + beta_star(I.cb, k, m, rr, I.Ns, I.Nh, I.nray) *
+                                         I.S2[((int64_t)s * I.Ns + k) * I.Nmu + m];)
+  }
+}
+
+// r = b - tmp; partial ||r||^2 into part[0]
+__global__ void __launch_bounds__(kBT) kb_residual(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                                   const Counts* cnt) {
+  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    double s = 0.0;
+    CHUNK_LOOP(const double v = I.b[n_] - I.tmp[n_]; I.r[n_] = v; s = fma(v, v, s);)
+    s = bsum(s);
+    if (threadIdx.x == 0) I.part[it.y] = s;
+  }
+}
+
+__global__ void kb_set_bnorm(const InstDev* __restrict__ insts, const int* __restrict__ wi, const Counts* cnt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt->ni) return;
+  const InstDev& I = insts[wi[q]];
+  double s = 0.0;
+  for (int c = 0; c < I.nchunks; ++c) s += I.part[c];
+  I.gm->bnorm = sqrt(s);
+}
+
+// start of a cycle: beta = ||r||, v_0 = r / beta, g = beta e_1, step budget
+__global__ void __launch_bounds__(kBT) kb_cycle_start(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                                      const Counts* cnt, InstStatus* __restrict__ status) {
+  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    const double rn = sqrt(inst_sum(I, 0));
+    const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+    CHUNK_LOOP(I.V[n_] = I.r[n_] * inv;)
+    if (it.y == 0 && threadIdx.x == 0) {
+      GmresDev* gm = I.gm;
+      gm->rnorm = rn;
+      gm->rel = gm->bnorm > 0.0 ? rn / gm->bnorm : 0.0;
+      for (int i = 0; i <= I.m; ++i) gm->g[i] = 0.0;
+      gm->g[0] = rn;
+      gm->kdone = 0;
+      const int left = gm->maxit - gm->iters;
+      gm->kstop = left < I.m ? (left > 0 ? left : 0) : I.m;
+      if (!(gm->rel >= gm->tol)) gm->kstop = 0;
+      InstStatus st;
+      st.rel = gm->rel;
+      st.iters = gm->iters;
+      st.kstop = gm->kstop;
+      st.kdone = gm->kdone;
+      st.breakdown = gm->breakdown;
+      status[it.x] = st;
+    }
+  }
+}
+
+#undef CHUNK_LOOP
+
+// ------------------------------------------------------------ arena
+// First-fit allocator over one device allocation (256-byte granules).
+class Arena : public DevAllocator {
+ public:
+  rt_status init(size_t bytes) {
+    bytes_ = (bytes + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc(&base_, bytes_);
+    if (e != cudaSuccess) {
+      set_error("arena allocation of %zu bytes failed: %s", bytes_, cudaGetErrorString(e));
+      base_ = nullptr;
+      return RT_ENOMEM;
+    }
+    free_[0] = bytes_;
+    return RT_OK;
+  }
+  ~Arena() override {
+    if (base_) cudaFree(base_);
+  }
+  cudaError_t alloc(void** p, size_t bytes) override {
+    std::lock_guard<std::mutex> lk(mu_);
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t off = it->first, len = it->second;
+        free_.erase(it);
+        if (len > bytes) free_[off + bytes] = len - bytes;
+        used_[off] = bytes;
+        *p = static_cast<char*>(base_) + off;
+        in_use_ += bytes;
+        return cudaSuccess;
+      }
+    }
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  void release(void* p) override {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu_);
+    const size_t off = static_cast<char*>(p) - static_cast<char*>(base_);
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    size_t len = u->second;
+    used_.erase(u);
+    in_use_ -= len;
+    size_t start = off;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && nx->first == off + len) {   // merge with the next hole
+      len += nx->second;
+      free_.erase(nx);
+    }
+    auto pv = free_.lower_bound(off);
+    if (pv != free_.begin()) {                           // merge with the previous hole
+      --pv;
+      if (pv->first + pv->second == off) {
+        start = pv->first;
+        len += pv->second;
+        free_.erase(pv);
+      }
+    }
+    free_[start] = len;
+  }
+  size_t largest_hole() {
+    std::lock_guard<std::mutex> lk(mu_);
+    size_t b = 0;
+    for (auto& kv : free_) b = std::max(b, kv.second);
+    return b;
+  }
+  size_t in_use() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return in_use_;
+  }
+
+ private:
+  void* base_ = nullptr;
+  size_t bytes_ = 0, in_use_ = 0;
+  std::map<size_t, size_t> free_, used_;
+  std::mutex mu_;
+};
+
+inline double wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side
+struct Request {
+  uint64_t ticket = 0;
+  rt_problem_desc desc{};
+  std::vector<double> tau, B, phi;
+  double rtol = 1e-8;
+  int maxit = 10000;
+  double t_submit = 0, t_done = 0;
+  std::vector<double> x;   // solution on completion
+  rt_solve_info info{};
+  bool done = false;
+};
+
+struct Instance {
+  Request* req = nullptr;
+  Problem P;
+  int slot = -1;
+  int cycles = 0;
+  InstDev dev{};
+  void* block = nullptr;   // solver buffers (one arena block)
+};
+
+struct Server {
+  rt_server_opts opts{};
+  int device = 0, sms = 0;
+  Arena arena;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> pending;
+  std::map<uint64_t, std::unique_ptr<Request>> requests;
+  std::atomic<uint64_t> next_ticket{1};
+  std::thread worker;
+  bool stop = false;
+  std::string worker_error;
+  rt_status worker_status = RT_OK;
+  // worker-owned state
+  cudaStream_t st = nullptr, cap = nullptr;
+  std::vector<Instance*> slots;   // index = slot
+  InstDev* d_insts = nullptr;
+  InstStatus* d_status = nullptr;
+  Counts* d_counts = nullptr;
+  int2 *d_wl_h = nullptr, *d_wl_c = nullptr;
+  int4 *d_wl_g64 = nullptr, *d_wl_g32 = nullptr;
+  int* d_wl_i = nullptr;
+  size_t cap_h = 0, cap_c = 0, cap_g64 = 0, cap_g32 = 0;
+  int2* d_wl_new_c = nullptr;   // admission work lists (new instances only)
+  int* d_wl_new_i = nullptr;
+  Counts* d_new_counts = nullptr;
+  size_t cap_new_c = 0;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0;
+  std::atomic<long long> cycles{0}, completed{0};
+  std::atomic<int> resident{0};
+  int grid_h = 0, grid_g = 0, grid_v = 0, grid_i = 0;
+};
+
+namespace {
+
+template <typename T>
+rt_status grow(T** p, size_t* cap, size_t need) {
+  if (need <= *cap) return RT_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  size_t c = need + need / 2 + 64;
+  RT_TRY_CUDA(cudaMalloc((void**)p, c * sizeof(T)));
+  *cap = c;
+  return RT_OK;
+}
+
+// instance footprint of the solver buffers: basis (m+1), six work vectors,
+// the Jacobi inverse diagonal, partials, GMRES state
+size_t solver_bytes(int64_t N, int m, int nchunks) {
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  return al((size_t)(m + 1) * N * 8) + 7 * al((size_t)N * 8) + al((size_t)2 * nchunks * 8) + al(sizeof(GmresDev));
+}
+
+int64_t chunk_for(int64_t N) {
+  (void)N;
+  return 65536;
+}
+
+template <int MODE>
+void formal32(Server* S, cudaStream_t st, int src, int dst, int step) {
+  kb_formal<float, RT_FS_DELO_LINEAR, MODE><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(S->d_insts, S->d_wl_g32,
+                                                                                     S->d_counts, src, dst, step);
+  kb_formal<float, RT_FS_IMPLICIT_EULER, MODE><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(S->d_insts, S->d_wl_g32,
+                                                                                        S->d_counts, src, dst, step);
+  kb_formal<float, RT_FS_TRAPEZOIDAL, MODE><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(S->d_insts, S->d_wl_g32,
+                                                                                     S->d_counts, src, dst, step);
+}
+
+// enqueue one restart cycle for all resident instances (captured once)
+rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
+  const int m = S->opts.restart;
+  const int prec = S->opts.precond;
+  const bool fp32 = S->opts.precision == RT_PRECISION_FP32_REFINE;
+  const int mode = prec == RT_PREC_JACOBI ? KM_JACOBI : prec == RT_PREC_LOCAL_LAMBDA ? KM_LOCAL_LAMBDA : KM_PLAIN;
+  const InstDev* I = S->d_insts;
+  const Counts* C = S->d_counts;
+  auto apply = [&](int src, int dst, int md, bool f32, int step) {
+    if (!f32) {
+      switch (md) {
+        case KM_JACOBI:
+          kb_moments<double, KM_JACOBI><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+          kb_formal<double, 0, KM_JACOBI><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
+          break;
+        case KM_LOCAL_LAMBDA:
+          kb_moments<double, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+          kb_formal<double, 0, KM_LOCAL_LAMBDA><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst,
+                                                                                       step);
+          break;
+        default:
+          kb_moments<double, KM_PLAIN><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+          kb_formal<double, 0, KM_PLAIN><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
+      }
+    } else {
+      switch (md) {
+        case KM_JACOBI:
+          kb_moments<float, KM_JACOBI><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+          formal32<KM_JACOBI>(S, st, src, dst, step);
+          break;
+        case KM_LOCAL_LAMBDA:
+          kb_moments<float, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+          formal32<KM_LOCAL_LAMBDA>(S, st, src, dst, step);
+          break;
+        default:
+          kb_moments<float, KM_PLAIN><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+          formal32<KM_PLAIN>(S, st, src, dst, step);
+      }
+    }
+  };
+  for (int j = 0; j < m; ++j) {
+    apply(j, VW, mode, fp32, j);
+    int pb = 0;
+    kb_dot<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, VW, 0, pb, j);
+    for (int i = 0; i <= j; ++i) {
+      kb_mgs<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, i, j, pb);
+      pb ^= 1;
+    }
+    kb_normalize<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, pb);
+    kb_givens<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C, j);
+  }
+  kb_lsq<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C);
+  if (mode == KM_LOCAL_LAMBDA) {
+    kb_combine<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, 2);
+    kb_moments<double, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, VT, -1, 1);
+    kb_add_local<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C);
+  } else {
+    kb_combine<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, mode == KM_JACOBI ? 1 : 0);
+  }
+  apply(VX, VTMP, KM_PLAIN, false, -1);   // FP64 true residual
+  kb_residual<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C);
+  kb_cycle_start<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, S->d_status);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status capture_cycle(Server* S) {
+  if (S->graph) return RT_OK;
+  RT_TRY_CUDA(cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal));
+  g_capturing = 1;
+  rt_status s = enqueue_batch_cycle(S, S->cap);
+  g_capturing = 0;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(S->cap, &g);
+  if (s != RT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) {
+    set_error("batch graph capture failed: %s", cudaGetErrorString(e));
+    return RT_ECUDA;
+  }
+  size_t nn = 0;
+  S->graph_kernels = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++S->graph_kernels;
+      }
+  }
+  e = cudaGraphInstantiate(&S->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    S->graph = nullptr;
+    set_error("batch graph instantiate failed: %s", cudaGetErrorString(e));
+    return RT_ECUDA;
+  }
+  return RT_OK;
+}
+
+void drop_graph(Server* S) {
+  if (S->graph) cudaGraphExecDestroy(S->graph);
+  S->graph = nullptr;
+}
+
+// rebuild the work lists of all resident instances
+rt_status rebuild_lists(Server* S) {
+  std::vector<int2> h, c;
+  std::vector<int4> g64, g32, g32f[3];
+  std::vector<int> wi;
+  for (size_t q = 0; q < S->slots.size(); ++q) {
+    Instance* in = S->slots[q];
+    if (!in) continue;
+    const int sl = (int)q;
+    wi.push_back(sl);
+    for (int k = 0; k < in->P.Ns; ++k) h.push_back(make_int2(sl, k));
+    for (int g = 0; g < in->P.ngroups; ++g) {
+      g32f[in->P.fs].push_back(make_int4(sl, g, 0, 0));
+      for (int s = 0; s < 2; ++s) g64.push_back(make_int4(sl, g, s, 0));
+    }
+    for (int cc = 0; cc < in->dev.nchunks; ++cc) c.push_back(make_int2(sl, cc));
+  }
+  Counts cn{(int)h.size(), (int)g64.size(), (int)c.size(), (int)wi.size(), {0, 0, 0}, {0, 0, 0}};
+  for (int f = 0; f < 3; ++f) {
+    cn.off32[f] = (int)g32.size();
+    cn.ng32[f] = (int)g32f[f].size();
+    g32.insert(g32.end(), g32f[f].begin(), g32f[f].end());
+  }
+  // interleave the formal-solver items of different instances so that big
+  // instances do not end up on the same SMs
+  bool regrown = false;
+  const size_t ch = S->cap_h, cc = S->cap_c, c64 = S->cap_g64, c32 = S->cap_g32;
+  RT_TRY(grow(&S->d_wl_h, &S->cap_h, h.size()));
+  RT_TRY(grow(&S->d_wl_c, &S->cap_c, c.size()));
+  RT_TRY(grow(&S->d_wl_g64, &S->cap_g64, g64.size()));
+  RT_TRY(grow(&S->d_wl_g32, &S->cap_g32, g32.size()));
+  regrown = ch != S->cap_h || cc != S->cap_c || c64 != S->cap_g64 || c32 != S->cap_g32;
+  if (regrown) drop_graph(S);
+  if (!h.empty()) RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_h, h.data(), h.size() * sizeof(int2), cudaMemcpyHostToDevice, S->st));
+  if (!c.empty()) RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_c, c.data(), c.size() * sizeof(int2), cudaMemcpyHostToDevice, S->st));
+  if (!g64.empty())
+    RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_g64, g64.data(), g64.size() * sizeof(int4), cudaMemcpyHostToDevice, S->st));
+  if (!g32.empty())
+    RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_g32, g32.data(), g32.size() * sizeof(int4), cudaMemcpyHostToDevice, S->st));
+  if (!wi.empty()) RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_i, wi.data(), wi.size() * sizeof(int), cudaMemcpyHostToDevice, S->st));
+  RT_TRY_CUDA(cudaMemcpyAsync(S->d_counts, &cn, sizeof cn, cudaMemcpyHostToDevice, S->st));
+  RT_TRY_CUDA(cudaStreamSynchronize(S->st));
+  return RT_OK;
+}
+
+void free_instance(Server* S, Instance* in) {
+  if (in->block) S->arena.release(in->block);
+  in->block = nullptr;
+  free_device(&in->P);
+}
+
+// build one instance in the arena: tables, rhs, preconditioner data, solver buffers
+rt_status make_instance(Server* S, Request* rq, Instance* in, int slot) {
+  in->req = rq;
+  in->slot = slot;
+  Problem& P = in->P;
+  P.alloc = &S->arena;
+  host_grids(&rq->desc, P);
+  P.device = S->device;
+  P.num_sms = S->sms;
+  RT_TRY(setup_device_tables(&P, S->st));
+  const int m = S->opts.restart;
+  const int64_t N = P.N;
+  const int64_t chunk = chunk_for(N);
+  const int nchunks = (int)((N + chunk - 1) / chunk);
+  const size_t bytes = solver_bytes(N, m, nchunks);
+  void* blk = nullptr;
+  if (S->arena.alloc(&blk, bytes) != cudaSuccess) {
+    set_error("arena full");
+    return RT_ENOMEM;
+  }
+  in->block = blk;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char* p = static_cast<char*>(blk);
+  InstDev& D = in->dev;
+  D.V = reinterpret_cast<double*>(p);
+  p += al((size_t)(m + 1) * N * 8);
+  double** vecs[] = {&D.x, &D.b, &D.r, &D.w, &D.t, &D.tmp, &D.dinv};
+  for (double** v : vecs) {
+    *v = reinterpret_cast<double*>(p);
+    p += al((size_t)N * 8);
+  }
+  D.part = reinterpret_cast<double*>(p);
+  p += al((size_t)2 * nchunks * 8);
+  D.gm = reinterpret_cast<GmresDev*>(p);
+  D.Ns = P.Ns;
+  D.Nmu = P.Nmu;
+  D.Nnu = P.Nnu;
+  D.Nh = P.Nh;
+  D.ngd = P.ngroups / 2;
+  D.ngroups = P.ngroups;
+  D.fs = P.fs;
+  D.nchunks = nchunks;
+  D.chunk = (int)chunk;
+  D.m = m;
+  D.nray = P.nray;
+  D.nd = P.nd;
+  D.N = N;
+  D.xi = P.xi;
+  D.xiW2 = P.xi * P.W2;
+  D.inflow_bottom = P.B[P.Ns - 1];
+  D.ce = P.ce;
+  D.ca = P.ca;
+  D.cb = P.cb;
+  D.wnu = P.wI2;
+  D.wmu = P.wQ2;
+  D.t201 = P.t201d;
+  D.t202 = P.t202d;
+  D.Minv = P.Minv;
+  D.dtau32 = P.dtau32;
+  D.r32 = P.r32;
+  D.wnu32 = P.wI2f;
+  D.wmu32 = P.wQ2f;
+  D.t201f = P.t201f;
+  D.t202f = P.t202f;
+  D.S = P.S;
+  D.S2 = P.S2;
+  D.S32 = P.S32;
+  // rhs, preconditioner, x0 = 0, GMRES state
+  P.dinv = D.dinv;
+  RT_TRY(op_rhs(&P, D.b, S->st));
+  if (S->opts.precond == RT_PREC_JACOBI) RT_TRY(op_jacobi_inv(&P, D.dinv, S->st));
+  P.dinv = nullptr;   // the arena block owns it
+  RT_TRY_CUDA(cudaMemsetAsync(D.x, 0, (size_t)N * 8, S->st));
+  RT_TRY_CUDA(cudaMemsetAsync(D.tmp, 0, (size_t)N * 8, S->st));
+  GmresDev init;
+  memset(&init, 0, sizeof init);
+  init.tol = rq->rtol;
+  init.maxit = rq->maxit;
+  RT_TRY_CUDA(cudaMemcpyAsync(D.gm, &init, sizeof init, cudaMemcpyHostToDevice, S->st));
+  RT_TRY_CUDA(cudaMemcpyAsync(S->d_insts + slot, &D, sizeof D, cudaMemcpyHostToDevice, S->st));
+  return RT_OK;
+}
+
+// prologue of newly admitted instances: r = b, ||b||, v_0, step budget
+rt_status start_instances(Server* S, const std::vector<Instance*>& fresh) {
+  std::vector<int2> c;
+  std::vector<int> wi;
+  for (Instance* in : fresh) {
+    wi.push_back(in->slot);
+    for (int cc = 0; cc < in->dev.nchunks; ++cc) c.push_back(make_int2(in->slot, cc));
+  }
+  RT_TRY(grow(&S->d_wl_new_c, &S->cap_new_c, c.size()));
+  RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_new_c, c.data(), c.size() * sizeof(int2), cudaMemcpyHostToDevice, S->st));
+  RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_new_i, wi.data(), wi.size() * sizeof(int), cudaMemcpyHostToDevice, S->st));
+  Counts cn{0, 0, (int)c.size(), (int)wi.size(), {0, 0, 0}, {0, 0, 0}};
+  RT_TRY_CUDA(cudaMemcpyAsync(S->d_new_counts, &cn, sizeof cn, cudaMemcpyHostToDevice, S->st));
+  kb_residual<<<S->grid_v, kBT, 0, S->st>>>(S->d_insts, S->d_wl_new_c, S->d_new_counts); RT_COUNT(1);
+  kb_set_bnorm<<<(int)((wi.size() + kInstThreads - 1) / kInstThreads), kInstThreads, 0, S->st>>>(
+      S->d_insts, S->d_wl_new_i, S->d_new_counts); RT_COUNT(1);
+  kb_cycle_start<<<S->grid_v, kBT, 0, S->st>>>(S->d_insts, S->d_wl_new_c, S->d_new_counts, S->d_status); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+void finish_request(Server* S, Instance* in, const InstStatus& st, rt_status status) {
+  Request* rq = in->req;
+  rq->x.resize(in->P.N);
+  cudaMemcpyAsync(rq->x.data(), in->dev.x, (size_t)in->P.N * 8, cudaMemcpyDeviceToHost, S->st);
+  cudaStreamSynchronize(S->st);
+  rq->info.status = status;
+  rq->info.iters = st.iters;
+  rq->info.restarts = in->cycles;
+  rq->info.applies = st.iters + in->cycles;
+  rq->info.refine_steps = S->opts.precision == RT_PRECISION_FP32_REFINE ? in->cycles : 0;
+  rq->info.rel_resid = st.rel;
+  rq->t_done = wall_ms();
+  rq->info.t_total_ms = rq->t_done - rq->t_submit;
+  std::lock_guard<std::mutex> lk(S->mu);
+  rq->done = true;
+  S->completed.fetch_add(1);
+}
+
+void worker_main(Server* S) {
+  cudaSetDevice(S->device);
+  auto fail = [&](rt_status s) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->worker_status = s;
+    S->worker_error = rt_last_error();
+    for (Request* rq : S->pending) {
+      rq->info.status = s;
+      rq->done = true;
+    }
+    S->pending.clear();
+    for (Instance* in : S->slots)
+      if (in) {
+        in->req->info.status = s;
+        in->req->done = true;
+      }
+  };
+  std::vector<InstStatus> hs;
+  for (;;) {
+    // admission
+    std::vector<Request*> admit;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      bool any_active = false;
+      for (Instance* in : S->slots) any_active |= in != nullptr;
+      if (!any_active) S->cv.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+      if (S->stop) break;
+      int freeslots = 0;
+      for (Instance* in : S->slots) freeslots += in == nullptr;
+      while (!S->pending.empty() && (int)admit.size() < freeslots) {
+        admit.push_back(S->pending.front());
+        S->pending.pop_front();
+      }
+    }
+    std::vector<Instance*> fresh;
+    std::vector<Request*> back;   // did not fit: requeue at the front
+    for (Request* rq : admit) {
+      int slot = -1;
+      for (size_t q = 0; q < S->slots.size(); ++q)
+        if (!S->slots[q]) {
+          slot = (int)q;
+          break;
+        }
+      Instance* in = new Instance();
+      rt_status s = make_instance(S, rq, in, slot);
+      if (s == RT_ENOMEM) {
+        free_instance(S, in);
+        delete in;
+        back.push_back(rq);
+        continue;
+      }
+      if (s != RT_OK) {
+        free_instance(S, in);
+        delete in;
+        std::lock_guard<std::mutex> lk(S->mu);
+        rq->info.status = s;
+        rq->done = true;
+        continue;
+      }
+      S->slots[slot] = in;
+      fresh.push_back(in);
+      S->resident.fetch_add(1);
+    }
+    if (!back.empty()) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (auto it = back.rbegin(); it != back.rend(); ++it) S->pending.push_front(*it);
+    }
+    bool any = false;
+    for (Instance* in : S->slots) any |= in != nullptr;
+    if (!any) {
+      if (!back.empty()) {
+        // the arena cannot hold even one of them alone: fail the head request
+        std::lock_guard<std::mutex> lk(S->mu);
+        Request* rq = S->pending.front();
+        S->pending.pop_front();
+        rq->info.status = RT_ENOMEM;
+        rq->done = true;
+      }
+      continue;
+    }
+    rt_status s = RT_OK;
+    if (!fresh.empty()) s = start_instances(S, fresh);
+    if (s == RT_OK) s = rebuild_lists(S);
+    if (s == RT_OK) s = capture_cycle(S);
+    if (s != RT_OK) {
+      fail(s);
+      break;
+    }
+    // one restart cycle for every resident instance
+    cudaError_t e = cudaGraphLaunch(S->graph, S->st);
+    if (e == cudaSuccess) count_launches(S->graph_kernels);
+    S->cycles.fetch_add(1);
+    hs.resize(S->slots.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hs.data(), S->d_status, hs.size() * sizeof(InstStatus), cudaMemcpyDeviceToHost, S->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+    if (e != cudaSuccess) {
+      set_error("batch cycle failed: %s", cudaGetErrorString(e));
+      fail(RT_ECUDA);
+      break;
+    }
+    // retire finished instances
+    int nres = 0;
+    for (size_t q = 0; q < S->slots.size(); ++q) {
+      Instance* in = S->slots[q];
+      if (!in) continue;
+      in->cycles += 1;
+      const InstStatus& st = hs[q];
+      rt_status fin = RT_EPENDING;
+      if (st.rel != st.rel) fin = RT_ENUMERIC;
+      else if (st.rel < in->req->rtol) fin = RT_OK;
+      else if (st.iters >= in->req->maxit) fin = RT_ENOTCONV;
+      else if (st.breakdown && st.kdone == 0) fin = RT_EBREAKDOWN;
+      else if (st.kstop == 0) fin = RT_ENOTCONV;
+      if (fin != RT_EPENDING) {
+        finish_request(S, in, st, fin);
+        free_instance(S, in);
+        delete in;
+        S->slots[q] = nullptr;
+      } else {
+        ++nres;
+      }
+    }
+    S->resident.store(nres);
+  }
+  for (Instance*& in : S->slots)
+    if (in) {
+      free_instance(S, in);
+      delete in;
+      in = nullptr;
+    }
+}
+
+}  // namespace
+
+}  // namespace rt
+
+using namespace rt;
+
+struct rt_server {
+  rt::Server S;
+};
+
+extern "C" {
+
+void rt_server_opts_default(rt_server_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->mem_budget_bytes = (int64_t)8 << 30;
+  o->max_slots = 64;
+  o->restart = 30;
+  o->precond = RT_PREC_LOCAL_LAMBDA;
+  o->precision = RT_PRECISION_FP64;
+}
+
+rt_status rt_server_create(const rt_server_opts* opts, rt_server** out) {
+  clear_error();
+  if (!opts || !out) { set_error("opts and out are required"); return RT_EINVAL; }
+  *out = nullptr;
+  if (opts->max_slots < 1 || opts->max_slots > 4096) { set_error("max_slots must be in [1,4096]"); return RT_EINVAL; }
+  if (opts->restart < 1 || opts->restart > kMaxRestart) { set_error("restart must be in [1,%d]", kMaxRestart); return RT_EINVAL; }
+  if (opts->precond < RT_PREC_NONE || opts->precond > RT_PREC_LOCAL_LAMBDA) { set_error("bad precond"); return RT_EINVAL; }
+  if (opts->precision != RT_PRECISION_FP64 && opts->precision != RT_PRECISION_FP32_REFINE) { set_error("bad precision"); return RT_EINVAL; }
+  if (opts->mem_budget_bytes < ((int64_t)1 << 20)) { set_error("mem_budget_bytes must be >= 1 MiB"); return RT_EINVAL; }
+  rt_server* srv = new (std::nothrow) rt_server();
+  if (!srv) { set_error("host allocation failed"); return RT_ENOMEM; }
+  Server* S = &srv->S;
+  S->opts = *opts;
+  cudaError_t e = cudaGetDevice(&S->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
+  if (e != cudaSuccess) {
+    set_error("no CUDA device: %s", cudaGetErrorString(e));
+    delete srv;
+    return RT_ECUDA;
+  }
+  rt_status s = S->arena.init((size_t)opts->mem_budget_bytes);
+  if (s != RT_OK) {
+    delete srv;
+    return s;
+  }
+  S->slots.assign(opts->max_slots, nullptr);
+  S->grid_h = 4 * S->sms;
+  S->grid_g = 8 * S->sms;
+  S->grid_v = 4 * S->sms;
+  S->grid_i = (opts->max_slots + kInstThreads - 1) / kInstThreads;
+  e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_insts, sizeof(InstDev) * opts->max_slots);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_status, sizeof(InstStatus) * opts->max_slots);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_counts, sizeof(Counts));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_new_counts, sizeof(Counts));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_wl_i, sizeof(int) * opts->max_slots);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_wl_new_i, sizeof(int) * opts->max_slots);
+  if (e != cudaSuccess) {
+    set_error("server setup failed: %s", cudaGetErrorString(e));
+    rt_server_destroy(srv);
+    return RT_ECUDA;
+  }
+  S->worker = std::thread(worker_main, S);
+  *out = srv;
+  return RT_OK;
+}
+
+rt_status rt_batch_submit(rt_server* srv, const rt_problem_desc* desc, const rt_solver_opts* opts, uint64_t* ticket) {
+  clear_error();
+  if (!srv || !desc || !ticket) { set_error("srv, desc and ticket are required"); return RT_EINVAL; }
+  RT_TRY(validate_desc(desc));
+  if (desc->Ns > 4096) { set_error("batched instances need Ns <= 4096"); return RT_EINVAL; }
+  Server* S = &srv->S;
+  auto rq = std::make_unique<Request>();
+  rq->desc = *desc;
+  rq->tau.assign(desc->tau, desc->tau + desc->Ns);
+  rq->desc.tau = rq->tau.data();
+  if (desc->B) {
+    rq->B.assign(desc->B, desc->B + desc->Ns);
+    rq->desc.B = rq->B.data();
+  }
+  if (desc->phi) {
+    rq->phi.assign(desc->phi, desc->phi + desc->Nnu);
+    rq->desc.phi = rq->phi.data();
+  }
+  if (opts) {
+    if (!(opts->rtol > 0.0) || opts->maxit < 1) { set_error("rtol must be > 0 and maxit >= 1"); return RT_EINVAL; }
+    rq->rtol = opts->rtol;
+    rq->maxit = opts->maxit;
+  }
+  rq->t_submit = wall_ms();
+  rq->info.status = RT_EPENDING;
+  const uint64_t t = S->next_ticket.fetch_add(1);
+  rq->ticket = t;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->worker_status != RT_OK) {
+      set_error("server failed: %s", S->worker_error.c_str());
+      return S->worker_status;
+    }
+    S->pending.push_back(rq.get());
+    S->requests[t] = std::move(rq);
+  }
+  S->cv.notify_one();
+  *ticket = t;
+  return RT_OK;
+}
+
+rt_status rt_poll(rt_server* srv, uint64_t ticket, rt_solve_info* info, double* x_host) {
+  clear_error();
+  if (!srv) { set_error("srv is NULL"); return RT_EINVAL; }
+  Server* S = &srv->S;
+  std::unique_ptr<Request> done;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->requests.find(ticket);
+    if (it == S->requests.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return RT_EINVAL; }
+    if (!it->second->done) {
+      if (info) {
+        memset(info, 0, sizeof *info);
+        info->status = RT_EPENDING;
+      }
+      return RT_EPENDING;
+    }
+    done = std::move(it->second);
+    S->requests.erase(it);
+  }
+  if (info) *info = done->info;
+  if (x_host && !done->x.empty()) memcpy(x_host, done->x.data(), done->x.size() * sizeof(double));
+  return done->info.status;
+}
+
+rt_status rt_server_stats_get(rt_server* srv, rt_server_stats* out) {
+  clear_error();
+  if (!srv || !out) { set_error("srv and out are required"); return RT_EINVAL; }
+  Server* S = &srv->S;
+  memset(out, 0, sizeof *out);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->queued = (int32_t)S->pending.size();
+  }
+  out->resident = S->resident.load();
+  out->arena_in_use = (int64_t)S->arena.in_use();
+  out->arena_largest_free = (int64_t)S->arena.largest_hole();
+  out->cycles = S->cycles.load();
+  out->completed = S->completed.load();
+  return RT_OK;
+}
+
+rt_status rt_server_destroy(rt_server* srv) {
+  if (!srv) return RT_OK;
+  Server* S = &srv->S;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  drop_graph(S);
+  void* ptrs[] = {S->d_insts, S->d_status, S->d_counts, S->d_new_counts, S->d_wl_i, S->d_wl_new_i, S->d_wl_h,
+                  S->d_wl_c, S->d_wl_g64, S->d_wl_g32, S->d_wl_new_c};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (S->st) cudaStreamDestroy(S->st);
+  if (S->cap) cudaStreamDestroy(S->cap);
+  delete srv;
+  return RT_OK;
+}
+
+}  // extern "C"

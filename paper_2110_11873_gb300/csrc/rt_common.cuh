@@ -79,7 +79,16 @@ struct BicgDev {
   int half;        // BiCGSTAB converged at the half step
 };
 
+// Device memory source of a problem: NULL means cudaMalloc/cudaFree; the
+// batch server passes its arena.
+struct DevAllocator {
+  virtual ~DevAllocator() {}
+  virtual cudaError_t alloc(void** p, size_t bytes) = 0;
+  virtual void release(void* p) = 0;
+};
+
 struct Problem {
+  DevAllocator* alloc = nullptr;
   // sizes
   int Ns = 0, Nmu = 0, Nnu = 0, Nh = 0;
   int64_t nray = 0;   // Nmu*Nnu rays per Stokes parameter
@@ -144,6 +153,12 @@ rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st)
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st);
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st);
 void release_graphs(Problem* P);
+rt_status setup_device_tables(Problem* P, cudaStream_t st);
+void free_device(Problem* P);
+rt_status validate_desc(const rt_problem_desc* d);
+void host_grids(const rt_problem_desc* d, Problem& P);
+cudaError_t dev_alloc(Problem* P, void** p, size_t bytes);
+void dev_free(Problem* P, void* p);
 
 }  // namespace rt
 

@@ -26,26 +26,11 @@
 // x and y.
 #include <math.h>
 
-#include "rt_common.cuh"
+#include "rt_device.cuh"
 
 namespace rt {
 
 namespace {
-
-constexpr int kMomThreads = 256;
-constexpr int kMaxTiles = 8;     // FP32 kernel: up to 256 threads per CTA (255 registers a lane)
-constexpr int kMaxTiles64 = 8;   // FP64 kernel: up to 256 threads, so each lane may hold 255 registers
-constexpr int kRing = 8;         // prefetch depth of the FP64 formal-solver kernel (steps)
-constexpr int kRing32 = 16;      // prefetch depth of the FP32 kernel (one lane carries I and Q)
-
-enum KMode { KM_PLAIN = 0, KM_JACOBI = 1, KM_LOCAL_LAMBDA = 2, KM_RHS = 3 };
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // ------------------------------------------------------------- setup kernels
 // Step coefficients of the formal solvers, FP64, per interval i and ray r:
@@ -93,13 +78,6 @@ __global__ void k_coeffs64(const double* __restrict__ dtau, const double* __rest
     ca[t] = al;
     cb[t] = be;
   }
-}
-
-// beta* (coefficient of S_k in I_k) of ray r = m*Nnu + p at height k
-__device__ __forceinline__ double beta_star(const double* __restrict__ cb, int k, int m, int64_t r, int Ns,
-                                            int Nh, int64_t nray) {
-  if (m < Nh) return k == 0 ? 0.0 : cb[(int64_t)(k - 1) * nray + r];
-  return k == Ns - 1 ? 0.0 : cb[(int64_t)k * nray + r];
 }
 
 // 2x2 local blocks M_k = Id - J_k Lambda*_k T_k of the sigma-form and their
@@ -179,14 +157,6 @@ __global__ void k_add_local(const double* __restrict__ v, const double* __restri
   }
 }
 
-// ----------------------------------------------------------------- K1: T∘J
-// One block per height; warp w sums the direction rows m = w, w+8, ...:
-// a_m = sum_p w_p z_I(k,m,p), b_m = sum_p w_p z_Q(k,m,p) (one multiply-add
-// per element), then J00 += w_m a_m and J20 += w_m (T201_m a_m + T202_m b_m).
-// Every lane issues the loads of a whole row before it adds.  MODE:
-// KM_PLAIN z = x; KM_JACOBI z = x * dinv; KM_LOCAL_LAMBDA z = x and
-// sigma_k <- M_k^{-1} sigma_k.  TI: input vector type, TC: arithmetic type.
-constexpr int kRowChunk = 8;   // loads per lane in flight per Stokes parameter
 
 template <typename TI, typename TC, int MODE>
 __global__ void __launch_bounds__(kMomThreads) k_moments(
@@ -195,224 +165,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(
     const double* __restrict__ Minv, int Ns, int Nmu, int Nnu, TC xi, TC xiW2, TC* __restrict__ S,
     const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
-  const int k = blockIdx.x;
-  const int64_t nray = (int64_t)Nmu * Nnu;
-  const int64_t oI = (int64_t)k * nray, oQ = ((int64_t)Ns + k) * nray;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int nw = kMomThreads / 32;
-  TC j00 = 0, j20 = 0;
-  for (int m = warp; m < Nmu; m += nw) {
-    const int64_t row = (int64_t)m * Nnu;
-    TC aI = 0, aQ = 0;
-    for (int p0 = 0; p0 < Nnu; p0 += 32 * kRowChunk) {
-      TC vI[kRowChunk], vQ[kRowChunk], wv[kRowChunk];
-#pragma unroll
-      for (int c = 0; c < kRowChunk; ++c) {
-        const int p = p0 + c * 32 + lane;
-        const bool ok = p < Nnu;
-        const int64_t q = row + (ok ? p : 0);
-        vI[c] = ok ? (TC)x[oI + q] : (TC)0;
-        vQ[c] = ok ? (TC)x[oQ + q] : (TC)0;
-        wv[c] = ok ? wnu[p] : (TC)0;
-        if (MODE == KM_JACOBI && ok) {
-          vI[c] *= (TC)dinv[oI + q];
-          vQ[c] *= (TC)dinv[oQ + q];
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < kRowChunk; ++c) {
-        aI = fma(wv[c], vI[c], aI);
-        aQ = fma(wv[c], vQ[c], aQ);
-      }
-    }
-    aI = warp_sum(aI);
-    aQ = warp_sum(aQ);
-    const TC wm = wmu[m];
-    j00 = fma(wm, aI, j00);
-    j20 = fma(wm, fma(t201[m], aI, t202[m] * aQ), j20);
-  }
-  __shared__ TC red[2][nw];
-  __shared__ TC sig[2];
-  if (lane == 0) { red[0][warp] = j00; red[1][warp] = j20; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    TC a = 0, b = 0;
-    for (int w = 0; w < nw; ++w) { a += red[0][w]; b += red[1][w]; }
-    TC s0 = xi * a, s2 = xiW2 * b;
-    if (MODE == KM_LOCAL_LAMBDA) {
-      const double* Mi = Minv + 4 * k;
-      const TC u0 = (TC)Mi[0] * s0 + (TC)Mi[1] * s2;
-      const TC u2 = (TC)Mi[2] * s0 + (TC)Mi[3] * s2;
-      s0 = u0;
-      s2 = u2;
-    }
-    sig[0] = s0;
-    sig[1] = s2;
-  }
-  __syncthreads();
-  for (int m = threadIdx.x; m < Nmu; m += blockDim.x) {
-    S[(int64_t)k * Nmu + m] = sig[0] + t201[m] * sig[1];
-    S[((int64_t)Ns + k) * Nmu + m] = t202[m] * sig[1];
-  }
-}
-
-// --------------------------------------------------------------- K2: Lambda
-// FP32 step coefficients from Delta (DELO-linear: Taylor branch below 0.5)
-template <int FS>
-__device__ __forceinline__ void coeffs32(float D, float& e, float& al, float& be) {
-  if (FS == RT_FS_DELO_LINEAR) {
-    e = __expf(-D);
-    if (D < 0.5f) {
-      // beta = D/2 - D^2/6 + D^3/24 - ..., alpha = D/2 - D^2/3 + D^3/8 - ...  (9 terms)
-      float b = -1.0f / 3628800.0f, a = -9.0f / 3628800.0f;
-      b = fmaf(b, D, 1.0f / 362880.0f);  a = fmaf(a, D, 8.0f / 362880.0f);
-      b = fmaf(b, D, -1.0f / 40320.0f);  a = fmaf(a, D, -7.0f / 40320.0f);
-      b = fmaf(b, D, 1.0f / 5040.0f);    a = fmaf(a, D, 6.0f / 5040.0f);
-      b = fmaf(b, D, -1.0f / 720.0f);    a = fmaf(a, D, -5.0f / 720.0f);
-      b = fmaf(b, D, 1.0f / 120.0f);     a = fmaf(a, D, 4.0f / 120.0f);
-      b = fmaf(b, D, -1.0f / 24.0f);     a = fmaf(a, D, -3.0f / 24.0f);
-      b = fmaf(b, D, 1.0f / 6.0f);       a = fmaf(a, D, 2.0f / 6.0f);
-      b = fmaf(b, D, -0.5f);             a = fmaf(a, D, -0.5f);
-      be = -b * D;
-      al = -a * D;
-    } else {
-      const float q = __fdividef(1.0f - e, D);
-      be = 1.0f - q;
-      al = q - e;
-    }
-  } else if (FS == RT_FS_IMPLICIT_EULER) {
-    e = __frcp_rn(1.0f + D);
-    al = 0.0f;
-    be = D * e;
-  } else {
-    const float h = 0.5f * D, q = __frcp_rn(1.0f + h);
-    e = (1.0f - h) * q;
-    al = h * q;
-    be = al;
-  }
-}
-
-struct FormalArgs {
-  const void* x;          // input vector (TV)
-  const double* dinv;     // Jacobi inverse diagonal (KM_JACOBI)
-  const double* ce;       // FP64 coefficient tables [(Ns-1)][nray]
-  const double* ca;
-  const double* cb;
-  const float* dtau32;    // FP32: interval optical depths
-  const float* r32;       // FP32: per-ray scale phi_hat/|mu|
-  const void* S;          // source functions (TC) [2][Ns][Nmu]
-  void* y;                // output vector (TV)
-  int Ns, Nmu, Nnu;
-  int64_t nray, nd;       // rays per Stokes parameter, downward rays
-  int ngd;                // ray groups of downward rays
-  int ntile;              // depth tiles per group (warps per CTA)
-  double inflow_bottom;   // KM_RHS: I entering at the bottom (mu > 0)
-  const int* kstop;       // graph early exit (NULL: run)
-  int step;
-};
-
-// One lane: NS Stokes parameters (s0 .. s0+NS-1) of ray r, depth steps
-// [j0, j1) in marching order (node index j; height k = j for downward rays,
-// Ns-1-j for upward rays).  PHASE 0 composes the tile map (E, B) with zero
-// inflow; PHASE 1 sweeps from the inflow I and writes the output.
-template <typename TC, typename TV, int FS, int MODE, int PHASE, int NS, int RING>
-__device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, int64_t r, int m, bool active, int j0,
-                                      int j1, TC (&I)[NS], TC& E) {
-  const int Ns = A.Ns;
-  const int64_t nray = A.nray;
-  const int64_t plane = (int64_t)Ns * nray;
-  const TC* __restrict__ Sm = reinterpret_cast<const TC*>(A.S) + (int64_t)s0 * Ns * A.Nmu + m;
-  const int64_t sstride = (int64_t)Ns * A.Nmu;
-  const TV* __restrict__ x = reinterpret_cast<const TV*>(A.x) + (int64_t)s0 * plane;
-  TV* __restrict__ y = reinterpret_cast<TV*>(A.y) + (int64_t)s0 * plane;
-  const double* __restrict__ dinv = A.dinv + (int64_t)s0 * plane;
-  const float rs = (sizeof(TC) == 4) ? A.r32[r] : 0.0f;
-  auto height = [&](int j) { return down ? j : Ns - 1 - j; };
-  auto interval = [&](int j) { return down ? j - 1 : Ns - 1 - j; };
-  TC sp[NS];
-#pragma unroll
-  for (int q = 0; q < NS; ++q) sp[q] = Sm[q * sstride + (int64_t)height(j0 - 1) * A.Nmu];  // upwind source
-  // register ring of the next RING steps
-  TC re[RING], ra[RING], rb[RING], rsv[RING][NS], rx[RING][NS], rd[RING][NS];
-  auto load = [&](int u, int j) {
-    if (j < j1) {
-      const int k = height(j), i = interval(j);
-      if (sizeof(TC) == 8) {
-        const int64_t c = (int64_t)i * nray + r;
-        re[u] = (TC)A.ce[c];
-        ra[u] = (TC)A.ca[c];
-        rb[u] = (TC)A.cb[c];
-      } else {
-        re[u] = (TC)A.dtau32[i];   // Delta = dtau_i * r_ray; coefficients formed at use
-      }
-#pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        rsv[u][q] = Sm[q * sstride + (int64_t)k * A.Nmu];
-        if (PHASE == 1 && MODE != KM_RHS) {
-          const int64_t o = q * plane + (int64_t)k * nray + r;
-          rx[u][q] = (TC)x[o];
-          if (MODE == KM_JACOBI) rd[u][q] = (TC)dinv[o];
-        }
-      }
-    }
-  };
-  auto step = [&](int u, int j) {
-    TC e, al, be;
-    if (sizeof(TC) == 8) {
-      e = re[u];
-      al = ra[u];
-      be = rb[u];
-    } else {
-      float ef, af, bf;
-      coeffs32<FS>((float)re[u] * rs, ef, af, bf);
-      e = (TC)ef;
-      al = (TC)af;
-      be = (TC)bf;
-    }
-    if (PHASE == 0) E *= e;
-    const int64_t o = (int64_t)height(j) * nray + r;
-#pragma unroll
-    for (int q = 0; q < NS; ++q) {
-      const TC sk = rsv[u][q];
-      if (PHASE == 0) {
-        I[q] = fma(e, I[q], fma(al, sp[q], be * sk));
-      } else if (MODE == KM_LOCAL_LAMBDA) {
-        // y = (x + beta* S) - I = x - (e I_prev + alpha S_prev)
-        const TC t = fma(e, I[q], al * sp[q]);
-        if (active) y[q * plane + o] = (TV)(rx[u][q] - t);
-        I[q] = fma(be, sk, t);
-      } else {
-        I[q] = fma(e, I[q], fma(al, sp[q], be * sk));
-        if (active) {
-          if (MODE == KM_RHS) y[q * plane + o] = (TV)I[q];
-          else if (MODE == KM_JACOBI) y[q * plane + o] = (TV)(rx[u][q] * rd[u][q] - I[q]);
-          else y[q * plane + o] = (TV)(rx[u][q] - I[q]);
-        }
-      }
-      sp[q] = sk;
-    }
-  };
-#pragma unroll
-  for (int u = 0; u < RING; ++u) load(u, j0 + u);
-  int jb = j0;
-  // full rounds: every step of the round and every refill is in range, so the
-  // round is straight-line code the compiler can interleave across steps
-  for (; jb + 2 * RING <= j1; jb += RING) {
-#pragma unroll
-    for (int u = 0; u < RING; ++u) {
-      step(u, jb + u);
-      load(u, jb + u + RING);
-    }
-  }
-  for (; jb < j1; jb += RING) {
-#pragma unroll
-    for (int u = 0; u < RING; ++u) {
-      if (jb + u < j1) {
-        step(u, jb + u);
-        load(u, jb + u + RING);
-      }
-    }
-  }
+  moments_height<TI, TC, MODE>(x, dinv, wnu, wmu, t201, t202, Minv, Ns, Nmu, Nnu, xi, xiW2, S, blockIdx.x);
 }
 
 // grid: NSPLIT * ngroups CTAs (ray group g, and with NSPLIT = 2 the Stokes
@@ -501,12 +254,23 @@ inline int grid_for(int64_t n, int threads, int cap) {
 }  // namespace
 
 // --------------------------------------------------------------- host side
+cudaError_t dev_alloc(Problem* P, void** p, size_t bytes) {
+  return P->alloc ? P->alloc->alloc(p, bytes) : cudaMalloc(p, bytes);
+}
+
+void dev_free(Problem* P, void* p) {
+  if (!p) return;
+  if (P->alloc) P->alloc->release(p);
+  else cudaFree(p);
+}
+
 void free_device(Problem* P) {
-  void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wI2, P->wQ2,  P->t201d, P->t202d,
-                  P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32,  P->wI2f, P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,      P->work, P->dinv,  P->work32,
+  void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wray,   P->wI2,  P->wQ2,   P->t201d, P->t202d,
+                  P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
+                  P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
                   P->partials, P->gm,  P->bc,     P->hist};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
   P->dtau32 = P->r32 = P->wray32 = P->wI2f = P->wQ2f = P->t201f = P->t202f = P->S32 = nullptr;
   P->V = P->work = P->dinv = P->partials = P->hist = nullptr;
@@ -516,8 +280,8 @@ void free_device(Problem* P) {
 }
 
 template <typename T>
-static rt_status upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
-  RT_TRY_CUDA(cudaMalloc((void**)dst, src.size() * sizeof(T)));
+static rt_status upload(Problem* P, T** dst, const std::vector<T>& src, cudaStream_t st) {
+  RT_TRY_CUDA(dev_alloc(P, (void**)dst, src.size() * sizeof(T)));
   RT_TRY_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   return RT_OK;
 }
@@ -570,21 +334,34 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
       w0[r] = 0.5 * P->w_mu[m] * P->w_nu[p];
     }
   double *d_dtau = nullptr, *d_rs = nullptr;
-  RT_TRY(upload(&d_dtau, dtau, st));
-  RT_TRY(upload(&d_rs, rscale, st));
-  RT_TRY(upload(&P->wray, w0, st));
-  RT_TRY(upload(&P->wI2, wnu, st));   // spectral weights hat-w_p
-  RT_TRY(upload(&P->wQ2, wmu, st));   // angular weights hat-w_m
-  RT_TRY(upload(&P->t201d, P->t201, st));
-  RT_TRY(upload(&P->t202d, P->t202, st));
-  RT_TRY(upload(&P->Bd, P->B, st));
+  // the two temporaries are returned on every path (in an arena a leaked
+  // block would fragment the memory of later instances)
+  struct Temps {
+    Problem* P;
+    cudaStream_t st;
+    double** a;
+    double** b;
+    ~Temps() {
+      if (*a || *b) cudaStreamSynchronize(st);
+      dev_free(P, *a);
+      dev_free(P, *b);
+    }
+  } temps{P, st, &d_dtau, &d_rs};
+  RT_TRY(upload(P, &d_dtau, dtau, st));
+  RT_TRY(upload(P, &d_rs, rscale, st));
+  RT_TRY(upload(P, &P->wray, w0, st));
+  RT_TRY(upload(P, &P->wI2, wnu, st));   // spectral weights hat-w_p
+  RT_TRY(upload(P, &P->wQ2, wmu, st));   // angular weights hat-w_m
+  RT_TRY(upload(P, &P->t201d, P->t201, st));
+  RT_TRY(upload(P, &P->t202d, P->t202, st));
+  RT_TRY(upload(P, &P->Bd, P->B, st));
   const size_t nc = (size_t)(Ns - 1) * nray;
-  RT_TRY_CUDA(cudaMalloc((void**)&P->ce, nc * sizeof(double)));
-  RT_TRY_CUDA(cudaMalloc((void**)&P->ca, nc * sizeof(double)));
-  RT_TRY_CUDA(cudaMalloc((void**)&P->cb, nc * sizeof(double)));
-  RT_TRY_CUDA(cudaMalloc((void**)&P->Minv, (size_t)Ns * 4 * sizeof(double)));
-  RT_TRY_CUDA(cudaMalloc((void**)&P->S, (size_t)2 * Ns * Nmu * sizeof(double)));
-  RT_TRY_CUDA(cudaMalloc((void**)&P->S2, (size_t)2 * Ns * Nmu * sizeof(double)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->ce, nc * sizeof(double)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->ca, nc * sizeof(double)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->cb, nc * sizeof(double)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->Minv, (size_t)Ns * 4 * sizeof(double)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->S, (size_t)2 * Ns * Nmu * sizeof(double)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->S2, (size_t)2 * Ns * Nmu * sizeof(double)));
   k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_rs, Ns, nray, P->fs, P->ce,
                                                                          P->ca, P->cb); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
@@ -601,17 +378,15 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   for (int p = 0; p < Nnu; ++p) wI32[p] = (float)wnu[p];
   for (int m = 0; m < Nmu; ++m) wQ32[m] = (float)wmu[m];
   for (int m = 0; m < Nmu; ++m) { t201f[m] = (float)P->t201[m]; t202f[m] = (float)P->t202[m]; }
-  RT_TRY(upload(&P->dtau32, dtau32, st));
-  RT_TRY(upload(&P->r32, r32, st));
-  RT_TRY(upload(&P->wray32, w032, st));
-  RT_TRY(upload(&P->wI2f, wI32, st));
-  RT_TRY(upload(&P->wQ2f, wQ32, st));
-  RT_TRY(upload(&P->t201f, t201f, st));
-  RT_TRY(upload(&P->t202f, t202f, st));
-  RT_TRY_CUDA(cudaMalloc((void**)&P->S32, (size_t)2 * Ns * Nmu * sizeof(float)));
+  RT_TRY(upload(P, &P->dtau32, dtau32, st));
+  RT_TRY(upload(P, &P->r32, r32, st));
+  RT_TRY(upload(P, &P->wray32, w032, st));
+  RT_TRY(upload(P, &P->wI2f, wI32, st));
+  RT_TRY(upload(P, &P->wQ2f, wQ32, st));
+  RT_TRY(upload(P, &P->t201f, t201f, st));
+  RT_TRY(upload(P, &P->t202f, t202f, st));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->S32, (size_t)2 * Ns * Nmu * sizeof(float)));
   RT_TRY_CUDA(cudaStreamSynchronize(st));
-  cudaFree(d_dtau);
-  cudaFree(d_rs);
   return RT_OK;
 }
 

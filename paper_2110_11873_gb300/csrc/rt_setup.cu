@@ -128,7 +128,7 @@ static double voigt_H(double a, double x) {
 }
 
 // ------------------------------------------------------------ validation
-static rt_status validate(const rt_problem_desc* d) {
+rt_status validate_desc(const rt_problem_desc* d) {
   if (!d) { set_error("desc is NULL"); return RT_EINVAL; }
   if (d->Ns < 2) { set_error("Ns must be >= 2 (got %d)", d->Ns); return RT_EINVAL; }
   if (d->Nmu < 2 || d->Nmu % 2 || d->Nmu > 256) {
@@ -160,7 +160,7 @@ static rt_status validate(const rt_problem_desc* d) {
   return RT_OK;
 }
 
-static void host_grids(const rt_problem_desc* d, Problem& P) {
+void host_grids(const rt_problem_desc* d, Problem& P) {
   P.Ns = d->Ns; P.Nmu = d->Nmu; P.Nnu = d->Nnu; P.Nh = d->Nmu / 2;
   P.nray = (int64_t)d->Nmu * d->Nnu;
   P.N = 2 * (int64_t)d->Ns * P.nray;
@@ -225,9 +225,6 @@ static void host_grids(const rt_problem_desc* d, Problem& P) {
     P.phi_hat[p] = (d->tau_kind == RT_TAU_LINE_CENTER) ? P.phi[p] / phi_c : P.phi[p];
 }
 
-// device setup kernels (rt_operator.cu)
-rt_status setup_device_tables(Problem* P, cudaStream_t st);
-void free_device(Problem* P);
 
 }  // namespace rt
 
@@ -243,7 +240,7 @@ rt_status rt_problem_create(const rt_problem_desc* desc, void* stream, rt_proble
   clear_error();
   if (!out) { set_error("out is NULL"); return RT_EINVAL; }
   *out = nullptr;
-  RT_TRY(validate(desc));
+  RT_TRY(validate_desc(desc));
   rt_problem* pr = new (std::nothrow) rt_problem();
   if (!pr) { set_error("host allocation failed"); return RT_ENOMEM; }
   Problem& P = pr->P;

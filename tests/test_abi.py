@@ -46,8 +46,9 @@ _LAYOUT_C = r"""
 #include "rt_krylov.h"
 #define F(T, f) printf("%s.%s %zu\n", #T, #f, offsetof(T, f))
 int main(void) {
-  printf("rt_problem_desc %zu\nrt_solver_opts %zu\nrt_solve_info %zu\n",
-         sizeof(rt_problem_desc), sizeof(rt_solver_opts), sizeof(rt_solve_info));
+  printf("rt_problem_desc %zu\nrt_solver_opts %zu\nrt_solve_info %zu\nrt_server_opts %zu\n",
+         sizeof(rt_problem_desc), sizeof(rt_solver_opts), sizeof(rt_solve_info), sizeof(rt_server_opts));
+  F(rt_server_opts, precision);
   F(rt_problem_desc, tau); F(rt_problem_desc, phi_center); F(rt_problem_desc, W2);
   F(rt_problem_desc, freq_norm);
   F(rt_solver_opts, rtol); F(rt_solver_opts, resid_hist); F(rt_solver_opts, hist_cap);
@@ -64,7 +65,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                                check=True).stdout.split("\n") if line)
-    structs = {"rt_problem_desc": N.ProblemDesc, "rt_solver_opts": N.SolverOpts, "rt_solve_info": N.SolveInfo}
+    structs = {"rt_problem_desc": N.ProblemDesc, "rt_solver_opts": N.SolverOpts, "rt_solve_info": N.SolveInfo,
+               "rt_server_opts": N.ServerOpts}
     for name, cls in structs.items():
         assert int(got[name]) == C.sizeof(cls), name
     for key, val in got.items():
@@ -113,3 +115,11 @@ def test_null_arguments_are_rejected(lib):
     assert (o.restart, o.maxit, o.precond, o.rtol) == (30, 10000, N.RT_PREC_JACOBI, 1e-8)
     info = N.SolveInfo()
     assert lib.rt_solve_gmres(None, C.byref(o), None, None, C.byref(info), None) == N.RT_EINVAL
+    so = N.ServerOpts()
+    lib.rt_server_opts_default(C.byref(so))
+    assert so.max_slots == 64 and so.restart == 30
+    so.max_slots = 0
+    h = C.c_void_p()
+    assert lib.rt_server_create(C.byref(so), C.byref(h)) == N.RT_EINVAL and not h.value
+    assert lib.rt_poll(None, 1, None, None) == N.RT_EINVAL
+    assert lib.rt_server_destroy(None) == N.RT_OK

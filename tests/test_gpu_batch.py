@@ -1,0 +1,137 @@
+"""Batched uneven instances and the serving loop (rt_server_*), GPU.
+
+* every instance of a batch reaches ||b - A x||/||b|| < 1e-8 measured with the
+  oracle's FP64 operator, and lies within 1e-7 of the oracle's exact (LU)
+  solution (1e-6 with the FP32 operator inside FP64 refinement);
+* GMRES iteration counts equal those of the single-instance GPU solver
+  within 1 (same algorithm; reductions summed in a different order);
+* an instance's result is bit-identical alone and in a mix (each instance's
+  arithmetic depends only on its own data);
+* admission by memory budget: more requests than the arena holds are solved
+  as slots free up; one that cannot fit even alone fails with RT_ENOMEM.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import rt_workloads as W
+from oracle.transfer import Transfer
+from paper_2110_11873_gb300 import Server
+from paper_2110_11873_gb300 import _native as N
+
+from gpu_util import problem, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _uneven(count=6, seed=7):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        Ns = int(rng.integers(20, 60))
+        Nmu = int(rng.choice([4, 8, 16]))
+        Nnu = int(2 * rng.integers(5, 16) + 1)
+        eps = float(10 ** rng.uniform(-4, -2))
+        a = float(10 ** rng.uniform(-4, -2))
+        out.append(W.slab(Ns, Nmu, Nnu, 1e-4, 1e6, 6.0, eps=eps, a=a, Bc=float(rng.uniform(0, 1)),
+                          name=f"u{i}"))
+    return out
+
+
+def _wait(srv, tickets, timeout=120.0):
+    res = {}
+    t0 = time.time()
+    while len(res) < len(tickets):
+        for t in tickets:
+            if t not in res:
+                r = srv.poll(t)
+                if r is not None:
+                    res[t] = r
+        assert time.time() - t0 < timeout, "server did not finish"
+        time.sleep(0.002)
+    return res
+
+
+@pytest.fixture(scope="module")
+def cases():
+    ats = _uneven()
+    trs = [Transfer(a) for a in ats]
+    return ats, trs, [t.rhs_I() for t in trs], [t.exact_I() for t in trs]
+
+
+@pytest.mark.parametrize("precision,tol_exact", [("fp64", 1e-7), ("fp32_refine", 1e-6)])
+def test_batch_solutions(cases, precision, tol_exact):
+    ats, trs, bs, xs = cases
+    problem(ats[0])   # builds the library
+    srv = Server(mem_budget_bytes=1 << 30, max_slots=8, precond="local_lambda", precision=precision)
+    tickets = [srv.submit(a) for a in ats]
+    res = _wait(srv, tickets)
+    for t, at, tr, b, x_ex in zip(tickets, ats, trs, bs, xs):
+        st, info, x = res[t]
+        assert st == N.RT_OK, (at.name, info)
+        rel = np.linalg.norm(b - tr.apply_I(x)) / np.linalg.norm(b)
+        assert rel < 1e-8, (at.name, rel)
+        assert np.linalg.norm(x - x_ex) / np.linalg.norm(x_ex) < tol_exact
+        if precision == "fp64":
+            P = problem(at)
+            _, si = P.solve(to_dev(b), "gmres", restart=30, precond="local_lambda", rtol=1e-8)
+            assert abs(si.iters - info.iters) <= 1, (at.name, si.iters, info.iters)
+    srv.close()
+
+
+def test_result_is_the_same_alone_and_in_the_mix(cases):
+    ats, trs, bs, xs = cases
+    target = ats[2]
+    srv = Server(mem_budget_bytes=1 << 30, max_slots=8, precond="local_lambda")
+    (st, info_alone, x_alone), = _wait(srv, [srv.submit(target)]).values()
+    tickets = [srv.submit(a) for a in ats[:2]]
+    t_target = srv.submit(target)
+    tickets += [srv.submit(a) for a in ats[3:]]
+    res = _wait(srv, tickets + [t_target])
+    st2, info_mix, x_mix = res[t_target]
+    assert st == st2 == N.RT_OK
+    assert info_alone.iters == info_mix.iters
+    assert np.array_equal(x_alone, x_mix)
+    srv.close()
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "none"])
+def test_batch_other_preconditioners(cases, precond):
+    ats, trs, bs, xs = cases
+    srv = Server(mem_budget_bytes=1 << 30, max_slots=8, precond=precond)
+    tickets = [srv.submit(a, maxit=20000) for a in ats[:3]]
+    res = _wait(srv, tickets, timeout=300)
+    for t, tr, b in zip(tickets, trs[:3], bs[:3]):
+        st, info, x = res[t]
+        assert st == N.RT_OK, info
+        assert np.linalg.norm(b - tr.apply_I(x)) / np.linalg.norm(b) < 1e-8
+    srv.close()
+
+
+def test_admission_by_memory_budget_and_late_arrivals(cases):
+    ats, trs, bs, xs = cases
+    small = W.slab(30, 8, 21, 1e-4, 1e6, 6.0)
+    tr = Transfer(small)
+    b = tr.rhs_I()
+    # an arena that holds two such instances at a time, and more slots than that
+    srv = Server(mem_budget_bytes=6 << 20, max_slots=8, precond="local_lambda")
+    first = [srv.submit(small) for _ in range(2)]
+    time.sleep(0.01)
+    late = [srv.submit(small) for _ in range(4)]   # arrive while the first ones are resident
+    res = _wait(srv, first + late)
+    xs_ = [res[t][2] for t in first + late]
+    for st, info, x in res.values():
+        assert st == N.RT_OK, info
+        assert np.linalg.norm(b - tr.apply_I(x)) / np.linalg.norm(b) < 1e-8
+    for x in xs_[1:]:
+        assert np.array_equal(x, xs_[0])
+    st_ = srv.stats()
+    assert st_["completed"] == 6 and st_["resident"] == 0
+    assert st_["arena_in_use"] == 0 and st_["arena_largest_free"] == 6 << 20   # every block returned
+    # larger than the whole arena: rejected once nothing else is resident
+    big = W.slab(300, 16, 61, 1e-4, 1e8, 8.0)
+    t = srv.submit(big)
+    (st, info, x), = _wait(srv, [t]).values()
+    assert st == N.RT_ENOMEM
+    srv.close()
