@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--apply-reps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-deep", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -165,6 +169,97 @@ def reference_main(args, rank, world):
            "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+# ------------------------------------------------------- batching / serving
+def _drain(srv, tickets, timeout_s=600.0):
+    import time as _t
+    out = {}
+    t0 = _t.perf_counter()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = srv.poll(t, want_x=False)
+                if r is not None:
+                    out[t] = (r, _t.perf_counter())
+        if _t.perf_counter() - t0 > timeout_s:
+            raise RuntimeError("server did not finish")
+        _t.sleep(0.0005)
+    return out
+
+
+def batch_bench(W, Server, Problem, torch, count):
+    """512 seeded uneven atmospheres submitted at once to one server: FP32
+    operator inside FP64 refinement, local-Lambda preconditioner, resident
+    together (one launch per phase for all of them).  Compared with the plain
+    FP64 single-instance path on the first 16 of the same atmospheres."""
+    import time as _t
+    ats = W.batch_instances(count)
+    srv = Server(mem_budget_bytes=160 << 30, max_slots=count, precond="local_lambda", precision="fp32_refine")
+    t0 = _t.perf_counter()
+    tickets = [srv.submit(a) for a in ats]
+    res = _drain(srv, tickets)
+    wall = _t.perf_counter() - t0
+    ok = [r for (r, _) in res.values() if r[0] == 0]
+    rel = [r[1].rel_resid for r in ok]
+    its = [r[1].iters for r in ok]
+    stats = srv.stats()
+    srv.close()
+    # plain FP64 single-instance path, same atmospheres, same final residual
+    n1 = min(16, count)
+    torch.cuda.synchronize()
+    t1 = _t.perf_counter()
+    for a in ats[:n1]:
+        P = Problem(a)
+        b = P.rhs()
+        _, info = P.solve(b, "gmres", restart=30, precond="local_lambda", rtol=1e-8)
+        P.close()
+    torch.cuda.synchronize()
+    single = n1 / (_t.perf_counter() - t1)
+    return {"workload": f"{count} uneven atmospheres (splitmix64 seed 0x2110118730000001): Ns~U[50,400], "
+                        "Nnu~U{21..101} odd, Nmu in {8,16,32}, eps log-U[1e-6,1e-2], a log-U[1e-4,1e-2], "
+                        "B=1+c log10(1+tau)",
+            "precision": "FP32 operator, FP64 Arnoldi and FP64 restart residual (refinement)",
+            "solves": len(ok), "failed": count - len(ok), "wall_s": wall, "solves_per_s": len(ok) / wall,
+            "iters_mean": sum(its) / max(len(its), 1), "rel_resid_max": max(rel) if rel else None,
+            "cycles": stats["cycles"],
+            "fp64_single_instance_solves_per_s": single, "fp64_single_instance_sample": n1}
+
+
+def serve_bench(W, Server, rates, nreq):
+    """Served stream: Poisson arrivals of requests drawn like the uneven batch,
+    admitted by a 64 GB device-memory budget; per-request latency from
+    submission to completion."""
+    import time as _t
+    ats = W.batch_instances(nreq, seed=W.STREAM_SEED)
+    out = {}
+    for rate in rates:
+        arr = W.poisson_arrivals(rate, nreq)
+        srv = Server(mem_budget_bytes=64 << 30, max_slots=512, precond="local_lambda", precision="fp32_refine")
+        pending, lat, done_t = {}, [], []
+        t0 = _t.perf_counter()
+        i = 0
+        while i < nreq or pending:
+            now = _t.perf_counter() - t0
+            while i < nreq and arr[i] <= now:
+                pending[srv.submit(ats[i])] = i
+                i += 1
+            for t in list(pending):
+                r = srv.poll(t, want_x=False)
+                if r is not None:
+                    del pending[t]
+                    lat.append(r[1].t_total_ms)
+                    done_t.append(_t.perf_counter() - t0)
+            if now > 600:
+                raise RuntimeError("served stream did not finish")
+            _t.sleep(0.0002)
+        srv.close()
+        lat.sort()
+        span = max(done_t) - float(arr[0])
+        out[str(rate)] = {"offered_req_per_s": rate, "requests": nreq,
+                          "achieved_solves_per_s": nreq / span,
+                          "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+    return out
 
 
 # ------------------------------------------------------------------- main
@@ -341,6 +436,15 @@ def main():
     torch.cuda.synchronize()
     ll_solve_ms = (time.perf_counter() - tl0) * 1000 / nl
 
+    batch = None
+    if not args.no_batch:
+        from paper_2110_11873_gb300 import Server
+        batch = batch_bench(W, Server, Problem, torch, args.batch_count)
+    served = None
+    if not args.no_serve:
+        from paper_2110_11873_gb300 import Server
+        served = serve_bench(W, Server, (200, 1000, 5000), args.serve_requests)
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
@@ -356,6 +460,8 @@ def main():
             "apply_fp32": {"ms": apply32_ms, "applies_per_s": 1000.0 / apply32_ms, "alg_gbs": apply32_gbs},
             "apply_fp32_deep": deep,
             "local_lambda_solve": {"iters": li.iters, "ms": ll_solve_ms, "solves_per_s": 1000.0 / ll_solve_ms},
+            "batched": batch,
+            "served": served,
             "roofline": {"kernel": "MGS Arnoldi orthogonalisation (k_dot + 16 x k_mgs + k_norm_out, j=15)",
                          "bound": "hbm", "achieved": mgs_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": mgs_gbs / hbm_peak, "traffic": None,

@@ -114,7 +114,7 @@ def test_admission_by_memory_budget_and_late_arrivals(cases):
     small = W.slab(30, 8, 21, 1e-4, 1e6, 6.0)
     tr = Transfer(small)
     b = tr.rhs_I()
-    # an arena that holds two such instances at a time, and more slots than that
+    # an arena that holds one such instance at a time, and more slots than that
     srv = Server(mem_budget_bytes=6 << 20, max_slots=8, precond="local_lambda")
     first = [srv.submit(small) for _ in range(2)]
     time.sleep(0.01)
