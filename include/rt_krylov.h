@@ -109,8 +109,26 @@ rt_status rt_problem_grids(const rt_problem* prob, double* mu, double* w_mu, dou
 rt_status rt_apply(rt_problem* prob, const double* x_dev, double* y_dev, void* stream);
 
 /* Same operator with FP32 vectors and FP32 quadrature and formal solver
-   (coefficients recomputed in FP32 with the small-Delta series). */
+   (coefficients recomputed in FP32 with the small-Delta series).  When the
+   layout allows (Nmu*Nnu and Nmu/2*Nnu multiples of 4, x_dev 16-byte
+   aligned) the formal solver streams x through shared memory with tensor
+   copies whose waits are bounded; a wait that gives up leaves y invalid and
+   is reported by rt_problem_check.  Setting RT_NO_TMA=1 in the environment
+   before rt_problem_create selects the register-ring kernel instead; both
+   give bit-identical results. */
 rt_status rt_apply_f32(rt_problem* prob, const float* x_dev, float* y_dev, void* stream);
+
+/* Synchronises `stream` and reports RT_ETIMEOUT (then clears the condition)
+   when a bounded device-side wait of this problem's kernels gave up since the
+   last check; RT_OK otherwise.  The paper has no counterpart: it guards this
+   library's asynchronous copies.  rt_solve_gmres performs the same check
+   before it returns. */
+rt_status rt_problem_check(rt_problem* prob, void* stream);
+
+/* Which formal-solver kernel the FP32 applies of this problem use (no
+   counterpart in the paper): 1 = shared-memory tensor-copy staging, 0 = the
+   register-ring kernel, -1 for NULL.  Host only. */
+int rt_problem_formal_kernel(const rt_problem* prob);
 
 /* b = Lambda T c + t of Eq. (19): one formal solve with S_I = eps B, S_Q = 0
    and the boundary radiation.  b_dev: N doubles. */

@@ -74,6 +74,8 @@ SIGNATURES = [
     ("rt_problem_grids", C.c_int, [_P] + [C.POINTER(C.c_double)] * 6),
     ("rt_apply", C.c_int, [_P, _P, _P, _P]),
     ("rt_apply_f32", C.c_int, [_P, _P, _P, _P]),
+    ("rt_problem_check", C.c_int, [_P, _P]),
+    ("rt_problem_formal_kernel", C.c_int, [_P]),
     ("rt_rhs", C.c_int, [_P, _P, _P]),
     ("rt_jacobi_diag", C.c_int, [_P, _P, _P]),
     ("rt_precond_local_lambda", C.c_int, [_P, _P, _P, _P]),

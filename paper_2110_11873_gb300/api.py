@@ -207,6 +207,16 @@ class Problem:
                                       _stream_handle(stream)), "rt_apply_f32")
         return y
 
+    @property
+    def staged_formal(self) -> bool:
+        """True when FP32 applies use the shared-memory tensor-copy kernel."""
+        return self.lib.rt_problem_formal_kernel(self.handle) == 1
+
+    def check(self, stream=None) -> None:
+        """Raise RTError(RT_ETIMEOUT) when a bounded device wait of this
+        problem's kernels gave up since the last check (synchronises)."""
+        N.check(self.lib.rt_problem_check(self.handle, _stream_handle(stream)), "rt_problem_check")
+
     def rhs(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         b = self._vec(out)
         N.check(self.lib.rt_rhs(self.handle, C.c_void_p(b.data_ptr()), _stream_handle(stream)), "rt_rhs")

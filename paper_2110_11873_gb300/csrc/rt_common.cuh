@@ -138,6 +138,15 @@ struct Problem {
   double* hist = nullptr;     // device history
   int hist_cap_dev = 0;
   int vec_grid = 0;           // blocks of the reduction kernels
+  // fast FP32 apply (rt_tma.cu): usable for this problem, its tables, and
+  // the device flag its bounded waits set when they give up
+  int staged = 0;
+  int ntile_st = 1;            // depth tiles per ray group of the staged formal solver
+  int quad_gx = 1, quad_gy = 1, quad_hpc = 1;   // quadrature grid, heights per CTA
+  float* qw = nullptr;         // [3][nray] quadrature weights w0, w0*T201, w0*T202
+  float* St = nullptr;         // [2][Nmu][Ns] source functions, transposed
+  float* qpart = nullptr;      // [Ns][quad_gx][2] partial moments
+  int* dev_err = nullptr;
 };
 
 // operator entry points used by the solvers (all enqueue on `st`)
@@ -153,6 +162,12 @@ rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st)
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st);
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st);
 void release_graphs(Problem* P);
+// fast FP32 apply (rt_tma.cu)
+rt_status staged_setup(Problem* P, cudaStream_t st);
+bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cudaStream_t st, const int* kstop,
+                    int step, rt_status* status);
+// RT_ETIMEOUT (and clears the flag) when a bounded device wait gave up
+rt_status check_device_flag(Problem* P, cudaStream_t st);
 rt_status setup_device_tables(Problem* P, cudaStream_t st);
 void free_device(Problem* P);
 rt_status validate_desc(const rt_problem_desc* d);

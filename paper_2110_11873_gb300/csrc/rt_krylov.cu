@@ -900,6 +900,10 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
     if (hl) RT_TRY_CUDA(cudaMemcpyAsync(o->resid_hist, P->hist, hl * sizeof(double), cudaMemcpyDeviceToHost, st));
   }
   RT_TRY_CUDA(cudaStreamSynchronize(st));
+  if (o->precision == RT_PRECISION_FP32_REFINE) {
+    const rt_status f = check_device_flag(P, st);
+    if (f != RT_OK) s = f;
+  }
   if (info) {
     info->iters = iters;
     info->restarts = cycles;

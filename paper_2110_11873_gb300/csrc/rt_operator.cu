@@ -268,7 +268,7 @@ void free_device(Problem* P) {
   void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wray,   P->wI2,  P->wQ2,   P->t201d, P->t202d,
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
-                  P->partials, P->gm,  P->bc,     P->hist};
+                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->qw, P->St, P->qpart};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
@@ -277,6 +277,9 @@ void free_device(Problem* P) {
   P->work32 = nullptr;
   P->gm = nullptr;
   P->bc = nullptr;
+  P->dev_err = nullptr;
+  P->qw = P->St = P->qpart = nullptr;
+  P->staged = 0;
 }
 
 template <typename T>
@@ -386,8 +389,10 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   RT_TRY(upload(P, &P->t201f, t201f, st));
   RT_TRY(upload(P, &P->t202f, t202f, st));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->S32, (size_t)2 * Ns * Nmu * sizeof(float)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->dev_err, sizeof(int)));
+  RT_TRY_CUDA(cudaMemsetAsync(P->dev_err, 0, sizeof(int), st));
   RT_TRY_CUDA(cudaStreamSynchronize(st));
-  return RT_OK;
+  return staged_setup(P, st);
 }
 
 static FormalArgs formal_args(const Problem* P, const void* x, void* y, const void* S, int ntile, const int* kstop,
@@ -470,6 +475,8 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
 
 template <typename TV>
 static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStream_t st, const int* kstop, int step) {
+  rt_status s = RT_OK;
+  if (staged_apply32(P, x, y, sizeof(TV) == 8, mode, st, kstop, step, &s)) return s;
   const float xi = (float)P->xi, xiW2 = (float)(P->xi * P->W2);
   const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu;
   switch (mode) {

@@ -272,6 +272,14 @@ rt_status rt_problem_destroy(rt_problem* prob) {
 
 int64_t rt_problem_size(const rt_problem* prob) { return prob ? prob->P.N : -1; }
 
+rt_status rt_problem_check(rt_problem* prob, void* stream) {
+  clear_error();
+  if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
+  return check_device_flag(&prob->P, as_stream(stream));
+}
+
+int rt_problem_formal_kernel(const rt_problem* prob) { return prob ? prob->P.staged : -1; }
+
 rt_status rt_problem_grids(const rt_problem* prob, double* mu, double* w_mu, double* x,
                            double* phi, double* w_nu, double* phi_hat) {
   if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }

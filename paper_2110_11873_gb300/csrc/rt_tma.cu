@@ -1,0 +1,764 @@
+// The FP32 operator apply of single problems (sm_103a): a vectorised
+// quadrature (T then J, Eq. 11-14) and a formal solver (Eq. 9-10) whose input
+// streams through shared memory with tensor copies.
+//
+//   k_quad     partial moments.  Each thread owns four consecutive rays (one
+//              16-byte load per Stokes parameter and height) and keeps their
+//              quadrature weights in registers:  w0 = w_m w_p,
+//              w1 = w0 T201_m, w2 = w0 T202_m, so that
+//              J00_k = sum_r w0 x_I  and  J20_k = sum_r (w1 x_I + w2 x_Q).
+//              A CTA covers 1024 rays and a range of heights; warp sums are
+//              combined in a fixed order into one partial per (height, CTA
+//              column), so the result does not depend on scheduling.
+//   k_sigma    sums the partials of a height in a fixed order, forms sigma00,
+//              sigma20 (Eq. 7-8, with the local-Lambda block inverse in that
+//              mode) and writes the source functions transposed, S[s][m][k],
+//              so that a lane walking along a ray reads consecutive words.
+//   k_staged   the formal solve.  A CTA takes 32 rays of one direction sign
+//              and splits the depth into `ntile` tiles, one warp each; the
+//              depth recurrence I_k = e I_prev + alpha S_prev + beta S_k is
+//              solved as an affine scan (tile maps, chained inflows, re-sweep).
+//              In the re-sweep every warp streams its rows of x (and of the
+//              Jacobi diagonal) into a ring of shared-memory stages with
+//              cp.async.bulk.tensor, one 3D box (rays x heights x Stokes) per
+//              stage completing on an mbarrier, so the recurrence never waits
+//              on HBM.  The two Stokes parameters of a lane share the step
+//              coefficients and are updated as one packed FP32x2 operation; the
+//              two Taylor polynomials of the DELO-linear coefficients are
+//              evaluated as one packed pair as well.  The sweep direction is a
+//              template parameter, so operand offsets inside an unrolled round
+//              are compile-time constants.
+//
+// Every mbarrier wait is bounded (kWaitNs of wall time): a warp whose copy
+// does not arrive sets the problem's device error flag, waits (again
+// bounded) for its copies still in flight and returns.
+//
+// Used when the tensor-copy and vector-load alignment rules hold (x 16-byte
+// aligned, Nmu*Nnu and Nmu/2*Nnu multiples of 4); otherwise the
+// register-ring kernels of rt_operator.cu run.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "rt_device.cuh"
+
+namespace rt {
+
+namespace {
+
+#ifndef RT_STAGED_DK
+#define RT_STAGED_DK 8
+#endif
+#ifndef RT_STAGED_NST
+#define RT_STAGED_NST 2
+#endif
+#ifndef RT_STAGED_RS
+#define RT_STAGED_RS 4
+#endif
+#ifndef RT_STAGED_MAXT
+#define RT_STAGED_MAXT 16
+#endif
+#ifndef RT_STAGED_MINB
+#define RT_STAGED_MINB 2
+#endif
+#ifndef RT_STAGED_WARPS_PER_SM
+#define RT_STAGED_WARPS_PER_SM 48
+#endif
+
+constexpr int kNST = RT_STAGED_NST;            // stages per warp
+constexpr int kRS = RT_STAGED_RS;              // prefetch distance of dtau and S (steps)
+constexpr int kMaxT = RT_STAGED_MAXT;          // warps per CTA (depth tiles of a ray group)
+constexpr unsigned long long kWaitNs = 1000000000ull;   // bound of one wait
+constexpr int kQuadThreads = 256;
+constexpr int kQuadMaxHeights = 64;            // heights per CTA of k_quad
+constexpr int kQuadUnroll = 4;                 // heights in flight per thread
+
+template <typename TV, int MODE>
+struct Cfg {
+  // depth steps per stage: FP64 vectors use half the steps of FP32 ones
+  static constexpr int DK = sizeof(TV) == 4 ? RT_STAGED_DK : RT_STAGED_DK / 2;
+  static constexpr bool JAC = MODE == KM_JACOBI;
+  static constexpr int XBYTES = 2 * DK * 32 * (int)sizeof(TV);   // x box
+  static constexpr int DBYTES = JAC ? 2 * DK * 32 * 8 : 0;       // Jacobi diagonal box
+  static constexpr int STAGE = XBYTES + DBYTES;
+  static constexpr int WARP = kNST * STAGE + kNST * 8;           // stages and their barriers
+  static_assert(DK % kRS == 0, "the operand ring divides a stage");
+  static_assert(XBYTES % 128 == 0 && STAGE % 128 == 0, "tensor-copy destinations stay 128-byte aligned");
+};
+
+// Dynamic shared memory of a CTA of ntile warps: the stages of all warps
+// (each a multiple of 128 bytes, from a 128-byte aligned base), then the
+// barriers of all warps.
+constexpr size_t smem_bytes(int warp_bytes, int ntile) { return 128 + (size_t)ntile * warp_bytes; }
+static_assert(smem_bytes(Cfg<double, KM_JACOBI>::WARP, kMaxT) <= 227 * 1024, "a CTA fits the shared memory");
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for the phase of `parity` to complete; false after kWaitNs
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_wait(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ------------------------------------------------------- packed FP32 pairs
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return f2(-a.x, -a.y); }
+
+// The step coefficients of coeffs32 (same values, bit for bit): the Taylor
+// polynomials of beta and alpha run as one packed pair.
+template <int FS>
+__device__ __forceinline__ void coeffs_packed(float D, float& e, float& al, float& be) {
+  if (FS == RT_FS_DELO_LINEAR) {
+    e = __expf(-D);
+    if (D < 0.5f) {
+      const float2 DD = f2(D, D);
+      float2 ba = f2(-1.0f / 3628800.0f, -9.0f / 3628800.0f);
+      ba = fma2(ba, DD, f2(1.0f / 362880.0f, 8.0f / 362880.0f));
+      ba = fma2(ba, DD, f2(-1.0f / 40320.0f, -7.0f / 40320.0f));
+      ba = fma2(ba, DD, f2(1.0f / 5040.0f, 6.0f / 5040.0f));
+      ba = fma2(ba, DD, f2(-1.0f / 720.0f, -5.0f / 720.0f));
+      ba = fma2(ba, DD, f2(1.0f / 120.0f, 4.0f / 120.0f));
+      ba = fma2(ba, DD, f2(-1.0f / 24.0f, -3.0f / 24.0f));
+      ba = fma2(ba, DD, f2(1.0f / 6.0f, 2.0f / 6.0f));
+      ba = fma2(ba, DD, f2(-0.5f, -0.5f));
+      const float2 r = mul2(ba, f2(-D, -D));
+      be = r.x;
+      al = r.y;
+    } else {
+      const float q = __fdividef(1.0f - e, D);
+      const float2 r = add2(f2(1.0f, q), f2(-q, -e));
+      be = r.x;
+      al = r.y;
+    }
+  } else {
+    coeffs32<FS>(D, e, al, be);
+  }
+}
+
+// ---------------------------------------------------------------- k_quad
+template <typename TV>
+__device__ __forceinline__ float4 load4(const TV* p);
+template <>
+__device__ __forceinline__ float4 load4<float>(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <>
+__device__ __forceinline__ float4 load4<double>(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+template <typename TV, int MODE>
+__global__ void __launch_bounds__(kQuadThreads) k_quad(const TV* __restrict__ x, const double* __restrict__ dinv,
+                                                       const float* __restrict__ qw, int Ns, int64_t nray, int hpc,
+                                                       float* __restrict__ part, const int* kstop, int step) {
+  if (kstop && step >= *kstop) return;
+  constexpr int nw = kQuadThreads / 32;
+  __shared__ float red[kQuadMaxHeights][nw][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nc = nray / 4;
+  const int64_t c = (int64_t)blockIdx.x * kQuadThreads + threadIdx.x;
+  const bool ok = c < nc;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 w0 = ok ? __ldg(reinterpret_cast<const float4*>(qw) + c) : z;
+  const float4 w1 = ok ? __ldg(reinterpret_cast<const float4*>(qw + nray) + c) : z;
+  const float4 w2 = ok ? __ldg(reinterpret_cast<const float4*>(qw + 2 * nray) + c) : z;
+  const int k_lo = blockIdx.y * hpc, k_hi = min(Ns, k_lo + hpc);
+  const int64_t plane = (int64_t)Ns * nray;
+  for (int k = k_lo; k < k_hi; k += kQuadUnroll) {
+    float4 vI[kQuadUnroll], vQ[kQuadUnroll];
+#pragma unroll
+    for (int v = 0; v < kQuadUnroll; ++v) {
+      vI[v] = z;
+      vQ[v] = z;
+      if (ok && k + v < k_hi) {
+        const int64_t o = (int64_t)(k + v) * nray + 4 * c;
+        vI[v] = load4<TV>(x + o);
+        vQ[v] = load4<TV>(x + plane + o);
+        if (MODE == KM_JACOBI) {
+          const float4 dI = load4<double>(dinv + o), dQ = load4<double>(dinv + plane + o);
+          vI[v] = make_float4(vI[v].x * dI.x, vI[v].y * dI.y, vI[v].z * dI.z, vI[v].w * dI.w);
+          vQ[v] = make_float4(vQ[v].x * dQ.x, vQ[v].y * dQ.y, vQ[v].z * dQ.z, vQ[v].w * dQ.w);
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kQuadUnroll; ++v) {
+      float a0 = w0.x * vI[v].x;
+      a0 = fmaf(w0.y, vI[v].y, a0);
+      a0 = fmaf(w0.z, vI[v].z, a0);
+      a0 = fmaf(w0.w, vI[v].w, a0);
+      float a2 = w1.x * vI[v].x;
+      a2 = fmaf(w1.y, vI[v].y, a2);
+      a2 = fmaf(w1.z, vI[v].z, a2);
+      a2 = fmaf(w1.w, vI[v].w, a2);
+      a2 = fmaf(w2.x, vQ[v].x, a2);
+      a2 = fmaf(w2.y, vQ[v].y, a2);
+      a2 = fmaf(w2.z, vQ[v].z, a2);
+      a2 = fmaf(w2.w, vQ[v].w, a2);
+      a0 = warp_sum(a0);
+      a2 = warp_sum(a2);
+      if (lane == 0 && k + v < k_hi) {
+        red[k + v - k_lo][warp][0] = a0;
+        red[k + v - k_lo][warp][1] = a2;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k_hi - k_lo; i += kQuadThreads) {
+    float s0 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int w = 0; w < nw; ++w) {
+      s0 += red[i][w][0];
+      s2 += red[i][w][1];
+    }
+    float* o = part + ((int64_t)(k_lo + i) * gridDim.x + blockIdx.x) * 2;
+    o[0] = s0;
+    o[1] = s2;
+  }
+}
+
+// --------------------------------------------------------------- k_sigma
+// One thread per (m, k): sum the gx partials of height k in order, then
+// S_I = sigma00 + T201_m sigma20, S_Q = T202_m sigma20 into St[s][m][k].
+template <int MODE>
+__global__ void k_sigma(const float* __restrict__ part, int gx, const float* __restrict__ t201,
+                        const float* __restrict__ t202, const double* __restrict__ Minv, int Ns, int Nmu, float xi,
+                        float xiW2, float* __restrict__ St, const int* kstop, int step) {
+  if (kstop && step >= *kstop) return;
+  const int64_t n = (int64_t)Ns * Nmu;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % Ns), m = (int)(i / Ns);
+    const float* p = part + (int64_t)k * gx * 2;
+    float a = 0.f, b = 0.f;
+    for (int j = 0; j < gx; ++j) {
+      a += p[2 * j];
+      b += p[2 * j + 1];
+    }
+    float s0 = xi * a, s2 = xiW2 * b;
+    if (MODE == KM_LOCAL_LAMBDA) {
+      const double* Mi = Minv + 4 * k;
+      const float u0 = (float)Mi[0] * s0 + (float)Mi[1] * s2;
+      const float u2 = (float)Mi[2] * s0 + (float)Mi[3] * s2;
+      s0 = u0;
+      s2 = u2;
+    }
+    St[i] = s0 + t201[m] * s2;
+    St[n + i] = t202[m] * s2;
+  }
+}
+
+// -------------------------------------------------------------- k_staged
+struct StagedArgs {
+  const void* x;          // input (TV), [2][Ns][nray]
+  void* y;                // output (TV)
+  const double* dinv;     // Jacobi diagonal (KM_JACOBI)
+  const float* dtau;      // [Ns-1]
+  const float* r32;       // [nray] phi_hat / |mu|
+  const float* St;        // source functions [2][Nmu][Ns]
+  int Ns, Nmu, Nnu;
+  int64_t nray, nd;
+  int ngd, ntile;
+  const int* kstop;
+  int step;
+  int* err;
+};
+
+// tensor maps of x and of the Jacobi diagonal, split at the direction
+// boundary: [0] the nd downward rays, [1] the upward ones
+struct Maps {
+  CUtensorMap x[2];
+  CUtensorMap d[2];
+};
+
+template <bool DOWN>
+__device__ __forceinline__ constexpr int dir(int v) {
+  return DOWN ? v : -v;
+}
+
+// ring of the next kRS steps' dtau and S (both Stokes parameters)
+struct Operands {
+  const float* dt;   // dtau of the interval of the ring's first step
+  const float* sI;   // S_I at the height of the ring's first step
+  int64_t sq;        // S_Q - S_I
+  float re[kRS];
+  float2 ss[kRS];
+};
+
+template <bool DOWN>
+__device__ __forceinline__ void opload(Operands& O, int u, int ahead) {
+  O.re[u] = O.dt[dir<DOWN>(ahead)];
+  O.ss[u] = f2(O.sI[dir<DOWN>(ahead)], O.sI[O.sq + dir<DOWN>(ahead)]);
+}
+
+template <bool DOWN>
+__device__ __forceinline__ void opadvance(Operands& O) {
+  O.dt += dir<DOWN>(kRS);
+  O.sI += dir<DOWN>(kRS);
+}
+
+// phase A: map I_out = E I_in + B of n1 steps with zero inflow
+template <int FS, bool DOWN>
+__device__ __forceinline__ void tile_map(Operands O, float rsc, float2 sp, int n1, float& E, float2& B) {
+#pragma unroll
+  for (int u = 0; u < kRS; ++u)
+    if (u < n1) opload<DOWN>(O, u, u);
+  auto step = [&](int u) {
+    float e, al, be;
+    coeffs_packed<FS>(O.re[u] * rsc, e, al, be);
+    E *= e;
+    B = fma2(f2(e, e), B, fma2(f2(al, al), sp, mul2(f2(be, be), O.ss[u])));
+    sp = O.ss[u];
+  };
+  int n = 0;
+  for (; n + 2 * kRS <= n1; n += kRS) {
+#pragma unroll
+    for (int u = 0; u < kRS; ++u) {
+      step(u);
+      opload<DOWN>(O, u, u + kRS);
+    }
+    opadvance<DOWN>(O);
+  }
+  for (; n < n1; n += kRS) {
+#pragma unroll
+    for (int u = 0; u < kRS; ++u) {
+      if (n + u < n1) {
+        step(u);
+        if (n + u + kRS < n1) opload<DOWN>(O, u, u + kRS);
+      }
+    }
+    opadvance<DOWN>(O);
+  }
+}
+
+template <typename TV, int FS, int MODE, bool DOWN>
+__device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, unsigned char* dsm,
+                                            float (*sh)[kMaxT][32], int g, int t, int lane) {
+  using C = Cfg<TV, MODE>;
+  constexpr int DK = C::DK;
+  const int T = A.ntile, Ns = A.Ns;
+  const int h = DOWN ? 0 : 1;
+  const int64_t hbase = DOWN ? 0 : A.nd;
+  const int64_t hext = DOWN ? A.nd : A.nray - A.nd;
+  const int c0 = (DOWN ? g : g - A.ngd) * 32;   // first ray of the group within its half
+  const bool active = c0 + lane < hext;
+  const int64_t r = hbase + (active ? c0 + lane : hext - 1);
+  const int m = (int)(r / A.Nnu);
+  const float rsc = A.r32[r];
+  const int L = (Ns - 1 + T - 1) / T;   // steps per tile
+  const int j0 = 1 + t * L;
+  const int n1 = max(min(Ns, j0 + L) - j0, 0);
+  const int nst = (n1 + DK - 1) / DK;
+  unsigned char* wbase = dsm + (size_t)t * kNST * C::STAGE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + (size_t)T * kNST * C::STAGE) + t * kNST;
+  auto issue = [&](int q) {
+    const int slot = q % kNST;
+    const int c1 = DOWN ? j0 + q * DK : Ns - j0 - (q + 1) * DK;   // lowest height of the box
+    unsigned char* s = wbase + slot * C::STAGE;
+    mbar_expect_tx(&bar[slot], C::STAGE);
+    tma_load_3d(s, &M.x[h], c0, c1, 0, &bar[slot]);
+    if (C::JAC) tma_load_3d(s + C::XBYTES, &M.d[h], c0, c1, 0, &bar[slot]);
+  };
+  if (lane == 0 && nst > 0) {
+    for (int s = 0; s < kNST; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int q = 0; q < kNST && q < nst; ++q) issue(q);   // they land while the tile maps are composed
+  }
+  __syncwarp();
+  // operands at the tile's first step; upwind S at the node before it
+  Operands O;
+  O.sq = (int64_t)A.Nmu * Ns;
+  O.dt = A.dtau + (DOWN ? j0 - 1 : Ns - 1 - j0);
+  O.sI = A.St + (int64_t)m * Ns + (DOWN ? j0 : Ns - 1 - j0);
+  float2 sp0 = f2(0.f, 0.f);
+  if (n1 > 0) sp0 = f2(O.sI[dir<DOWN>(-1)], O.sI[O.sq + dir<DOWN>(-1)]);
+  float2 I = f2(0.f, 0.f);
+  if (T > 1) {
+    if (t < T - 1 && n1 > 0) {
+      float E = 1.f;
+      float2 B = f2(0.f, 0.f);
+      tile_map<FS, DOWN>(O, rsc, sp0, n1, E, B);
+      sh[0][t][lane] = E;
+      sh[1][t][lane] = B.x;
+      sh[2][t][lane] = B.y;
+    }
+    __syncthreads();
+    if (t == 0) {
+      float in0 = 0.f, in1 = 0.f;
+      for (int u = 0; u < T; ++u) {
+        const bool has = u < T - 1 && 1 + u * L < Ns;
+        const float E = has ? sh[0][u][lane] : 1.f;
+        const float B0 = has ? sh[1][u][lane] : 0.f, B1 = has ? sh[2][u][lane] : 0.f;
+        sh[1][u][lane] = in0;
+        sh[2][u][lane] = in1;
+        if (has) {
+          in0 = fmaf(E, in0, B0);
+          in1 = fmaf(E, in1, B1);
+        }
+      }
+    }
+    __syncthreads();
+    I = f2(sh[1][t][lane], sh[2][t][lane]);
+  }
+  const int64_t plane = (int64_t)Ns * A.nray;
+  // entry node (tile 0): zero inflow
+  if (t == 0 && active) {
+    const int64_t o = (int64_t)(DOWN ? 0 : Ns - 1) * A.nray + r;
+    const TV* x = reinterpret_cast<const TV*>(A.x);
+    TV* y = reinterpret_cast<TV*>(A.y);
+    for (int s = 0; s < 2; ++s) {
+      if (C::JAC) y[s * plane + o] = (TV)((float)x[s * plane + o] * (float)A.dinv[s * plane + o]);
+      else y[s * plane + o] = x[s * plane + o];
+    }
+  }
+  if (nst == 0) return;
+  // phase C: re-sweep from the tile's inflow, x from the staged ring
+  TV* yI = reinterpret_cast<TV*>(A.y) + (int64_t)(DOWN ? j0 : Ns - 1 - j0) * A.nray + r;
+  const int64_t dy = DOWN ? A.nray : -A.nray;
+  float2 sp = sp0;
+#pragma unroll
+  for (int u = 0; u < kRS; ++u)
+    if (u < n1) opload<DOWN>(O, u, u);
+  int qfail = -1;
+  for (int q = 0; q < nst; ++q) {
+    const int slot = q % kNST;
+    const bool ok = mbar_wait(&bar[slot], (uint32_t)((q / kNST) & 1));
+    if (!__all_sync(0xffffffffu, ok)) {
+      qfail = q;
+      break;
+    }
+    const TV* xs = reinterpret_cast<const TV*>(wbase + slot * C::STAGE);
+    const double* ds = reinterpret_cast<const double*>(wbase + slot * C::STAGE + C::XBYTES);
+    const int nb = q * DK;
+    auto step = [&](int u, bool guard) {
+      const int ru = u % kRS;
+      const int row = DOWN ? u : DK - 1 - u;   // the box runs up in height
+      float e, al, be;
+      coeffs_packed<FS>(O.re[ru] * rsc, e, al, be);
+      const float2 xv = f2((float)xs[row * 32 + lane], (float)xs[(DK + row) * 32 + lane]);
+      const float2 ss = O.ss[ru];
+      float2 yv;
+      if (MODE == KM_LOCAL_LAMBDA) {
+        const float2 tt = fma2(f2(e, e), I, mul2(f2(al, al), sp));
+        yv = add2(xv, neg2(tt));
+        I = fma2(f2(be, be), ss, tt);
+      } else {
+        I = fma2(f2(e, e), I, fma2(f2(al, al), sp, mul2(f2(be, be), ss)));
+        if (MODE == KM_JACOBI) {
+          const float2 dv = f2((float)ds[row * 32 + lane], (float)ds[(DK + row) * 32 + lane]);
+          yv = fma2(xv, dv, neg2(I));
+        } else {
+          yv = add2(xv, neg2(I));
+        }
+      }
+      sp = ss;
+      if (active) {
+        yI[0] = (TV)yv.x;
+        yI[plane] = (TV)yv.y;
+      }
+      yI += dy;
+      // refill this ring slot with the operands kRS steps ahead
+      if (!guard || nb + u + kRS < n1) opload<DOWN>(O, ru, kRS + ru);
+      if (ru == kRS - 1) opadvance<DOWN>(O);
+    };
+    if (nb + DK + kRS <= n1) {
+#pragma unroll
+      for (int u = 0; u < DK; ++u) step(u, false);
+    } else {
+#pragma unroll
+      for (int u = 0; u < DK; ++u)
+        if (nb + u < n1) step(u, true);
+    }
+    __syncwarp();
+    if (lane == 0 && q + kNST < nst) {
+      // the warp's reads of this slot come before the copy that overwrites it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(q + kNST);
+    }
+    __syncwarp();
+  }
+  if (qfail >= 0) {
+    // a copy did not arrive: flag it and wait (bounded) for the copies
+    // still in flight before the CTA's shared memory is released
+    if (lane == 0) atomicExch(A.err, 1);
+    const int last = min(nst, qfail + kNST);
+    for (int q = qfail; q < last; ++q) mbar_wait(&bar[q % kNST], (uint32_t)((q / kNST) & 1));
+  }
+}
+
+template <typename TV, int FS, int MODE>
+__global__ void __launch_bounds__(32 * kMaxT, RT_STAGED_MINB)
+    k_staged(const StagedArgs A, const __grid_constant__ Maps M) {
+  if (A.kstop && A.step >= *A.kstop) return;
+  extern __shared__ unsigned char dsm_raw[];
+  unsigned char* dsm = dsm_raw + ((128 - (smem_u32(dsm_raw) & 127)) & 127);   // 128-byte aligned stages
+  __shared__ float sh[3][kMaxT][32];   // per tile: E and B, then the tile's inflow
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const int g = blockIdx.x;
+  if (g < A.ngd) staged_body<TV, FS, MODE, true>(A, M, dsm, sh, g, t, lane);
+  else staged_body<TV, FS, MODE, false>(A, M, dsm, sh, g, t, lane);
+}
+
+// ---------------------------------------------------------------- host
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode;
+}
+
+template <typename TV, int MODE>
+cudaError_t set_smem_attr() {
+  const int b = (int)smem_bytes(Cfg<TV, MODE>::WARP, kMaxT);
+  cudaError_t e = cudaFuncSetAttribute(k_staged<TV, RT_FS_DELO_LINEAR, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_staged<TV, RT_FS_IMPLICIT_EULER, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_staged<TV, RT_FS_TRAPEZOIDAL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
+}
+
+// 3D tensor map over one direction half of a [2][Ns][nray] vector
+bool encode_half(CUtensorMap* tm, const void* base, int64_t first_ray, int64_t nrays, const Problem* P, bool f64,
+                 int dk) {
+  const cuuint64_t es = f64 ? 8 : 4;
+  const cuuint64_t dims[3] = {(cuuint64_t)nrays, (cuuint64_t)P->Ns, 2};
+  const cuuint64_t strides[2] = {(cuuint64_t)P->nray * es, (cuuint64_t)P->nray * P->Ns * es};
+  const cuuint32_t box[3] = {32, (cuuint32_t)dk, 2};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  void* addr = const_cast<char*>(static_cast<const char*>(base)) + first_ray * es;
+  return encoder()(tm, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, addr, dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename TV, int MODE>
+void launch_staged(const Problem* P, const StagedArgs& A, const Maps& M, cudaStream_t st) {
+  const dim3 grid(P->ngroups), block(32 * P->ntile_st);
+  const size_t sm = smem_bytes(Cfg<TV, MODE>::WARP, P->ntile_st);
+  switch (P->fs) {
+    case RT_FS_DELO_LINEAR:
+      k_staged<TV, RT_FS_DELO_LINEAR, MODE><<<grid, block, sm, st>>>(A, M); RT_COUNT(1);
+      break;
+    case RT_FS_IMPLICIT_EULER:
+      k_staged<TV, RT_FS_IMPLICIT_EULER, MODE><<<grid, block, sm, st>>>(A, M); RT_COUNT(1);
+      break;
+    default:
+      k_staged<TV, RT_FS_TRAPEZOIDAL, MODE><<<grid, block, sm, st>>>(A, M); RT_COUNT(1);
+  }
+}
+
+template <typename TV, int MODE>
+rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step) {
+  constexpr bool f64 = sizeof(TV) == 8;
+  Maps M;
+  memset(&M, 0, sizeof M);
+  const int dk = Cfg<TV, MODE>::DK;
+  if (!encode_half(&M.x[0], x, 0, P->nd, P, f64, dk) || !encode_half(&M.x[1], x, P->nd, P->nray - P->nd, P, f64, dk)) {
+    set_error("cuTensorMapEncodeTiled failed for the FP32 apply");
+    return RT_ECUDA;
+  }
+  if (MODE == KM_JACOBI && (!encode_half(&M.d[0], P->dinv, 0, P->nd, P, true, dk) ||
+                            !encode_half(&M.d[1], P->dinv, P->nd, P->nray - P->nd, P, true, dk))) {
+    set_error("cuTensorMapEncodeTiled failed for the Jacobi diagonal");
+    return RT_ECUDA;
+  }
+  const float xi = (float)P->xi, xiW2 = (float)(P->xi * P->W2);
+  k_quad<TV, MODE><<<dim3(P->quad_gx, P->quad_gy), kQuadThreads, 0, st>>>(x, P->dinv, P->qw, P->Ns, P->nray,
+                                                                          P->quad_hpc, P->qpart, kstop, step);
+  RT_COUNT(1);
+  const int64_t nsig = (int64_t)P->Ns * P->Nmu;
+  const int gs = (int)std::min<int64_t>((nsig + 255) / 256, 4LL * P->num_sms);
+  k_sigma<MODE == KM_LOCAL_LAMBDA ? KM_LOCAL_LAMBDA : KM_PLAIN><<<gs, 256, 0, st>>>(
+      P->qpart, P->quad_gx, P->t201f, P->t202f, P->Minv, P->Ns, P->Nmu, xi, xiW2, P->St, kstop, step);
+  RT_COUNT(1);
+  StagedArgs A;
+  A.x = x;
+  A.y = y;
+  A.dinv = P->dinv;
+  A.dtau = P->dtau32;
+  A.r32 = P->r32;
+  A.St = P->St;
+  A.Ns = P->Ns;
+  A.Nmu = P->Nmu;
+  A.Nnu = P->Nnu;
+  A.nray = P->nray;
+  A.nd = P->nd;
+  A.ngd = P->ngroups / 2;
+  A.ntile = P->ntile_st;
+  A.kstop = kstop;
+  A.step = step;
+  A.err = P->dev_err;
+  launch_staged<TV, MODE>(P, A, M, st);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+// depth tiles of the staged kernel: about RT_STAGED_WARPS_PER_SM warps per
+// SM, tiles of at least two stages
+int choose_tiles_staged(const Problem* P) {
+  const int64_t want = ((int64_t)RT_STAGED_WARPS_PER_SM * P->num_sms + P->ngroups - 1) / P->ngroups;
+  int T = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxT, want));
+  while (T > 1 && (P->Ns - 1) / T < 2 * RT_STAGED_DK) --T;
+  return T;
+}
+
+}  // namespace
+
+// Prepares the fast FP32 apply of a single problem: quadrature weights,
+// transposed source functions, partial sums, the tile count, the kernels'
+// shared-memory opt-in.  Leaves it off (P->staged = 0) when the layout does
+// not allow the vector loads and tensor copies, when the problem lives in a
+// batch arena, or when RT_NO_TMA=1 is set in the environment.
+rt_status staged_setup(Problem* P, cudaStream_t st) {
+  P->staged = 0;
+  if (P->alloc) return RT_OK;
+  const char* off = std::getenv("RT_NO_TMA");
+  if (off && off[0] && off[0] != '0') return RT_OK;
+  if ((P->nray % 4) || (P->nd % 4) || !P->dev_err) return RT_OK;
+  if (P->Ns > (1 << 24) || P->nray > (1LL << 30)) return RT_OK;
+  if (!encoder()) return RT_OK;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = set_smem_attr<float, KM_PLAIN>();
+    if (attr == cudaSuccess) attr = set_smem_attr<double, KM_PLAIN>();
+    if (attr == cudaSuccess) attr = set_smem_attr<double, KM_JACOBI>();
+    if (attr == cudaSuccess) attr = set_smem_attr<double, KM_LOCAL_LAMBDA>();
+  });
+  if (attr != cudaSuccess) {
+    cudaGetLastError();
+    return RT_OK;
+  }
+  const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu;
+  const int64_t nray = P->nray;
+  // quadrature weights w0 = w_m w_p, w1 = w0 T201_m, w2 = w0 T202_m (the hat weights of Eq. 11-14)
+  std::vector<float> qw(3 * nray);
+  for (int m = 0; m < Nmu; ++m)
+    for (int p = 0; p < Nnu; ++p) {
+      const int64_t r = (int64_t)m * Nnu + p;
+      const double w0 = 0.5 * P->w_mu[m] * P->w_nu[p];
+      qw[r] = (float)w0;
+      qw[nray + r] = (float)(w0 * P->t201[m]);
+      qw[2 * nray + r] = (float)(w0 * P->t202[m]);
+    }
+  const int64_t nc = nray / 4;
+  P->quad_gx = (int)((nc + kQuadThreads - 1) / kQuadThreads);
+  const int64_t target = 8LL * P->num_sms;   // CTAs of k_quad
+  const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(Ns, target / P->quad_gx));
+  P->quad_hpc = std::min((Ns + gy - 1) / gy, kQuadMaxHeights);
+  P->quad_gy = (Ns + P->quad_hpc - 1) / P->quad_hpc;
+  P->ntile_st = choose_tiles_staged(P);
+#ifdef RT_EXPERIMENT
+  if (const char* t = std::getenv("RT_STAGED_TILES")) P->ntile_st = std::min(kMaxT, std::max(1, std::atoi(t)));
+#endif
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->qw, qw.size() * sizeof(float)));
+  RT_TRY_CUDA(cudaMemcpyAsync(P->qw, qw.data(), qw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->St, (size_t)2 * Ns * Nmu * sizeof(float)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->qpart, (size_t)Ns * P->quad_gx * 2 * sizeof(float)));
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  P->staged = 1;
+  return RT_OK;
+}
+
+// The whole FP32 apply (quadrature, source functions, formal solve) through
+// the kernels above, for FP32 vectors or, with f64io, FP64 vectors; false
+// when they do not apply (nothing launched, *status untouched).
+bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cudaStream_t st, const int* kstop,
+                    int step, rt_status* status) {
+  if (!P->staged || (reinterpret_cast<uintptr_t>(x) & 15)) return false;
+  if (!f64io) {
+    if (mode != AM_PLAIN) return false;
+    *status = staged_apply<float, KM_PLAIN>(P, static_cast<const float*>(x), static_cast<float*>(y), st, kstop, step);
+    return true;
+  }
+  const double* xd = static_cast<const double*>(x);
+  double* yd = static_cast<double*>(y);
+  switch (mode) {
+    case AM_PLAIN:
+      *status = staged_apply<double, KM_PLAIN>(P, xd, yd, st, kstop, step);
+      return true;
+    case AM_JACOBI:
+      if (reinterpret_cast<uintptr_t>(P->dinv) & 15) return false;
+      *status = staged_apply<double, KM_JACOBI>(P, xd, yd, st, kstop, step);
+      return true;
+    case AM_LOCAL_LAMBDA:
+      *status = staged_apply<double, KM_LOCAL_LAMBDA>(P, xd, yd, st, kstop, step);
+      return true;
+    default:
+      return false;
+  }
+}
+
+rt_status check_device_flag(Problem* P, cudaStream_t st) {
+  if (!P->dev_err) return RT_OK;
+  int h = 0;
+  RT_TRY_CUDA(cudaMemcpyAsync(&h, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  if (!h) return RT_OK;
+  RT_TRY_CUDA(cudaMemsetAsync(P->dev_err, 0, sizeof(int), st));
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  set_error("a device-side wait for a tensor copy gave up; results of the affected applies are invalid");
+  return RT_ETIMEOUT;
+}
+
+}  // namespace rt

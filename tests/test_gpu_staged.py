@@ -1,0 +1,111 @@
+"""The fast FP32 apply: vectorised quadrature and the formal solver with
+tensor-copy staging of x (GPU).
+
+Checked against the oracle's FP64 operator at 2e-5 relative to the largest
+entry (the bound of every FP32 apply), and against the register-ring FP32
+kernels (selected by RT_NO_TMA=1) at 2e-6: the two paths sum the quadrature
+in different orders, so they agree to FP32 rounding, not bit for bit.
+Shapes cover partial ray groups (Nmu/2*Nnu not a multiple of 32), depth tiles
+that end inside a stage, boxes that start below height 0 or end above Ns-1
+(zero-filled rows), the minimal Ns = 2, the three formal solvers, a layout
+the tensor copies cannot serve and an input that is not 16-byte aligned (the
+register kernels run), and the FP32-REFINE solvers, whose FP64-vector applies
+(no preconditioner, Jacobi, local Lambda) run inside captured graphs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import rt_workloads as W
+from oracle.transfer import Transfer
+
+from gpu_util import assert_close_scaled, problem, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-5
+TOL_PATHS = 2e-6
+
+SHAPES = [
+    ("ragged-37x8x10", W.slab(37, 8, 10, 1e-4, 1e6, 6.0, Bc=0.3, eps=1e-3)),
+    ("ns2-4x2", W.slab(2, 4, 2, 1e-2, 1e2, 3.0)),
+    ("ns19-16x6-euler", W.slab(19, 16, 6, 1e-3, 1e4, 5.0, eps=1e-2).with_(formal_solver=W.FS_IMPLICIT_EULER)),
+    ("ns53-8x12-trap", W.slab(53, 8, 12, 1e-3, 1e4, 5.0).with_(formal_solver=W.FS_TRAPEZOIDAL)),
+    ("slab70", W.slab70()),
+    ("paper-140", W.paper(140)),
+    ("slab300", W.slab300()),
+]
+
+
+def _pair(at, monkeypatch):
+    staged = problem(at)
+    monkeypatch.setenv("RT_NO_TMA", "1")
+    ring = problem(at)
+    monkeypatch.delenv("RT_NO_TMA")
+    assert staged.staged_formal and not ring.staged_formal
+    return staged, ring
+
+
+@pytest.mark.parametrize("name,at", SHAPES, ids=[s[0] for s in SHAPES])
+def test_staged_apply_matches_the_oracle_and_the_register_path(name, at, monkeypatch):
+    staged, ring = _pair(at, monkeypatch)
+    tr = Transfer(at)
+    x = W.random_vector(tr.N, 23)
+    xd = to_dev(x, torch.float32)
+    ys = staged.apply_f32(xd)
+    yr = ring.apply_f32(xd)
+    staged.check()
+    ys_h = to_host(ys)
+    assert_close_scaled(ys_h, tr.apply_I(x.astype(np.float32).astype(np.float64)), TOL32, name)
+    assert_close_scaled(ys_h, to_host(yr), TOL_PATHS, name + " vs register path")
+
+
+def test_deep_atmosphere_matches_the_register_path(monkeypatch):
+    at = W.sweep(1000)
+    staged, ring = _pair(at, monkeypatch)
+    x = torch.rand(staged.N, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(5))
+    ys = staged.apply_f32(x)
+    yr = ring.apply_f32(x)
+    staged.check()
+    assert_close_scaled(to_host(ys), to_host(yr), TOL_PATHS, "sweep1000")
+
+
+def test_layout_the_copies_cannot_serve_uses_the_register_kernels():
+    at = W.slab(20, 4, 3, 1e-3, 1e3, 4.0)   # Nmu/2*Nnu = 6: ray groups not 16-byte aligned
+    P = problem(at)
+    assert not P.staged_formal
+    tr = Transfer(at)
+    x = W.random_vector(tr.N, 3)
+    y = to_host(P.apply_f32(to_dev(x, torch.float32)))
+    assert_close_scaled(y, tr.apply_I(x.astype(np.float32).astype(np.float64)), TOL32, "unaligned layout")
+
+
+def test_unaligned_input_takes_the_register_kernels(monkeypatch):
+    at = W.slab70()
+    staged, ring = _pair(at, monkeypatch)
+    buf = torch.rand(staged.N + 1, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(9))
+    x = buf[1:]   # 4 bytes past a 16-byte boundary
+    assert x.data_ptr() % 16 != 0
+    assert torch.equal(staged.apply_f32(x), ring.apply_f32(x.clone()))
+    staged.check()
+
+
+@pytest.mark.parametrize("precond", ["none", "jacobi", "local_lambda"])
+def test_fp32_refine_solves_through_the_staged_kernels(precond, monkeypatch):
+    at = W.slab70()
+    staged, ring = _pair(at, monkeypatch)
+    tr = Transfer(at)
+    b_h = tr.rhs_I()
+    x_ex = tr.exact_I()
+    b = to_dev(b_h)
+    iters = {}
+    for name, P in (("staged", staged), ("ring", ring)):
+        x, res = P.solve(b, "gmres", restart=30, precond=precond, precision="fp32_refine", rtol=1e-8, maxit=20000)
+        assert res.status == 0, (name, res)
+        xh = to_host(x)
+        assert np.linalg.norm(b_h - tr.apply_I(xh)) / np.linalg.norm(b_h) < 1e-8, name
+        if precond == "local_lambda":   # well conditioned: the residual bounds the error
+            assert np.linalg.norm(xh - x_ex) / np.linalg.norm(x_ex) < 1e-6, name
+        iters[name] = res.iters
+    # same algorithm, FP32 sums in a different order
+    assert abs(iters["staged"] - iters["ring"]) <= max(2, iters["ring"] // 10), iters
