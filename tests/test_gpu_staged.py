@@ -3,8 +3,9 @@ tensor-copy staging of x (GPU).
 
 Checked against the oracle's FP64 operator at 2e-5 relative to the largest
 entry (the bound of every FP32 apply), and against the register-ring FP32
-kernels (selected by RT_NO_TMA=1) at 2e-6: the two paths sum the quadrature
-in different orders, so they agree to FP32 rounding, not bit for bit.
+kernels (selected by RT_NO_TMA=1) at 1e-5: the two paths sum the quadrature
+in different orders and split the depth scan into different tiles, so they
+agree to FP32 rounding accumulated along the rays, not bit for bit.
 Shapes cover partial ray groups (Nmu/2*Nnu not a multiple of 32), depth tiles
 that end inside a stage, boxes that start below height 0 or end above Ns-1
 (zero-filled rows), the minimal Ns = 2, the three formal solvers, a layout
@@ -24,7 +25,7 @@ from gpu_util import assert_close_scaled, problem, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 TOL32 = 2e-5
-TOL_PATHS = 2e-6
+TOL_PATHS = 1e-5
 
 SHAPES = [
     ("ragged-37x8x10", W.slab(37, 8, 10, 1e-4, 1e6, 6.0, Bc=0.3, eps=1e-3)),
