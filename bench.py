@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "operator applies/s & HBM GB/s; batched solves/s at resid 1e-8; p50/p99 latency"
+FP64_PEAK_TFLOPS = 1.25   # 2 FLOP x 2 FP64 lanes/clk/SM x 152 SMs x 2.06 GHz
 WORKLOAD = "slab300: Ns=300 Nmu=32 Nnu=101 (1,939,200 unknowns), line-centre tau 1e-4..1e8, x in [-8,8], " \
            "eps=1e-4 a=1e-3 W2=1, DELO-linear; Jacobi-GMRES(30) to 1e-8"
 
@@ -46,11 +47,47 @@ def parse():
     ap.add_argument("--apply-reps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-deep", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--probe", choices=["apply32", "apply64", "gmres32", "gmres64"],
+                    help="run only a short sequence of one operation (the target of ncu captures) and exit")
+    ap.add_argument("--probe-ns", type=int, default=1000, help="N_s of the sweep atmosphere (300: slab300)")
+    ap.add_argument("--probe-reps", type=int, default=4)
     return ap.parse_args()
+
+
+def probe_main(args):
+    """A few operations on one atmosphere, for profilers: FP32 / FP64 applies
+    (apply32, apply64) or one Jacobi-GMRES(30) solve (gmres32: FP32 operator
+    with FP64 refinement, gmres64: FP64), 60 iterations at most."""
+    import torch
+
+    import rt_workloads as W
+    from paper_2110_11873_gb300 import Problem
+    from paper_2110_11873_gb300 import build as B
+
+    B.build()
+    at = W.slab300() if args.probe_ns == 300 else W.sweep(args.probe_ns)
+    P = Problem(at)
+    if args.probe.startswith("apply"):
+        dt = torch.float32 if args.probe == "apply32" else torch.float64
+        x = torch.rand(P.N, dtype=dt, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+        y = torch.empty_like(x)
+        for _ in range(args.probe_reps):
+            (P.apply_f32 if args.probe == "apply32" else P.apply)(x, out=y)
+    else:
+        b = P.rhs()
+        for _ in range(args.probe_reps):
+            P.solve(b, "gmres", restart=30, precond="jacobi", rtol=1e-8, maxit=60,
+                    precision="fp32_refine" if args.probe == "gmres32" else "fp64")
+    torch.cuda.synchronize()
+    P.check()
+    print(json.dumps({"probe": args.probe, "ns": args.probe_ns, "reps": args.probe_reps, "N": P.N,
+                      "staged": P.staged_formal}))
+    P.close()
 
 
 # ----------------------------------------------------------------- clocks
@@ -272,6 +309,9 @@ def main():
     if world > 1:
         import torch.distributed as dist_mod
         dist = dist_mod
+    if args.probe:
+        probe_main(args)
+        return
     if args.impl == "reference":
         if dist is not None:
             import torch
@@ -369,16 +409,21 @@ def main():
         torch.cuda.synchronize()
         return statistics.mean(a.elapsed_time(b_) for a, b_ in evs)
 
-    # ---- dominant kernel of the step: the MGS Arnoldi orthogonalisation
-    # (k_dot + (j+1) k_mgs + k_norm_out launches of rt_arnoldi_mgs), at the
+    # ---- dominant kernels of the step: the block-MGS Arnoldi orthogonalisation
+    # (k_bdot + 4 x k_bmgs + k_bnorm + k_gram_fold of rt_arnoldi_bmgs), at the
     # mean Arnoldi index j = 15 of a GMRES(30) cycle; the 17-vector basis
-    # (264 MB) is larger than L2
+    # (264 MB) is larger than L2.  FP64-pipe bound on this GPU: algorithmic
+    # work per step = the MGS loop's 2(j+1) FMA + 1 FMA (norm) + 1 multiply
+    # per element, 2 FLOP per FMA.
     jm = 15
     V = torch.randn((jm + 2) * N, dtype=torch.float64, device="cuda")
     w = torch.randn(N, dtype=torch.float64, device="cuda")
+    gram = torch.zeros((jm + 2) * 4, dtype=torch.float64, device="cuda")
     hbuf = torch.empty(jm + 2, dtype=torch.float64, device="cuda")
-    mgs_ms = timed(lambda: P.arnoldi_mgs(V, jm, w, hbuf), 20, False)
-    mgs_bytes = (4 * jm + 7) * N * 8
+    mgs_ms = timed(lambda: P.arnoldi_bmgs(V, jm, w, gram, hbuf), 20, False)
+    mgs_flop = (2 * (2 * (jm + 1) + 1) + 1) * N
+    mgs_tflops = mgs_flop / (mgs_ms * 1e-3) / 1e12
+    mgs_bytes = (2 * (jm + 1) + 6) * N * 8   # each basis vector read twice, w read/written per pass, v_{j+1} written
     mgs_gbs = mgs_bytes / (mgs_ms * 1e-3) / 1e9
     del V
 
@@ -400,8 +445,14 @@ def main():
         yd = torch.empty_like(xd)
         deep_ms = timed(lambda: Pd.apply_f32(xd, out=yd), 20, True)
         deep = {"workload": "sweep: Ns=2000 Nmu=64 Nnu=201 (51,456,000 unknowns), FP32 operator",
-                "ms": deep_ms, "alg_gbs": 2 * Pd.N * 4 / (deep_ms * 1e-3) / 1e9}
+                "kernels": "k_quad + k_sigma + k_staged (TMA-staged formal solver)" if Pd.staged_formal
+                else "k_moments + k_formal",
+                "ms": deep_ms, "alg_gbs": 2 * Pd.N * 4 / (deep_ms * 1e-3) / 1e9,
+                "two_pass_gbs": 3 * Pd.N * 4 / (deep_ms * 1e-3) / 1e9,
+                "note": "alg_gbs counts x read + y written (2*N*4 B); two_pass_gbs adds the quadrature's read of x "
+                        "(3*N*4 B), the traffic of the two-kernel design (x does not fit in L2)"}
         deep["frac_of_hbm"] = deep["alg_gbs"] / hbm_peak
+        deep["two_pass_frac_of_hbm"] = deep["two_pass_gbs"] / hbm_peak
         del xd, yd
         Pd.close()
 
@@ -436,6 +487,39 @@ def main():
     torch.cuda.synchronize()
     ll_solve_ms = (time.perf_counter() - tl0) * 1000 / nl
 
+    # ---- FP32 operator inside FP64 refinement on the same atmosphere
+    refine = {}
+    for pc in ("jacobi", "local_lambda"):
+        P.solve(b, "gmres", x=x, restart=30, precond=pc, rtol=1e-8, precision="fp32_refine")
+        torch.cuda.synchronize()
+        t0r = time.perf_counter()
+        _, ri = P.solve(b, "gmres", x=x, restart=30, precond=pc, rtol=1e-8, precision="fp32_refine")
+        torch.cuda.synchronize()
+        refine[pc] = {"iters": ri.iters, "refine_steps": ri.refine_steps, "rel_resid": ri.rel_resid,
+                      "ms": (time.perf_counter() - t0r) * 1000}
+
+    # ---- size sweep: Jacobi-GMRES(30), FP32 operator with FP64 Arnoldi and refinement
+    sweep = None
+    if not args.no_sweep:
+        sweep = []
+        for ns in (500, 2000):
+            Ps = Problem(W.sweep(ns))
+            bs = Ps.rhs()
+            torch.cuda.synchronize()
+            t0s = time.perf_counter()
+            _, si = Ps.solve(bs, "gmres", restart=30, precond="jacobi", rtol=1e-8, precision="fp32_refine",
+                             maxit=20000)
+            torch.cuda.synchronize()
+            solve_ms = (time.perf_counter() - t0s) * 1000
+            xs = torch.randn(Ps.N, dtype=torch.float32, device="cuda")
+            ys = torch.empty_like(xs)
+            ams = timed(lambda: Ps.apply_f32(xs, out=ys), 10, True)
+            sweep.append({"Ns": ns, "N": Ps.N, "iters": si.iters, "refine_steps": si.refine_steps,
+                          "rel_resid": si.rel_resid, "status": si.status, "solve_ms": solve_ms,
+                          "apply_fp32_ms": ams, "apply_alg_gbs": 2 * Ps.N * 4 / (ams * 1e-3) / 1e9})
+            del xs, ys, bs
+            Ps.close()
+
     batch = None
     if not args.no_batch:
         from paper_2110_11873_gb300 import Server
@@ -460,13 +544,18 @@ def main():
             "apply_fp32": {"ms": apply32_ms, "applies_per_s": 1000.0 / apply32_ms, "alg_gbs": apply32_gbs},
             "apply_fp32_deep": deep,
             "local_lambda_solve": {"iters": li.iters, "ms": ll_solve_ms, "solves_per_s": 1000.0 / ll_solve_ms},
+            "fp32_refine_solve": refine,
+            "size_sweep": sweep,
             "batched": batch,
             "served": served,
-            "roofline": {"kernel": "MGS Arnoldi orthogonalisation (k_dot + 16 x k_mgs + k_norm_out, j=15)",
-                         "bound": "hbm", "achieved": mgs_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": mgs_gbs / hbm_peak, "traffic": None,
-                         "note": "of measured hbm_gbs; algorithmic bytes (4j+7)*N*8 per step, "
-                                 "burst peak (kernel timed alone)"},
+            "roofline": {"kernel": "block-MGS Arnoldi step (k_bdot + 4 x k_bmgs + k_bnorm + k_gram_fold, j=15)",
+                         "bound": "alu", "achieved": mgs_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": mgs_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                         "hbm_gbs": mgs_gbs, "hbm_frac": mgs_gbs / hbm_peak,
+                         "note": "FP64-pipe bound: peak = 2 FLOP x 2 FP64 lanes/clk/SM x 152 SMs x 2.06 GHz "
+                                 "(the 1.25 TFLOP/s FP64 rate of this GPU); algorithmic FLOP per step "
+                                 "(2(2(j+1)+1)+1)*N of the MGS loop; hbm_gbs counts (2(j+1)+6)*N*8 bytes "
+                                 "against the measured copy bandwidth"},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": "applies/s", "h2d_bytes_per_step": N * 8,
                     "d2h_bytes_per_step": N * 8},

@@ -156,6 +156,22 @@ rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double*
    Reductions are deterministic (fixed block partials, fixed summation order). */
 rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* h_dev, void* stream);
 
+/* One Arnoldi step by block modified Gram-Schmidt, the orthogonalisation
+   inside rt_solve_gmres (Sect. 2.1; the coefficients of rt_arnoldi_mgs in
+   exact arithmetic).  The basis is taken in blocks of RT_GRAM_BLOCK vectors:
+   with r_k = <w, v_k> formed before a block's updates, modified Gram-Schmidt
+   gives h_k = r_k - sum_{l<k} h_l <v_l, v_k> (l, k in the block), so one pass
+   over the data applies a whole block and forms the dots with the next one.
+   The paper has no block form; it is a reformulation of its MGS loop with the
+   same FP64 operations per element and a quarter of the passes.
+   gram_dev: (j+2) x RT_GRAM_BLOCK doubles; row i holds <v_i, v_{i-d}> in
+   column d = 1..RT_GRAM_BLOCK-1 (column 0 unused).  Rows 1..j are read (all
+   zero for an exactly orthonormal basis); row j+1 is written for the new
+   vector.  V_dev, w_dev, h_dev and the limits as rt_arnoldi_mgs. */
+#define RT_GRAM_BLOCK 4
+rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* gram_dev,
+                          double* h_dev, void* stream);
+
 /* The same MGS Arnoldi step for callers that cannot allocate device memory
    (code running while a stream is captured into a CUDA graph, processes whose
    device memory belongs to another allocator that must account for every

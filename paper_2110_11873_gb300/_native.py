@@ -80,6 +80,7 @@ SIGNATURES = [
     ("rt_jacobi_diag", C.c_int, [_P, _P, _P]),
     ("rt_precond_local_lambda", C.c_int, [_P, _P, _P, _P]),
     ("rt_arnoldi_mgs", C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
+    ("rt_arnoldi_bmgs", C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P]),
     ("rt_arnoldi_mgs_static", C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P]),
     ("rt_solver_opts_default", None, [C.POINTER(SolverOpts)]),
     ("rt_solve_gmres", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),

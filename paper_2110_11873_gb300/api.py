@@ -248,6 +248,22 @@ class Problem:
                                         C.c_void_p(h.data_ptr()), _stream_handle(stream)), "rt_arnoldi_mgs")
         return h
 
+    def arnoldi_bmgs(self, V: torch.Tensor, j: int, w: torch.Tensor, gram: torch.Tensor,
+                     h: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """One block-MGS Arnoldi step (the GMRES orthogonalisation): as
+        arnoldi_mgs, with gram ((j+2) x 4 doubles, rows 1..j read, row j+1
+        written) holding <v_i, v_{i-d}>, d = 1..3."""
+        if V.dtype != torch.float64 or not V.is_contiguous() or V.numel() < (j + 2) * self.N:
+            raise ValueError("V must be a contiguous float64 tensor of at least (j+2)*N values")
+        if gram.dtype != torch.float64 or not gram.is_contiguous() or gram.numel() < (j + 2) * 4:
+            raise ValueError("gram must be a contiguous float64 tensor of at least (j+2)*4 values")
+        w = self._vec(w)
+        h = torch.empty(j + 2, dtype=torch.float64, device=self.device) if h is None else h
+        N.check(self.lib.rt_arnoldi_bmgs(self.handle, C.c_void_p(V.data_ptr()), int(j), C.c_void_p(w.data_ptr()),
+                                         C.c_void_p(gram.data_ptr()), C.c_void_p(h.data_ptr()),
+                                         _stream_handle(stream)), "rt_arnoldi_bmgs")
+        return h
+
     # --------------------------------------------------------------- solvers
     def solve(self, b: torch.Tensor, method: str = "gmres", x: Optional[torch.Tensor] = None, *,
               restart: int = 30, maxit: int = 10000, precond: str = "jacobi", rtol: float = 1e-8,

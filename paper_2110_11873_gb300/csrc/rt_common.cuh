@@ -53,6 +53,7 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 constexpr int kBlockVec = 512;          // threads per block of the vector kernels
 constexpr int kMaxPartials = 2048;      // upper bound on reduction partials per column
 constexpr int kMaxRestart = 64;
+constexpr int kGramB = 4;                // basis vectors per block pass of the GMRES Arnoldi step
 
 // device-side state of a GMRES cycle (lives in device memory)
 struct GmresDev {
@@ -60,6 +61,7 @@ struct GmresDev {
   double cs[kMaxRestart], sn[kMaxRestart];
   double g[kMaxRestart + 1];
   double y[kMaxRestart];
+  double gram[(kMaxRestart + 1) * kGramB];   // gram[i*kGramB + d] = <v_i, v_{i-d}>, d = 1..kGramB-1
   double bnorm, tol, rnorm, rel;   // ||b||, rtol, last true residual norm, rnorm/bnorm
   int kstop;                       // steps this cycle may take (set at cycle start)
   int kdone;                       // steps completed this cycle
@@ -133,6 +135,7 @@ struct Problem {
   double* dinv = nullptr;     // N, Jacobi inverse diagonal
   float* work32 = nullptr;    // 2 vectors of N (FP32 operator)
   double* partials = nullptr; // 2 x kMaxPartials x 8
+  double* bpart = nullptr;    // 3 x kGramB x kMaxPartials: block-pass partials (two ping-pong buffers, Gram)
   GmresDev* gm = nullptr;
   BicgDev* bc = nullptr;
   double* hist = nullptr;     // device history

@@ -17,6 +17,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -140,25 +141,38 @@ __global__ void __launch_bounds__(kVecThreads) k_dot2(const double* __restrict__
   }
 }
 
-// MGS pass: h = sum(part_in); w -= h * vprev; partial <w, vnext> (or <w,w>)
+// MGS pass: h = sum(part_in); w -= h * vprev; partial <w, vnext> (or <w,w>).
+// The first round's loads do not depend on h, so they are issued before the
+// block sums the previous pass's partials and their latency overlaps it.
 __global__ void __launch_bounds__(kVecThreads) k_mgs(double* __restrict__ w, const double* __restrict__ vprev,
                                                      const double* __restrict__ vnext, int64_t N,
                                                      const double* __restrict__ part_in, double* __restrict__ part_out,
                                                      double* __restrict__ hslot, const int* kstop, int step) {
   if (step >= *kstop) return;
-  const double h = block_partials(part_in, gridDim.x);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *hslot = h;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double s = 0.0;
   const double* __restrict__ vn = vnext ? vnext : w;
-  for (; i + (kU - 1) * stride < N; i += kU * stride) {
-    double wv[kU], pv[kU], nv[kU];
+  double wv[kU], pv[kU], nv[kU];
+  const bool first = i + (kU - 1) * stride < N;
+  if (first) {
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       wv[u] = w[i + u * stride];
       pv[u] = vprev[i + u * stride];
       if (vnext) nv[u] = vnext[i + u * stride];
+    }
+  }
+  const double h = block_partials(part_in, gridDim.x);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hslot = h;
+  double s = 0.0;
+  for (bool loaded = first; i + (kU - 1) * stride < N; i += kU * stride, loaded = false) {
+    if (!loaded) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        wv[u] = w[i + u * stride];
+        pv[u] = vprev[i + u * stride];
+        if (vnext) nv[u] = vnext[i + u * stride];
+      }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -176,20 +190,27 @@ __global__ void __launch_bounds__(kVecThreads) k_mgs(double* __restrict__ w, con
   if (threadIdx.x == 0) part_out[blockIdx.x] = s;
 }
 
-// h_{j+1,j} = ||w||; v_{j+1} = w / h
+// h_{j+1,j} = ||w||; v_{j+1} = w / h (first round loaded before the norm)
 __global__ void __launch_bounds__(kVecThreads) k_normalize(const double* __restrict__ w, double* __restrict__ v,
                                                            int64_t N, const double* __restrict__ part_in,
                                                            GmresDev* gm, int m, const int* kstop, int step) {
   if (step >= *kstop) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double wv[kU];
+  const bool first = i + (kU - 1) * stride < N;
+  if (first) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) wv[u] = w[i + u * stride];
+  }
   const double hn = sqrt(block_partials(part_in, gridDim.x));
   if (blockIdx.x == 0 && threadIdx.x == 0) gm->H[step * (m + 1) + step + 1] = hn;
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; i + (kU - 1) * stride < N; i += kU * stride) {
-    double wv[kU];
+  for (bool loaded = first; i + (kU - 1) * stride < N; i += kU * stride, loaded = false) {
+    if (!loaded) {
 #pragma unroll
-    for (int u = 0; u < kU; ++u) wv[u] = w[i + u * stride];
+      for (int u = 0; u < kU; ++u) wv[u] = w[i + u * stride];
+    }
 #pragma unroll
     for (int u = 0; u < kU; ++u) v[i + u * stride] = wv[u] * inv;
   }
@@ -205,6 +226,228 @@ __global__ void __launch_bounds__(kVecThreads) k_norm_out(const double* __restri
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = w[i] * inv;
+}
+
+// ------------------------------------------------- block MGS Arnoldi step
+// The GMRES Arnoldi step orthogonalises w against v_0..v_j in passes of
+// kGramB basis vectors.  With r_k = <w, v_k> taken before a block's updates,
+// modified Gram-Schmidt's coefficients satisfy exactly
+//     h_k = <w - sum_{l<k} h_l v_l, v_k> = r_k - sum_{l<k} h_l <v_l, v_k>
+// (l, k in the block), so each pass sums the previous pass's dots, solves
+// this small triangular system with the stored Gram entries <v_l, v_k>,
+// applies all of the block's updates to w element by element (in MGS order)
+// and accumulates the dots of the updated w with the next block.  One launch
+// per block instead of one per basis vector; the same FP64 operations per
+// element as MGS.  The Gram entries of v_{j+1} with its kGramB-1
+// predecessors are accumulated when it is normalised.
+constexpr int kB = kGramB;
+constexpr int kUB = 1;   // elements in flight per thread and vector
+
+// warps 0..n-1 each sum one set of G partials (fixed order) into out[k]
+__device__ __forceinline__ void sum_sets(const double* __restrict__ part, int G, int n, double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < n) {
+    const double s = sum_partials_warp(part + (size_t)warp * G, G);
+    if (lane == 0) out[warp] = s;
+  }
+  __syncthreads();
+}
+
+// first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk; block 0
+// also folds the Gram partials of v_j (from the previous normalisation)
+// into gram (row j)
+__global__ void __launch_bounds__(kVecThreads, 2) k_bdot(const double* __restrict__ w, const double* __restrict__ V,
+                                                        int64_t N, int nk, double* __restrict__ part_out,
+                                                        const double* __restrict__ gpart, int j,
+                                                        double* __restrict__ gram, const int* kstop) {
+  if (j >= *kstop) return;
+  const int G = gridDim.x;
+  if (blockIdx.x == 0 && j >= 1) {
+    __shared__ double gs[kB];
+    const int nd = min(kB - 1, j);
+    sum_sets(gpart, G, nd, gs);
+    if (threadIdx.x < nd) gram[j * kB + 1 + threadIdx.x] = gs[threadIdx.x];
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double s[kB] = {0.0, 0.0, 0.0, 0.0};
+  for (; i + (kUB - 1) * stride < N; i += kUB * stride) {
+    double wv[kUB], vv[kB][kUB];
+#pragma unroll
+    for (int u = 0; u < kUB; ++u) {
+      wv[u] = w[i + u * stride];
+#pragma unroll
+      for (int k = 0; k < kB; ++k)
+        if (k < nk) vv[k][u] = V[(size_t)k * N + i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < kUB; ++u)
+#pragma unroll
+      for (int k = 0; k < kB; ++k)
+        if (k < nk) s[k] = fma(wv[u], vv[k][u], s[k]);
+  }
+  for (; i < N; i += stride) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < kB; ++k)
+      if (k < nk) s[k] = fma(wi, V[(size_t)k * N + i], s[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    if (k < nk) {
+      const double t = block_sum(s[k]);
+      if (threadIdx.x == 0) part_out[(size_t)k * G + blockIdx.x] = t;
+    }
+  }
+}
+
+// one block pass of Arnoldi step j over v_{i0} .. v_{i0+nb-1}; dots with the
+// next nn vectors, or ||w||^2 when nn == 0
+__global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w, const double* __restrict__ V,
+                                                        int64_t N, int i0, int nb, int nn,
+                                                        const double* __restrict__ part_in,
+                                                        double* __restrict__ part_out, double* __restrict__ hcol,
+                                                        const double* __restrict__ gram, int j, const int* kstop) {
+  if (j >= *kstop) return;
+  const int G = gridDim.x;
+  const double* __restrict__ vb = V + (size_t)i0 * N;
+  const double* __restrict__ vn = V + (size_t)(i0 + nb) * N;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // the first round's loads do not depend on h: issue them first
+  double wv[kUB], bv[kB][kUB], nv[kB][kUB];
+  auto load = [&](int64_t e) {
+#pragma unroll
+    for (int u = 0; u < kUB; ++u) {
+      wv[u] = w[e + u * stride];
+#pragma unroll
+      for (int k = 0; k < kB; ++k) {
+        if (k < nb) bv[k][u] = vb[(size_t)k * N + e + u * stride];
+        if (k < nn) nv[k][u] = vn[(size_t)k * N + e + u * stride];
+      }
+    }
+  };
+  const bool first = i + (kUB - 1) * stride < N;
+  if (first) load(i);
+  __shared__ double rs[kB], hs[kB];
+  sum_sets(part_in, G, nb, rs);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < nb; ++k) {
+      double h = rs[k];
+      for (int l = 0; l < k; ++l) h -= hs[l] * gram[(i0 + k) * kB + (k - l)];
+      hs[k] = h;
+      if (blockIdx.x == 0) hcol[i0 + k] = h;
+    }
+  }
+  __syncthreads();
+  double h[kB];
+#pragma unroll
+  for (int k = 0; k < kB; ++k) h[k] = k < nb ? hs[k] : 0.0;
+  double s[kB] = {0.0, 0.0, 0.0, 0.0};
+  for (bool loaded = first; i + (kUB - 1) * stride < N; i += kUB * stride, loaded = false) {
+    if (!loaded) load(i);
+#pragma unroll
+    for (int u = 0; u < kUB; ++u) {
+      double wi = wv[u];
+#pragma unroll
+      for (int k = 0; k < kB; ++k)
+        if (k < nb) wi = fma(-h[k], bv[k][u], wi);
+      w[i + u * stride] = wi;
+      if (nn) {
+#pragma unroll
+        for (int k = 0; k < kB; ++k)
+          if (k < nn) s[k] = fma(wi, nv[k][u], s[k]);
+      } else {
+        s[0] = fma(wi, wi, s[0]);
+      }
+    }
+  }
+  for (; i < N; i += stride) {
+    double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < kB; ++k)
+      if (k < nb) wi = fma(-h[k], vb[(size_t)k * N + i], wi);
+    w[i] = wi;
+    if (nn) {
+#pragma unroll
+      for (int k = 0; k < kB; ++k)
+        if (k < nn) s[k] = fma(wi, vn[(size_t)k * N + i], s[k]);
+    } else {
+      s[0] = fma(wi, wi, s[0]);
+    }
+  }
+  const int ns = nn ? nn : 1;
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    if (k < ns) {
+      const double t = block_sum(s[k]);
+      if (threadIdx.x == 0) part_out[(size_t)k * G + blockIdx.x] = t;
+    }
+  }
+}
+
+// h_{j+1,j} = ||w||, v_{j+1} = w / h, and the partial Gram dots
+// <v_{j+1}, v_{j+1-d}>, d = 1..min(kGramB-1, j+1)
+__global__ void __launch_bounds__(kVecThreads, 2) k_bnorm(const double* __restrict__ w, double* __restrict__ V,
+                                                         int64_t N, const double* __restrict__ part_in,
+                                                         double* __restrict__ gpart, double* __restrict__ hcol, int j,
+                                                         const int* kstop) {
+  if (j >= *kstop) return;
+  const int G = gridDim.x;
+  double* __restrict__ vo = V + (size_t)(j + 1) * N;
+  const int nd = min(kB - 1, j + 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double wv[kUB], pv[kB - 1][kUB];
+  auto load = [&](int64_t e) {
+#pragma unroll
+    for (int u = 0; u < kUB; ++u) {
+      wv[u] = w[e + u * stride];
+#pragma unroll
+      for (int d = 1; d < kB; ++d)
+        if (d <= nd) pv[d - 1][u] = V[(size_t)(j + 1 - d) * N + e + u * stride];
+    }
+  };
+  const bool first = i + (kUB - 1) * stride < N;
+  if (first) load(i);
+  const double hn = sqrt(block_partials(part_in, G));
+  if (blockIdx.x == 0 && threadIdx.x == 0) hcol[j + 1] = hn;
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double s[kB - 1] = {0.0, 0.0, 0.0};
+  for (bool loaded = first; i + (kUB - 1) * stride < N; i += kUB * stride, loaded = false) {
+    if (!loaded) load(i);
+#pragma unroll
+    for (int u = 0; u < kUB; ++u) {
+      const double v = wv[u] * inv;
+      vo[i + u * stride] = v;
+#pragma unroll
+      for (int d = 1; d < kB; ++d)
+        if (d <= nd) s[d - 1] = fma(v, pv[d - 1][u], s[d - 1]);
+    }
+  }
+  for (; i < N; i += stride) {
+    const double v = w[i] * inv;
+    vo[i] = v;
+#pragma unroll
+    for (int d = 1; d < kB; ++d)
+      if (d <= nd) s[d - 1] = fma(v, V[(size_t)(j + 1 - d) * N + i], s[d - 1]);
+  }
+#pragma unroll
+  for (int d = 1; d < kB; ++d) {
+    if (d <= nd) {
+      const double t = block_sum(s[d - 1]);
+      if (threadIdx.x == 0) gpart[(size_t)(d - 1) * G + blockIdx.x] = t;
+    }
+  }
+}
+
+// row `row` of the Gram entries from the partials of the normalisation
+// (standalone Arnoldi step; inside GMRES the next k_bdot does this)
+__global__ void k_gram_fold(const double* __restrict__ gpart, int G, int row, double* __restrict__ gram) {
+  __shared__ double gs[kB];
+  const int nd = min(kB - 1, row);
+  sum_sets(gpart, G, nd, gs);
+  if (threadIdx.x < nd) gram[row * kB + 1 + threadIdx.x] = gs[threadIdx.x];
 }
 
 // Givens rotations on column j of the Hessenberg matrix (one thread)
@@ -543,6 +786,7 @@ static rt_status ensure_workspace(Problem* P, int restart, cudaStream_t st) {
   if (!P->work) RT_TRY_CUDA(cudaMalloc((void**)&P->work, (size_t)kWorkVecs * P->N * sizeof(double)));
   if (!P->dinv) RT_TRY_CUDA(cudaMalloc((void**)&P->dinv, (size_t)P->N * sizeof(double)));
   if (!P->partials) RT_TRY_CUDA(cudaMalloc((void**)&P->partials, (size_t)2 * 2 * kMaxPartials * sizeof(double)));
+  if (!P->bpart) RT_TRY_CUDA(cudaMalloc((void**)&P->bpart, (size_t)3 * kGramB * kMaxPartials * sizeof(double)));
   if (!P->gm) RT_TRY_CUDA(cudaMalloc((void**)&P->gm, sizeof(GmresDev)));
   if (!P->bc) RT_TRY_CUDA(cudaMalloc((void**)&P->bc, sizeof(BicgDev)));
   if (restart > P->ws_restart) {
@@ -559,6 +803,8 @@ static rt_status ensure_workspace(Problem* P, int restart, cudaStream_t st) {
 
 static inline double* wk(Problem* P, int i) { return P->work + (size_t)i * P->N; }
 static inline double* partb(Problem* P, int i) { return P->partials + (size_t)i * 2 * kMaxPartials; }
+// block-pass partials: buffers 0 and 1 ping-pong, 2 holds the Gram partials
+static inline double* bpartb(Problem* P, int i) { return P->bpart + (size_t)i * kGramB * kMaxPartials; }
 
 // A M^{-1} v with the chosen preconditioner and operator precision
 static rt_status apply_prec(Problem* P, const double* v, double* y, int precond, int fp32, cudaStream_t st,
@@ -647,16 +893,20 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
   for (int j = 0; j < m; ++j) {
     double* vj = P->V + (size_t)j * N;
     RT_TRY(apply_prec(P, vj, w, precond, fp32, st, kstop, j));
+    // block MGS: dots with the first block, one pass per block of kGramB
+    // basis vectors, normalisation with the Gram dots of v_{j+1}
     int pb = 0;
-    k_dot<<<G, kVecThreads, 0, st>>>(w, P->V, N, partb(P, pb), kstop, j, nullptr); RT_COUNT(1);
-    for (int i = 0; i <= j; ++i) {
-      const double* vprev = P->V + (size_t)i * N;
-      const double* vnext = (i < j) ? P->V + (size_t)(i + 1) * N : nullptr;
-      k_mgs<<<G, kVecThreads, 0, st>>>(w, vprev, vnext, N, partb(P, pb), partb(P, pb ^ 1), &gm->H[j * (m + 1) + i],
-                                       kstop, j); RT_COUNT(1);
+    double* hcol = &gm->H[j * (m + 1)];
+    k_bdot<<<G, kVecThreads, 0, st>>>(w, P->V, N, std::min(kGramB, j + 1), bpartb(P, 0), bpartb(P, 2), j, gm->gram,
+                                      kstop); RT_COUNT(1);
+    for (int i0 = 0; i0 <= j; i0 += kGramB) {
+      const int nb = std::min(kGramB, j + 1 - i0);
+      const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
+      k_bmgs<<<G, kVecThreads, 0, st>>>(w, P->V, N, i0, nb, nn, bpartb(P, pb), bpartb(P, pb ^ 1), hcol, gm->gram, j,
+                                        kstop); RT_COUNT(1);
       pb ^= 1;
     }
-    k_normalize<<<G, kVecThreads, 0, st>>>(w, P->V + (size_t)(j + 1) * N, N, partb(P, pb), gm, m, kstop, j); RT_COUNT(1);
+    k_bnorm<<<G, kVecThreads, 0, st>>>(w, P->V, N, bpartb(P, pb), bpartb(P, 2), hcol, j, kstop); RT_COUNT(1);
     k_givens<<<1, 1, 0, st>>>(gm, m, j, hist, hcap); RT_COUNT(1);
   }
   RT_TRY_CUDA(cudaGetLastError());
@@ -1093,6 +1343,39 @@ rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_d
     pb ^= 1;
   }
   k_norm_out<<<G, kVecThreads, 0, st>>>(w_dev, V_dev + (size_t)(j + 1) * N, N, partb(P, pb), h_dev + j + 1); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* gram_dev,
+                          double* h_dev, void* stream) {
+  clear_error();
+  if (!prob || !V_dev || !w_dev || !gram_dev || !h_dev) {
+    set_error("prob, V_dev, w_dev, gram_dev and h_dev are required");
+    return RT_EINVAL;
+  }
+  if (j < 0 || j >= kMaxRestart) { set_error("j must be in [0,%d)", kMaxRestart); return RT_EINVAL; }
+  Problem* P = &prob->P;
+  cudaStream_t st = as_stream(stream);
+  RT_TRY(ensure_workspace(P, 1, st));
+  const int G = P->vec_grid;
+  const int64_t N = P->N;
+  int* always = reinterpret_cast<int*>(&P->gm->kstop);   // a gate that never stops the kernels
+  const int big = 1 << 30;
+  RT_TRY_CUDA(cudaMemcpyAsync(always, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+  // the Gram rows of v_0..v_j are inputs: no fold at the first kernel
+  k_bdot<<<G, kVecThreads, 0, st>>>(w_dev, V_dev, N, std::min(kGramB, j + 1), bpartb(P, 0), bpartb(P, 2), 0,
+                                    gram_dev, always); RT_COUNT(1);
+  int pb = 0;
+  for (int i0 = 0; i0 <= j; i0 += kGramB) {
+    const int nb = std::min(kGramB, j + 1 - i0);
+    const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
+    k_bmgs<<<G, kVecThreads, 0, st>>>(w_dev, V_dev, N, i0, nb, nn, bpartb(P, pb), bpartb(P, pb ^ 1), h_dev, gram_dev,
+                                      j, always); RT_COUNT(1);
+    pb ^= 1;
+  }
+  k_bnorm<<<G, kVecThreads, 0, st>>>(w_dev, V_dev, N, bpartb(P, pb), bpartb(P, 2), h_dev, j, always); RT_COUNT(1);
+  k_gram_fold<<<1, 32 * kGramB, 0, st>>>(bpartb(P, 2), G, j + 1, gram_dev); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }

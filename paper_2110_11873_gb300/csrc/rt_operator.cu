@@ -268,12 +268,12 @@ void free_device(Problem* P) {
   void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wray,   P->wI2,  P->wQ2,   P->t201d, P->t202d,
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
-                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->qw, P->St, P->qpart};
+                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
   P->dtau32 = P->r32 = P->wray32 = P->wI2f = P->wQ2f = P->t201f = P->t202f = P->S32 = nullptr;
-  P->V = P->work = P->dinv = P->partials = P->hist = nullptr;
+  P->V = P->work = P->dinv = P->partials = P->hist = P->bpart = nullptr;
   P->work32 = nullptr;
   P->gm = nullptr;
   P->bc = nullptr;

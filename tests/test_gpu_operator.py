@@ -157,3 +157,43 @@ def test_arnoldi_mgs_step_against_plain_mgs():
     np.testing.assert_allclose(h, href, rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(to_host(Vd)[(j + 1) * N:], w / href[j + 1], rtol=1e-11, atol=1e-14)
     np.testing.assert_allclose(to_host(wd), w, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("j", [0, 3, 4, 9])
+def test_arnoldi_block_mgs_step_against_plain_mgs(j):
+    """rt_arnoldi_bmgs (the GMRES orthogonalisation): blocks of 4 basis vectors
+    with the Gram correction give the MGS coefficients of the same loop in
+    numpy, on a basis that is orthonormal only to rounding (its Gram rows
+    computed in numpy), and write the Gram row of the new vector."""
+    at = W.slab(37, 6, 33, 1e-4, 1e6, 6.0)
+    P = problem(at)
+    N = P.N
+    rng = np.random.default_rng(7 + j)
+    Q, _ = np.linalg.qr(rng.standard_normal((N, j + 1)))
+    # a slightly non-orthogonal basis, so the Gram correction matters
+    Q = Q + 1e-9 * rng.standard_normal(Q.shape)
+    Q /= np.linalg.norm(Q, axis=0)
+    gram = np.zeros((j + 2, 4))
+    for i in range(1, j + 1):
+        for d in range(1, 4):
+            if i - d >= 0:
+                gram[i, d] = Q[:, i] @ Q[:, i - d]
+    w0 = rng.standard_normal(N)
+    V = np.zeros((j + 2) * N)
+    V[: (j + 1) * N] = Q.T.reshape(-1)
+    Vd, wd, gd = to_dev(V), to_dev(w0), to_dev(gram.reshape(-1))
+    h = to_host(P.arnoldi_bmgs(Vd, j, wd, gd))
+    w = w0.copy()
+    href = np.zeros(j + 2)
+    for i in range(j + 1):
+        href[i] = np.dot(w, Q[:, i])
+        w = w - href[i] * Q[:, i]
+    href[j + 1] = np.linalg.norm(w)
+    np.testing.assert_allclose(h, href, rtol=1e-10, atol=1e-13)
+    vnew = w / href[j + 1]
+    np.testing.assert_allclose(to_host(Vd)[(j + 1) * N:], vnew, rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(to_host(wd), w, rtol=1e-9, atol=1e-13)
+    g_out = to_host(gd).reshape(j + 2, 4)
+    for d in range(1, 4):
+        if j + 1 - d >= 0:
+            assert abs(g_out[j + 1, d] - vnew @ Q[:, j + 1 - d]) < 1e-13
