@@ -115,6 +115,27 @@ __device__ __forceinline__ double inst_sum(const InstDev& I, int pb) {
   return v;
 }
 
+// sqrt(inst_sum) and its inverse (0 for a zero norm), computed once by
+// thread 0 (FP64 square roots and divisions are long FP64-pipe sequences)
+__device__ __forceinline__ double inst_norm_inv(const InstDev& I, int pb, double* hn_out) {
+  __shared__ double nb[2];
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int c = threadIdx.x; c < I.nchunks; c += 32) s += I.part[pb * I.nchunks + c];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) {
+      const double h = sqrt(s);
+      nb[0] = h;
+      nb[1] = h > 0.0 ? 1.0 / h : 0.0;
+    }
+  }
+  __syncthreads();
+  *hn_out = nb[0];
+  const double inv = nb[1];
+  __syncthreads();
+  return inv;
+}
+
 // ------------------------------------------------------------ operator
 template <typename TC, int MODE>
 __global__ void __launch_bounds__(kMomThreads) kb_moments(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
@@ -254,9 +275,9 @@ __global__ void __launch_bounds__(kBT) kb_normalize(const InstDev* __restrict__ 
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
     if (step_gated(I, j)) continue;
-    const double hn = sqrt(inst_sum(I, pb));
+    double hn;
+    const double inv = inst_norm_inv(I, pb, &hn);
     if (it.y == 0 && threadIdx.x == 0) I.gm->H[j * (I.m + 1) + j + 1] = hn;
-    const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
     const double* wv = I.w;
     double* v = I.V + (int64_t)(j + 1) * I.N;
     CHUNK_LOOP(v[n_] = wv[n_] * inv;)
@@ -367,8 +388,8 @@ __global__ void __launch_bounds__(kBT) kb_cycle_start(const InstDev* __restrict_
   for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
-    const double rn = sqrt(inst_sum(I, 0));
-    const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+    double rn;
+    const double inv = inst_norm_inv(I, 0, &rn);
     CHUNK_LOOP(I.V[n_] = I.r[n_] * inv;)
     if (it.y == 0 && threadIdx.x == 0) {
       GmresDev* gm = I.gm;

@@ -75,6 +75,26 @@ __device__ __forceinline__ double block_partials(const double* __restrict__ part
   return v;
 }
 
+// sqrt(sum of the partials) and its inverse (0 for a zero norm), computed
+// once per block by thread 0 (FP64 square roots and divisions are long
+// sequences on this GPU's narrow FP64 pipe) and broadcast to the block
+__device__ __forceinline__ double block_norm_inv(const double* __restrict__ part, int G, double* hn_out) {
+  __shared__ double nb[2];
+  if (threadIdx.x < 32) {
+    const double s = sum_partials_warp(part, G);
+    if (threadIdx.x == 0) {
+      const double h = sqrt(s);
+      nb[0] = h;
+      nb[1] = h > 0.0 ? 1.0 / h : 0.0;
+    }
+  }
+  __syncthreads();
+  *hn_out = nb[0];
+  const double inv = nb[1];
+  __syncthreads();
+  return inv;
+}
+
 // ------------------------------------------------------------------ kernels
 // Grid-stride loops unrolled by kU with all loads of a round issued before
 // any arithmetic, so each thread keeps kU independent loads in flight.
@@ -203,9 +223,9 @@ __global__ void __launch_bounds__(kVecThreads) k_normalize(const double* __restr
 #pragma unroll
     for (int u = 0; u < kU; ++u) wv[u] = w[i + u * stride];
   }
-  const double hn = sqrt(block_partials(part_in, gridDim.x));
+  double hn;
+  const double inv = block_norm_inv(part_in, gridDim.x, &hn);
   if (blockIdx.x == 0 && threadIdx.x == 0) gm->H[step * (m + 1) + step + 1] = hn;
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   for (bool loaded = first; i + (kU - 1) * stride < N; i += kU * stride, loaded = false) {
     if (!loaded) {
 #pragma unroll
@@ -221,9 +241,9 @@ __global__ void __launch_bounds__(kVecThreads) k_normalize(const double* __restr
 __global__ void __launch_bounds__(kVecThreads) k_norm_out(const double* __restrict__ w, double* __restrict__ v,
                                                           int64_t N, const double* __restrict__ part_in,
                                                           double* __restrict__ hout) {
-  const double hn = sqrt(block_partials(part_in, gridDim.x));
+  double hn;
+  const double inv = block_norm_inv(part_in, gridDim.x, &hn);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hout = hn;
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = w[i] * inv;
 }
@@ -410,9 +430,9 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bnorm(const double* __restri
   };
   const bool first = i + (kUB - 1) * stride < N;
   if (first) load(i);
-  const double hn = sqrt(block_partials(part_in, G));
+  double hn;
+  const double inv = block_norm_inv(part_in, G, &hn);
   if (blockIdx.x == 0 && threadIdx.x == 0) hcol[j + 1] = hn;
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   double s[kB - 1] = {0.0, 0.0, 0.0};
   for (bool loaded = first; i + (kUB - 1) * stride < N; i += kUB * stride, loaded = false) {
     if (!loaded) load(i);
@@ -532,8 +552,8 @@ __global__ void __launch_bounds__(kVecThreads) k_residual(const double* __restri
 __global__ void __launch_bounds__(kVecThreads) k_cycle_start(const double* __restrict__ r, double* __restrict__ v0,
                                                              int64_t N, const double* __restrict__ part, GmresDev* gm,
                                                              int m) {
-  const double rn = sqrt(block_partials(part, gridDim.x));
-  const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+  double rn;
+  const double inv = block_norm_inv(part, gridDim.x, &rn);
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
     v0[n] = r[n] * inv;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
