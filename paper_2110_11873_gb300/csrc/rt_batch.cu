@@ -100,28 +100,21 @@ __device__ __forceinline__ double bsum(double v) {
   return s;
 }
 
-// sum of an instance's chunk partials in a fixed order, broadcast to the block
-__device__ __forceinline__ double inst_sum(const InstDev& I, int pb) {
-  __shared__ double bc;
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int c = threadIdx.x; c < I.nchunks; c += 32) s += I.part[pb * I.nchunks + c];
-    s = warp_sum(s);
-    if (threadIdx.x == 0) bc = s;
-  }
-  __syncthreads();
-  const double v = bc;
-  __syncthreads();
-  return v;
+// an instance's partials: three buffers of kGramB sets of nchunks values
+// (buffers 0 and 1 ping-pong between Arnoldi passes, buffer 2 holds the
+// Gram dots of the newest basis vector)
+__device__ __forceinline__ double* pset(const InstDev& I, int buf, int k) {
+  return I.part + ((size_t)buf * kGramB + k) * I.nchunks;
 }
 
-// sqrt(inst_sum) and its inverse (0 for a zero norm), computed once by
+// sqrt of the sum of an instance's chunk partials (set 0 of buffer pb, in a
+// fixed order) and its inverse (0 for a zero norm), computed once by
 // thread 0 (FP64 square roots and divisions are long FP64-pipe sequences)
 __device__ __forceinline__ double inst_norm_inv(const InstDev& I, int pb, double* hn_out) {
   __shared__ double nb[2];
   if (threadIdx.x < 32) {
     double s = 0.0;
-    for (int c = threadIdx.x; c < I.nchunks; c += 32) s += I.part[pb * I.nchunks + c];
+    for (int c = threadIdx.x; c < I.nchunks; c += 32) s += pset(I, pb, 0)[c];
     s = warp_sum(s);
     if (threadIdx.x == 0) {
       const double h = sqrt(s);
@@ -234,43 +227,99 @@ __global__ void __launch_bounds__(32 * kFormalWarps) kb_formal(const InstDev* __
     for (int64_t n_ = lo + threadIdx.x; n_ < hi; n_ += blockDim.x) { body }   \
   }
 
-__global__ void __launch_bounds__(kBT) kb_dot(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
-                                              const Counts* cnt, int ida, int idb, int pb, int step) {
-  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
-    const int2 it = wl[w];
-    const InstDev& I = insts[it.x];
-    if (step_gated(I, step)) continue;
-    const double* a = vec(I, ida);
-    const double* b = vec(I, idb);
+// Block MGS (the single-instance GMRES's Arnoldi step, per instance): passes
+// of kGramB basis vectors, the MGS coefficients of a block from the dots r_k
+// taken before it and the Gram entries, h_k = r_k - sum_{l<k} h_l <v_l, v_k>.
+
+// warps k < n each sum set k of buffer buf into out[k] (fixed order)
+__device__ __forceinline__ void inst_sets(const InstDev& I, int buf, int n, double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < n) {
+    const double* p = pset(I, buf, warp);
     double s = 0.0;
-    CHUNK_LOOP(s = fma(a[n_], b[n_], s);)
-    s = bsum(s);
-    if (threadIdx.x == 0) I.part[pb * I.nchunks + it.y] = s;
+    for (int c = lane; c < I.nchunks; c += 32) s += p[c];
+    s = warp_sum(s);
+    if (lane == 0) out[warp] = s;
   }
+  __syncthreads();
 }
 
-// MGS pass i of Arnoldi step j: h = <w, v_i> (from the partials); w -= h v_i;
-// partial <w, v_{i+1}> (or <w, w> for i == j)
-__global__ void __launch_bounds__(kBT) kb_mgs(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
-                                              const Counts* cnt, int i, int j, int pb) {
+// first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk, into buffer
+// 0; the first chunk of each instance folds the Gram dots of v_j into gram
+__global__ void __launch_bounds__(kBT) kb_bdot(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                               const Counts* cnt, int j, int nk) {
+  __shared__ double gs[kGramB];
   for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
     if (step_gated(I, j)) continue;
-    const double h = inst_sum(I, pb);
-    if (it.y == 0 && threadIdx.x == 0) I.gm->H[j * (I.m + 1) + i] = h;
-    double* wv = I.w;
-    const double* vp = I.V + (int64_t)i * I.N;
-    const double* vn = i < j ? I.V + (int64_t)(i + 1) * I.N : nullptr;
-    double s = 0.0;
-    CHUNK_LOOP(const double wi = fma(-h, vp[n_], wv[n_]); wv[n_] = wi; s = fma(wi, vn ? vn[n_] : wi, s);)
-    s = bsum(s);
-    if (threadIdx.x == 0) I.part[(pb ^ 1) * I.nchunks + it.y] = s;
+    if (it.y == 0 && j >= 1) {
+      const int nd = min(kGramB - 1, j);
+      inst_sets(I, 2, nd, gs);
+      if (threadIdx.x < nd) I.gm->gram[j * kGramB + 1 + threadIdx.x] = gs[threadIdx.x];
+      __syncthreads();
+    }
+    double s[kGramB] = {0.0, 0.0, 0.0, 0.0};
+    CHUNK_LOOP(const double wi = I.w[n_]; _Pragma("unroll")
+               for (int k = 0; k < kGramB; ++k) if (k < nk) s[k] = fma(wi, I.V[(int64_t)k * I.N + n_], s[k]);)
+#pragma unroll
+    for (int k = 0; k < kGramB; ++k) {
+      if (k < nk) {
+        const double t = bsum(s[k]);
+        if (threadIdx.x == 0) pset(I, 0, k)[it.y] = t;
+      }
+    }
   }
 }
 
-__global__ void __launch_bounds__(kBT) kb_normalize(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
-                                                    const Counts* cnt, int j, int pb) {
+// one block pass over v_{i0} .. v_{i0+nb-1}: dots with the next nn vectors
+// (or ||w||^2 when nn == 0) into buffer pb ^ 1
+__global__ void __launch_bounds__(kBT) kb_bmgs(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                               const Counts* cnt, int j, int i0, int nb, int nn, int pb) {
+  __shared__ double rs[kGramB], hs[kGramB];
+  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
+    const int2 it = wl[w];
+    const InstDev& I = insts[it.x];
+    if (step_gated(I, j)) continue;
+    inst_sets(I, pb, nb, rs);
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < nb; ++k) {
+        double h = rs[k];
+        for (int l = 0; l < k; ++l) h -= hs[l] * I.gm->gram[(i0 + k) * kGramB + (k - l)];
+        hs[k] = h;
+        if (it.y == 0) I.gm->H[j * (I.m + 1) + i0 + k] = h;
+      }
+    }
+    __syncthreads();
+    double h[kGramB];
+#pragma unroll
+    for (int k = 0; k < kGramB; ++k) h[k] = k < nb ? hs[k] : 0.0;
+    __syncthreads();
+    const double* vb = I.V + (int64_t)i0 * I.N;
+    const double* vn = I.V + (int64_t)(i0 + nb) * I.N;
+    double s[kGramB] = {0.0, 0.0, 0.0, 0.0};
+    CHUNK_LOOP(double wi = I.w[n_]; _Pragma("unroll")
+               for (int k = 0; k < kGramB; ++k) if (k < nb) wi = fma(-h[k], vb[(int64_t)k * I.N + n_], wi);
+               I.w[n_] = wi;
+               if (nn) { _Pragma("unroll")
+                 for (int k = 0; k < kGramB; ++k) if (k < nn) s[k] = fma(wi, vn[(int64_t)k * I.N + n_], s[k]);
+               } else {
+                 s[0] = fma(wi, wi, s[0]);
+               })
+    const int ns = nn ? nn : 1;
+#pragma unroll
+    for (int k = 0; k < kGramB; ++k) {
+      if (k < ns) {
+        const double t = bsum(s[k]);
+        if (threadIdx.x == 0) pset(I, pb ^ 1, k)[it.y] = t;
+      }
+    }
+  }
+}
+
+// h_{j+1,j} = ||w||, v_{j+1} = w / h, Gram dots <v_{j+1}, v_{j+1-d}> into buffer 2
+__global__ void __launch_bounds__(kBT) kb_bnorm(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                                const Counts* cnt, int j, int pb) {
   for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
@@ -278,9 +327,18 @@ __global__ void __launch_bounds__(kBT) kb_normalize(const InstDev* __restrict__ 
     double hn;
     const double inv = inst_norm_inv(I, pb, &hn);
     if (it.y == 0 && threadIdx.x == 0) I.gm->H[j * (I.m + 1) + j + 1] = hn;
-    const double* wv = I.w;
-    double* v = I.V + (int64_t)(j + 1) * I.N;
-    CHUNK_LOOP(v[n_] = wv[n_] * inv;)
+    const int nd = min(kGramB - 1, j + 1);
+    double* vo = I.V + (int64_t)(j + 1) * I.N;
+    double s[kGramB - 1] = {0.0, 0.0, 0.0};
+    CHUNK_LOOP(const double v = I.w[n_] * inv; vo[n_] = v; _Pragma("unroll")
+               for (int d = 1; d < kGramB; ++d) if (d <= nd) s[d - 1] = fma(v, I.V[(int64_t)(j + 1 - d) * I.N + n_], s[d - 1]);)
+#pragma unroll
+    for (int d = 1; d < kGramB; ++d) {
+      if (d <= nd) {
+        const double t = bsum(s[d - 1]);
+        if (threadIdx.x == 0) pset(I, 2, d - 1)[it.y] = t;
+      }
+    }
   }
 }
 
@@ -573,7 +631,8 @@ rt_status grow(T** p, size_t* cap, size_t need) {
 // the Jacobi inverse diagonal, partials, GMRES state
 size_t solver_bytes(int64_t N, int m, int nchunks) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  return al((size_t)(m + 1) * N * 8) + 7 * al((size_t)N * 8) + al((size_t)2 * nchunks * 8) + al(sizeof(GmresDev));
+  return al((size_t)(m + 1) * N * 8) + 7 * al((size_t)N * 8) + al((size_t)3 * kGramB * nchunks * 8) +
+         al(sizeof(GmresDev));
 }
 
 int64_t chunk_for(int64_t N) {
@@ -634,12 +693,14 @@ rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
   for (int j = 0; j < m; ++j) {
     apply(j, VW, mode, fp32, j);
     int pb = 0;
-    kb_dot<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, VW, 0, pb, j);
-    for (int i = 0; i <= j; ++i) {
-      kb_mgs<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, i, j, pb);
+    kb_bdot<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, std::min(kGramB, j + 1));
+    for (int i0 = 0; i0 <= j; i0 += kGramB) {
+      const int nb = std::min(kGramB, j + 1 - i0);
+      const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
+      kb_bmgs<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, i0, nb, nn, pb);
       pb ^= 1;
     }
-    kb_normalize<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, pb);
+    kb_bnorm<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, pb);
     kb_givens<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C, j);
   }
   kb_lsq<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C);
@@ -781,7 +842,7 @@ rt_status make_instance(Server* S, Request* rq, Instance* in, int slot) {
     p += al((size_t)N * 8);
   }
   D.part = reinterpret_cast<double*>(p);
-  p += al((size_t)2 * nchunks * 8);
+  p += al((size_t)3 * kGramB * nchunks * 8);
   D.gm = reinterpret_cast<GmresDev*>(p);
   D.Ns = P.Ns;
   D.Nmu = P.Nmu;
