@@ -209,14 +209,14 @@ def reference_main(args, rank, world):
 
 
 # ------------------------------------------------------- batching / serving
-def _drain(srv, tickets, timeout_s=600.0):
+def _drain(srv, tickets, timeout_s=600.0, want_x=()):
     import time as _t
     out = {}
     t0 = _t.perf_counter()
     while len(out) < len(tickets):
         for t in tickets:
             if t not in out:
-                r = srv.poll(t, want_x=False)
+                r = srv.poll(t, want_x=t in want_x)
                 if r is not None:
                     out[t] = (r, _t.perf_counter())
         if _t.perf_counter() - t0 > timeout_s:
@@ -226,33 +226,41 @@ def _drain(srv, tickets, timeout_s=600.0):
 
 
 def batch_bench(W, Server, Problem, torch, count):
+    import numpy as np
     """512 seeded uneven atmospheres submitted at once to one server: FP32
     operator inside FP64 refinement, local-Lambda preconditioner, resident
     together (one launch per phase for all of them).  Compared with the plain
     FP64 single-instance path on the first 16 of the same atmospheres."""
     import time as _t
     ats = W.batch_instances(count)
+    n1 = min(16, count)
     srv = Server(mem_budget_bytes=160 << 30, max_slots=count, precond="local_lambda", precision="fp32_refine")
     t0 = _t.perf_counter()
     tickets = [srv.submit(a) for a in ats]
-    res = _drain(srv, tickets)
+    res = _drain(srv, tickets, want_x=set(tickets[:n1]))
     wall = _t.perf_counter() - t0
     ok = [r for (r, _) in res.values() if r[0] == 0]
     rel = [r[1].rel_resid for r in ok]
     its = [r[1].iters for r in ok]
     stats = srv.stats()
     srv.close()
-    # plain FP64 single-instance path, same atmospheres, same final residual
-    n1 = min(16, count)
+    # plain FP64 single-instance path, same atmospheres, same final residual;
+    # its solutions are the reference of the batched ones' errors
     torch.cuda.synchronize()
     t1 = _t.perf_counter()
+    xref = []
     for a in ats[:n1]:
         P = Problem(a)
         b = P.rhs()
-        _, info = P.solve(b, "gmres", restart=30, precond="local_lambda", rtol=1e-8)
+        xs, info = P.solve(b, "gmres", restart=30, precond="local_lambda", rtol=1e-8)
+        xref.append(xs.cpu().numpy())
         P.close()
     torch.cuda.synchronize()
     single = n1 / (_t.perf_counter() - t1)
+    errs = []
+    for t, xr in zip(tickets[:n1], xref):
+        xb = res[t][0][2]
+        errs.append(float(np.linalg.norm(xb - xr) / np.linalg.norm(xr)))
     return {"workload": f"{count} uneven atmospheres (splitmix64 seed 0x2110118730000001): Ns~U[50,400], "
                         "Nnu~U{21..101} odd, Nmu in {8,16,32}, eps log-U[1e-6,1e-2], a log-U[1e-4,1e-2], "
                         "B=1+c log10(1+tau)",
@@ -260,7 +268,10 @@ def batch_bench(W, Server, Problem, torch, count):
             "solves": len(ok), "failed": count - len(ok), "wall_s": wall, "solves_per_s": len(ok) / wall,
             "iters_mean": sum(its) / max(len(its), 1), "rel_resid_max": max(rel) if rel else None,
             "cycles": stats["cycles"],
-            "fp64_single_instance_solves_per_s": single, "fp64_single_instance_sample": n1}
+            "fp64_single_instance_solves_per_s": single, "fp64_single_instance_sample": n1,
+            "rel_err_vs_fp64_max": max(errs), "rel_err_vs_fp64_mean": sum(errs) / len(errs),
+            "rel_err_note": "||x_batched - x_fp64|| / ||x_fp64|| on the first 16 atmospheres; the FP64 "
+                            "single-instance GPU solver is parity-tested against the oracle's LU solution"}
 
 
 def serve_bench(W, Server, rates, nreq):
@@ -268,12 +279,21 @@ def serve_bench(W, Server, rates, nreq):
     admitted by a 64 GB device-memory budget; per-request latency from
     submission to completion."""
     import time as _t
+    import numpy as np
+    from paper_2110_11873_gb300 import Problem
     ats = W.batch_instances(nreq, seed=W.STREAM_SEED)
+    nref = min(8, nreq)
+    xref = []
+    for a in ats[:nref]:   # FP64 single-instance reference solutions of the first requests
+        P = Problem(a)
+        xs, _ = P.solve(P.rhs(), "gmres", restart=30, precond="local_lambda", rtol=1e-8)
+        xref.append(xs.cpu().numpy())
+        P.close()
     out = {}
     for rate in rates:
         arr = W.poisson_arrivals(rate, nreq)
         srv = Server(mem_budget_bytes=64 << 30, max_slots=512, precond="local_lambda", precision="fp32_refine")
-        pending, lat, done_t = {}, [], []
+        pending, lat, done_t, errs = {}, [], [], []
         t0 = _t.perf_counter()
         i = 0
         while i < nreq or pending:
@@ -282,11 +302,14 @@ def serve_bench(W, Server, rates, nreq):
                 pending[srv.submit(ats[i])] = i
                 i += 1
             for t in list(pending):
-                r = srv.poll(t, want_x=False)
+                k = pending[t]
+                r = srv.poll(t, want_x=k < nref)
                 if r is not None:
                     del pending[t]
                     lat.append(r[1].t_total_ms)
                     done_t.append(_t.perf_counter() - t0)
+                    if k < nref:
+                        errs.append(float(np.linalg.norm(r[2] - xref[k]) / np.linalg.norm(xref[k])))
             if now > 600:
                 raise RuntimeError("served stream did not finish")
             _t.sleep(0.0002)
@@ -295,7 +318,8 @@ def serve_bench(W, Server, rates, nreq):
         span = max(done_t) - float(arr[0])
         out[str(rate)] = {"offered_req_per_s": rate, "requests": nreq,
                           "achieved_solves_per_s": nreq / span,
-                          "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+                          "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                          "rel_err_vs_fp64_max": max(errs), "rel_err_sample": nref}
     return out
 
 
