@@ -63,6 +63,15 @@ enum { RT_TAU_LINE_CENTER = 0, RT_TAU_FREQ_INTEGRATED = 1 };
 enum { RT_MU_GL_HALF = 0, RT_MU_GL_FULL = 1 };
 /* formal solver (Sect. 4.1): DELO-linear, implicit Euler, trapezoidal */
 enum { RT_FS_DELO_LINEAR = 0, RT_FS_IMPLICIT_EULER = 1, RT_FS_TRAPEZOIDAL = 2 };
+/* linear system (Sect. 3.2):
+   RT_FORM_I      Eq. (19): unknown I, N = 2*Ns*Nmu*Nnu values x[s][k][m][p],
+                  A x = x - Lambda(T(J x)), b = Lambda T c + t;
+   RT_FORM_SIGMA  Eq. (18): unknown sigma, N = 2*Ns values interleaved per
+                  height (sigma^0_0(k), sigma^2_0(k)), A s = s - J(Lambda(T s))
+                  with J including the factors 1-eps and W2, b = J t + c.
+                  The sigma-form operator is FP64 in every precision; the
+                  batch server takes I-form problems only. */
+enum { RT_FORM_I = 0, RT_FORM_SIGMA = 1 };
 
 typedef struct {
   int32_t Ns;              /* heights, >= 2 */
@@ -85,6 +94,9 @@ typedef struct {
   int32_t formal_solver;   /* RT_FS_* */
   int32_t freq_norm;       /* 1: divide the trapezoidal spectral weights by their sum;
                               0: plain trapezoid (the paper's tables) */
+  int32_t form;            /* RT_FORM_*: the linear system rt_apply, rt_rhs,
+                              rt_jacobi_diag, rt_precond_local_lambda and the
+                              solvers work on (0, the I-form, when unset) */
 } rt_problem_desc;
 
 typedef struct rt_problem rt_problem;
@@ -95,7 +107,8 @@ typedef struct rt_problem rt_problem;
    phi == NULL), non-increasing tau, x_min >= x_max, unknown enums. */
 rt_status rt_problem_create(const rt_problem_desc* desc, void* stream, rt_problem** out);
 rt_status rt_problem_destroy(rt_problem* prob);
-/* N = 2*Ns*Nmu*Nnu, or -1 for NULL */
+/* Length N of the system's vectors: 2*Ns*Nmu*Nnu (RT_FORM_I) or 2*Ns
+   (RT_FORM_SIGMA); -1 for NULL */
 int64_t rt_problem_size(const rt_problem* prob);
 
 /* Host copies of the discrete grids (any pointer may be NULL):
@@ -104,8 +117,9 @@ int64_t rt_problem_size(const rt_problem* prob);
 rt_status rt_problem_grids(const rt_problem* prob, double* mu, double* w_mu, double* x,
                            double* phi, double* w_nu, double* phi_hat);
 
-/* y = x - Lambda(T(J x))   (Eq. 19; Algorithm 1).  x_dev, y_dev: N doubles,
-   distinct buffers.  FP64 throughout. */
+/* y = x - Lambda(T(J x))   (Eq. 19; Algorithm 1), or for RT_FORM_SIGMA
+   y = s - J(Lambda(T s)) (Eq. 18; Algorithm 1 itself).  x_dev, y_dev: N
+   doubles, distinct buffers.  FP64 throughout. */
 rt_status rt_apply(rt_problem* prob, const double* x_dev, double* y_dev, void* stream);
 
 /* Same operator with FP32 vectors and FP32 quadrature and formal solver
@@ -131,20 +145,24 @@ rt_status rt_problem_check(rt_problem* prob, void* stream);
 int rt_problem_formal_kernel(const rt_problem* prob);
 
 /* b = Lambda T c + t of Eq. (19): one formal solve with S_I = eps B, S_Q = 0
-   and the boundary radiation.  b_dev: N doubles. */
+   and the boundary radiation; for RT_FORM_SIGMA b = J t + c of Eq. (18), t
+   the boundary radiation transmitted with S = 0.  b_dev: N doubles. */
 rt_status rt_rhs(rt_problem* prob, double* b_dev, void* stream);
 
 /* Diagonal of Id - Lambda T J (Jacobi P = D, Sect. 2.3):
    D_I = 1 - xi beta* w_m w_p (1 + W2 T201^2), D_Q = 1 - xi W2 beta* w_m w_p T202^2,
    beta* the coefficient of S_k in the last formal-solver step ending at k.
-   d_dev: N doubles. */
+   For RT_FORM_SIGMA the diagonal of Eq. (18): the diagonals of the per-height
+   blocks M_k = Id - J_k Lambda*_k T_k.  d_dev: N doubles. */
 rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream);
 
 /* z = P^{-1} v for the local-Lambda preconditioner P = Id - Lambda* T J
    (Lambda* the diagonal of Lambda): P^{-1} v = v + Lambda* T M^{-1} J v with
    M_k = Id - J_k Lambda*_k T_k the 2x2 per-height block of the sigma-form
    (Eq. 18).  This is the sigma-form block-Jacobi preconditioner of Sect. 2.3
-   carried to the I-form by the Woodbury identity.  v_dev, z_dev: N doubles. */
+   carried to the I-form by the Woodbury identity.  For RT_FORM_SIGMA the
+   block-Jacobi preconditioner itself: z_k = M_k^{-1} v_k per height.
+   v_dev, z_dev: N doubles. */
 rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double* z_dev, void* stream);
 
 /* One Arnoldi orthogonalisation step by modified Gram-Schmidt (Sect. 2.1:
@@ -152,7 +170,7 @@ rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double*
      for i = 0..j: h_i = <w, v_i>; w -= h_i v_i;   h_{j+1} = ||w||;  v_{j+1} = w / h_{j+1}
    V_dev: j+2 vectors of N doubles, contiguous (v_i at V_dev + i*N), v_0..v_j
    orthonormal; v_{j+1} is written.  w_dev: N doubles, overwritten.
-   h_dev: j+2 doubles (device), receives h_0..h_{j+1}.  0 <= j < 64.
+   h_dev: j+2 doubles (device), receives h_0..h_{j+1}.  0 <= j < 160.
    Reductions are deterministic (fixed block partials, fixed summation order). */
 rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* h_dev, void* stream);
 
@@ -196,13 +214,20 @@ rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_
 rt_status rt_arnoldi_mgs_static(double* V_dev, int64_t N, int32_t j, double* w_dev, double* h_dev, void* stream);
 
 /* ---------------------------------------------------------------- solvers */
-enum { RT_PREC_NONE = 0, RT_PREC_JACOBI = 1, RT_PREC_LOCAL_LAMBDA = 2 };
+/* preconditioners.  NONE, JACOBI and LOCAL_LAMBDA are applied from the
+   right (A M^-1 y = b, x = M^-1 y), so the stopping test is on the
+   unpreconditioned residual.  JACOBI_LEFT (GMRES, FP64 only) solves
+   D^-1 A x = D^-1 b and stops on the preconditioned residual, as the
+   paper's experiments do (Sect. 4.2, Table 3).  For the sigma-form, JACOBI
+   uses the diagonal of A (Eq. 18) and LOCAL_LAMBDA the inverse 2x2 blocks
+   M_k = Id - J_k Lambda*_k T_k per height. */
+enum { RT_PREC_NONE = 0, RT_PREC_JACOBI = 1, RT_PREC_LOCAL_LAMBDA = 2, RT_PREC_JACOBI_LEFT = 3 };
 enum { RT_X0_ZERO = 0, RT_X0_USER = 1 };
 enum { RT_ORTHO_MGS = 0, RT_ORTHO_CGS2 = 1 };
 enum { RT_PRECISION_FP64 = 0, RT_PRECISION_FP32_REFINE = 1 };
 
 typedef struct {
-  int32_t restart;       /* GMRES restart length m, 1..64 (Sect. 2.1) */
+  int32_t restart;       /* GMRES restart length m, 1..160 (Sect. 2.1) */
   int32_t maxit;         /* cap on iterations (Arnoldi steps / BiCGSTAB-CGS iterations) */
   int32_t precond;       /* RT_PREC_*, applied from the right */
   int32_t x0_kind;       /* RT_X0_ZERO, or RT_X0_USER: x_dev holds the initial guess */
@@ -230,15 +255,20 @@ typedef struct {
    FP64, rtol 1e-8, inner_rtol 1e-4, max_refine 20, no history. */
 void rt_solver_opts_default(rt_solver_opts* opts);
 
-/* Right-preconditioned restarted GMRES(m) (Sect. 2.1; Saad & Schultz 1986).
-   b_dev, x_dev: N doubles.  Returns RT_OK when converged, RT_ENOTCONV at
-   maxit, RT_EBREAKDOWN, RT_ENUMERIC; in each case x_dev holds the iterate. */
+/* Right-preconditioned restarted GMRES(m) (Sect. 2.1; Saad & Schultz 1986),
+   left-preconditioned with RT_PREC_JACOBI_LEFT (then FP64 only; rel_resid is
+   the preconditioned residual).  A cycle with m >= the steps needed is the
+   paper's unrestarted GMRES.  b_dev, x_dev: N doubles.  Returns RT_OK when
+   converged, RT_ENOTCONV at maxit, RT_EBREAKDOWN, RT_ENUMERIC; in each case
+   x_dev holds the iterate. */
 rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                          double* x_dev, rt_solve_info* info, void* stream);
-/* Right-preconditioned BiCGSTAB (Sect. 2.2; van der Vorst 1992). */
+/* Right-preconditioned BiCGSTAB (Sect. 2.2; van der Vorst 1992); not with
+   RT_PREC_JACOBI_LEFT. */
 rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                             double* x_dev, rt_solve_info* info, void* stream);
-/* Right-preconditioned CGS (Sect. 2.2; Sonneveld 1989). */
+/* Right-preconditioned CGS (Sect. 2.2; Sonneveld 1989); not with
+   RT_PREC_JACOBI_LEFT. */
 rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                        double* x_dev, rt_solve_info* info, void* stream);
 
@@ -261,7 +291,7 @@ rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const doubl
 typedef struct {
   int64_t mem_budget_bytes;  /* device arena for resident instances, allocated at creation */
   int32_t max_slots;         /* instances resident at once, 1..4096 */
-  int32_t restart;           /* GMRES restart length for all instances, 1..64 */
+  int32_t restart;           /* GMRES restart length for all instances, 1..160 */
   int32_t precond;           /* RT_PREC_* for all instances */
   int32_t precision;         /* RT_PRECISION_FP64, or RT_PRECISION_FP32_REFINE: FP32 operator in the
                                 Arnoldi steps, FP64 true residual at every restart (each restart is

@@ -18,7 +18,8 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "R
 RT_TAU_LINE_CENTER, RT_TAU_FREQ_INTEGRATED = 0, 1
 RT_MU_GL_HALF, RT_MU_GL_FULL = 0, 1
 RT_FS_DELO_LINEAR, RT_FS_IMPLICIT_EULER, RT_FS_TRAPEZOIDAL = 0, 1, 2
-RT_PREC_NONE, RT_PREC_JACOBI, RT_PREC_LOCAL_LAMBDA = 0, 1, 2
+RT_PREC_NONE, RT_PREC_JACOBI, RT_PREC_LOCAL_LAMBDA, RT_PREC_JACOBI_LEFT = 0, 1, 2, 3
+RT_FORM_I, RT_FORM_SIGMA = 0, 1
 RT_X0_ZERO, RT_X0_USER = 0, 1
 RT_ORTHO_MGS, RT_ORTHO_CGS2 = 0, 1
 RT_PRECISION_FP64, RT_PRECISION_FP32_REFINE = 0, 1
@@ -31,7 +32,7 @@ class ProblemDesc(C.Structure):
         ("phi_center", C.c_double), ("x_min", C.c_double), ("x_max", C.c_double),
         ("a", C.c_double), ("eps", C.c_double), ("W2", C.c_double),
         ("tau_kind", C.c_int32), ("mu_quad", C.c_int32), ("formal_solver", C.c_int32),
-        ("freq_norm", C.c_int32),
+        ("freq_norm", C.c_int32), ("form", C.c_int32),
     ]
 
 

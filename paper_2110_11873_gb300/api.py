@@ -129,11 +129,14 @@ class Problem:
     ``atm`` is any object with the descriptor fields of rt_problem_desc
     (Ns, Nmu, Nnu, tau, B, x_min, x_max, a, eps, W2, tau_kind, mu_quad,
     formal_solver, freq_norm); ``phi`` optionally overrides the internal
-    Voigt profile (with ``phi_center`` for line-centre tau).
+    Voigt profile (with ``phi_center`` for line-centre tau).  ``form``
+    selects the linear system: "I" (Eq. 19, N = 2*Ns*Nmu*Nnu) or "sigma"
+    (Eq. 18, N = 2*Ns); apply, rhs, jacobi_diag, precond_local_lambda and
+    solve then work on that system.
     """
 
     def __init__(self, atm, phi: Optional[np.ndarray] = None, phi_center: float = 0.0,
-                 stream: Optional[torch.cuda.Stream] = None):
+                 stream: Optional[torch.cuda.Stream] = None, form: str = "I"):
         self.lib = N.load()
         f = {k: getattr(atm, k) for k in _DESC_FIELDS}
         self._tau = np.ascontiguousarray(f["tau"], dtype=np.float64)
@@ -149,6 +152,8 @@ class Problem:
         d.a, d.eps, d.W2 = float(f["a"]), float(f["eps"]), float(f["W2"])
         d.tau_kind, d.mu_quad = int(f["tau_kind"]), int(f["mu_quad"])
         d.formal_solver, d.freq_norm = int(f["formal_solver"]), int(f["freq_norm"])
+        d.form = {"I": N.RT_FORM_I, "sigma": N.RT_FORM_SIGMA}[form]
+        self.form = form
         self.desc = d
         self.Ns, self.Nmu, self.Nnu = d.Ns, d.Nmu, d.Nnu
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -276,7 +281,7 @@ class Problem:
         self.lib.rt_solver_opts_default(C.byref(o))
         o.restart, o.maxit, o.rtol = restart, maxit, rtol
         o.precond = {"none": N.RT_PREC_NONE, "jacobi": N.RT_PREC_JACOBI,
-                     "local_lambda": N.RT_PREC_LOCAL_LAMBDA}[precond]
+                     "local_lambda": N.RT_PREC_LOCAL_LAMBDA, "jacobi_left": N.RT_PREC_JACOBI_LEFT}[precond]
         o.x0_kind = N.RT_X0_USER if x0 else N.RT_X0_ZERO
         o.precision = {"fp64": N.RT_PRECISION_FP64, "fp32_refine": N.RT_PRECISION_FP32_REFINE}[precision]
         o.inner_rtol, o.max_refine = inner_rtol, max_refine

@@ -884,12 +884,14 @@ rt_status make_instance(Server* S, Request* rq, Instance* in, int slot) {
   P.dinv = nullptr;   // the arena block owns it
   RT_TRY_CUDA(cudaMemsetAsync(D.x, 0, (size_t)N * 8, S->st));
   RT_TRY_CUDA(cudaMemsetAsync(D.tmp, 0, (size_t)N * 8, S->st));
-  GmresDev init;
-  memset(&init, 0, sizeof init);
+  std::unique_ptr<GmresDev> initp(new GmresDev);   // large arrays: not on the stack
+  GmresDev& init = *initp;
+  memset(&init, 0, kGmresHeader);
   init.tol = rq->rtol;
   init.maxit = rq->maxit;
-  RT_TRY_CUDA(cudaMemcpyAsync(D.gm, &init, sizeof init, cudaMemcpyHostToDevice, S->st));
+  RT_TRY_CUDA(cudaMemcpyAsync(D.gm, &init, kGmresHeader, cudaMemcpyHostToDevice, S->st));
   RT_TRY_CUDA(cudaMemcpyAsync(S->d_insts + slot, &D, sizeof D, cudaMemcpyHostToDevice, S->st));
+  RT_TRY_CUDA(cudaStreamSynchronize(S->st));   // init is freed on return
   return RT_OK;
 }
 
@@ -1140,6 +1142,7 @@ rt_status rt_batch_submit(rt_server* srv, const rt_problem_desc* desc, const rt_
   if (!srv || !desc || !ticket) { set_error("srv, desc and ticket are required"); return RT_EINVAL; }
   RT_TRY(validate_desc(desc));
   if (desc->Ns > 4096) { set_error("batched instances need Ns <= 4096"); return RT_EINVAL; }
+  if (desc->form != RT_FORM_I) { set_error("the batch server solves I-form problems only"); return RT_EINVAL; }
   Server* S = &srv->S;
   auto rq = std::make_unique<Request>();
   rq->desc = *desc;

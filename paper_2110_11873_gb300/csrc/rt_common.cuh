@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <string>
@@ -52,16 +53,13 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // number of SMs on the device (152 on GB300), queried once per problem
 constexpr int kBlockVec = 512;          // threads per block of the vector kernels
 constexpr int kMaxPartials = 2048;      // upper bound on reduction partials per column
-constexpr int kMaxRestart = 64;
+constexpr int kMaxRestart = 160;         // longest GMRES cycle (the paper runs GMRES unrestarted, up to 134 steps)
 constexpr int kGramB = 4;                // basis vectors per block pass of the GMRES Arnoldi step
 
-// device-side state of a GMRES cycle (lives in device memory)
+// device-side state of a GMRES cycle (lives in device memory).  The scalars
+// come first: the host reads only that header (kGmresHeader bytes) after a
+// cycle; the arrays are written before they are read within a cycle.
 struct GmresDev {
-  double H[(kMaxRestart + 1) * kMaxRestart];  // column-major (m+1) x m, rotated in place
-  double cs[kMaxRestart], sn[kMaxRestart];
-  double g[kMaxRestart + 1];
-  double y[kMaxRestart];
-  double gram[(kMaxRestart + 1) * kGramB];   // gram[i*kGramB + d] = <v_i, v_{i-d}>, d = 1..kGramB-1
   double bnorm, tol, rnorm, rel;   // ||b||, rtol, last true residual norm, rnorm/bnorm
   int kstop;                       // steps this cycle may take (set at cycle start)
   int kdone;                       // steps completed this cycle
@@ -69,7 +67,13 @@ struct GmresDev {
   int maxit;
   int breakdown;
   int hist_len;
+  double H[(kMaxRestart + 1) * kMaxRestart];  // column-major (m+1) x m, rotated in place
+  double cs[kMaxRestart], sn[kMaxRestart];
+  double g[kMaxRestart + 1];
+  double y[kMaxRestart];
+  double gram[(kMaxRestart + 1) * kGramB];   // gram[i*kGramB + d] = <v_i, v_{i-d}>, d = 1..kGramB-1
 };
+constexpr size_t kGmresHeader = offsetof(GmresDev, H);
 
 // device-side scalars of BiCGSTAB / CGS
 struct BicgDev {
@@ -94,7 +98,9 @@ struct Problem {
   // sizes
   int Ns = 0, Nmu = 0, Nnu = 0, Nh = 0;
   int64_t nray = 0;   // Nmu*Nnu rays per Stokes parameter
-  int64_t N = 0;      // 2*Ns*nray
+  int64_t N = 0;      // 2*Ns*nray: length of the radiation field (the I-form unknown)
+  int form = 0;       // RT_FORM_I or RT_FORM_SIGMA: the system the solvers and rt_apply work on
+  int64_t Nop = 0;    // length of that system's vectors: N (I-form) or 2*Ns (sigma-form)
   int device = 0, num_sms = 0;
   // physics
   double eps = 0, xi = 0, W2 = 0, a = 0;
@@ -117,6 +123,8 @@ struct Problem {
   double* t202d = nullptr; // [Nmu]
   double* Bd = nullptr;    // [Ns]
   double* Minv = nullptr;  // [Ns][4] inverse of the 2x2 local blocks M_k (row-major)
+  double* Mdiag = nullptr; // [Ns][2] diagonal of M_k (the sigma-form Jacobi diagonal)
+  double* Ibuf = nullptr;  // sigma-form only: [2][Ns][nray] radiation field of one apply
   double* S = nullptr;     // [2][Ns][Nmu] source-function scratch
   double* S2 = nullptr;    // second source-function scratch
   // FP32 device tables
@@ -141,7 +149,17 @@ struct Problem {
   double* hist = nullptr;     // device history
   int hist_cap_dev = 0;
   int vec_grid = 0;           // blocks of the reduction kernels
-  // fast FP32 apply (rt_tma.cu): usable for this problem, its tables, and
+  // the formal solver alone (Eq. 9-10): I = Lambda S with the given inflow at
+// the bottom for Stokes I (zero elsewhere), FP64, written to I_out [2][Ns][nray]
+void formal64_lambda(Problem* P, const double* S, double* I_out, double inflow_bottom, cudaStream_t st,
+                     const int* kstop = nullptr, int step = 0);
+// sigma-form operator and its companions (rt_sigma.cu); vectors of 2*Ns
+rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaStream_t st,
+                         const int* kstop = nullptr, int step = 0);
+rt_status op_rhs_sigma(Problem* P, double* b, cudaStream_t st);
+rt_status op_jacobi_sigma(Problem* P, double* d, int inverse, cudaStream_t st);
+rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st);
+// fast FP32 apply (rt_tma.cu): usable for this problem, its tables, and
   // the device flag its bounded waits set when they give up
   int staged = 0;
   int ntile_st = 1;            // depth tiles per ray group of the staged formal solver
@@ -165,6 +183,16 @@ rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st)
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st);
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st);
 void release_graphs(Problem* P);
+// the formal solver alone (Eq. 9-10): I = Lambda S with the given inflow at
+// the bottom for Stokes I (zero elsewhere), FP64, written to I_out [2][Ns][nray]
+void formal64_lambda(Problem* P, const double* S, double* I_out, double inflow_bottom, cudaStream_t st,
+                     const int* kstop = nullptr, int step = 0);
+// sigma-form operator and its companions (rt_sigma.cu); vectors of 2*Ns
+rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaStream_t st,
+                         const int* kstop = nullptr, int step = 0);
+rt_status op_rhs_sigma(Problem* P, double* b, cudaStream_t st);
+rt_status op_jacobi_sigma(Problem* P, double* d, int inverse, cudaStream_t st);
+rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st);
 // fast FP32 apply (rt_tma.cu)
 rt_status staged_setup(Problem* P, cudaStream_t st);
 bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cudaStream_t st, const int* kstop,

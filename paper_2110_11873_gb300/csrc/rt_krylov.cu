@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 
@@ -786,6 +787,15 @@ __global__ void __launch_bounds__(kVecThreads) k_mul(const double* __restrict__ 
     y[n] = x[n] * d[n];
 }
 
+// y = d * x inside a captured GMRES cycle (skipped once step >= *kstop)
+__global__ void __launch_bounds__(kVecThreads) k_mul_gated(const double* __restrict__ x,
+                                                           const double* __restrict__ d, double* __restrict__ y,
+                                                           int64_t N, const int* kstop, int step) {
+  if (step >= *kstop) return;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+    y[n] = x[n] * d[n];
+}
+
 }  // namespace
 
 
@@ -798,13 +808,13 @@ struct Workspace {
 
 static rt_status ensure_workspace(Problem* P, int restart, cudaStream_t st) {
   if (!P->vec_grid) {
-    int64_t g = (P->N + 2 * kVecThreads - 1) / (2 * kVecThreads);
+    int64_t g = (P->Nop + 2 * kVecThreads - 1) / (2 * kVecThreads);
     int cap = 4 * P->num_sms;
     if (cap > kMaxPartials) cap = kMaxPartials;
     P->vec_grid = (int)(g < 1 ? 1 : (g > cap ? cap : g));
   }
-  if (!P->work) RT_TRY_CUDA(cudaMalloc((void**)&P->work, (size_t)kWorkVecs * P->N * sizeof(double)));
-  if (!P->dinv) RT_TRY_CUDA(cudaMalloc((void**)&P->dinv, (size_t)P->N * sizeof(double)));
+  if (!P->work) RT_TRY_CUDA(cudaMalloc((void**)&P->work, (size_t)kWorkVecs * P->Nop * sizeof(double)));
+  if (!P->dinv) RT_TRY_CUDA(cudaMalloc((void**)&P->dinv, (size_t)P->Nop * sizeof(double)));
   if (!P->partials) RT_TRY_CUDA(cudaMalloc((void**)&P->partials, (size_t)2 * 2 * kMaxPartials * sizeof(double)));
   if (!P->bpart) RT_TRY_CUDA(cudaMalloc((void**)&P->bpart, (size_t)3 * kGramB * kMaxPartials * sizeof(double)));
   if (!P->gm) RT_TRY_CUDA(cudaMalloc((void**)&P->gm, sizeof(GmresDev)));
@@ -814,14 +824,14 @@ static rt_status ensure_workspace(Problem* P, int restart, cudaStream_t st) {
     if (P->V) cudaFree(P->V);
     P->V = nullptr;
     P->ws_restart = 0;
-    RT_TRY_CUDA(cudaMalloc((void**)&P->V, (size_t)(restart + 1) * P->N * sizeof(double)));
+    RT_TRY_CUDA(cudaMalloc((void**)&P->V, (size_t)(restart + 1) * P->Nop * sizeof(double)));
     P->ws_restart = restart;
   }
   (void)st;
   return RT_OK;
 }
 
-static inline double* wk(Problem* P, int i) { return P->work + (size_t)i * P->N; }
+static inline double* wk(Problem* P, int i) { return P->work + (size_t)i * P->Nop; }
 static inline double* partb(Problem* P, int i) { return P->partials + (size_t)i * 2 * kMaxPartials; }
 // block-pass partials: buffers 0 and 1 ping-pong, 2 holds the Gram partials
 static inline double* bpartb(Problem* P, int i) { return P->bpart + (size_t)i * kGramB * kMaxPartials; }
@@ -829,6 +839,14 @@ static inline double* bpartb(Problem* P, int i) { return P->bpart + (size_t)i * 
 // A M^{-1} v with the chosen preconditioner and operator precision
 static rt_status apply_prec(Problem* P, const double* v, double* y, int precond, int fp32, cudaStream_t st,
                             const int* kstop = nullptr, int step = 0) {
+  if (precond == RT_PREC_JACOBI_LEFT) {
+    // D^-1 A v: the FP64 apply into the scratch vector wk(6), then the scaling
+    double* t = P->work + (size_t)6 * P->Nop;
+    RT_TRY(op_apply64(P, v, t, AM_PLAIN, st, kstop, step));
+    k_mul_gated<<<P->vec_grid, kVecThreads, 0, st>>>(t, P->dinv, y, P->Nop, kstop, step); RT_COUNT(1);
+    RT_TRY_CUDA(cudaGetLastError());
+    return RT_OK;
+  }
   const int mode = precond == RT_PREC_JACOBI ? AM_JACOBI : precond == RT_PREC_LOCAL_LAMBDA ? AM_LOCAL_LAMBDA : AM_PLAIN;
   if (fp32) return op_apply32_f64io(P, v, y, mode, st, kstop, step);
   return op_apply64(P, v, y, mode, st, kstop, step);
@@ -838,13 +856,13 @@ static rt_status apply_prec(Problem* P, const double* v, double* y, int precond,
 static rt_status add_precond(Problem* P, double* x, double* t, int precond, double* tmp, cudaStream_t st) {
   const int G = P->vec_grid;
   if (precond == RT_PREC_NONE) {
-    k_axpy1<<<G, kVecThreads, 0, st>>>(x, t, P->N); RT_COUNT(1);
+    k_axpy1<<<G, kVecThreads, 0, st>>>(x, t, P->Nop); RT_COUNT(1);
   } else if (precond == RT_PREC_JACOBI) {
-    k_mul<<<G, kVecThreads, 0, st>>>(t, P->dinv, tmp, P->N); RT_COUNT(1);
-    k_axpy1<<<G, kVecThreads, 0, st>>>(x, tmp, P->N); RT_COUNT(1);
+    k_mul<<<G, kVecThreads, 0, st>>>(t, P->dinv, tmp, P->Nop); RT_COUNT(1);
+    k_axpy1<<<G, kVecThreads, 0, st>>>(x, tmp, P->Nop); RT_COUNT(1);
   } else {
     RT_TRY(op_precond_ll(P, t, tmp, st));
-    k_axpy1<<<G, kVecThreads, 0, st>>>(x, tmp, P->N); RT_COUNT(1);
+    k_axpy1<<<G, kVecThreads, 0, st>>>(x, tmp, P->Nop); RT_COUNT(1);
   }
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
@@ -904,7 +922,7 @@ void release_graphs(Problem* P) {
 // r = wk(2), w = wk(3), t = wk(4), Ax = wk(5), tmp = wk(6).
 static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStream_t st) {
   const int G = P->vec_grid;
-  const int64_t N = P->N;
+  const int64_t N = P->Nop;
   GmresDev* gm = P->gm;
   const int* kstop = &gm->kstop;
   double* w = wk(P, 3);
@@ -941,7 +959,12 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
     k_combine<<<G, kVecThreads, 0, st>>>(P->V, N, gm, x, P->dinv, t, precond == RT_PREC_JACOBI ? 1 : 0); RT_COUNT(1);
   }
   RT_TRY(op_apply64(P, x, wk(P, 5), AM_PLAIN, st));
-  k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
+  if (precond == RT_PREC_JACOBI_LEFT) {   // the residual of D^-1 A x = D^-1 b
+    k_mul<<<G, kVecThreads, 0, st>>>(wk(P, 5), P->dinv, wk(P, 6), N); RT_COUNT(1);
+    k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 6), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
+  } else {
+    k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
+  }
   k_cycle_start<<<G, kVecThreads, 0, st>>>(wk(P, 2), P->V, N, partb(P, 0), gm, m); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
@@ -1024,13 +1047,15 @@ static rt_status ensure_hist(Problem* P, int cap) {
 static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, double tol, int maxit, bool x0_zero,
                             GmresDev* hs, int* cycles, cudaStream_t st) {
   const int G = P->vec_grid;
-  const int64_t N = P->N;
+  const int64_t N = P->Nop;
   const int m = o->restart;
-  GmresDev init;
-  memset(&init, 0, sizeof init);
+  std::unique_ptr<GmresDev> initp(new GmresDev);   // large arrays: not on the stack
+  GmresDev& init = *initp;
+  memset(&init, 0, kGmresHeader);
   init.tol = tol;
   init.maxit = maxit;
-  RT_TRY_CUDA(cudaMemcpyAsync(P->gm, &init, sizeof init, cudaMemcpyHostToDevice, st));
+  RT_TRY_CUDA(cudaMemcpyAsync(P->gm, &init, kGmresHeader, cudaMemcpyHostToDevice, st));
+  RT_TRY_CUDA(cudaStreamSynchronize(st));   // init is freed on return
   k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), N, partb(P, 1), nullptr, 0, nullptr); RT_COUNT(1);
   k_set_bnorm<<<1, 32, 0, st>>>(partb(P, 1), G, P->gm); RT_COUNT(1);
   if (x0_zero) {
@@ -1038,11 +1063,16 @@ static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, doubl
     k_cycle_start<<<G, kVecThreads, 0, st>>>(wk(P, 1), P->V, N, partb(P, 0), P->gm, m); RT_COUNT(1);
   } else {
     RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
-    k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
+    const double* ax = wk(P, 5);
+    if (o->precond == RT_PREC_JACOBI_LEFT) {
+      k_mul<<<G, kVecThreads, 0, st>>>(wk(P, 5), P->dinv, wk(P, 6), N); RT_COUNT(1);
+      ax = wk(P, 6);
+    }
+    k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), ax, wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
     k_cycle_start<<<G, kVecThreads, 0, st>>>(wk(P, 2), P->V, N, partb(P, 0), P->gm, m); RT_COUNT(1);
   }
   RT_TRY_CUDA(cudaGetLastError());
-  RT_TRY_CUDA(cudaMemcpyAsync(hs, P->gm, sizeof(GmresDev), cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaMemcpyAsync(hs, P->gm, kGmresHeader, cudaMemcpyDeviceToHost, st));
   RT_TRY_CUDA(cudaStreamSynchronize(st));
   *cycles = 0;
   if (hs->bnorm == 0.0 || !(hs->rel >= tol) || hs->rel != hs->rel) return RT_OK;
@@ -1051,7 +1081,7 @@ static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, doubl
   RT_TRY(get_graph(P, gc, m, o->precond, fp32, &ex));
   for (;;) {
     RT_TRY(launch_graph(gc, ex, st));
-    RT_TRY_CUDA(cudaMemcpyAsync(hs, P->gm, sizeof(GmresDev), cudaMemcpyDeviceToHost, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(hs, P->gm, kGmresHeader, cudaMemcpyDeviceToHost, st));
     RT_TRY_CUDA(cudaStreamSynchronize(st));
     *cycles += 1;
     if (hs->rel != hs->rel) return RT_OK;
@@ -1065,7 +1095,7 @@ static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, doubl
 static rt_status prepare(Problem* P, const rt_solver_opts* o, int restart, cudaStream_t st) {
   RT_TRY(ensure_workspace(P, restart, st));
   if (o->resid_hist && o->hist_cap > 0) RT_TRY(ensure_hist(P, o->hist_cap));
-  if (o->precond == RT_PREC_JACOBI) RT_TRY(op_jacobi_inv(P, P->dinv, st));
+  if (o->precond == RT_PREC_JACOBI || o->precond == RT_PREC_JACOBI_LEFT) RT_TRY(op_jacobi_inv(P, P->dinv, st));
   return RT_OK;
 }
 
@@ -1073,7 +1103,7 @@ static rt_status check_opts(const rt_solver_opts* o, const double* b, const doub
   if (!o || !b || !x) { set_error("opts, b_dev and x_dev are required"); return RT_EINVAL; }
   if (o->restart < 1 || o->restart > kMaxRestart) { set_error("restart must be in [1,%d]", kMaxRestart); return RT_EINVAL; }
   if (o->maxit < 1) { set_error("maxit must be >= 1"); return RT_EINVAL; }
-  if (o->precond < RT_PREC_NONE || o->precond > RT_PREC_LOCAL_LAMBDA) { set_error("bad precond"); return RT_EINVAL; }
+  if (o->precond < RT_PREC_NONE || o->precond > RT_PREC_JACOBI_LEFT) { set_error("bad precond"); return RT_EINVAL; }
   if (o->x0_kind != RT_X0_ZERO && o->x0_kind != RT_X0_USER) { set_error("bad x0_kind"); return RT_EINVAL; }
   if (o->ortho != RT_ORTHO_MGS) { set_error("only RT_ORTHO_MGS is implemented"); return RT_EINVAL; }
   if (o->precision != RT_PRECISION_FP64 && o->precision != RT_PRECISION_FP32_REFINE) { set_error("bad precision"); return RT_EINVAL; }
@@ -1097,8 +1127,8 @@ static rt_status finish_info(rt_solve_info* info, rt_status s, double t0) {
 static rt_status true_residual(Problem* P, double* rel, cudaStream_t st) {
   const int G = P->vec_grid;
   RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
-  k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), P->N, partb(P, 0)); RT_COUNT(1);
-  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), P->N, partb(P, 1), nullptr, 0, nullptr); RT_COUNT(1);
+  k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), P->Nop, partb(P, 0)); RT_COUNT(1);
+  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), P->Nop, partb(P, 1), nullptr, 0, nullptr); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   std::vector<double> h(2 * G);
   RT_TRY_CUDA(cudaMemcpyAsync(h.data(), partb(P, 0), G * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1114,12 +1144,22 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
                              cudaStream_t st) {
   const double t0 = now_ms();
   if (info) memset(info, 0, sizeof *info);
+  if (o->precond == RT_PREC_JACOBI_LEFT && o->precision != RT_PRECISION_FP64) {
+    set_error("RT_PREC_JACOBI_LEFT needs RT_PRECISION_FP64");
+    return finish_info(info, RT_EINVAL, t0);
+  }
   RT_TRY(prepare(P, o, o->restart, st));
-  const size_t bytes = (size_t)P->N * sizeof(double);
-  RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
+  const size_t bytes = (size_t)P->Nop * sizeof(double);
+  if (o->precond == RT_PREC_JACOBI_LEFT) {   // the system D^-1 A x = D^-1 b
+    k_mul<<<P->vec_grid, kVecThreads, 0, st>>>(b, P->dinv, wk(P, 1), P->Nop); RT_COUNT(1);
+    RT_TRY_CUDA(cudaGetLastError());
+  } else {
+    RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
+  }
   if (o->x0_kind == RT_X0_USER) RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), x, bytes, cudaMemcpyDeviceToDevice, st));
   else RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
-  GmresDev hs;
+  std::unique_ptr<GmresDev> hsp(new GmresDev);   // only its header is read back
+  GmresDev& hs = *hsp;
   int cycles = 0;
   rt_status s = RT_OK;
   int iters = 0, applies = 0, refine = 0;
@@ -1152,7 +1192,7 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
       iters += hs.iters;
       applies += hs.iters + cycles;
       refine += 1;
-      k_axpy1<<<P->vec_grid, kVecThreads, 0, st>>>(xb, wk(P, 0), P->N); RT_COUNT(1);
+      k_axpy1<<<P->vec_grid, kVecThreads, 0, st>>>(xb, wk(P, 0), P->Nop); RT_COUNT(1);
       RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), xb, bytes, cudaMemcpyDeviceToDevice, st));
       RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), bsave, bytes, cudaMemcpyDeviceToDevice, st));
       RT_TRY(true_residual(P, &rel, st));
@@ -1192,7 +1232,7 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
 // unpreconditioned direction sum; x = x0 + M^{-1} acc at the end.
 static rt_status enqueue_bicg_iter(Problem* P, int method, int precond, int fp32, cudaStream_t st) {
   const int G = P->vec_grid;
-  const int64_t N = P->N;
+  const int64_t N = P->Nop;
   BicgDev* bc = P->bc;
   double* acc = P->V + 2 * (size_t)N;
   double *r = wk(P, 2), *rhat = wk(P, 3), *p = wk(P, 4);
@@ -1238,9 +1278,13 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
     set_error("BiCGSTAB/CGS support FP64 only");
     return finish_info(info, RT_EINVAL, t0);
   }
+  if (o->precond == RT_PREC_JACOBI_LEFT) {
+    set_error("BiCGSTAB/CGS are preconditioned from the right only");
+    return finish_info(info, RT_EINVAL, t0);
+  }
   RT_TRY(prepare(P, o, 2, st));
   const int G = P->vec_grid;
-  const int64_t N = P->N;
+  const int64_t N = P->Nop;
   const size_t bytes = (size_t)N * sizeof(double);
   double *x0 = wk(P, 0), *bb = wk(P, 1), *r = wk(P, 2), *rhat = wk(P, 3);
   double* acc = P->V + 2 * (size_t)N;
@@ -1349,7 +1393,7 @@ rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_d
   cudaStream_t st = as_stream(stream);
   RT_TRY(ensure_workspace(P, 1, st));
   const int G = P->vec_grid;
-  const int64_t N = P->N;
+  const int64_t N = P->Nop;
   // the kernels gate on kstop: point it at a device int that never stops them
   int* always = reinterpret_cast<int*>(&P->gm->kstop);
   const int big = 1 << 30;
@@ -1379,7 +1423,7 @@ rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_
   cudaStream_t st = as_stream(stream);
   RT_TRY(ensure_workspace(P, 1, st));
   const int G = P->vec_grid;
-  const int64_t N = P->N;
+  const int64_t N = P->Nop;
   int* always = reinterpret_cast<int*>(&P->gm->kstop);   // a gate that never stops the kernels
   const int big = 1 << 30;
   RT_TRY_CUDA(cudaMemcpyAsync(always, &big, sizeof(int), cudaMemcpyHostToDevice, st));

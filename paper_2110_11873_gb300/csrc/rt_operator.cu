@@ -80,14 +80,15 @@ __global__ void k_coeffs64(const double* __restrict__ dtau, const double* __rest
   }
 }
 
-// 2x2 local blocks M_k = Id - J_k Lambda*_k T_k of the sigma-form and their
-// inverses, one block per height.
+// 2x2 local blocks M_k = Id - J_k Lambda*_k T_k of the sigma-form, their
+// inverses and their diagonals, one block per height.
 __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __restrict__ cb,
                                                              const double* __restrict__ wray,
                                                              const double* __restrict__ t201,
                                                              const double* __restrict__ t202, int Ns, int Nmu,
                                                              int Nnu, double xi, double W2,
-                                                             double* __restrict__ Minv) {
+                                                             double* __restrict__ Minv,
+                                                             double* __restrict__ Mdiag) {
   const int k = blockIdx.x;
   const int Nh = Nmu / 2;
   const int64_t nray = (int64_t)Nmu * Nnu;
@@ -115,6 +116,8 @@ __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __re
     Minv[4 * k + 1] = -m01 / det;
     Minv[4 * k + 2] = -m10 / det;
     Minv[4 * k + 3] = m00 / det;
+    Mdiag[2 * k + 0] = m00;
+    Mdiag[2 * k + 1] = m11;
   }
 }
 
@@ -268,7 +271,7 @@ void free_device(Problem* P) {
   void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wray,   P->wI2,  P->wQ2,   P->t201d, P->t202d,
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
-                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart};
+                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
@@ -279,6 +282,7 @@ void free_device(Problem* P) {
   P->bc = nullptr;
   P->dev_err = nullptr;
   P->qw = P->St = P->qpart = nullptr;
+  P->Mdiag = P->Ibuf = nullptr;
   P->staged = 0;
 }
 
@@ -368,8 +372,10 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_rs, Ns, nray, P->fs, P->ce,
                                                                          P->ca, P->cb); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mdiag, (size_t)Ns * 2 * sizeof(double)));
   k_local_blocks<<<Ns, kMomThreads, 0, st>>>(P->cb, P->wray, P->t201d, P->t202d, Ns, Nmu, Nnu, P->xi, P->W2,
-                                             P->Minv); RT_COUNT(1);
+                                             P->Minv, P->Mdiag); RT_COUNT(1);
+  if (P->form == RT_FORM_SIGMA) RT_TRY_CUDA(dev_alloc(P, (void**)&P->Ibuf, (size_t)P->N * sizeof(double)));
   RT_TRY_CUDA(cudaGetLastError());
   // FP32 tables
   std::vector<float> dtau32(Ns - 1), r32(nray), w032(nray), wI32(Nnu), wQ32(Nmu), t201f(Nmu), t202f(Nmu);
@@ -427,6 +433,14 @@ static void launch_formal64(const Problem* P, const double* x, double* y, const 
   k_formal<double, double, 0, MODE, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A); RT_COUNT(1);
 }
 
+void formal64_lambda(Problem* P, const double* S, double* I_out, double inflow_bottom, cudaStream_t st,
+                     const int* kstop, int step) {
+  FormalArgs A = formal_args(P, nullptr, I_out, S, P->ntile64, kstop, step);
+  A.inflow_bottom = inflow_bottom;
+  k_formal<double, double, 0, KM_RHS, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
+  RT_COUNT(1);
+}
+
 template <typename TV, int MODE>
 static void launch_formal32(const Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step) {
   const FormalArgs A = formal_args(P, x, y, P->S32, P->ntile32, kstop, step);
@@ -444,6 +458,7 @@ static void launch_formal32(const Problem* P, const TV* x, TV* y, cudaStream_t s
 }
 
 rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st, const int* kstop, int step) {
+  if (P->form == RT_FORM_SIGMA) return op_apply_sigma(P, x, y, mode, st, kstop, step);
   const double xiW2 = P->xi * P->W2;
   const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu;
   switch (mode) {
@@ -475,6 +490,14 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
 
 template <typename TV>
 static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStream_t st, const int* kstop, int step) {
+  if (P->form == RT_FORM_SIGMA) {
+    // the sigma-form operator has no FP32 variant: the solvers use the FP64 one
+    if (sizeof(TV) == 8)
+      return op_apply_sigma(P, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y), mode, st, kstop,
+                            step);
+    set_error("the sigma-form operator is FP64 only (use rt_apply)");
+    return RT_EINVAL;
+  }
   rt_status s = RT_OK;
   if (staged_apply32(P, x, y, sizeof(TV) == 8, mode, st, kstop, step, &s)) return s;
   const float xi = (float)P->xi, xiW2 = (float)(P->xi * P->W2);
@@ -516,6 +539,7 @@ rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cud
 }
 
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st) {
+  if (P->form == RT_FORM_SIGMA) return op_jacobi_sigma(P, dinv, 1, st);
   k_jacobi<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(P->cb, P->wray, P->t201d, P->t202d, P->Ns, P->Nmu,
                                                                  P->Nnu, P->xi, P->W2, 1, dinv); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
@@ -523,6 +547,7 @@ rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st) {
 }
 
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st) {
+  if (P->form == RT_FORM_SIGMA) return op_rhs_sigma(P, b, st);
   k_rhs_source<<<grid_for((int64_t)P->Ns * P->Nmu, 256, 4 * P->num_sms), 256, 0, st>>>(P->Bd, P->Ns, P->Nmu, P->eps,
                                                                                       P->S2); RT_COUNT(1);
   launch_formal64<KM_RHS>(P, nullptr, b, P->S2, st, nullptr, 0);
@@ -532,6 +557,7 @@ rt_status op_rhs(Problem* P, double* b, cudaStream_t st) {
 
 // z = P^{-1} v = v + beta* T M^{-1} J v
 rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st) {
+  if (P->form == RT_FORM_SIGMA) return op_precond_sigma(P, v, z, st);
   const double xiW2 = P->xi * P->W2;
   k_moments<double, double, KM_LOCAL_LAMBDA><<<P->Ns, kMomThreads, 0, st>>>(
       v, nullptr, P->wI2, P->wQ2, P->t201d, P->t202d, P->Minv, P->Ns, P->Nmu, P->Nnu, P->xi, xiW2, P->S2,
@@ -590,6 +616,7 @@ rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream) {
     return RT_EINVAL;
   }
   Problem* P = &prob->P;
+  if (P->form == RT_FORM_SIGMA) return op_jacobi_sigma(P, d_dev, 0, as_stream(stream));
   k_jacobi<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, as_stream(stream)>>>(
       P->cb, P->wray, P->t201d, P->t202d, P->Ns, P->Nmu, P->Nnu, P->xi, P->W2, 0, d_dev); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());

@@ -155,6 +155,7 @@ rt_status validate_desc(const rt_problem_desc* d) {
   if (d->tau_kind != RT_TAU_LINE_CENTER && d->tau_kind != RT_TAU_FREQ_INTEGRATED) { set_error("bad tau_kind"); return RT_EINVAL; }
   if (d->mu_quad != RT_MU_GL_HALF && d->mu_quad != RT_MU_GL_FULL) { set_error("bad mu_quad"); return RT_EINVAL; }
   if (d->formal_solver < RT_FS_DELO_LINEAR || d->formal_solver > RT_FS_TRAPEZOIDAL) { set_error("bad formal_solver"); return RT_EINVAL; }
+  if (d->form != RT_FORM_I && d->form != RT_FORM_SIGMA) { set_error("bad form"); return RT_EINVAL; }
   const int64_t N = 2LL * d->Ns * d->Nmu * d->Nnu;
   if (N > (int64_t)1 << 34) { set_error("problem too large (N=%lld)", (long long)N); return RT_EINVAL; }
   return RT_OK;
@@ -164,6 +165,8 @@ void host_grids(const rt_problem_desc* d, Problem& P) {
   P.Ns = d->Ns; P.Nmu = d->Nmu; P.Nnu = d->Nnu; P.Nh = d->Nmu / 2;
   P.nray = (int64_t)d->Nmu * d->Nnu;
   P.N = 2 * (int64_t)d->Ns * P.nray;
+  P.form = d->form;
+  P.Nop = d->form == RT_FORM_SIGMA ? 2 * (int64_t)d->Ns : P.N;
   P.eps = d->eps; P.xi = 1.0 - d->eps; P.W2 = d->W2; P.a = d->a;
   P.tau_kind = d->tau_kind; P.mu_quad = d->mu_quad; P.fs = d->formal_solver;
   P.freq_norm = d->freq_norm;
@@ -270,7 +273,7 @@ rt_status rt_problem_destroy(rt_problem* prob) {
   return RT_OK;
 }
 
-int64_t rt_problem_size(const rt_problem* prob) { return prob ? prob->P.N : -1; }
+int64_t rt_problem_size(const rt_problem* prob) { return prob ? prob->P.Nop : -1; }
 
 rt_status rt_problem_check(rt_problem* prob, void* stream) {
   clear_error();

@@ -50,7 +50,7 @@ int main(void) {
          sizeof(rt_problem_desc), sizeof(rt_solver_opts), sizeof(rt_solve_info), sizeof(rt_server_opts));
   F(rt_server_opts, precision);
   F(rt_problem_desc, tau); F(rt_problem_desc, phi_center); F(rt_problem_desc, W2);
-  F(rt_problem_desc, freq_norm);
+  F(rt_problem_desc, freq_norm); F(rt_problem_desc, form);
   F(rt_solver_opts, rtol); F(rt_solver_opts, resid_hist); F(rt_solver_opts, hist_cap);
   F(rt_solve_info, rel_resid); F(rt_solve_info, t_total_ms);
   return 0;
@@ -94,7 +94,7 @@ def _desc(**kw):
 
 @pytest.mark.parametrize("bad", [
     dict(Ns=1), dict(Nmu=3), dict(Nmu=0), dict(Nnu=1), dict(eps=0.0), dict(eps=1.5), dict(a=0.0),
-    dict(a=0.5), dict(x_min=4.0), dict(tau_kind=7), dict(mu_quad=5), dict(formal_solver=9),
+    dict(a=0.5), dict(x_min=4.0), dict(tau_kind=7), dict(mu_quad=5), dict(formal_solver=9), dict(form=2),
     dict(tau=np.r_[np.logspace(-4, 6, 9), 1.0]),
 ])
 def test_invalid_descriptors_are_rejected_on_the_host(lib, bad):
