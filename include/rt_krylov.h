@@ -272,6 +272,15 @@ rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const 
 rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                        double* x_dev, rt_solve_info* info, void* stream);
 
+/* Preconditioned Richardson iteration x <- x + M^-1 (b - A x) (Eq. 20); with
+   the Jacobi preconditioner this is the Jacobi-Richardson (ALI) iteration the
+   paper compares the Krylov solvers with (Sect. 2.3, Table 3).  Stops when
+   ||b - A x|| / ||b|| < rtol (the unpreconditioned residual, computed every
+   iteration) or after maxit updates; iters counts the updates.  FP64;
+   preconditioners NONE, JACOBI, LOCAL_LAMBDA; either form. */
+rt_status rt_solve_richardson(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
+                              double* x_dev, rt_solve_info* info, void* stream);
+
 /* ----------------------------------------------------- batching and serving
    A server keeps many atmospheres resident on the device and solves them
    together by restarted GMRES(m) in lock-step: every phase of an Arnoldi step

@@ -87,6 +87,7 @@ SIGNATURES = [
     ("rt_solve_gmres", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),
     ("rt_solve_bicgstab", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),
     ("rt_solve_cgs", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),
+    ("rt_solve_richardson", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),
     ("rt_server_opts_default", None, [C.POINTER(ServerOpts)]),
     ("rt_server_create", C.c_int, [C.POINTER(ServerOpts), C.POINTER(_P)]),
     ("rt_batch_submit", C.c_int, [_P, C.POINTER(ProblemDesc), C.POINTER(SolverOpts), C.POINTER(C.c_uint64)]),

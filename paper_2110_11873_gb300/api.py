@@ -290,7 +290,7 @@ class Problem:
             o.resid_hist, o.hist_cap = _dptr(hist), hist_cap
         info = N.SolveInfo()
         fn = {"gmres": self.lib.rt_solve_gmres, "bicgstab": self.lib.rt_solve_bicgstab,
-              "cgs": self.lib.rt_solve_cgs}[method]
+              "cgs": self.lib.rt_solve_cgs, "richardson": self.lib.rt_solve_richardson}[method]
         st = fn(self.handle, C.byref(o), C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), C.byref(info),
                 _stream_handle(stream))
         res = SolveResult(info.status, info.iters, info.restarts, info.applies, info.refine_steps,

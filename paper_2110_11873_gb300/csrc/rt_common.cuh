@@ -158,7 +158,8 @@ rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaS
                          const int* kstop = nullptr, int step = 0);
 rt_status op_rhs_sigma(Problem* P, double* b, cudaStream_t st);
 rt_status op_jacobi_sigma(Problem* P, double* d, int inverse, cudaStream_t st);
-rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st);
+rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop = nullptr,
+                           int step = 0);
 // fast FP32 apply (rt_tma.cu): usable for this problem, its tables, and
   // the device flag its bounded waits set when they give up
   int staged = 0;
@@ -179,7 +180,8 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
 rt_status op_apply32(Problem* P, const float* x, float* y, int mode, cudaStream_t st);
 rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cudaStream_t st,
                            const int* kstop = nullptr, int step = 0);
-rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st);
+rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop = nullptr,
+                        int step = 0);
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st);
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st);
 void release_graphs(Problem* P);
@@ -192,7 +194,8 @@ rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaS
                          const int* kstop = nullptr, int step = 0);
 rt_status op_rhs_sigma(Problem* P, double* b, cudaStream_t st);
 rt_status op_jacobi_sigma(Problem* P, double* d, int inverse, cudaStream_t st);
-rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st);
+rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop = nullptr,
+                           int step = 0);
 // fast FP32 apply (rt_tma.cu)
 rt_status staged_setup(Problem* P, cudaStream_t st);
 bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cudaStream_t st, const int* kstop,

@@ -787,6 +787,59 @@ __global__ void __launch_bounds__(kVecThreads) k_mul(const double* __restrict__ 
     y[n] = x[n] * d[n];
 }
 
+// ----------------------------------------------------------- Richardson
+// x <- x + M^-1 r, r = b - A x (Eq. 20), kRichSteps iterations per graph
+// launch, each gated on the step counter kstop of the GMRES state, which the
+// check kernel lowers (and flags in kdone) once the iteration has stopped.
+constexpr int kRichSteps = 8;
+
+__global__ void k_rich_begin(GmresDev* gm) { gm->kstop = kRichSteps; }
+
+// x += d * z (Jacobi) or x += z
+__global__ void __launch_bounds__(kVecThreads) k_rich_update(double* __restrict__ x, const double* __restrict__ z,
+                                                             const double* __restrict__ d, int64_t N,
+                                                             const int* kstop, int step) {
+  if (step >= *kstop) return;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+    x[n] += d ? d[n] * z[n] : z[n];
+}
+
+// r = b - Ax, partials of ||r||^2
+__global__ void __launch_bounds__(kVecThreads) k_rich_resid(const double* __restrict__ b,
+                                                            const double* __restrict__ Ax, double* __restrict__ r,
+                                                            int64_t N, double* __restrict__ part, const int* kstop,
+                                                            int step) {
+  if (step >= *kstop) return;
+  double s = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[n] - Ax[n];
+    r[n] = v;
+    s = fma(v, v, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// one warp: rel = ||r|| / ||b||, one more iteration; stop (kstop = step + 1)
+// once rel < tol (or is not a number) or the iteration budget is spent
+__global__ void k_rich_check(const double* __restrict__ part, int G, GmresDev* gm, double* hist, int hist_cap,
+                             int step) {
+  if (step >= gm->kstop) return;
+  const double s = sum_partials_warp(part, G);
+  if (threadIdx.x == 0) {
+    const double rel = sqrt(s) / gm->bnorm;
+    const int it = gm->iters;
+    if (hist && it < hist_cap) hist[it] = rel;
+    gm->iters = it + 1;
+    gm->rel = rel;
+    gm->hist_len = it + 1 < hist_cap ? it + 1 : hist_cap;
+    if (!(rel >= gm->tol) || it + 1 >= gm->maxit) {
+      gm->kstop = step + 1;
+      gm->kdone = 1;   // stopped: the host launches no further graph
+    }
+  }
+}
+
 // y = d * x inside a captured GMRES cycle (skipped once step >= *kstop)
 __global__ void __launch_bounds__(kVecThreads) k_mul_gated(const double* __restrict__ x,
                                                            const double* __restrict__ d, double* __restrict__ y,
@@ -879,6 +932,7 @@ struct GmresGraphKey {
 struct GraphCache {
   std::map<GmresGraphKey, cudaGraphExec_t> gmres;
   cudaGraphExec_t bicg[2][3][2] = {};  // [method][precond][fp32]
+  cudaGraphExec_t rich[3] = {};         // [precond]
   std::map<cudaGraphExec_t, long long> kernels;  // kernel nodes per executable graph
   cudaStream_t cap = nullptr;
   ~GraphCache() {
@@ -887,6 +941,8 @@ struct GraphCache {
       for (auto& b : a)
         for (auto& c : b)
           if (c) cudaGraphExecDestroy(c);
+    for (auto& r : rich)
+      if (r) cudaGraphExecDestroy(r);
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -1270,6 +1326,106 @@ static rt_status enqueue_bicg_iter(Problem* P, int method, int precond, int fp32
 // not look at the flag, so an iteration after convergence still computes an
 // (unused) product; the graph therefore holds one iteration and the host
 // checks the flag after every launch.
+// Richardson iterations of one graph launch: vectors x = wk(0), b = wk(1),
+// r = wk(2), Ax = wk(5), z = wk(6)
+static rt_status enqueue_rich(Problem* P, int precond, cudaStream_t st) {
+  const int G = P->vec_grid;
+  const int64_t N = P->Nop;
+  GmresDev* gm = P->gm;
+  const int* kstop = &gm->kstop;
+  k_rich_begin<<<1, 1, 0, st>>>(gm); RT_COUNT(1);
+  for (int s = 0; s < kRichSteps; ++s) {
+    if (precond == RT_PREC_LOCAL_LAMBDA) {
+      RT_TRY(op_precond_ll(P, wk(P, 2), wk(P, 6), st, kstop, s));
+      k_rich_update<<<G, kVecThreads, 0, st>>>(wk(P, 0), wk(P, 6), nullptr, N, kstop, s); RT_COUNT(1);
+    } else {
+      k_rich_update<<<G, kVecThreads, 0, st>>>(wk(P, 0), wk(P, 2), precond == RT_PREC_JACOBI ? P->dinv : nullptr, N,
+                                               kstop, s); RT_COUNT(1);
+    }
+    RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st, kstop, s));
+    k_rich_resid<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0), kstop, s); RT_COUNT(1);
+    k_rich_check<<<1, 32, 0, st>>>(partb(P, 0), G, gm, P->hist, P->hist_cap_dev, s); RT_COUNT(1);
+  }
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+static rt_status solve_richardson(Problem* P, const rt_solver_opts* o, const double* b, double* x,
+                                  rt_solve_info* info, cudaStream_t st) {
+  const double t0 = now_ms();
+  if (info) memset(info, 0, sizeof *info);
+  if (o->precision != RT_PRECISION_FP64 || o->precond == RT_PREC_JACOBI_LEFT) {
+    set_error("Richardson: FP64, preconditioned from the right (NONE, JACOBI, LOCAL_LAMBDA)");
+    return finish_info(info, RT_EINVAL, t0);
+  }
+  RT_TRY(prepare(P, o, 1, st));
+  const int G = P->vec_grid;
+  const int64_t N = P->Nop;
+  const size_t bytes = (size_t)N * sizeof(double);
+  RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
+  int applies = 0;
+  if (o->x0_kind == RT_X0_USER) {
+    RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), x, bytes, cudaMemcpyDeviceToDevice, st));
+    RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
+    k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
+    applies = 1;
+  } else {
+    RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 2), b, bytes, cudaMemcpyDeviceToDevice, st));
+    k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 2), wk(P, 2), N, partb(P, 0), nullptr, 0, nullptr); RT_COUNT(1);
+  }
+  k_dot<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 1), N, partb(P, 1), nullptr, 0, nullptr); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  std::vector<double> h(2 * G);
+  RT_TRY_CUDA(cudaMemcpyAsync(h.data(), partb(P, 0), G * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaMemcpyAsync(h.data() + G, partb(P, 1), G * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  double rr = 0, bb = 0;
+  for (int i = 0; i < G; ++i) { rr += h[i]; bb += h[G + i]; }
+  std::unique_ptr<GmresDev> hsp(new GmresDev);
+  GmresDev& hs = *hsp;
+  memset(&hs, 0, kGmresHeader);
+  hs.bnorm = sqrt(bb);
+  hs.tol = o->rtol;
+  hs.maxit = o->maxit;
+  hs.rel = hs.bnorm > 0.0 ? sqrt(rr) / hs.bnorm : 0.0;
+  rt_status s = RT_OK;
+  if (hs.bnorm > 0.0 && hs.rel >= o->rtol) {
+    RT_TRY_CUDA(cudaMemcpyAsync(P->gm, &hs, kGmresHeader, cudaMemcpyHostToDevice, st));
+    GraphCache* gc = cache_of(P);
+    cudaGraphExec_t& ex = gc->rich[o->precond];
+    if (!ex) {
+      const int prec = o->precond;
+      RT_TRY(capture_graph(gc, [&](cudaStream_t cs) { return enqueue_rich(P, prec, cs); }, &ex));
+    }
+    for (;;) {
+      RT_TRY(launch_graph(gc, ex, st));
+      RT_TRY_CUDA(cudaMemcpyAsync(&hs, P->gm, kGmresHeader, cudaMemcpyDeviceToHost, st));
+      RT_TRY_CUDA(cudaStreamSynchronize(st));
+      if (hs.kdone) break;   // stopped inside this launch
+    }
+  } else if (hs.bnorm == 0.0) {
+    RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
+    hs.rel = 0.0;
+  }
+  if (hs.rel != hs.rel) s = RT_ENUMERIC;
+  else if (!(hs.rel < o->rtol) && hs.bnorm > 0.0) s = RT_ENOTCONV;
+  RT_TRY_CUDA(cudaMemcpyAsync(x, wk(P, 0), bytes, cudaMemcpyDeviceToDevice, st));
+  int hl = 0;
+  if (o->resid_hist && o->hist_cap > 0 && P->hist) {
+    hl = hs.iters < o->hist_cap ? hs.iters : o->hist_cap;
+    if (hl) RT_TRY_CUDA(cudaMemcpyAsync(o->resid_hist, P->hist, hl * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
+  if (info) {
+    info->iters = hs.iters;
+    info->applies = applies + hs.iters;
+    info->rel_resid = hs.rel;
+    info->hist_len = hl;
+  }
+  return finish_info(info, s, t0);
+}
+
 static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, const double* b, double* x,
                             rt_solve_info* info, cudaStream_t st) {
   const double t0 = now_ms();
@@ -1466,6 +1622,14 @@ rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const doubl
   if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
   RT_TRY(check_opts(opts, b_dev, x_dev));
   return solve_bicg(&prob->P, 1, opts, b_dev, x_dev, info, as_stream(stream));
+}
+
+rt_status rt_solve_richardson(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,
+                              rt_solve_info* info, void* stream) {
+  clear_error();
+  if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
+  RT_TRY(check_opts(opts, b_dev, x_dev));
+  return solve_richardson(&prob->P, opts, b_dev, x_dev, info, as_stream(stream));
 }
 
 }  // extern "C"

@@ -149,7 +149,8 @@ __global__ void k_rhs_source(const double* __restrict__ B, int Ns, int Nmu, doub
 
 // z = v + beta* S (the Lambda* T M^{-1} J part of P^{-1} v, S = T M^{-1} J v)
 __global__ void k_add_local(const double* __restrict__ v, const double* __restrict__ cb, const double* __restrict__ S,
-                            int Ns, int Nmu, int Nnu, double* __restrict__ z) {
+                            int Ns, int Nmu, int Nnu, double* __restrict__ z, const int* kstop, int step) {
+  if (kstop && step >= *kstop) return;
   const int Nh = Nmu / 2;
   const int64_t nray = (int64_t)Nmu * Nnu, N = 2 * (int64_t)Ns * nray;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -556,13 +557,14 @@ rt_status op_rhs(Problem* P, double* b, cudaStream_t st) {
 }
 
 // z = P^{-1} v = v + beta* T M^{-1} J v
-rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st) {
-  if (P->form == RT_FORM_SIGMA) return op_precond_sigma(P, v, z, st);
+rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop, int step) {
+  if (P->form == RT_FORM_SIGMA) return op_precond_sigma(P, v, z, st, kstop, step);
   const double xiW2 = P->xi * P->W2;
   k_moments<double, double, KM_LOCAL_LAMBDA><<<P->Ns, kMomThreads, 0, st>>>(
       v, nullptr, P->wI2, P->wQ2, P->t201d, P->t202d, P->Minv, P->Ns, P->Nmu, P->Nnu, P->xi, xiW2, P->S2,
-      nullptr, 0); RT_COUNT(1);
-  k_add_local<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(v, P->cb, P->S2, P->Ns, P->Nmu, P->Nnu, z); RT_COUNT(1);
+      kstop, step); RT_COUNT(1);
+  k_add_local<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(v, P->cb, P->S2, P->Ns, P->Nmu, P->Nnu, z, kstop,
+                                                                    step); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }

@@ -117,7 +117,8 @@ __global__ void k_sig_jacobi(const double* __restrict__ Mdiag, int n, int invers
 
 // z_k = M_k^-1 v_k
 __global__ void k_sig_block(const double* __restrict__ v, const double* __restrict__ Minv, int Ns,
-                            double* __restrict__ z) {
+                            double* __restrict__ z, const int* kstop, int step) {
+  if (kstop && step >= *kstop) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Ns; k += gridDim.x * blockDim.x) {
     double z0, z1;
     precond_pair(KM_LOCAL_LAMBDA, v, nullptr, Minv, k, z0, z1);
@@ -177,8 +178,8 @@ rt_status op_jacobi_sigma(Problem* P, double* d, int inverse, cudaStream_t st) {
   return RT_OK;
 }
 
-rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st) {
-  k_sig_block<<<blocks_for(P->Ns, 256, 4 * P->num_sms), 256, 0, st>>>(v, P->Minv, P->Ns, z);
+rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop, int step) {
+  k_sig_block<<<blocks_for(P->Ns, 256, 4 * P->num_sms), 256, 0, st>>>(v, P->Minv, P->Ns, z, kstop, step);
   RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;

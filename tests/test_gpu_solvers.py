@@ -178,3 +178,22 @@ def test_slab300_gmres_fp64_and_mixed(fs):
     x = to_host(xm)
     assert _true_rel(tr, b, x) < 1e-8
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-6
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "local_lambda"])
+def test_richardson_matches_the_oracle(precond):
+    """Preconditioned Richardson (Eq. 20) on an I-form atmosphere with
+    eps = 1e-2 (a few dozen sweeps): the same count as the oracle's loop
+    within 1, and the true residual below the tolerance."""
+    at = W.slab(30, 8, 21, 1e-4, 1e6, 6.0, eps=1e-2)
+    tr = Transfer(at)
+    P = problem(at)
+    b = tr.rhs_I()
+    M_inv = (lambda v: v / tr.jacobi_I()) if precond == "jacobi" else tr.local_lambda_I_inverse
+    _, oi = K.richardson(tr.apply_I, b, M_inv=M_inv, tol=1e-8, maxit=5000)
+    xg, info = P.solve(to_dev(b), "richardson", precond=precond, rtol=1e-8, maxit=5000, hist_cap=5000)
+    assert info.status == 0, info
+    assert abs(info.iters - oi.iters) <= 1, (info.iters, oi.iters)
+    x = to_host(xg)
+    assert np.linalg.norm(b - tr.apply_I(x)) / np.linalg.norm(b) < 1e-8
+    assert len(info.history) == info.iters and info.history[-1] < 1e-8 <= info.history[-2]
