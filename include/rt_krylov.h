@@ -61,8 +61,13 @@ enum { RT_TAU_LINE_CENTER = 0, RT_TAU_FREQ_INTEGRATED = 1 };
 /* angular quadrature: Gauss-Legendre per hemisphere (Nmu/2 nodes on [0,1] and
    their mirror) or Nmu Gauss-Legendre nodes on [-1,1] (Sect. 4.1) */
 enum { RT_MU_GL_HALF = 0, RT_MU_GL_FULL = 1 };
-/* formal solver (Sect. 4.1): DELO-linear, implicit Euler, trapezoidal */
-enum { RT_FS_DELO_LINEAR = 0, RT_FS_IMPLICIT_EULER = 1, RT_FS_TRAPEZOIDAL = 2 };
+/* formal solver (Sect. 4.1): DELO-linear, implicit Euler, trapezoidal, and
+   DELO-parabolic (the exponential integrator with the source function
+   interpolated by the parabola through the upwind, current and downwind
+   nodes; the paper names the parabolic DELO methods without formulas).
+   DELO-parabolic is FP64 only: rt_apply_f32, RT_PRECISION_FP32_REFINE and the
+   batch server reject it. */
+enum { RT_FS_DELO_LINEAR = 0, RT_FS_IMPLICIT_EULER = 1, RT_FS_TRAPEZOIDAL = 2, RT_FS_DELO_PARABOLIC = 3 };
 /* linear system (Sect. 3.2):
    RT_FORM_I      Eq. (19): unknown I, N = 2*Ns*Nmu*Nnu values x[s][k][m][p],
                   A x = x - Lambda(T(J x)), b = Lambda T c + t;

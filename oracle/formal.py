@@ -22,6 +22,19 @@ earlier papers for their formulas, which are not reproduced in it.  Readings:
 * implicit Euler (backward Euler in t):  I_k = (I_prev + Delta S_k)/(1+Delta).
 * trapezoidal (Crank-Nicolson in t):
       I_k = ((1 - Delta/2) I_prev + Delta/2 (S_prev + S_k)) / (1 + Delta/2).
+* DELO-parabolic (the paper also names DELOPAR and DELO-parabolic, Sect. 4.1,
+  again without formulas): S is interpolated by the parabola through the
+  upwind, current and downwind nodes of the ray and the RTE is integrated
+  exactly over the interval, so the step map gains a downwind term,
+      I_k = e * I_prev + alpha * S_prev + beta * S_k + gamma * S_next.
+  With Delta' the downwind optical path and
+      q = int_0^Delta e^{-v} v (v - Delta) dv = Delta ((2 - Delta) a - Delta e)
+  (a = alpha of DELO-linear; the Taylor series of q/Delta^3 for small Delta)
+  the weights are those of DELO-linear plus a correction in q:
+      alpha = a + q / (Delta (Delta + Delta')),  beta = b - q / (Delta Delta'),
+      gamma = q / (Delta' (Delta + Delta')).
+  On the last interval of a ray (no downwind node) the step is DELO-linear.
+  The method is exact for S quadratic in t.
 
 Geometry (Sect. 3.1, boundary conditions after Eq. 10; Algorithm 1): heights
 are indexed top (k=0, smallest tau) to bottom (k=N_s-1).  Rays with mu<0 enter
@@ -39,6 +52,7 @@ import numpy as np
 FS_DELO_LINEAR = 0
 FS_IMPLICIT_EULER = 1
 FS_TRAPEZOIDAL = 2
+FS_DELO_PARABOLIC = 3
 
 # below this optical path, DELO-linear coefficients come from their Taylor series
 DELO_SERIES_BELOW = 1.0
@@ -83,6 +97,40 @@ def trapezoidal(D: np.ndarray):
     return e, ab, ab.copy()
 
 
+def parabolic_q(D: np.ndarray) -> np.ndarray:
+    """q = int_0^Delta e^{-v} v (v - Delta) dv, from the DELO-linear alpha for
+    Delta >= DELO_SERIES_BELOW and from the Taylor series
+    q = -sum_{j>=0} (-1)^j Delta^{j+3} / (j! (j+2) (j+3)) below."""
+    D = np.asarray(D, dtype=np.float64)
+    e, a, _ = delo_linear(D)
+    q = D * ((2.0 - D) * a - D * e)
+    small = D < DELO_SERIES_BELOW
+    if np.any(small):
+        d = D[small]
+        acc = np.zeros_like(d)
+        for j in range(_SERIES_TERMS + 1):
+            acc += (-1.0) ** j * d ** j / (math.factorial(j) * (j + 2) * (j + 3))
+        q = q.copy()
+        q[small] = -acc * d ** 3
+    return q
+
+
+def delo_parabolic(D: np.ndarray, Dn: np.ndarray):
+    """(e, alpha, beta, gamma) of the parabolic step over an interval of optical
+    path D whose downwind interval has optical path Dn (Dn = 0: no downwind
+    node, the DELO-linear step)."""
+    D = np.asarray(D, dtype=np.float64)
+    Dn = np.asarray(Dn, dtype=np.float64)
+    e, a, b = delo_linear(D)
+    q = parabolic_q(D)
+    has = Dn > 0.0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        alpha = np.where(has, a + q / (D * (D + Dn)), a)
+        beta = np.where(has, b - q / (D * Dn), b)
+        gamma = np.where(has, q / (Dn * (D + Dn)), 0.0)
+    return e, alpha, beta, gamma
+
+
 def step_coefficients(fs: int, D: np.ndarray):
     if fs == FS_DELO_LINEAR:
         return delo_linear(D)
@@ -105,9 +153,17 @@ class FormalSolver:
     def __init__(self, g):
         self.g = g
         self.D = path_depths(g)
-        self.e, self.alpha, self.beta = step_coefficients(g.at.formal_solver, self.D)
         self.down = g.mu < 0.0      # enters at the top
         self.up = g.mu > 0.0        # enters at the bottom
+        self.gamma = None
+        if g.at.formal_solver == FS_DELO_PARABOLIC:
+            # downwind interval of every step: i+1 for mu<0 rays, i-1 for mu>0
+            Dn = np.zeros_like(self.D)
+            Dn[:-1, self.down, :] = self.D[1:, self.down, :]
+            Dn[1:, self.up, :] = self.D[:-1, self.up, :]
+            self.e, self.alpha, self.beta, self.gamma = delo_parabolic(self.D, Dn)
+        else:
+            self.e, self.alpha, self.beta = step_coefficients(g.at.formal_solver, self.D)
 
     def solve(self, S: np.ndarray, inflow_top=0.0, inflow_bottom=0.0) -> np.ndarray:
         """Formal solution of one Stokes parameter.
@@ -121,6 +177,7 @@ class FormalSolver:
         I = np.zeros((Ns, g.Nmu, Nnu))
         dn, up = self.down, self.up
         e, al, be = self.e, self.alpha, self.beta
+        ga = self.gamma
         # mu < 0: k = 0 -> N_s-1
         I[0, dn, :] = inflow_top
         for k in range(1, Ns):
@@ -128,6 +185,8 @@ class FormalSolver:
             I[k, dn, :] = (e[i, dn, :] * I[k - 1, dn, :]
                            + al[i, dn, :] * S[k - 1, dn][:, None]
                            + be[i, dn, :] * S[k, dn][:, None])
+            if ga is not None and k + 1 < Ns:
+                I[k, dn, :] += ga[i, dn, :] * S[k + 1, dn][:, None]
         # mu > 0: k = N_s-1 -> 0
         I[Ns - 1, up, :] = inflow_bottom
         for k in range(Ns - 2, -1, -1):
@@ -135,17 +194,27 @@ class FormalSolver:
             I[k, up, :] = (e[i, up, :] * I[k + 1, up, :]
                            + al[i, up, :] * S[k + 1, up][:, None]
                            + be[i, up, :] * S[k, up][:, None])
+            if ga is not None and k >= 1:
+                I[k, up, :] += ga[i, up, :] * S[k - 1, up][:, None]
         return I
 
     def beta_star(self) -> np.ndarray:
         """Coefficient of S_k in I_k (the diagonal of Lambda), shape (N_s, N_mu, N_nu).
 
         It is the beta of the step that ends at k; the node where a ray enters
-        takes the inflow only, so its entry is 0.
+        takes the inflow only, so its entry is 0.  With DELO-parabolic, S_k
+        also enters the step before (as its downwind node), and that part of
+        I_prev reaches I_k multiplied by e: beta* = beta_k + e_k gamma_{k-1}.
         """
         g = self.g
         bs = np.zeros((g.Ns, g.Nmu, g.Nnu))
         dn, up = self.down, self.up
         bs[1:, dn, :] = self.beta[:, dn, :]
         bs[:-1, up, :] = self.beta[:, up, :]
+        if self.gamma is not None:
+            e, ga = self.e, self.gamma
+            # mu<0: step ending at k uses interval k-1, the one before interval k-2
+            bs[2:, dn, :] += e[1:, dn, :] * ga[:-1, dn, :]
+            # mu>0: step ending at k uses interval k, the one before interval k+1
+            bs[:-2, up, :] += e[:-1, up, :] * ga[1:, up, :]
         return bs

@@ -1143,6 +1143,10 @@ rt_status rt_batch_submit(rt_server* srv, const rt_problem_desc* desc, const rt_
   RT_TRY(validate_desc(desc));
   if (desc->Ns > 4096) { set_error("batched instances need Ns <= 4096"); return RT_EINVAL; }
   if (desc->form != RT_FORM_I) { set_error("the batch server solves I-form problems only"); return RT_EINVAL; }
+  if (desc->formal_solver == RT_FS_DELO_PARABOLIC) {
+    set_error("the batch server does not take the DELO-parabolic formal solver");
+    return RT_EINVAL;
+  }
   Server* S = &srv->S;
   auto rq = std::make_unique<Request>();
   rq->desc = *desc;

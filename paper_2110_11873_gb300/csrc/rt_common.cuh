@@ -116,6 +116,7 @@ struct Problem {
   double* ce = nullptr;    // [(Ns-1)][nray] step factor e of the interval (i, i+1) on ray r
   double* ca = nullptr;    // ... alpha (coefficient of the upwind S)
   double* cb = nullptr;    // ... beta  (coefficient of S at the new node)
+  double* cg = nullptr;    // ... gamma (DELO-parabolic only: coefficient of S at the downwind node)
   double* wray = nullptr;  // [nray] hat-w_m * hat-w_p
   double* wI2 = nullptr;   // [Nnu] spectral weights hat-w_p
   double* wQ2 = nullptr;   // [Nmu] angular weights hat-w_m = w_m / 2

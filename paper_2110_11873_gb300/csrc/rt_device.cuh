@@ -23,11 +23,23 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// beta* (coefficient of S_k in I_k) of ray r = m*Nnu + p at height k
+// beta* (coefficient of S_k in I_k) of ray r = m*Nnu + p at height k: the
+// beta of the step ending at k; with the DELO-parabolic downwind coefficients
+// cg (else NULL) also e_k times the gamma of the step before, whose downwind
+// node is k.
 __device__ __forceinline__ double beta_star(const double* __restrict__ cb, int k, int m, int64_t r, int Ns,
-                                            int Nh, int64_t nray) {
-  if (m < Nh) return k == 0 ? 0.0 : cb[(int64_t)(k - 1) * nray + r];
-  return k == Ns - 1 ? 0.0 : cb[(int64_t)k * nray + r];
+                                            int Nh, int64_t nray, const double* __restrict__ ce = nullptr,
+                                            const double* __restrict__ cg = nullptr) {
+  if (m < Nh) {
+    if (k == 0) return 0.0;
+    double b = cb[(int64_t)(k - 1) * nray + r];
+    if (cg && k >= 2) b += ce[(int64_t)(k - 1) * nray + r] * cg[(int64_t)(k - 2) * nray + r];
+    return b;
+  }
+  if (k == Ns - 1) return 0.0;
+  double b = cb[(int64_t)k * nray + r];
+  if (cg && k <= Ns - 3) b += ce[(int64_t)k * nray + r] * cg[(int64_t)(k + 1) * nray + r];
+  return b;
 }
 
 // ----------------------------------------------------------------- K1: T∘J
@@ -147,6 +159,7 @@ struct FormalArgs {
   const double* ce;       // FP64 coefficient tables [(Ns-1)][nray]
   const double* ca;
   const double* cb;
+  const double* cg;       // DELO-parabolic: downwind coefficient table (else NULL)
   const float* dtau32;    // FP32: interval optical depths
   const float* r32;       // FP32: per-ray scale phi_hat/|mu|
   const void* S;          // source functions (TC) [2][Ns][Nmu]
@@ -164,9 +177,13 @@ struct FormalArgs {
 // [j0, j1) in marching order (node index j; height k = j for downward rays,
 // Ns-1-j for upward rays).  PHASE 0 composes the tile map (E, B) with zero
 // inflow; PHASE 1 sweeps from the inflow I and writes the output.
+// FP64 with FS = RT_FS_DELO_PARABOLIC: each step also takes gamma times S at
+// the downwind node (read from the ring, which then holds one node past the
+// tile; gamma is 0 on the last interval of a ray).
 template <typename TC, typename TV, int FS, int MODE, int PHASE, int NS, int RING>
 __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, int64_t r, int m, bool active, int j0,
                                       int j1, TC (&I)[NS], TC& E) {
+  constexpr bool PARA = sizeof(TC) == 8 && FS == RT_FS_DELO_PARABOLIC;
   const int Ns = A.Ns;
   const int64_t nray = A.nray;
   const int64_t plane = (int64_t)Ns * nray;
@@ -181,8 +198,17 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
   TC sp[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) sp[q] = Sm[q * sstride + (int64_t)height(j0 - 1) * A.Nmu];  // upwind source
+  // gamma of the step before j0 (its downwind node is the tile's first node)
+  TC gp = 0;
+  if (PARA && j0 >= 2) gp = (TC)A.cg[(int64_t)interval(j0 - 1) * nray + r];
   // register ring of the next RING steps
-  TC re[RING], ra[RING], rb[RING], rsv[RING][NS], rx[RING][NS], rd[RING][NS];
+  TC re[RING], ra[RING], rb[RING], rg[RING], rsv[RING][NS], rx[RING][NS], rd[RING][NS];
+  if (PARA) {
+#pragma unroll
+    for (int u = 0; u < RING; ++u)
+#pragma unroll
+      for (int q = 0; q < NS; ++q) rsv[u][q] = 0;
+  }
   auto load = [&](int u, int j) {
     if (j < j1) {
       const int k = height(j), i = interval(j);
@@ -191,6 +217,7 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
         re[u] = (TC)A.ce[c];
         ra[u] = (TC)A.ca[c];
         rb[u] = (TC)A.cb[c];
+        if (PARA) rg[u] = (TC)A.cg[c];
       } else {
         re[u] = (TC)A.dtau32[i];   // Delta = dtau_i * r_ray; coefficients formed at use
       }
@@ -203,6 +230,10 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
           if (MODE == KM_JACOBI) rd[u][q] = (TC)dinv[o];
         }
       }
+    } else if (PARA && j == j1 && j < Ns) {
+      // the downwind node of the tile's last step
+#pragma unroll
+      for (int q = 0; q < NS; ++q) rsv[u][q] = Sm[q * sstride + (int64_t)height(j) * A.Nmu];
     }
   };
   auto step = [&](int u, int j) {
@@ -223,15 +254,25 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
       const TC sk = rsv[u][q];
+      // beta S_k, plus gamma S_next for DELO-parabolic
+      const TC cur = PARA ? fma(be, sk, rg[u] * rsv[(u + 1) % RING][q]) : be * sk;
       if (PHASE == 0) {
-        I[q] = fma(e, I[q], fma(al, sp[q], be * sk));
+        I[q] = fma(e, I[q], fma(al, sp[q], cur));
       } else if (MODE == KM_LOCAL_LAMBDA) {
-        // y = (x + beta* S) - I = x - (e I_prev + alpha S_prev)
-        const TC t = fma(e, I[q], al * sp[q]);
-        if (active) y[q * plane + o] = (TV)(rx[u][q] - t);
-        I[q] = fma(be, sk, t);
+        // y = (x + beta* S) - I.  DELO-linear: x - (e I_prev + alpha S_prev).
+        // DELO-parabolic (beta* = beta + e gamma_prev, gamma_prev S_k being
+        // part of I_prev): x - (e (I_prev - gamma_prev S_k) + alpha S_prev + gamma S_next)
+        if (PARA) {
+          const TC t = fma(e, fma(-gp, sk, I[q]), fma(al, sp[q], rg[u] * rsv[(u + 1) % RING][q]));
+          if (active) y[q * plane + o] = (TV)(rx[u][q] - t);
+          I[q] = fma(fma(e, gp, be), sk, t);
+        } else {
+          const TC t = fma(e, I[q], al * sp[q]);
+          if (active) y[q * plane + o] = (TV)(rx[u][q] - t);
+          I[q] = fma(be, sk, t);
+        }
       } else {
-        I[q] = fma(e, I[q], fma(al, sp[q], be * sk));
+        I[q] = fma(e, I[q], fma(al, sp[q], cur));
         if (active) {
           if (MODE == KM_RHS) y[q * plane + o] = (TV)I[q];
           else if (MODE == KM_JACOBI) y[q * plane + o] = (TV)(rx[u][q] * rd[u][q] - I[q]);
@@ -240,6 +281,7 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
       }
       sp[q] = sk;
     }
+    if (PARA) gp = rg[u];
   };
 #pragma unroll
   for (int u = 0; u < RING; ++u) load(u, j0 + u);

@@ -35,16 +35,21 @@ namespace {
 // ------------------------------------------------------------- setup kernels
 // Step coefficients of the formal solvers, FP64, per interval i and ray r:
 // Delta = dtau_i * phi_hat_p / |mu_m|.
+// DELO-parabolic (cg != NULL): the DELO-linear coefficients corrected by
+// q = int_0^Delta e^{-v} v (v - Delta) dv and the downwind optical path Dn
+// (interval i+1 for downward rays, i-1 for upward ones; none on the last
+// interval of a ray, where the step stays DELO-linear):
+//   alpha += q / (D (D + Dn)),  beta -= q / (D Dn),  gamma = q / (Dn (D + Dn)).
 __global__ void k_coeffs64(const double* __restrict__ dtau, const double* __restrict__ rscale, int Ns,
-                           int64_t nray, int fs, double* __restrict__ ce, double* __restrict__ ca,
-                           double* __restrict__ cb) {
+                           int64_t nray, int Nh, int Nnu, int fs, double* __restrict__ ce, double* __restrict__ ca,
+                           double* __restrict__ cb, double* __restrict__ cg) {
   const int64_t n = (int64_t)(Ns - 1) * nray;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t % nray;
     const int i = (int)(t / nray);
     const double D = dtau[i] * rscale[r];
     double e, al, be;
-    if (fs == RT_FS_DELO_LINEAR) {
+    if (fs == RT_FS_DELO_LINEAR || fs == RT_FS_DELO_PARABOLIC) {
       e = exp(-D);
       if (D < 0.5) {
         // beta = sum_{n>=1} (-1)^{n+1} D^n/(n+1)!,  alpha = sum (-1)^{n+1} n D^n/(n+1)!
@@ -74,6 +79,30 @@ __global__ void k_coeffs64(const double* __restrict__ dtau, const double* __rest
       al = h * q2;
       be = al;
     }
+    if (fs == RT_FS_DELO_PARABOLIC) {
+      const bool down = (int)(r / Nnu) < Nh;
+      const int in = down ? i + 1 : i - 1;
+      double ga = 0.0;
+      if (in >= 0 && in < Ns - 1) {
+        const double Dn = dtau[in] * rscale[r];
+        double q;
+        if (D < 0.5) {
+          // q = -D^3 sum_{j>=0} (-D)^j / (j! (j+2) (j+3)) (0.5^25/25! ~ 1e-33)
+          double acc = 0.0, tj = 1.0;
+          for (int j = 0; j <= 24; ++j) {
+            acc += tj / ((j + 2.0) * (j + 3.0));
+            tj *= -D / (j + 1.0);
+          }
+          q = -acc * D * D * D;
+        } else {
+          q = D * ((2.0 - D) * al - D * e);
+        }
+        al += q / (D * (D + Dn));
+        be -= q / (D * Dn);
+        ga = q / (Dn * (D + Dn));
+      }
+      cg[t] = ga;
+    }
     ce[t] = e;
     ca[t] = al;
     cb[t] = be;
@@ -83,6 +112,8 @@ __global__ void k_coeffs64(const double* __restrict__ dtau, const double* __rest
 // 2x2 local blocks M_k = Id - J_k Lambda*_k T_k of the sigma-form, their
 // inverses and their diagonals, one block per height.
 __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __restrict__ cb,
+                                                             const double* __restrict__ ce,
+                                                             const double* __restrict__ cg,
                                                              const double* __restrict__ wray,
                                                              const double* __restrict__ t201,
                                                              const double* __restrict__ t202, int Ns, int Nmu,
@@ -95,7 +126,7 @@ __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __re
   double a0 = 0, a1 = 0, a2 = 0;
   for (int64_t r = threadIdx.x; r < nray; r += blockDim.x) {
     const int m = (int)(r / Nnu);
-    const double s = wray[r] * beta_star(cb, k, m, r, Ns, Nh, nray);
+    const double s = wray[r] * beta_star(cb, k, m, r, Ns, Nh, nray, ce, cg);
     a0 += s;
     a1 += t201[m] * s;
     a2 += (t201[m] * t201[m] + t202[m] * t202[m]) * s;
@@ -122,7 +153,8 @@ __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __re
 }
 
 // Jacobi diagonal of Id - Lambda T J, or its inverse
-__global__ void k_jacobi(const double* __restrict__ cb, const double* __restrict__ wray,
+__global__ void k_jacobi(const double* __restrict__ cb, const double* __restrict__ ce, const double* __restrict__ cg,
+                         const double* __restrict__ wray,
                          const double* __restrict__ t201, const double* __restrict__ t202, int Ns, int Nmu, int Nnu,
                          double xi, double W2, int inverse, double* __restrict__ d) {
   const int Nh = Nmu / 2;
@@ -132,7 +164,7 @@ __global__ void k_jacobi(const double* __restrict__ cb, const double* __restrict
     const int64_t sk = t / nray;
     const int k = (int)(sk % Ns), s = (int)(sk / Ns);
     const int m = (int)(r / Nnu);
-    const double bw = beta_star(cb, k, m, r, Ns, Nh, nray) * wray[r];
+    const double bw = beta_star(cb, k, m, r, Ns, Nh, nray, ce, cg) * wray[r];
     const double v = s == 0 ? 1.0 - xi * bw * (1.0 + W2 * t201[m] * t201[m]) : 1.0 - xi * W2 * bw * t202[m] * t202[m];
     d[t] = inverse ? 1.0 / v : v;
   }
@@ -148,7 +180,8 @@ __global__ void k_rhs_source(const double* __restrict__ B, int Ns, int Nmu, doub
 }
 
 // z = v + beta* S (the Lambda* T M^{-1} J part of P^{-1} v, S = T M^{-1} J v)
-__global__ void k_add_local(const double* __restrict__ v, const double* __restrict__ cb, const double* __restrict__ S,
+__global__ void k_add_local(const double* __restrict__ v, const double* __restrict__ cb, const double* __restrict__ ce,
+                            const double* __restrict__ cg, const double* __restrict__ S,
                             int Ns, int Nmu, int Nnu, double* __restrict__ z, const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
   const int Nh = Nmu / 2;
@@ -157,7 +190,7 @@ __global__ void k_add_local(const double* __restrict__ v, const double* __restri
     const int64_t r = t % nray, sk = t / nray;
     const int k = (int)(sk % Ns), s = (int)(sk / Ns);
     const int m = (int)(r / Nnu);
-    z[t] = v[t] + beta_star(cb, k, m, r, Ns, Nh, nray) * S[((int64_t)s * Ns + k) * Nmu + m];
+    z[t] = v[t] + beta_star(cb, k, m, r, Ns, Nh, nray, ce, cg) * S[((int64_t)s * Ns + k) * Nmu + m];
   }
 }
 
@@ -272,7 +305,7 @@ void free_device(Problem* P) {
   void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wray,   P->wI2,  P->wQ2,   P->t201d, P->t202d,
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
-                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf};
+                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf, P->cg};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
@@ -283,7 +316,7 @@ void free_device(Problem* P) {
   P->bc = nullptr;
   P->dev_err = nullptr;
   P->qw = P->St = P->qpart = nullptr;
-  P->Mdiag = P->Ibuf = nullptr;
+  P->Mdiag = P->Ibuf = P->cg = nullptr;
   P->staged = 0;
 }
 
@@ -370,12 +403,13 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->Minv, (size_t)Ns * 4 * sizeof(double)));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->S, (size_t)2 * Ns * Nmu * sizeof(double)));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->S2, (size_t)2 * Ns * Nmu * sizeof(double)));
-  k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_rs, Ns, nray, P->fs, P->ce,
-                                                                         P->ca, P->cb); RT_COUNT(1);
+  if (P->fs == RT_FS_DELO_PARABOLIC) RT_TRY_CUDA(dev_alloc(P, (void**)&P->cg, nc * sizeof(double)));
+  k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_rs, Ns, nray, Nh, Nnu, P->fs,
+                                                                         P->ce, P->ca, P->cb, P->cg); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mdiag, (size_t)Ns * 2 * sizeof(double)));
-  k_local_blocks<<<Ns, kMomThreads, 0, st>>>(P->cb, P->wray, P->t201d, P->t202d, Ns, Nmu, Nnu, P->xi, P->W2,
-                                             P->Minv, P->Mdiag); RT_COUNT(1);
+  k_local_blocks<<<Ns, kMomThreads, 0, st>>>(P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d, Ns, Nmu, Nnu, P->xi,
+                                             P->W2, P->Minv, P->Mdiag); RT_COUNT(1);
   if (P->form == RT_FORM_SIGMA) RT_TRY_CUDA(dev_alloc(P, (void**)&P->Ibuf, (size_t)P->N * sizeof(double)));
   RT_TRY_CUDA(cudaGetLastError());
   // FP32 tables
@@ -410,6 +444,7 @@ static FormalArgs formal_args(const Problem* P, const void* x, void* y, const vo
   A.ce = P->ce;
   A.ca = P->ca;
   A.cb = P->cb;
+  A.cg = P->cg;
   A.dtau32 = P->dtau32;
   A.r32 = P->r32;
   A.S = S;
@@ -431,14 +466,23 @@ template <int MODE>
 static void launch_formal64(const Problem* P, const double* x, double* y, const double* S, cudaStream_t st,
                             const int* kstop, int step) {
   const FormalArgs A = formal_args(P, x, y, S, P->ntile64, kstop, step);
-  k_formal<double, double, 0, MODE, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A); RT_COUNT(1);
+  if (P->fs == RT_FS_DELO_PARABOLIC)
+    k_formal<double, double, RT_FS_DELO_PARABOLIC, MODE, 2, kRing, kMaxTiles64>
+        <<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
+  else
+    k_formal<double, double, 0, MODE, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
+  RT_COUNT(1);
 }
 
 void formal64_lambda(Problem* P, const double* S, double* I_out, double inflow_bottom, cudaStream_t st,
                      const int* kstop, int step) {
   FormalArgs A = formal_args(P, nullptr, I_out, S, P->ntile64, kstop, step);
   A.inflow_bottom = inflow_bottom;
-  k_formal<double, double, 0, KM_RHS, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
+  if (P->fs == RT_FS_DELO_PARABOLIC)
+    k_formal<double, double, RT_FS_DELO_PARABOLIC, KM_RHS, 2, kRing, kMaxTiles64>
+        <<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
+  else
+    k_formal<double, double, 0, KM_RHS, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
   RT_COUNT(1);
 }
 
@@ -491,6 +535,10 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
 
 template <typename TV>
 static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStream_t st, const int* kstop, int step) {
+  if (P->fs == RT_FS_DELO_PARABOLIC) {
+    set_error("the DELO-parabolic formal solver is FP64 only (use rt_apply, FP64 solvers)");
+    return RT_EINVAL;
+  }
   if (P->form == RT_FORM_SIGMA) {
     // the sigma-form operator has no FP32 variant: the solvers use the FP64 one
     if (sizeof(TV) == 8)
@@ -541,8 +589,9 @@ rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cud
 
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st) {
   if (P->form == RT_FORM_SIGMA) return op_jacobi_sigma(P, dinv, 1, st);
-  k_jacobi<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(P->cb, P->wray, P->t201d, P->t202d, P->Ns, P->Nmu,
-                                                                 P->Nnu, P->xi, P->W2, 1, dinv); RT_COUNT(1);
+  k_jacobi<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d,
+                                                                 P->Ns, P->Nmu, P->Nnu, P->xi, P->W2, 1, dinv);
+  RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
@@ -563,8 +612,8 @@ rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st,
   k_moments<double, double, KM_LOCAL_LAMBDA><<<P->Ns, kMomThreads, 0, st>>>(
       v, nullptr, P->wI2, P->wQ2, P->t201d, P->t202d, P->Minv, P->Ns, P->Nmu, P->Nnu, P->xi, xiW2, P->S2,
       kstop, step); RT_COUNT(1);
-  k_add_local<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(v, P->cb, P->S2, P->Ns, P->Nmu, P->Nnu, z, kstop,
-                                                                    step); RT_COUNT(1);
+  k_add_local<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(v, P->cb, P->ce, P->cg, P->S2, P->Ns, P->Nmu,
+                                                                    P->Nnu, z, kstop, step); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
@@ -620,7 +669,7 @@ rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream) {
   Problem* P = &prob->P;
   if (P->form == RT_FORM_SIGMA) return op_jacobi_sigma(P, d_dev, 0, as_stream(stream));
   k_jacobi<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, as_stream(stream)>>>(
-      P->cb, P->wray, P->t201d, P->t202d, P->Ns, P->Nmu, P->Nnu, P->xi, P->W2, 0, d_dev); RT_COUNT(1);
+      P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d, P->Ns, P->Nmu, P->Nnu, P->xi, P->W2, 0, d_dev); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }

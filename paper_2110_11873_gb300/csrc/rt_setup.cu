@@ -154,7 +154,7 @@ rt_status validate_desc(const rt_problem_desc* d) {
   }
   if (d->tau_kind != RT_TAU_LINE_CENTER && d->tau_kind != RT_TAU_FREQ_INTEGRATED) { set_error("bad tau_kind"); return RT_EINVAL; }
   if (d->mu_quad != RT_MU_GL_HALF && d->mu_quad != RT_MU_GL_FULL) { set_error("bad mu_quad"); return RT_EINVAL; }
-  if (d->formal_solver < RT_FS_DELO_LINEAR || d->formal_solver > RT_FS_TRAPEZOIDAL) { set_error("bad formal_solver"); return RT_EINVAL; }
+  if (d->formal_solver < RT_FS_DELO_LINEAR || d->formal_solver > RT_FS_DELO_PARABOLIC) { set_error("bad formal_solver"); return RT_EINVAL; }
   if (d->form != RT_FORM_I && d->form != RT_FORM_SIGMA) { set_error("bad form"); return RT_EINVAL; }
   const int64_t N = 2LL * d->Ns * d->Nmu * d->Nnu;
   if (N > (int64_t)1 << 34) { set_error("problem too large (N=%lld)", (long long)N); return RT_EINVAL; }

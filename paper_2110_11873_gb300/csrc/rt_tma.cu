@@ -671,7 +671,7 @@ int choose_tiles_staged(const Problem* P) {
 // batch arena, or when RT_NO_TMA=1 is set in the environment.
 rt_status staged_setup(Problem* P, cudaStream_t st) {
   P->staged = 0;
-  if (P->alloc || P->form == RT_FORM_SIGMA) return RT_OK;
+  if (P->alloc || P->form == RT_FORM_SIGMA || P->fs == RT_FS_DELO_PARABOLIC) return RT_OK;
   const char* off = std::getenv("RT_NO_TMA");
   if (off && off[0] && off[0] != '0') return RT_OK;
   if ((P->nray % 4) || (P->nd % 4) || !P->dev_err) return RT_OK;

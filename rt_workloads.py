@@ -34,6 +34,7 @@ MU_GL_FULL = 1
 FS_DELO_LINEAR = 0
 FS_IMPLICIT_EULER = 1
 FS_TRAPEZOIDAL = 2
+FS_DELO_PARABOLIC = 3
 
 
 @dataclasses.dataclass
