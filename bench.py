@@ -268,6 +268,8 @@ def batch_bench(W, Server, Problem, torch, count):
             "solves": len(ok), "failed": count - len(ok), "wall_s": wall, "solves_per_s": len(ok) / wall,
             "iters_mean": sum(its) / max(len(its), 1), "rel_resid_max": max(rel) if rel else None,
             "cycles": stats["cycles"],
+            "grids_ctas": {"quadrature": stats["grid_quad"], "formal": stats["grid_formal"],
+                           "vector": stats["grid_vec"], "autotuned": bool(stats["tuned"])},
             "fp64_single_instance_solves_per_s": single, "fp64_single_instance_sample": n1,
             "rel_err_vs_fp64_max": max(errs), "rel_err_vs_fp64_mean": sum(errs) / len(errs),
             "rel_err_note": "||x_batched - x_fp64|| / ||x_fp64|| on the first 16 atmospheres; the FP64 "

@@ -310,11 +310,15 @@ typedef struct {
   int32_t precision;         /* RT_PRECISION_FP64, or RT_PRECISION_FP32_REFINE: FP32 operator in the
                                 Arnoldi steps, FP64 true residual at every restart (each restart is
                                 an iterative-refinement step) */
+  int32_t autotune;          /* 1: before the first cycle, time candidate grids of the persistent
+                                kernels (quadrature, formal solver, vector passes) on the resident
+                                instances and keep the fastest; 0: fixed grids.  Results do not
+                                depend on the grids. */
 } rt_server_opts;
 
 typedef struct rt_server rt_server;
 
-/* defaults: 8 GiB budget, 64 slots, restart 30, local-Lambda, FP64 */
+/* defaults: 8 GiB budget, 64 slots, restart 30, local-Lambda, FP64, autotune on */
 void rt_server_opts_default(rt_server_opts* opts);
 /* Create a server on the current device (the device stays the worker's). */
 rt_status rt_server_create(const rt_server_opts* opts, rt_server** out);
@@ -337,6 +341,10 @@ typedef struct {
   int64_t arena_largest_free;/* largest contiguous free block of the budget */
   int64_t cycles;            /* restart cycles run so far */
   int64_t completed;         /* requests finished so far */
+  int32_t grid_quad;         /* CTAs of the persistent quadrature kernel */
+  int32_t grid_formal;       /* CTAs of the persistent formal-solver kernel */
+  int32_t grid_vec;          /* CTAs of the persistent vector kernels */
+  int32_t tuned;             /* 1 once the grids were autotuned */
 } rt_server_stats;
 
 /* Snapshot of the server's state (for monitoring). */

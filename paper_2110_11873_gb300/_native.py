@@ -55,7 +55,7 @@ class SolveInfo(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [
         ("mem_budget_bytes", C.c_int64), ("max_slots", C.c_int32), ("restart", C.c_int32),
-        ("precond", C.c_int32), ("precision", C.c_int32),
+        ("precond", C.c_int32), ("precision", C.c_int32), ("autotune", C.c_int32),
     ]
 
 
@@ -63,6 +63,7 @@ class ServerStats(C.Structure):
     _fields_ = [
         ("resident", C.c_int32), ("queued", C.c_int32), ("arena_in_use", C.c_int64),
         ("arena_largest_free", C.c_int64), ("cycles", C.c_int64), ("completed", C.c_int64),
+        ("grid_quad", C.c_int32), ("grid_formal", C.c_int32), ("grid_vec", C.c_int32), ("tuned", C.c_int32),
     ]
 
 

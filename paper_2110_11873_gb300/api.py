@@ -69,7 +69,7 @@ class Server:
     """Batched / served solves (rt_server_*): submit atmospheres, poll results."""
 
     def __init__(self, mem_budget_bytes: int = 8 << 30, max_slots: int = 64, restart: int = 30,
-                 precond: str = "local_lambda", precision: str = "fp64"):
+                 precond: str = "local_lambda", precision: str = "fp64", autotune: bool = True):
         self.lib = N.load()
         o = N.ServerOpts()
         self.lib.rt_server_opts_default(C.byref(o))
@@ -77,6 +77,7 @@ class Server:
         o.precond = {"none": N.RT_PREC_NONE, "jacobi": N.RT_PREC_JACOBI,
                      "local_lambda": N.RT_PREC_LOCAL_LAMBDA}[precond]
         o.precision = {"fp64": N.RT_PRECISION_FP64, "fp32_refine": N.RT_PRECISION_FP32_REFINE}[precision]
+        o.autotune = 1 if autotune else 0
         h = C.c_void_p()
         N.check(self.lib.rt_server_create(C.byref(o), C.byref(h)), "rt_server_create")
         self.handle = h

@@ -611,7 +611,9 @@ struct Server {
   long long graph_kernels = 0;
   std::atomic<long long> cycles{0}, completed{0};
   std::atomic<int> resident{0};
-  int grid_h = 0, grid_g = 0, grid_v = 0, grid_i = 0;
+  int grid_h = 0, grid_g = 0, grid_v = 0, grid_i = 0;   // persistent grids (CTAs)
+  bool tuned = false;                                    // autotune_grids has run
+  int tuned_at = 0;                                      // resident instances at the tuning
 };
 
 namespace {
@@ -650,6 +652,116 @@ void formal32(Server* S, cudaStream_t st, int src, int dst, int step) {
                                                                                      S->d_counts, src, dst, step);
 }
 
+// the operator of every resident instance: w[dst] = A v[src] (quadrature,
+// then the formal solver), with the server's current grids
+void enqueue_apply(Server* S, cudaStream_t st, int src, int dst, int md, bool f32, int step) {
+  const InstDev* I = S->d_insts;
+  const Counts* C = S->d_counts;
+  if (!f32) {
+    switch (md) {
+      case KM_JACOBI:
+        kb_moments<double, KM_JACOBI><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_formal<double, 0, KM_JACOBI><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
+        break;
+      case KM_LOCAL_LAMBDA:
+        kb_moments<double, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_formal<double, 0, KM_LOCAL_LAMBDA><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst,
+                                                                                     step);
+        break;
+      default:
+        kb_moments<double, KM_PLAIN><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_formal<double, 0, KM_PLAIN><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
+    }
+  } else {
+    switch (md) {
+      case KM_JACOBI:
+        kb_moments<float, KM_JACOBI><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        formal32<KM_JACOBI>(S, st, src, dst, step);
+        break;
+      case KM_LOCAL_LAMBDA:
+        kb_moments<float, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        formal32<KM_LOCAL_LAMBDA>(S, st, src, dst, step);
+        break;
+      default:
+        kb_moments<float, KM_PLAIN><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        formal32<KM_PLAIN>(S, st, src, dst, step);
+    }
+  }
+}
+
+// Autotuner of the persistent grids: CTAs per SM of the quadrature, the
+// formal-solver and the vector kernels.  Run once per server, when at least
+// kTuneResident instances (or all slots) are resident, so the timing reflects
+// a loaded batch rather than the first request of a stream; the cycle graph
+// is recaptured with the result.  Every candidate
+// pair of quadrature / formal-solver grids runs the operator of the first
+// Arnoldi step, every vector grid a dot-product pass, twice each, timed
+// with events on the worker's stream; the fastest are kept.  The probe writes
+// only what the cycle recomputes before reading (the source functions, w,
+// the partials of buffer 0), and the batch's reductions do not depend on the
+// grid (one block per work item), so tuning changes no result.
+constexpr int kTuneResident = 64;   // resident instances that make the timing representative
+constexpr float kTuneMargin = 0.95f; // a candidate must beat the current grid by 5%
+
+rt_status autotune_grids(Server* S, int resident) {
+  const int prec = S->opts.precond;
+  const bool fp32 = S->opts.precision == RT_PRECISION_FP32_REFINE;
+  const int mode = prec == RT_PREC_JACOBI ? KM_JACOBI : prec == RT_PREC_LOCAL_LAMBDA ? KM_LOCAL_LAMBDA : KM_PLAIN;
+  cudaStream_t st = S->st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RT_TRY_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    RT_TRY_CUDA(ce);
+  }
+  auto timeit = [&](auto&& launch, float* ms) -> cudaError_t {
+    launch();   // warm-up
+    cudaError_t e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+  };
+  const int sms = S->sms;
+  cudaError_t e = cudaSuccess;
+  // one grid at a time (formal solver, quadrature, vector kernels), each
+  // candidate against the current choice, which it must beat by kTuneMargin
+  auto tune = [&](int* grid, const int (&per_sm)[3], auto&& launch) {
+    const int keep = *grid;
+    float best = 0.f;
+    e = timeit(launch, &best);
+    int pick = keep;
+    for (int c : per_sm) {
+      if (e != cudaSuccess || c * sms == keep) continue;
+      *grid = c * sms;
+      float ms = 0.f;
+      e = timeit(launch, &ms);
+      if (e == cudaSuccess && ms < kTuneMargin * best) {
+        best = ms;
+        pick = *grid;
+      }
+    }
+    *grid = pick;
+  };
+  const int gs[] = {4, 8, 16}, hs[] = {2, 4, 8}, vs[] = {2, 4, 8};
+  auto apply = [&] { enqueue_apply(S, st, 0, VW, mode, fp32, 0); RT_COUNT(fp32 ? 4 : 2); };
+  tune(&S->grid_g, gs, apply);
+  tune(&S->grid_h, hs, apply);
+  tune(&S->grid_v, vs, [&] {
+    kb_bdot<<<S->grid_v, kBT, 0, st>>>(S->d_insts, S->d_wl_c, S->d_counts, 0, 1);
+    RT_COUNT(1);
+  });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S->tuned = true;
+  S->tuned_at = resident;
+  RT_TRY_CUDA(e);
+  return RT_OK;
+}
+
 // enqueue one restart cycle for all resident instances (captured once)
 rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
   const int m = S->opts.restart;
@@ -658,38 +770,7 @@ rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
   const int mode = prec == RT_PREC_JACOBI ? KM_JACOBI : prec == RT_PREC_LOCAL_LAMBDA ? KM_LOCAL_LAMBDA : KM_PLAIN;
   const InstDev* I = S->d_insts;
   const Counts* C = S->d_counts;
-  auto apply = [&](int src, int dst, int md, bool f32, int step) {
-    if (!f32) {
-      switch (md) {
-        case KM_JACOBI:
-          kb_moments<double, KM_JACOBI><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
-          kb_formal<double, 0, KM_JACOBI><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
-          break;
-        case KM_LOCAL_LAMBDA:
-          kb_moments<double, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
-          kb_formal<double, 0, KM_LOCAL_LAMBDA><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst,
-                                                                                       step);
-          break;
-        default:
-          kb_moments<double, KM_PLAIN><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
-          kb_formal<double, 0, KM_PLAIN><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
-      }
-    } else {
-      switch (md) {
-        case KM_JACOBI:
-          kb_moments<float, KM_JACOBI><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
-          formal32<KM_JACOBI>(S, st, src, dst, step);
-          break;
-        case KM_LOCAL_LAMBDA:
-          kb_moments<float, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
-          formal32<KM_LOCAL_LAMBDA>(S, st, src, dst, step);
-          break;
-        default:
-          kb_moments<float, KM_PLAIN><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
-          formal32<KM_PLAIN>(S, st, src, dst, step);
-      }
-    }
-  };
+  auto apply = [&](int src, int dst, int md, bool f32, int step) { enqueue_apply(S, st, src, dst, md, f32, step); };
   for (int j = 0; j < m; ++j) {
     apply(j, VW, mode, fp32, j);
     int pb = 0;
@@ -1017,6 +1098,17 @@ void worker_main(Server* S) {
     rt_status s = RT_OK;
     if (!fresh.empty()) s = start_instances(S, fresh);
     if (s == RT_OK) s = rebuild_lists(S);
+    if (s == RT_OK && S->opts.autotune && !S->tuned) {
+      int nres = 0;
+      for (Instance* in : S->slots) nres += in != nullptr;
+      if (nres >= std::min(kTuneResident, S->opts.max_slots)) {
+        s = autotune_grids(S, nres);
+        if (s == RT_OK && S->graph) {   // the graph holds the old grids
+          cudaGraphExecDestroy(S->graph);
+          S->graph = nullptr;
+        }
+      }
+    }
     if (s == RT_OK) s = capture_cycle(S);
     if (s != RT_OK) {
       fail(s);
@@ -1087,6 +1179,7 @@ void rt_server_opts_default(rt_server_opts* o) {
   o->restart = 30;
   o->precond = RT_PREC_LOCAL_LAMBDA;
   o->precision = RT_PRECISION_FP64;
+  o->autotune = 1;
 }
 
 rt_status rt_server_create(const rt_server_opts* opts, rt_server** out) {
@@ -1221,6 +1314,10 @@ rt_status rt_server_stats_get(rt_server* srv, rt_server_stats* out) {
   out->arena_largest_free = (int64_t)S->arena.largest_hole();
   out->cycles = S->cycles.load();
   out->completed = S->completed.load();
+  out->grid_quad = S->grid_h;
+  out->grid_formal = S->grid_g;
+  out->grid_vec = S->grid_v;
+  out->tuned = S->tuned ? 1 : 0;
   return RT_OK;
 }
 

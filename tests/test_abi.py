@@ -46,9 +46,11 @@ _LAYOUT_C = r"""
 #include "rt_krylov.h"
 #define F(T, f) printf("%s.%s %zu\n", #T, #f, offsetof(T, f))
 int main(void) {
-  printf("rt_problem_desc %zu\nrt_solver_opts %zu\nrt_solve_info %zu\nrt_server_opts %zu\n",
-         sizeof(rt_problem_desc), sizeof(rt_solver_opts), sizeof(rt_solve_info), sizeof(rt_server_opts));
-  F(rt_server_opts, precision);
+  printf("rt_problem_desc %zu\nrt_solver_opts %zu\nrt_solve_info %zu\nrt_server_opts %zu\nrt_server_stats %zu\n",
+         sizeof(rt_problem_desc), sizeof(rt_solver_opts), sizeof(rt_solve_info), sizeof(rt_server_opts),
+         sizeof(rt_server_stats));
+  F(rt_server_opts, precision); F(rt_server_opts, autotune);
+  F(rt_server_stats, completed); F(rt_server_stats, grid_quad); F(rt_server_stats, tuned);
   F(rt_problem_desc, tau); F(rt_problem_desc, phi_center); F(rt_problem_desc, W2);
   F(rt_problem_desc, freq_norm); F(rt_problem_desc, form);
   F(rt_solver_opts, rtol); F(rt_solver_opts, resid_hist); F(rt_solver_opts, hist_cap);
@@ -66,7 +68,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                                check=True).stdout.split("\n") if line)
     structs = {"rt_problem_desc": N.ProblemDesc, "rt_solver_opts": N.SolverOpts, "rt_solve_info": N.SolveInfo,
-               "rt_server_opts": N.ServerOpts}
+               "rt_server_opts": N.ServerOpts, "rt_server_stats": N.ServerStats}
     for name, cls in structs.items():
         assert int(got[name]) == C.sizeof(cls), name
     for key, val in got.items():

@@ -13,6 +13,7 @@
 import time
 
 import numpy as np
+import torch
 import pytest
 
 import rt_workloads as W
@@ -135,3 +136,28 @@ def test_admission_by_memory_budget_and_late_arrivals(cases):
     (st, info, x), = _wait(srv, [t]).values()
     assert st == N.RT_ENOMEM
     srv.close()
+
+
+def test_autotuned_grids_change_no_result(cases):
+    """The server times candidate grids of its persistent kernels on the
+    resident work before the first cycle and keeps the fastest; the batch's
+    reductions do not depend on the grids, so the solutions are bit-identical
+    with and without tuning."""
+    ats, trs, bs, xs = cases
+    out = {}
+    for tune in (True, False):
+        # tuning starts once all slots (or 64 instances) are resident
+        srv = Server(mem_budget_bytes=1 << 30, max_slots=len(ats), precond="local_lambda", autotune=tune)
+        tickets = [srv.submit(a) for a in ats]
+        res = _wait(srv, tickets)
+        st = srv.stats()
+        assert st["tuned"] == (1 if tune else 0)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        for key in ("grid_quad", "grid_formal", "grid_vec"):
+            assert st[key] > 0 and st[key] % sms == 0, (key, st)
+        out[tune] = [res[t] for t in tickets]
+        srv.close()
+    for (s1, i1, x1), (s2, i2, x2) in zip(out[True], out[False]):
+        assert s1 == s2 == N.RT_OK
+        assert i1.iters == i2.iters
+        assert np.array_equal(x1, x2)
