@@ -436,7 +436,7 @@ def main():
         return statistics.mean(a.elapsed_time(b_) for a, b_ in evs)
 
     # ---- dominant kernels of the step: the block-MGS Arnoldi orthogonalisation
-    # (k_bdot + 4 x k_bmgs + k_bnorm + k_gram_fold of rt_arnoldi_bmgs), at the
+    # (k_bdot + 4 x k_bmgs + k_bscale of rt_arnoldi_bmgs), at the
     # mean Arnoldi index j = 15 of a GMRES(30) cycle; the 17-vector basis
     # (264 MB) is larger than L2.  FP64-pipe bound on this GPU: algorithmic
     # work per step = the MGS loop's 2(j+1) FMA + 1 FMA (norm) + 1 multiply

@@ -189,8 +189,11 @@ rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_d
    same FP64 operations per element and a quarter of the passes.
    gram_dev: (j+2) x RT_GRAM_BLOCK doubles; row i holds <v_i, v_{i-d}> in
    column d = 1..RT_GRAM_BLOCK-1 (column 0 unused).  Rows 1..j are read (all
-   zero for an exactly orthonormal basis); row j+1 is written for the new
-   vector.  V_dev, w_dev, h_dev and the limits as rt_arnoldi_mgs. */
+   zero for an exactly orthonormal basis), each only in the columns whose
+   vectors share its block (d <= i mod RT_GRAM_BLOCK).  For the new vector,
+   row j+1 gets exactly those columns, d = 1..(j+1) mod RT_GRAM_BLOCK; its
+   other columns are left as they are.  V_dev, w_dev, h_dev and the limits
+   as rt_arnoldi_mgs. */
 #define RT_GRAM_BLOCK 4
 rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* gram_dev,
                           double* h_dev, void* stream);

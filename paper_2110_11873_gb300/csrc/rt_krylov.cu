@@ -259,10 +259,50 @@ __global__ void __launch_bounds__(kVecThreads) k_norm_out(const double* __restri
 // applies all of the block's updates to w element by element (in MGS order)
 // and accumulates the dots of the updated w with the next block.  One launch
 // per block instead of one per basis vector; the same FP64 operations per
-// element as MGS.  The Gram entries of v_{j+1} with its kGramB-1
-// predecessors are accumulated when it is normalised.
+// element as MGS.  The last pass also accumulates ||w||^2 and the dots of
+// the final w with the vectors of its block: those are the Gram entries of
+// v_{j+1} that the next step reads (v_{j+1} shares a block only with them).
+// The normalisation v_{j+1} = w / ||w|| is then a plain scaling pass, whose
+// last CTA folds h_{j+1,j} and the Gram row and rotates the Hessenberg
+// column.
+//
+// The FP64 pipe bounds these kernels, so the reductions are kept short: one
+// CTA per resident slot (a single wave, several elements per thread) and a
+// transposing warp reduction of the four accumulators (6 FP64 additions per
+// thread instead of 20).
 constexpr int kB = kGramB;
-constexpr int kUB = 1;   // elements in flight per thread and vector
+
+// lane l of the warp gets the warp sum of s[2*((l>>4)&1) + ((l>>3)&1)]
+__device__ __forceinline__ double wsum4(const double* s) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const double r0 = (h16 ? s[2] : s[0]) + __shfl_xor_sync(0xffffffffu, h16 ? s[0] : s[2], 16);
+  const double r1 = (h16 ? s[3] : s[1]) + __shfl_xor_sync(0xffffffffu, h16 ? s[1] : s[3], 16);
+  double t = (h8 ? r1 : r0) + __shfl_xor_sync(0xffffffffu, h8 ? r0 : r1, 8);
+  t += __shfl_xor_sync(0xffffffffu, t, 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
+// block sums of s[0..kB-1] in a fixed order; sum k < n goes to
+// out[k * gridDim.x + blockIdx.x].  Launch with kVecThreads threads.
+__device__ __forceinline__ void block_sum4_out(const double* s, int n, double* __restrict__ out) {
+  constexpr int NW = kVecThreads / 32;
+  static_assert(kB == 4 && kB * NW <= 64 && (NW & (NW - 1)) == 0, "reduction layout");
+  __shared__ double red[kB][NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double t = wsum4(s);
+  if ((lane & 7) == 0) red[lane >> 3][warp] = t;
+  __syncthreads();
+  if (threadIdx.x < kB * NW) {   // warps 0 and 1: value k = tid / NW, source warp tid % NW
+    const int k = threadIdx.x / NW, src = threadIdx.x % NW;
+    double x = red[k][src];
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (src == 0 && k < n) out[(size_t)k * gridDim.x + blockIdx.x] = x;
+  }
+}
 
 // warps 0..n-1 each sum one set of G partials (fixed order) into out[k]
 __device__ __forceinline__ void sum_sets(const double* __restrict__ part, int G, int n, double* out) {
@@ -274,56 +314,30 @@ __device__ __forceinline__ void sum_sets(const double* __restrict__ part, int G,
   __syncthreads();
 }
 
-// first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk; block 0
-// also folds the Gram partials of v_j (from the previous normalisation)
-// into gram (row j)
+// first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk
 __global__ void __launch_bounds__(kVecThreads, 2) k_bdot(const double* __restrict__ w, const double* __restrict__ V,
-                                                        int64_t N, int nk, double* __restrict__ part_out,
-                                                        const double* __restrict__ gpart, int j,
-                                                        double* __restrict__ gram, const int* kstop) {
+                                                        int64_t N, int nk, double* __restrict__ part_out, int j,
+                                                        const int* kstop) {
   if (j >= *kstop) return;
-  const int G = gridDim.x;
-  if (blockIdx.x == 0 && j >= 1) {
-    __shared__ double gs[kB];
-    const int nd = min(kB - 1, j);
-    sum_sets(gpart, G, nd, gs);
-    if (threadIdx.x < nd) gram[j * kB + 1 + threadIdx.x] = gs[threadIdx.x];
-  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double s[kB] = {0.0, 0.0, 0.0, 0.0};
-  for (; i + (kUB - 1) * stride < N; i += kUB * stride) {
-    double wv[kUB], vv[kB][kUB];
-#pragma unroll
-    for (int u = 0; u < kUB; ++u) {
-      wv[u] = w[i + u * stride];
-#pragma unroll
-      for (int k = 0; k < kB; ++k)
-        if (k < nk) vv[k][u] = V[(size_t)k * N + i + u * stride];
-    }
-#pragma unroll
-    for (int u = 0; u < kUB; ++u)
-#pragma unroll
-      for (int k = 0; k < kB; ++k)
-        if (k < nk) s[k] = fma(wv[u], vv[k][u], s[k]);
-  }
-  for (; i < N; i += stride) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
     const double wi = w[i];
+    double vv[kB];
 #pragma unroll
     for (int k = 0; k < kB; ++k)
-      if (k < nk) s[k] = fma(wi, V[(size_t)k * N + i], s[k]);
-  }
+      if (k < nk) vv[k] = V[(size_t)k * N + i];
 #pragma unroll
-  for (int k = 0; k < kB; ++k) {
-    if (k < nk) {
-      const double t = block_sum(s[k]);
-      if (threadIdx.x == 0) part_out[(size_t)k * G + blockIdx.x] = t;
-    }
+    for (int k = 0; k < kB; ++k)
+      if (k < nk) s[k] = fma(wi, vv[k], s[k]);
   }
+  block_sum4_out(s, nk, part_out);
 }
 
-// one block pass of Arnoldi step j over v_{i0} .. v_{i0+nb-1}; dots with the
-// next nn vectors, or ||w||^2 when nn == 0
+// one block pass of Arnoldi step j over v_{i0} .. v_{i0+nb-1}; with nn > 0
+// the dots of the updated w with the next nn vectors, with nn == 0 (the last
+// block) ||w||^2 and the Gram dots <w, v_{i0+k}>, k < ng (= nb when v_{j+1}
+// shares the block, else 0)
 __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w, const double* __restrict__ V,
                                                         int64_t N, int i0, int nb, int nn,
                                                         const double* __restrict__ part_in,
@@ -333,23 +347,20 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w,
   const int G = gridDim.x;
   const double* __restrict__ vb = V + (size_t)i0 * N;
   const double* __restrict__ vn = V + (size_t)(i0 + nb) * N;
+  const int ng = nn == 0 && nb < kB ? nb : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  // the first round's loads do not depend on h: issue them first
-  double wv[kUB], bv[kB][kUB], nv[kB][kUB];
+  // the first element's loads do not depend on h: issue them first
+  double wv = 0.0, bv[kB], nv[kB];
   auto load = [&](int64_t e) {
+    wv = w[e];
 #pragma unroll
-    for (int u = 0; u < kUB; ++u) {
-      wv[u] = w[e + u * stride];
-#pragma unroll
-      for (int k = 0; k < kB; ++k) {
-        if (k < nb) bv[k][u] = vb[(size_t)k * N + e + u * stride];
-        if (k < nn) nv[k][u] = vn[(size_t)k * N + e + u * stride];
-      }
+    for (int k = 0; k < kB; ++k) {
+      if (k < nb) bv[k] = vb[(size_t)k * N + e];
+      if (k < nn) nv[k] = vn[(size_t)k * N + e];
     }
   };
-  const bool first = i + (kUB - 1) * stride < N;
-  if (first) load(i);
+  if (i < N) load(i);
   __shared__ double rs[kB], hs[kB];
   sum_sets(part_in, G, nb, rs);
   if (threadIdx.x == 0) {
@@ -365,115 +376,30 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w,
 #pragma unroll
   for (int k = 0; k < kB; ++k) h[k] = k < nb ? hs[k] : 0.0;
   double s[kB] = {0.0, 0.0, 0.0, 0.0};
-  for (bool loaded = first; i + (kUB - 1) * stride < N; i += kUB * stride, loaded = false) {
+  for (bool loaded = true; i < N; i += stride, loaded = false) {
     if (!loaded) load(i);
-#pragma unroll
-    for (int u = 0; u < kUB; ++u) {
-      double wi = wv[u];
-#pragma unroll
-      for (int k = 0; k < kB; ++k)
-        if (k < nb) wi = fma(-h[k], bv[k][u], wi);
-      w[i + u * stride] = wi;
-      if (nn) {
-#pragma unroll
-        for (int k = 0; k < kB; ++k)
-          if (k < nn) s[k] = fma(wi, nv[k][u], s[k]);
-      } else {
-        s[0] = fma(wi, wi, s[0]);
-      }
-    }
-  }
-  for (; i < N; i += stride) {
-    double wi = w[i];
+    double wi = wv;
 #pragma unroll
     for (int k = 0; k < kB; ++k)
-      if (k < nb) wi = fma(-h[k], vb[(size_t)k * N + i], wi);
+      if (k < nb) wi = fma(-h[k], bv[k], wi);
     w[i] = wi;
     if (nn) {
 #pragma unroll
       for (int k = 0; k < kB; ++k)
-        if (k < nn) s[k] = fma(wi, vn[(size_t)k * N + i], s[k]);
+        if (k < nn) s[k] = fma(wi, nv[k], s[k]);
     } else {
       s[0] = fma(wi, wi, s[0]);
-    }
-  }
-  const int ns = nn ? nn : 1;
 #pragma unroll
-  for (int k = 0; k < kB; ++k) {
-    if (k < ns) {
-      const double t = block_sum(s[k]);
-      if (threadIdx.x == 0) part_out[(size_t)k * G + blockIdx.x] = t;
+      for (int k = 0; k < kB - 1; ++k)
+        if (k < ng) s[1 + k] = fma(wi, bv[k], s[1 + k]);
     }
   }
+  block_sum4_out(s, nn ? nn : 1 + ng, part_out);
 }
 
-// h_{j+1,j} = ||w||, v_{j+1} = w / h, and the partial Gram dots
-// <v_{j+1}, v_{j+1-d}>, d = 1..min(kGramB-1, j+1)
-__global__ void __launch_bounds__(kVecThreads, 2) k_bnorm(const double* __restrict__ w, double* __restrict__ V,
-                                                         int64_t N, const double* __restrict__ part_in,
-                                                         double* __restrict__ gpart, double* __restrict__ hcol, int j,
-                                                         const int* kstop) {
-  if (j >= *kstop) return;
-  const int G = gridDim.x;
-  double* __restrict__ vo = V + (size_t)(j + 1) * N;
-  const int nd = min(kB - 1, j + 1);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double wv[kUB], pv[kB - 1][kUB];
-  auto load = [&](int64_t e) {
-#pragma unroll
-    for (int u = 0; u < kUB; ++u) {
-      wv[u] = w[e + u * stride];
-#pragma unroll
-      for (int d = 1; d < kB; ++d)
-        if (d <= nd) pv[d - 1][u] = V[(size_t)(j + 1 - d) * N + e + u * stride];
-    }
-  };
-  const bool first = i + (kUB - 1) * stride < N;
-  if (first) load(i);
-  double hn;
-  const double inv = block_norm_inv(part_in, G, &hn);
-  if (blockIdx.x == 0 && threadIdx.x == 0) hcol[j + 1] = hn;
-  double s[kB - 1] = {0.0, 0.0, 0.0};
-  for (bool loaded = first; i + (kUB - 1) * stride < N; i += kUB * stride, loaded = false) {
-    if (!loaded) load(i);
-#pragma unroll
-    for (int u = 0; u < kUB; ++u) {
-      const double v = wv[u] * inv;
-      vo[i + u * stride] = v;
-#pragma unroll
-      for (int d = 1; d < kB; ++d)
-        if (d <= nd) s[d - 1] = fma(v, pv[d - 1][u], s[d - 1]);
-    }
-  }
-  for (; i < N; i += stride) {
-    const double v = w[i] * inv;
-    vo[i] = v;
-#pragma unroll
-    for (int d = 1; d < kB; ++d)
-      if (d <= nd) s[d - 1] = fma(v, V[(size_t)(j + 1 - d) * N + i], s[d - 1]);
-  }
-#pragma unroll
-  for (int d = 1; d < kB; ++d) {
-    if (d <= nd) {
-      const double t = block_sum(s[d - 1]);
-      if (threadIdx.x == 0) gpart[(size_t)(d - 1) * G + blockIdx.x] = t;
-    }
-  }
-}
-
-// row `row` of the Gram entries from the partials of the normalisation
-// (standalone Arnoldi step; inside GMRES the next k_bdot does this)
-__global__ void k_gram_fold(const double* __restrict__ gpart, int G, int row, double* __restrict__ gram) {
-  __shared__ double gs[kB];
-  const int nd = min(kB - 1, row);
-  sum_sets(gpart, G, nd, gs);
-  if (threadIdx.x < nd) gram[row * kB + 1 + threadIdx.x] = gs[threadIdx.x];
-}
-
-// Givens rotations on column j of the Hessenberg matrix (one thread)
-__global__ void k_givens(GmresDev* gm, int m, int j, double* hist, int hist_cap) {
-  if (j >= gm->kstop) return;
+// Givens rotations on column j of the Hessenberg matrix and the residual
+// estimate (one thread)
+__device__ void givens_step(GmresDev* gm, int m, int j, double* hist, int hist_cap) {
   double* Hc = gm->H + j * (m + 1);
   for (int i = 0; i < j; ++i) {
     const double t = gm->cs[i] * Hc[i] + gm->sn[i] * Hc[i + 1];
@@ -499,6 +425,43 @@ __global__ void k_givens(GmresDev* gm, int m, int j, double* hist, int hist_cap)
   const double est = fabs(gm->g[j + 1]) / gm->bnorm;
   if (hist && gm->hist_len < hist_cap) hist[gm->hist_len++] = est;
   if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
+}
+
+// v_{j+1} = w / ||w|| by blocks 0..gridDim.x-2 (||w||^2 is set 0 of the last
+// pass's partials, over Gp blocks).  The last block writes h_{j+1} = ||w||
+// to hcol[j+1] and the Gram row j+1: <v_{j+1}, v_{j+1-d}> = <w, v_{i0+k}> /
+// ||w|| (set 1+k, d = ng - k, k < ng), then, inside GMRES (gm set), applies
+// the Givens rotations to column j.
+__global__ void __launch_bounds__(kVecThreads) k_bscale(const double* __restrict__ w, double* __restrict__ V,
+                                                        int64_t N, const double* __restrict__ part_in, int Gp, int ng,
+                                                        double* __restrict__ hcol, double* __restrict__ gram,
+                                                        GmresDev* gm, int m, int j, double* hist, int hist_cap,
+                                                        const int* kstop) {
+  if (j >= *kstop) return;
+  if (blockIdx.x == gridDim.x - 1) {
+    __shared__ double sets[kB];
+    sum_sets(part_in, Gp, 1 + ng, sets);
+    if (threadIdx.x == 0) {
+      const double hn = sqrt(sets[0]);
+      const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+      hcol[j + 1] = hn;
+      for (int d = 1; d <= ng; ++d) gram[(j + 1) * kB + d] = sets[1 + ng - d] * inv;
+      if (gm) givens_step(gm, m, j, hist, hist_cap);
+    }
+    return;
+  }
+  double hn;
+  const double inv = block_norm_inv(part_in, Gp, &hn);
+  double* __restrict__ vo = V + (size_t)(j + 1) * N;
+  const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) vo[i] = w[i] * inv;
+}
+
+// the grid of the block-MGS passes: one CTA per resident slot
+inline int mgs_grid(const Problem* P) {
+  int64_t g = (P->Nop + kVecThreads - 1) / kVecThreads;
+  const int cap = std::min(2 * P->num_sms, kMaxPartials);
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 // back substitution H(0:k,0:k) y = g(0:k) (one thread)
@@ -921,6 +884,30 @@ static rt_status add_precond(Problem* P, double* x, double* t, int precond, doub
   return RT_OK;
 }
 
+// One block-MGS Arnoldi step on w against V[0..j] (see k_bmgs): h_0..h_j
+// and h_{j+1} = ||w|| to hcol, v_{j+1} to V, the Gram row j+1 to gram; with
+// gm set, the Givens rotations of column j (GMRES).
+static rt_status enqueue_bmgs(Problem* P, double* V, double* w, int j, double* hcol, double* gram, GmresDev* gm,
+                              int m, double* hist, int hcap, const int* kstop, cudaStream_t st) {
+  const int Gm = mgs_grid(P);
+  const int64_t N = P->Nop;
+  int pb = 0;
+  k_bdot<<<Gm, kVecThreads, 0, st>>>(w, V, N, std::min(kGramB, j + 1), bpartb(P, 0), j, kstop); RT_COUNT(1);
+  int ng = 0;
+  for (int i0 = 0; i0 <= j; i0 += kGramB) {
+    const int nb = std::min(kGramB, j + 1 - i0);
+    const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
+    if (nn == 0) ng = nb < kGramB ? nb : 0;
+    k_bmgs<<<Gm, kVecThreads, 0, st>>>(w, V, N, i0, nb, nn, bpartb(P, pb), bpartb(P, pb ^ 1), hcol, gram, j, kstop);
+    RT_COUNT(1);
+    pb ^= 1;
+  }
+  k_bscale<<<P->vec_grid + 1, kVecThreads, 0, st>>>(w, V, N, bpartb(P, pb), Gm, ng, hcol, gram, gm, m, j, hist, hcap,
+                                                    kstop); RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
 // --------------------------------------------------------------- GMRES
 struct GmresGraphKey {
   int m, precond, fp32;
@@ -988,20 +975,9 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
     double* vj = P->V + (size_t)j * N;
     RT_TRY(apply_prec(P, vj, w, precond, fp32, st, kstop, j));
     // block MGS: dots with the first block, one pass per block of kGramB
-    // basis vectors, normalisation with the Gram dots of v_{j+1}
-    int pb = 0;
-    double* hcol = &gm->H[j * (m + 1)];
-    k_bdot<<<G, kVecThreads, 0, st>>>(w, P->V, N, std::min(kGramB, j + 1), bpartb(P, 0), bpartb(P, 2), j, gm->gram,
-                                      kstop); RT_COUNT(1);
-    for (int i0 = 0; i0 <= j; i0 += kGramB) {
-      const int nb = std::min(kGramB, j + 1 - i0);
-      const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
-      k_bmgs<<<G, kVecThreads, 0, st>>>(w, P->V, N, i0, nb, nn, bpartb(P, pb), bpartb(P, pb ^ 1), hcol, gm->gram, j,
-                                        kstop); RT_COUNT(1);
-      pb ^= 1;
-    }
-    k_bnorm<<<G, kVecThreads, 0, st>>>(w, P->V, N, bpartb(P, pb), bpartb(P, 2), hcol, j, kstop); RT_COUNT(1);
-    k_givens<<<1, 1, 0, st>>>(gm, m, j, hist, hcap); RT_COUNT(1);
+    // basis vectors (the last with ||w|| and the Gram dots of v_{j+1}), then
+    // the normalisation with the Givens rotations of column j
+    RT_TRY(enqueue_bmgs(P, P->V, w, j, &gm->H[j * (m + 1)], gm->gram, gm, m, hist, hcap, kstop, st));
   }
   RT_TRY_CUDA(cudaGetLastError());
   k_lsq<<<1, 1, 0, st>>>(gm, m); RT_COUNT(1);
@@ -1578,26 +1554,10 @@ rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_
   Problem* P = &prob->P;
   cudaStream_t st = as_stream(stream);
   RT_TRY(ensure_workspace(P, 1, st));
-  const int G = P->vec_grid;
-  const int64_t N = P->Nop;
   int* always = reinterpret_cast<int*>(&P->gm->kstop);   // a gate that never stops the kernels
   const int big = 1 << 30;
   RT_TRY_CUDA(cudaMemcpyAsync(always, &big, sizeof(int), cudaMemcpyHostToDevice, st));
-  // the Gram rows of v_0..v_j are inputs: no fold at the first kernel
-  k_bdot<<<G, kVecThreads, 0, st>>>(w_dev, V_dev, N, std::min(kGramB, j + 1), bpartb(P, 0), bpartb(P, 2), 0,
-                                    gram_dev, always); RT_COUNT(1);
-  int pb = 0;
-  for (int i0 = 0; i0 <= j; i0 += kGramB) {
-    const int nb = std::min(kGramB, j + 1 - i0);
-    const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
-    k_bmgs<<<G, kVecThreads, 0, st>>>(w_dev, V_dev, N, i0, nb, nn, bpartb(P, pb), bpartb(P, pb ^ 1), h_dev, gram_dev,
-                                      j, always); RT_COUNT(1);
-    pb ^= 1;
-  }
-  k_bnorm<<<G, kVecThreads, 0, st>>>(w_dev, V_dev, N, bpartb(P, pb), bpartb(P, 2), h_dev, j, always); RT_COUNT(1);
-  k_gram_fold<<<1, 32 * kGramB, 0, st>>>(bpartb(P, 2), G, j + 1, gram_dev); RT_COUNT(1);
-  RT_TRY_CUDA(cudaGetLastError());
-  return RT_OK;
+  return enqueue_bmgs(P, V_dev, w_dev, j, h_dev, gram_dev, nullptr, 0, nullptr, 0, always, st);
 }
 
 rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,

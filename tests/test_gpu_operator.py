@@ -159,7 +159,7 @@ def test_arnoldi_mgs_step_against_plain_mgs():
     np.testing.assert_allclose(to_host(wd), w, rtol=1e-11, atol=1e-14)
 
 
-@pytest.mark.parametrize("j", [0, 3, 4, 9])
+@pytest.mark.parametrize("j", [0, 3, 4, 6, 9, 31])
 def test_arnoldi_block_mgs_step_against_plain_mgs(j):
     """rt_arnoldi_bmgs (the GMRES orthogonalisation): blocks of 4 basis vectors
     with the Gram correction give the MGS coefficients of the same loop in
@@ -194,6 +194,8 @@ def test_arnoldi_block_mgs_step_against_plain_mgs(j):
     np.testing.assert_allclose(to_host(Vd)[(j + 1) * N:], vnew, rtol=1e-9, atol=1e-13)
     np.testing.assert_allclose(to_host(wd), w, rtol=1e-9, atol=1e-13)
     g_out = to_host(gd).reshape(j + 2, 4)
-    for d in range(1, 4):
-        if j + 1 - d >= 0:
+    for d in range(1, 4):   # the new row holds the entries of v_{j+1}'s own block
+        if d <= (j + 1) % 4:
             assert abs(g_out[j + 1, d] - vnew @ Q[:, j + 1 - d]) < 1e-13
+        else:
+            assert g_out[j + 1, d] == gram[j + 1, d]   # left as it was
