@@ -449,7 +449,10 @@ def main():
     mgs_ms = timed(lambda: P.arnoldi_bmgs(V, jm, w, gram, hbuf), 20, False)
     mgs_flop = (2 * (2 * (jm + 1) + 1) + 1) * N
     mgs_tflops = mgs_flop / (mgs_ms * 1e-3) / 1e12
-    mgs_bytes = (2 * (jm + 1) + 6) * N * 8   # each basis vector read twice, w read/written per pass, v_{j+1} written
+    nblk = (jm + 1 + 3) // 4
+    # each basis vector read twice (dots, then update); w read by the first
+    # kernel, read and written by each block pass, read once more to write v_{j+1}
+    mgs_bytes = (2 * (jm + 1) + 2 * nblk + 3) * N * 8
     mgs_gbs = mgs_bytes / (mgs_ms * 1e-3) / 1e9
     del V
 

@@ -244,39 +244,49 @@ __device__ __forceinline__ void inst_sets(const InstDev& I, int buf, int n, doub
   __syncthreads();
 }
 
-// first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk, into buffer
-// 0; the first chunk of each instance folds the Gram dots of v_j into gram
+// block sums of s[0..kGramB-1] (fixed order) for one chunk: sum k < n goes
+// to set k of the instance's buffer buf, entry chunk
+__device__ __forceinline__ void chunk_sum4(const double* s, int n, const InstDev& I, int buf, int chunk) {
+  constexpr int NW = kBT / 32;
+  static_assert(kGramB == 4 && kGramB * NW <= 64 && (NW & (NW - 1)) == 0, "reduction layout");
+  __shared__ double red[kGramB][NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double t = warp_sum4(s);
+  if ((lane & 7) == 0) red[lane >> 3][warp] = t;
+  __syncthreads();
+  if (threadIdx.x < kGramB * NW) {
+    const int k = threadIdx.x / NW, src = threadIdx.x % NW;
+    double x = red[k][src];
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (src == 0 && k < n) pset(I, buf, k)[chunk] = x;
+  }
+  __syncthreads();
+}
+
+// first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk, into buffer 0
 __global__ void __launch_bounds__(kBT) kb_bdot(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
                                                const Counts* cnt, int j, int nk) {
-  __shared__ double gs[kGramB];
   for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
     if (step_gated(I, j)) continue;
-    if (it.y == 0 && j >= 1) {
-      const int nd = min(kGramB - 1, j);
-      inst_sets(I, 2, nd, gs);
-      if (threadIdx.x < nd) I.gm->gram[j * kGramB + 1 + threadIdx.x] = gs[threadIdx.x];
-      __syncthreads();
-    }
     double s[kGramB] = {0.0, 0.0, 0.0, 0.0};
-    CHUNK_LOOP(const double wi = I.w[n_]; _Pragma("unroll")
-               for (int k = 0; k < kGramB; ++k) if (k < nk) s[k] = fma(wi, I.V[(int64_t)k * I.N + n_], s[k]);)
-#pragma unroll
-    for (int k = 0; k < kGramB; ++k) {
-      if (k < nk) {
-        const double t = bsum(s[k]);
-        if (threadIdx.x == 0) pset(I, 0, k)[it.y] = t;
-      }
-    }
+    CHUNK_LOOP(const double wi = I.w[n_]; double vv[kGramB]; _Pragma("unroll")
+               for (int k = 0; k < kGramB; ++k) if (k < nk) vv[k] = I.V[(int64_t)k * I.N + n_]; _Pragma("unroll")
+               for (int k = 0; k < kGramB; ++k) if (k < nk) s[k] = fma(wi, vv[k], s[k]);)
+    chunk_sum4(s, nk, I, 0, it.y);
   }
 }
 
-// one block pass over v_{i0} .. v_{i0+nb-1}: dots with the next nn vectors
-// (or ||w||^2 when nn == 0) into buffer pb ^ 1
+// one block pass over v_{i0} .. v_{i0+nb-1} into buffer pb ^ 1: the dots with
+// the next nn vectors, or, for the last block (nn == 0), ||w||^2 (set 0) and
+// the Gram dots <w, v_{i0+k}>, k < ng (set 1+k; ng = nb when v_{j+1} shares
+// the block, else 0)
 __global__ void __launch_bounds__(kBT) kb_bmgs(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
                                                const Counts* cnt, int j, int i0, int nb, int nn, int pb) {
   __shared__ double rs[kGramB], hs[kGramB];
+  const int ng = nn == 0 && nb < kGramB ? nb : 0;
   for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
@@ -298,51 +308,38 @@ __global__ void __launch_bounds__(kBT) kb_bmgs(const InstDev* __restrict__ insts
     const double* vb = I.V + (int64_t)i0 * I.N;
     const double* vn = I.V + (int64_t)(i0 + nb) * I.N;
     double s[kGramB] = {0.0, 0.0, 0.0, 0.0};
-    CHUNK_LOOP(double wi = I.w[n_]; _Pragma("unroll")
-               for (int k = 0; k < kGramB; ++k) if (k < nb) wi = fma(-h[k], vb[(int64_t)k * I.N + n_], wi);
+    CHUNK_LOOP(double wi = I.w[n_]; double bv[kGramB]; _Pragma("unroll")
+               for (int k = 0; k < kGramB; ++k) if (k < nb) bv[k] = vb[(int64_t)k * I.N + n_]; _Pragma("unroll")
+               for (int k = 0; k < kGramB; ++k) if (k < nb) wi = fma(-h[k], bv[k], wi);
                I.w[n_] = wi;
                if (nn) { _Pragma("unroll")
                  for (int k = 0; k < kGramB; ++k) if (k < nn) s[k] = fma(wi, vn[(int64_t)k * I.N + n_], s[k]);
                } else {
-                 s[0] = fma(wi, wi, s[0]);
+                 s[0] = fma(wi, wi, s[0]); _Pragma("unroll")
+                 for (int k = 0; k < kGramB - 1; ++k) if (k < ng) s[1 + k] = fma(wi, bv[k], s[1 + k]);
                })
-    const int ns = nn ? nn : 1;
-#pragma unroll
-    for (int k = 0; k < kGramB; ++k) {
-      if (k < ns) {
-        const double t = bsum(s[k]);
-        if (threadIdx.x == 0) pset(I, pb ^ 1, k)[it.y] = t;
-      }
-    }
+    chunk_sum4(s, nn ? nn : 1 + ng, I, pb ^ 1, it.y);
   }
 }
 
-// h_{j+1,j} = ||w||, v_{j+1} = w / h, Gram dots <v_{j+1}, v_{j+1-d}> into buffer 2
-__global__ void __launch_bounds__(kBT) kb_bnorm(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
-                                                const Counts* cnt, int j, int pb) {
+// v_{j+1} = w / ||w|| with the inverse norm kb_givens stored
+__global__ void __launch_bounds__(kBT) kb_bscale(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
+                                                 const Counts* cnt, int j) {
   for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
     if (step_gated(I, j)) continue;
-    double hn;
-    const double inv = inst_norm_inv(I, pb, &hn);
-    if (it.y == 0 && threadIdx.x == 0) I.gm->H[j * (I.m + 1) + j + 1] = hn;
-    const int nd = min(kGramB - 1, j + 1);
+    const double inv = I.gm->vscale;
     double* vo = I.V + (int64_t)(j + 1) * I.N;
-    double s[kGramB - 1] = {0.0, 0.0, 0.0};
-    CHUNK_LOOP(const double v = I.w[n_] * inv; vo[n_] = v; _Pragma("unroll")
-               for (int d = 1; d < kGramB; ++d) if (d <= nd) s[d - 1] = fma(v, I.V[(int64_t)(j + 1 - d) * I.N + n_], s[d - 1]);)
-#pragma unroll
-    for (int d = 1; d < kGramB; ++d) {
-      if (d <= nd) {
-        const double t = bsum(s[d - 1]);
-        if (threadIdx.x == 0) pset(I, 2, d - 1)[it.y] = t;
-      }
-    }
+    CHUNK_LOOP(vo[n_] = I.w[n_] * inv;)
   }
 }
 
-__global__ void kb_givens(const InstDev* __restrict__ insts, const int* __restrict__ wi, const Counts* cnt, int j) {
+// per instance: h_{j+1,j} = ||w|| and the Gram row j+1 of v_{j+1} from the
+// last pass's partials (buffer pb, ng Gram sets), then the Givens rotations
+// of column j and the residual estimate
+__global__ void kb_givens(const InstDev* __restrict__ insts, const int* __restrict__ wi, const Counts* cnt, int j,
+                          int pb, int ng) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= cnt->ni) return;
   const InstDev& I = insts[wi[q]];
@@ -350,6 +347,23 @@ __global__ void kb_givens(const InstDev* __restrict__ insts, const int* __restri
   if (j >= gm->kstop) return;
   const int m = I.m;
   double* Hc = gm->H + j * (m + 1);
+  double sets[kGramB] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < kGramB; ++k) {
+    if (k <= ng) {
+      const double* p = pset(I, pb, k);
+      double t = 0.0;
+      for (int c = 0; c < I.nchunks; ++c) t += p[c];
+      sets[k] = t;
+    }
+  }
+  const double hj = sqrt(sets[0]);
+  const double inv = hj > 0.0 ? 1.0 / hj : 0.0;
+  Hc[j + 1] = hj;
+  gm->vscale = inv;
+#pragma unroll
+  for (int k = 0; k < kGramB - 1; ++k)   // set 1+k: <w, v_{j+1-d}> with d = ng - k
+    if (k < ng) gm->gram[(j + 1) * kGramB + (ng - k)] = sets[1 + k] * inv;
   for (int i = 0; i < j; ++i) {
     const double t = gm->cs[i] * Hc[i] + gm->sn[i] * Hc[i + 1];
     Hc[i + 1] = -gm->sn[i] * Hc[i] + gm->cs[i] * Hc[i + 1];
@@ -781,8 +795,11 @@ rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
       kb_bmgs<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, i0, nb, nn, pb);
       pb ^= 1;
     }
-    kb_bnorm<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, pb);
-    kb_givens<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C, j);
+    // h_{j+1,j}, the Gram row and the rotations first: the scaling pass is
+    // skipped by an instance whose Givens step broke down
+    const int ng = (j + 1) % kGramB;
+    kb_givens<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C, j, pb, ng);
+    kb_bscale<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j);
   }
   kb_lsq<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C);
   if (mode == KM_LOCAL_LAMBDA) {

@@ -211,33 +211,6 @@ __global__ void __launch_bounds__(kVecThreads) k_mgs(double* __restrict__ w, con
   if (threadIdx.x == 0) part_out[blockIdx.x] = s;
 }
 
-// h_{j+1,j} = ||w||; v_{j+1} = w / h (first round loaded before the norm)
-__global__ void __launch_bounds__(kVecThreads) k_normalize(const double* __restrict__ w, double* __restrict__ v,
-                                                           int64_t N, const double* __restrict__ part_in,
-                                                           GmresDev* gm, int m, const int* kstop, int step) {
-  if (step >= *kstop) return;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double wv[kU];
-  const bool first = i + (kU - 1) * stride < N;
-  if (first) {
-#pragma unroll
-    for (int u = 0; u < kU; ++u) wv[u] = w[i + u * stride];
-  }
-  double hn;
-  const double inv = block_norm_inv(part_in, gridDim.x, &hn);
-  if (blockIdx.x == 0 && threadIdx.x == 0) gm->H[step * (m + 1) + step + 1] = hn;
-  for (bool loaded = first; i + (kU - 1) * stride < N; i += kU * stride, loaded = false) {
-    if (!loaded) {
-#pragma unroll
-      for (int u = 0; u < kU; ++u) wv[u] = w[i + u * stride];
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) v[i + u * stride] = wv[u] * inv;
-  }
-  for (; i < N; i += stride) v[i] = w[i] * inv;
-}
-
 // v = w / ||w|| with ||w|| from the partials, written to *hout
 __global__ void __launch_bounds__(kVecThreads) k_norm_out(const double* __restrict__ w, double* __restrict__ v,
                                                           int64_t N, const double* __restrict__ part_in,
@@ -272,19 +245,6 @@ __global__ void __launch_bounds__(kVecThreads) k_norm_out(const double* __restri
 // thread instead of 20).
 constexpr int kB = kGramB;
 
-// lane l of the warp gets the warp sum of s[2*((l>>4)&1) + ((l>>3)&1)]
-__device__ __forceinline__ double wsum4(const double* s) {
-  const int lane = threadIdx.x & 31;
-  const bool h16 = lane & 16, h8 = lane & 8;
-  const double r0 = (h16 ? s[2] : s[0]) + __shfl_xor_sync(0xffffffffu, h16 ? s[0] : s[2], 16);
-  const double r1 = (h16 ? s[3] : s[1]) + __shfl_xor_sync(0xffffffffu, h16 ? s[1] : s[3], 16);
-  double t = (h8 ? r1 : r0) + __shfl_xor_sync(0xffffffffu, h8 ? r0 : r1, 8);
-  t += __shfl_xor_sync(0xffffffffu, t, 4);
-  t += __shfl_xor_sync(0xffffffffu, t, 2);
-  t += __shfl_xor_sync(0xffffffffu, t, 1);
-  return t;
-}
-
 // block sums of s[0..kB-1] in a fixed order; sum k < n goes to
 // out[k * gridDim.x + blockIdx.x].  Launch with kVecThreads threads.
 __device__ __forceinline__ void block_sum4_out(const double* s, int n, double* __restrict__ out) {
@@ -292,7 +252,7 @@ __device__ __forceinline__ void block_sum4_out(const double* s, int n, double* _
   static_assert(kB == 4 && kB * NW <= 64 && (NW & (NW - 1)) == 0, "reduction layout");
   __shared__ double red[kB][NW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double t = wsum4(s);
+  const double t = warp_sum4(s);
   if ((lane & 7) == 0) red[lane >> 3][warp] = t;
   __syncthreads();
   if (threadIdx.x < kB * NW) {   // warps 0 and 1: value k = tid / NW, source warp tid % NW
@@ -314,19 +274,24 @@ __device__ __forceinline__ void sum_sets(const double* __restrict__ part, int G,
   __syncthreads();
 }
 
+// Each pass sweeps the vectors in the opposite direction to the pass before
+// (rev): it starts on the elements the previous pass touched last, which are
+// still in L2 -- w and the vectors whose dots that pass just formed.
+
 // first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk
 __global__ void __launch_bounds__(kVecThreads, 2) k_bdot(const double* __restrict__ w, const double* __restrict__ V,
                                                         int64_t N, int nk, double* __restrict__ part_out, int j,
-                                                        const int* kstop) {
+                                                        int rev, const int* kstop) {
   if (j >= *kstop) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double s[kB] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
-    const double wi = w[i];
+    const int64_t e = rev ? N - 1 - i : i;
+    const double wi = w[e];
     double vv[kB];
 #pragma unroll
     for (int k = 0; k < kB; ++k)
-      if (k < nk) vv[k] = V[(size_t)k * N + i];
+      if (k < nk) vv[k] = V[(size_t)k * N + e];
 #pragma unroll
     for (int k = 0; k < kB; ++k)
       if (k < nk) s[k] = fma(wi, vv[k], s[k]);
@@ -342,7 +307,8 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w,
                                                         int64_t N, int i0, int nb, int nn,
                                                         const double* __restrict__ part_in,
                                                         double* __restrict__ part_out, double* __restrict__ hcol,
-                                                        const double* __restrict__ gram, int j, const int* kstop) {
+                                                        const double* __restrict__ gram, int j, int rev,
+                                                        const int* kstop) {
   if (j >= *kstop) return;
   const int G = gridDim.x;
   const double* __restrict__ vb = V + (size_t)i0 * N;
@@ -360,13 +326,20 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w,
       if (k < nn) nv[k] = vn[(size_t)k * N + e];
     }
   };
-  if (i < N) load(i);
-  __shared__ double rs[kB], hs[kB];
+  if (i < N) load(rev ? N - 1 - i : i);
+  // the block's Gram entries <v_{i0+l}, v_{i0+k}> (l < k), fetched by the
+  // warp after the partial sums while those are being summed
+  __shared__ double rs[kB], hs[kB], gs[kB][kB];
+  const int t = threadIdx.x - 32 * kB;
+  if (t >= 0 && t < kB * kB) {
+    const int k = t / kB, d = t % kB;
+    gs[k][d] = k < nb && d >= 1 && d <= k ? gram[(i0 + k) * kB + d] : 0.0;
+  }
   sum_sets(part_in, G, nb, rs);
   if (threadIdx.x == 0) {
     for (int k = 0; k < nb; ++k) {
       double h = rs[k];
-      for (int l = 0; l < k; ++l) h -= hs[l] * gram[(i0 + k) * kB + (k - l)];
+      for (int l = 0; l < k; ++l) h -= hs[l] * gs[k][k - l];
       hs[k] = h;
       if (blockIdx.x == 0) hcol[i0 + k] = h;
     }
@@ -377,12 +350,13 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w,
   for (int k = 0; k < kB; ++k) h[k] = k < nb ? hs[k] : 0.0;
   double s[kB] = {0.0, 0.0, 0.0, 0.0};
   for (bool loaded = true; i < N; i += stride, loaded = false) {
-    if (!loaded) load(i);
+    const int64_t e = rev ? N - 1 - i : i;
+    if (!loaded) load(e);
     double wi = wv;
 #pragma unroll
     for (int k = 0; k < kB; ++k)
       if (k < nb) wi = fma(-h[k], bv[k], wi);
-    w[i] = wi;
+    w[e] = wi;
     if (nn) {
 #pragma unroll
       for (int k = 0; k < kB; ++k)
@@ -436,7 +410,7 @@ __global__ void __launch_bounds__(kVecThreads) k_bscale(const double* __restrict
                                                         int64_t N, const double* __restrict__ part_in, int Gp, int ng,
                                                         double* __restrict__ hcol, double* __restrict__ gram,
                                                         GmresDev* gm, int m, int j, double* hist, int hist_cap,
-                                                        const int* kstop) {
+                                                        int rev, const int* kstop) {
   if (j >= *kstop) return;
   if (blockIdx.x == gridDim.x - 1) {
     __shared__ double sets[kB];
@@ -454,7 +428,10 @@ __global__ void __launch_bounds__(kVecThreads) k_bscale(const double* __restrict
   const double inv = block_norm_inv(part_in, Gp, &hn);
   double* __restrict__ vo = V + (size_t)(j + 1) * N;
   const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) vo[i] = w[i] * inv;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const int64_t e = rev ? N - 1 - i : i;
+    vo[e] = w[e] * inv;
+  }
 }
 
 // the grid of the block-MGS passes: one CTA per resident slot
@@ -891,19 +868,21 @@ static rt_status enqueue_bmgs(Problem* P, double* V, double* w, int j, double* h
                               int m, double* hist, int hcap, const int* kstop, cudaStream_t st) {
   const int Gm = mgs_grid(P);
   const int64_t N = P->Nop;
-  int pb = 0;
-  k_bdot<<<Gm, kVecThreads, 0, st>>>(w, V, N, std::min(kGramB, j + 1), bpartb(P, 0), j, kstop); RT_COUNT(1);
+  int pb = 0, rev = 0;
+  k_bdot<<<Gm, kVecThreads, 0, st>>>(w, V, N, std::min(kGramB, j + 1), bpartb(P, 0), j, rev, kstop); RT_COUNT(1);
   int ng = 0;
   for (int i0 = 0; i0 <= j; i0 += kGramB) {
     const int nb = std::min(kGramB, j + 1 - i0);
     const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
     if (nn == 0) ng = nb < kGramB ? nb : 0;
-    k_bmgs<<<Gm, kVecThreads, 0, st>>>(w, V, N, i0, nb, nn, bpartb(P, pb), bpartb(P, pb ^ 1), hcol, gram, j, kstop);
-    RT_COUNT(1);
+    rev ^= 1;
+    k_bmgs<<<Gm, kVecThreads, 0, st>>>(w, V, N, i0, nb, nn, bpartb(P, pb), bpartb(P, pb ^ 1), hcol, gram, j, rev,
+                                       kstop); RT_COUNT(1);
     pb ^= 1;
   }
+  rev ^= 1;
   k_bscale<<<P->vec_grid + 1, kVecThreads, 0, st>>>(w, V, N, bpartb(P, pb), Gm, ng, hcol, gram, gm, m, j, hist, hcap,
-                                                    kstop); RT_COUNT(1);
+                                                    rev, kstop); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
