@@ -264,9 +264,14 @@ __device__ __forceinline__ void chunk_sum4(const double* s, int n, const InstDev
   __syncthreads();
 }
 
-// first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk, into buffer 0
+// The block sizes are template parameters: a DFMA under a false predicate
+// still takes its FP64-pipe slot.
+
+// first kernel of Arnoldi step j: partial dots <w, v_k>, k < NK, into buffer 0
+template <int NK>
 __global__ void __launch_bounds__(kBT) kb_bdot(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
-                                               const Counts* cnt, int j, int nk) {
+                                               const Counts* cnt, int j) {
+  constexpr int nk = NK;
   for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
@@ -279,14 +284,16 @@ __global__ void __launch_bounds__(kBT) kb_bdot(const InstDev* __restrict__ insts
   }
 }
 
-// one block pass over v_{i0} .. v_{i0+nb-1} into buffer pb ^ 1: the dots with
-// the next nn vectors, or, for the last block (nn == 0), ||w||^2 (set 0) and
-// the Gram dots <w, v_{i0+k}>, k < ng (set 1+k; ng = nb when v_{j+1} shares
+// one block pass over v_{i0} .. v_{i0+NB-1} into buffer pb ^ 1: the dots with
+// the next NN vectors, or, for the last block (NN == 0), ||w||^2 (set 0) and
+// the Gram dots <w, v_{i0+k}>, k < ng (set 1+k; ng = NB when v_{j+1} shares
 // the block, else 0)
+template <int NB, int NN>
 __global__ void __launch_bounds__(kBT) kb_bmgs(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
-                                               const Counts* cnt, int j, int i0, int nb, int nn, int pb) {
+                                               const Counts* cnt, int j, int i0, int pb) {
+  static_assert(NB >= 1 && NB <= kGramB && NN >= 0 && NN <= kGramB && (NN == 0 || NB == kGramB), "block shape");
+  constexpr int nb = NB, nn = NN, ng = NN == 0 && NB < kGramB ? NB : 0;
   __shared__ double rs[kGramB], hs[kGramB];
-  const int ng = nn == 0 && nb < kGramB ? nb : 0;
   for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
@@ -312,7 +319,7 @@ __global__ void __launch_bounds__(kBT) kb_bmgs(const InstDev* __restrict__ insts
                for (int k = 0; k < kGramB; ++k) if (k < nb) bv[k] = vb[(int64_t)k * I.N + n_]; _Pragma("unroll")
                for (int k = 0; k < kGramB; ++k) if (k < nb) wi = fma(-h[k], bv[k], wi);
                I.w[n_] = wi;
-               if (nn) { _Pragma("unroll")
+               if constexpr (nn > 0) { _Pragma("unroll")
                  for (int k = 0; k < kGramB; ++k) if (k < nn) s[k] = fma(wi, vn[(int64_t)k * I.N + n_], s[k]);
                } else {
                  s[0] = fma(wi, wi, s[0]); _Pragma("unroll")
@@ -388,6 +395,13 @@ __global__ void kb_givens(const InstDev* __restrict__ insts, const int* __restri
   const double est = fabs(gm->g[j + 1]) / gm->bnorm;
   if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
 }
+
+using KbBdotFn = void (*)(const InstDev*, const int2*, const Counts*, int);
+using KbBmgsFn = void (*)(const InstDev*, const int2*, const Counts*, int, int, int);
+static_assert(kGramB == 4, "kernel tables");
+const KbBdotFn kb_bdot_fn[kGramB] = {kb_bdot<1>, kb_bdot<2>, kb_bdot<3>, kb_bdot<4>};
+const KbBmgsFn kb_pass_fn[kGramB] = {kb_bmgs<4, 1>, kb_bmgs<4, 2>, kb_bmgs<4, 3>, kb_bmgs<4, 4>};
+const KbBmgsFn kb_last_fn[kGramB] = {kb_bmgs<1, 0>, kb_bmgs<2, 0>, kb_bmgs<3, 0>, kb_bmgs<4, 0>};
 
 __global__ void kb_lsq(const InstDev* __restrict__ insts, const int* __restrict__ wi, const Counts* cnt) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -765,7 +779,7 @@ rt_status autotune_grids(Server* S, int resident) {
   tune(&S->grid_g, gs, apply);
   tune(&S->grid_h, hs, apply);
   tune(&S->grid_v, vs, [&] {
-    kb_bdot<<<S->grid_v, kBT, 0, st>>>(S->d_insts, S->d_wl_c, S->d_counts, 0, 1);
+    kb_bdot<1><<<S->grid_v, kBT, 0, st>>>(S->d_insts, S->d_wl_c, S->d_counts, 0);
     RT_COUNT(1);
   });
   cudaEventDestroy(e0);
@@ -788,11 +802,11 @@ rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
   for (int j = 0; j < m; ++j) {
     apply(j, VW, mode, fp32, j);
     int pb = 0;
-    kb_bdot<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, std::min(kGramB, j + 1));
+    kb_bdot_fn[std::min(kGramB, j + 1) - 1]<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j);
     for (int i0 = 0; i0 <= j; i0 += kGramB) {
       const int nb = std::min(kGramB, j + 1 - i0);
       const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
-      kb_bmgs<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, i0, nb, nn, pb);
+      (nn ? kb_pass_fn[nn - 1] : kb_last_fn[nb - 1])<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, i0, pb);
       pb ^= 1;
     }
     // h_{j+1,j}, the Gram row and the rotations first: the scaling pass is

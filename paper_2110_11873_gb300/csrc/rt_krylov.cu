@@ -274,15 +274,34 @@ __device__ __forceinline__ void sum_sets(const double* __restrict__ part, int G,
   __syncthreads();
 }
 
+// The three kernels are launched as programmatic dependents of the kernel
+// before them (launch_pdl): a CTA may start while the previous grid drains,
+// runs what does not depend on it (the gate, the basis-vector loads of its
+// first element, the Gram entries), then waits in griddepcontrol.wait until
+// that grid has finished and its writes are visible.  The gate counter is
+// written only by the scaling kernel of the step before, which completed
+// before the operator apply between them started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Each pass sweeps the vectors in the opposite direction to the pass before
 // (rev): it starts on the elements the previous pass touched last, which are
 // still in L2 -- w and the vectors whose dots that pass just formed.
 
-// first kernel of Arnoldi step j: partial dots <w, v_k>, k < nk
+// The block sizes are template parameters: a DFMA under a false predicate
+// still takes its slot on the FP64 pipe, so a runtime guard "k < nb" would
+// cost every pass the work of a full block.  Passes before the last always
+// have kB vectors.
+
+// first kernel of Arnoldi step j: partial dots <w, v_k>, k < NK
+template <int NK>
 __global__ void __launch_bounds__(kVecThreads, 2) k_bdot(const double* __restrict__ w, const double* __restrict__ V,
-                                                        int64_t N, int nk, double* __restrict__ part_out, int j,
-                                                        int rev, const int* kstop) {
+                                                        int64_t N, double* __restrict__ part_out, int j, int rev,
+                                                        const int* kstop) {
+  constexpr int nk = NK;
   if (j >= *kstop) return;
+  pdl_launch_dependents();
+  pdl_wait();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double s[kB] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
@@ -299,34 +318,36 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bdot(const double* __restric
   block_sum4_out(s, nk, part_out);
 }
 
-// one block pass of Arnoldi step j over v_{i0} .. v_{i0+nb-1}; with nn > 0
-// the dots of the updated w with the next nn vectors, with nn == 0 (the last
-// block) ||w||^2 and the Gram dots <w, v_{i0+k}>, k < ng (= nb when v_{j+1}
+// one block pass of Arnoldi step j over v_{i0} .. v_{i0+NB-1}; with NN > 0
+// the dots of the updated w with the next NN vectors, with NN == 0 (the last
+// block) ||w||^2 and the Gram dots <w, v_{i0+k}>, k < ng (= NB when v_{j+1}
 // shares the block, else 0)
+template <int NB, int NN>
 __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w, const double* __restrict__ V,
-                                                        int64_t N, int i0, int nb, int nn,
-                                                        const double* __restrict__ part_in,
+                                                        int64_t N, int i0, const double* __restrict__ part_in,
                                                         double* __restrict__ part_out, double* __restrict__ hcol,
                                                         const double* __restrict__ gram, int j, int rev,
                                                         const int* kstop) {
+  static_assert(NB >= 1 && NB <= kB && NN >= 0 && NN <= kB && (NN == 0 || NB == kB), "block shape");
+  constexpr int nb = NB, nn = NN, ng = NN == 0 && NB < kB ? NB : 0;
   if (j >= *kstop) return;
+  pdl_launch_dependents();
   const int G = gridDim.x;
   const double* __restrict__ vb = V + (size_t)i0 * N;
   const double* __restrict__ vn = V + (size_t)(i0 + nb) * N;
-  const int ng = nn == 0 && nb < kB ? nb : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  // the first element's loads do not depend on h: issue them first
+  // the first element's basis-vector loads depend neither on h nor on the
+  // previous pass: issue them first
   double wv = 0.0, bv[kB], nv[kB];
-  auto load = [&](int64_t e) {
-    wv = w[e];
+  auto load_v = [&](int64_t e) {
 #pragma unroll
     for (int k = 0; k < kB; ++k) {
       if (k < nb) bv[k] = vb[(size_t)k * N + e];
       if (k < nn) nv[k] = vn[(size_t)k * N + e];
     }
   };
-  if (i < N) load(rev ? N - 1 - i : i);
+  if (i < N) load_v(rev ? N - 1 - i : i);
   // the block's Gram entries <v_{i0+l}, v_{i0+k}> (l < k), fetched by the
   // warp after the partial sums while those are being summed
   __shared__ double rs[kB], hs[kB], gs[kB][kB];
@@ -335,6 +356,8 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w,
     const int k = t / kB, d = t % kB;
     gs[k][d] = k < nb && d >= 1 && d <= k ? gram[(i0 + k) * kB + d] : 0.0;
   }
+  pdl_wait();
+  if (i < N) wv = w[rev ? N - 1 - i : i];
   sum_sets(part_in, G, nb, rs);
   if (threadIdx.x == 0) {
     for (int k = 0; k < nb; ++k) {
@@ -351,13 +374,16 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w,
   double s[kB] = {0.0, 0.0, 0.0, 0.0};
   for (bool loaded = true; i < N; i += stride, loaded = false) {
     const int64_t e = rev ? N - 1 - i : i;
-    if (!loaded) load(e);
+    if (!loaded) {
+      wv = w[e];
+      load_v(e);
+    }
     double wi = wv;
 #pragma unroll
     for (int k = 0; k < kB; ++k)
       if (k < nb) wi = fma(-h[k], bv[k], wi);
     w[e] = wi;
-    if (nn) {
+    if constexpr (nn > 0) {
 #pragma unroll
       for (int k = 0; k < kB; ++k)
         if (k < nn) s[k] = fma(wi, nv[k], s[k]);
@@ -401,18 +427,22 @@ __device__ void givens_step(GmresDev* gm, int m, int j, double* hist, int hist_c
   if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
 }
 
-// v_{j+1} = w / ||w|| by blocks 0..gridDim.x-2 (||w||^2 is set 0 of the last
-// pass's partials, over Gp blocks).  The last block writes h_{j+1} = ||w||
-// to hcol[j+1] and the Gram row j+1: <v_{j+1}, v_{j+1-d}> = <w, v_{i0+k}> /
-// ||w|| (set 1+k, d = ng - k, k < ng), then, inside GMRES (gm set), applies
-// the Givens rotations to column j.
-__global__ void __launch_bounds__(kVecThreads) k_bscale(const double* __restrict__ w, double* __restrict__ V,
-                                                        int64_t N, const double* __restrict__ part_in, int Gp, int ng,
-                                                        double* __restrict__ hcol, double* __restrict__ gram,
-                                                        GmresDev* gm, int m, int j, double* hist, int hist_cap,
-                                                        int rev, const int* kstop) {
+// v_{j+1} = w / ||w|| by blocks 1..gridDim.x-1 (||w||^2 is set 0 of the last
+// pass's partials, over Gp blocks).  Block 0, scheduled first, writes
+// h_{j+1} = ||w|| to hcol[j+1] and the Gram row j+1: <v_{j+1}, v_{j+1-d}> =
+// <w, v_{i0+k}> / ||w|| (set 1+k, d = ng - k, k < ng), then, inside GMRES
+// (gm set), applies the Givens rotations to column j.  Three CTAs fit on an
+// SM, so the grid (one CTA per block-pass slot, plus block 0) is one wave;
+// each thread loads its first elements while the norm is being formed.
+constexpr int kScaleU = 4;
+__global__ void __launch_bounds__(kVecThreads, 3) k_bscale(const double* __restrict__ w, double* __restrict__ V,
+                                                           int64_t N, const double* __restrict__ part_in, int Gp,
+                                                           int ng, double* __restrict__ hcol, double* __restrict__ gram,
+                                                           GmresDev* gm, int m, int j, double* hist, int hist_cap,
+                                                           int rev, const int* kstop) {
   if (j >= *kstop) return;
-  if (blockIdx.x == gridDim.x - 1) {
+  pdl_wait();
+  if (blockIdx.x == 0) {
     __shared__ double sets[kB];
     sum_sets(part_in, Gp, 1 + ng, sets);
     if (threadIdx.x == 0) {
@@ -424,11 +454,23 @@ __global__ void __launch_bounds__(kVecThreads) k_bscale(const double* __restrict
     }
     return;
   }
-  double hn;
-  const double inv = block_norm_inv(part_in, Gp, &hn);
   double* __restrict__ vo = V + (size_t)(j + 1) * N;
   const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+  const int64_t i0 = (blockIdx.x - 1) * (int64_t)blockDim.x + threadIdx.x;
+  double wv[kScaleU];
+#pragma unroll
+  for (int u = 0; u < kScaleU; ++u) {
+    const int64_t i = i0 + u * stride;
+    wv[u] = i < N ? w[rev ? N - 1 - i : i] : 0.0;
+  }
+  double hn;
+  const double inv = block_norm_inv(part_in, Gp, &hn);
+#pragma unroll
+  for (int u = 0; u < kScaleU; ++u) {
+    const int64_t i = i0 + u * stride;
+    if (i < N) vo[rev ? N - 1 - i : i] = wv[u] * inv;
+  }
+  for (int64_t i = i0 + kScaleU * stride; i < N; i += stride) {
     const int64_t e = rev ? N - 1 - i : i;
     vo[e] = w[e] * inv;
   }
@@ -861,6 +903,22 @@ static rt_status add_precond(Problem* P, double* x, double* t, int precond, doub
   return RT_OK;
 }
 
+// launch as a programmatic dependent of the stream's previous kernel
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kVecThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // One block-MGS Arnoldi step on w against V[0..j] (see k_bmgs): h_0..h_j
 // and h_{j+1} = ||w|| to hcol, v_{j+1} to V, the Gram row j+1 to gram; with
 // gm set, the Givens rotations of column j (GMRES).
@@ -868,21 +926,30 @@ static rt_status enqueue_bmgs(Problem* P, double* V, double* w, int j, double* h
                               int m, double* hist, int hcap, const int* kstop, cudaStream_t st) {
   const int Gm = mgs_grid(P);
   const int64_t N = P->Nop;
+  using BdotFn = void (*)(const double*, const double*, int64_t, double*, int, int, const int*);
+  using BmgsFn = void (*)(double*, const double*, int64_t, int, const double*, double*, double*, const double*, int,
+                          int, const int*);
+  static const BdotFn bdot[kGramB] = {k_bdot<1>, k_bdot<2>, k_bdot<3>, k_bdot<4>};
+  static const BmgsFn pass[kGramB] = {k_bmgs<4, 1>, k_bmgs<4, 2>, k_bmgs<4, 3>, k_bmgs<4, 4>};
+  static const BmgsFn last[kGramB] = {k_bmgs<1, 0>, k_bmgs<2, 0>, k_bmgs<3, 0>, k_bmgs<4, 0>};
+  static_assert(kGramB == 4, "kernel tables");
   int pb = 0, rev = 0;
-  k_bdot<<<Gm, kVecThreads, 0, st>>>(w, V, N, std::min(kGramB, j + 1), bpartb(P, 0), j, rev, kstop); RT_COUNT(1);
+  RT_TRY_CUDA(launch_pdl(bdot[std::min(kGramB, j + 1) - 1], Gm, st, (const double*)w, (const double*)V, N,
+                         bpartb(P, 0), j, rev, kstop)); RT_COUNT(1);
   int ng = 0;
   for (int i0 = 0; i0 <= j; i0 += kGramB) {
     const int nb = std::min(kGramB, j + 1 - i0);
     const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
     if (nn == 0) ng = nb < kGramB ? nb : 0;
     rev ^= 1;
-    k_bmgs<<<Gm, kVecThreads, 0, st>>>(w, V, N, i0, nb, nn, bpartb(P, pb), bpartb(P, pb ^ 1), hcol, gram, j, rev,
-                                       kstop); RT_COUNT(1);
+    RT_TRY_CUDA(launch_pdl(nn ? pass[nn - 1] : last[nb - 1], Gm, st, w, (const double*)V, N, i0,
+                           (const double*)bpartb(P, pb), bpartb(P, pb ^ 1), hcol, (const double*)gram, j, rev,
+                           kstop)); RT_COUNT(1);
     pb ^= 1;
   }
   rev ^= 1;
-  k_bscale<<<P->vec_grid + 1, kVecThreads, 0, st>>>(w, V, N, bpartb(P, pb), Gm, ng, hcol, gram, gm, m, j, hist, hcap,
-                                                    rev, kstop); RT_COUNT(1);
+  RT_TRY_CUDA(launch_pdl(k_bscale, Gm + 1, st, (const double*)w, V, N, (const double*)bpartb(P, pb), Gm, ng,
+                         hcol, gram, gm, m, j, hist, hcap, rev, kstop)); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
