@@ -53,7 +53,7 @@ struct InstDev {
   int Ns, Nmu, Nnu, Nh, ngd, ngroups, fs, nchunks, chunk, m;
   int64_t nray, nd, N;
   double xi, xiW2, inflow_bottom;
-  const double *ce, *ca, *cb, *wnu, *wmu, *t201, *t202, *Minv;
+  const double *ce, *ca, *cb, *wnu, *wmu, *wray, *t201, *t202, *Minv;
   const float *dtau32, *r32, *wnu32, *wmu32, *t201f, *t202f;
   double *S, *S2;
   float* S32;
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(kMomThreads) kb_moments(const InstDev* __restr
     if (step_gated(I, step)) continue;
     const double* x = vec(I, src);
     if (sizeof(TC) == 8) {
-      moments_height<double, double, MODE>(x, I.dinv, I.wnu, I.wmu, I.t201, I.t202, I.Minv, I.Ns, I.Nmu, I.Nnu, I.xi,
-                                           I.xiW2, useS2 ? I.S2 : I.S, it.y);
+      moments_flat64<MODE>(x, I.dinv, I.wray, I.t201, I.t202, I.Minv, I.Ns, I.Nmu, I.nray, I.xi, I.xiW2,
+                           useS2 ? I.S2 : I.S, it.y);
     } else {
       moments_height<double, float, MODE>(x, I.dinv, I.wnu32, I.wmu32, I.t201f, I.t202f, I.Minv, I.Ns, I.Nmu, I.Nnu,
                                           (float)I.xi, (float)I.xiW2, I.S32, it.y);
@@ -977,6 +977,7 @@ rt_status make_instance(Server* S, Request* rq, Instance* in, int slot) {
   D.cb = P.cb;
   D.wnu = P.wI2;
   D.wmu = P.wQ2;
+  D.wray = P.wray;
   D.t201 = P.t201d;
   D.t202 = P.t202d;
   D.Minv = P.Minv;

@@ -117,6 +117,71 @@ __device__ __forceinline__ void moments_height(
   }
 }
 
+// FP64 quadrature of height k as flat dot products over its rays (the CTA's
+// threads stride over r): with the per-ray weights w0 = hat-w_m hat-w_p,
+// w1 = w0 T201_m, w2 = w0 T202_m (wray, [3][nray]),
+//     J00 = sum_r w0 I_r,   J20 = sum_r (w1 I_r + w2 Q_r),
+// then S as in moments_height.  Every FP64 operation is useful work: no
+// lane idles on a short row and there is one reduction per height (the FP64
+// pipe bounds this kernel).  Any block size that is a multiple of 32.
+template <int MODE>
+__device__ __forceinline__ void moments_flat64(const double* __restrict__ x, const double* __restrict__ dinv,
+                                               const double* __restrict__ wray, const double* __restrict__ t201,
+                                               const double* __restrict__ t202, const double* __restrict__ Minv,
+                                               int Ns, int Nmu, int64_t nray, double xi, double xiW2,
+                                               double* __restrict__ S, int k) {
+  const double* __restrict__ xI = x + (int64_t)k * nray;
+  const double* __restrict__ xQ = x + ((int64_t)Ns + k) * nray;
+  const double* __restrict__ dI = MODE == KM_JACOBI ? dinv + (int64_t)k * nray : nullptr;
+  const double* __restrict__ dQ = MODE == KM_JACOBI ? dinv + ((int64_t)Ns + k) * nray : nullptr;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 2
+  for (int64_t r = threadIdx.x; r < nray; r += blockDim.x) {
+    double vI = xI[r], vQ = xQ[r];
+    if (MODE == KM_JACOBI) {
+      vI *= dI[r];
+      vQ *= dQ[r];
+    }
+    a0 = fma(wray[r], vI, a0);
+    a1 = fma(wray[nray + r], vI, a1);
+    a2 = fma(wray[2 * nray + r], vQ, a2);
+  }
+  a1 += a2;
+  // transposed warp sum: lanes 0-15 get the sum of a0, lanes 16-31 of a1
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool h16 = lane & 16;
+  double t = (h16 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, h16 ? a0 : a1, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __shared__ double red[2][32];
+  __shared__ double sig[2];
+  if ((lane & 15) == 0) red[lane >> 4][warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    double j00 = 0.0, j20 = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      j00 += red[0][w];
+      j20 += red[1][w];
+    }
+    double s0 = xi * j00, s2 = xiW2 * j20;
+    if (MODE == KM_LOCAL_LAMBDA) {
+      const double* Mi = Minv + 4 * k;
+      const double u0 = Mi[0] * s0 + Mi[1] * s2;
+      const double u2 = Mi[2] * s0 + Mi[3] * s2;
+      s0 = u0;
+      s2 = u2;
+    }
+    sig[0] = s0;
+    sig[1] = s2;
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < Nmu; m += blockDim.x) {
+    S[(int64_t)k * Nmu + m] = sig[0] + t201[m] * sig[1];
+    S[((int64_t)Ns + k) * Nmu + m] = t202[m] * sig[1];
+  }
+}
+
 // --------------------------------------------------------------- K2: Lambda
 // FP32 step coefficients from Delta (DELO-linear: Taylor branch below 0.5)
 template <int FS>

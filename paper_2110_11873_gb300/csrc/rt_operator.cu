@@ -205,6 +205,17 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(
   moments_height<TI, TC, MODE>(x, dinv, wnu, wmu, t201, t202, Minv, Ns, Nmu, Nnu, xi, xiW2, S, blockIdx.x);
 }
 
+// FP64 quadrature, one CTA per height (flat over the rays)
+constexpr int kMom64Threads = 512;
+template <int MODE>
+__global__ void __launch_bounds__(kMom64Threads) k_moments64(
+    const double* __restrict__ x, const double* __restrict__ dinv, const double* __restrict__ wray,
+    const double* __restrict__ t201, const double* __restrict__ t202, const double* __restrict__ Minv, int Ns,
+    int Nmu, int64_t nray, double xi, double xiW2, double* __restrict__ S, const int* kstop, int step) {
+  if (kstop && step >= *kstop) return;
+  moments_flat64<MODE>(x, dinv, wray, t201, t202, Minv, Ns, Nmu, nray, xi, xiW2, S, blockIdx.x);
+}
+
 // grid: NSPLIT * ngroups CTAs (ray group g, and with NSPLIT = 2 the Stokes
 // parameter s = blockIdx.x % 2 -- with NSPLIT = 1 one lane carries I and Q);
 // block: 32 * ntile threads (warp t = depth tile t)
@@ -365,7 +376,7 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   P->ngroups = 2 * ngd;
   P->ntile64 = choose_tiles64(P);
   P->ntile32 = choose_tiles32(P);
-  std::vector<double> dtau(Ns - 1), rscale(nray), w0(nray), wnu(P->w_nu), wmu(Nmu);
+  std::vector<double> dtau(Ns - 1), rscale(nray), w0(3 * nray), wnu(P->w_nu), wmu(Nmu);
   for (int m = 0; m < Nmu; ++m) wmu[m] = 0.5 * P->w_mu[m];
   for (int i = 0; i + 1 < Ns; ++i) dtau[i] = P->tau[i + 1] - P->tau[i];
   for (int m = 0; m < Nmu; ++m)
@@ -373,6 +384,8 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
       const size_t r = (size_t)m * Nnu + p;
       rscale[r] = P->phi_hat[p] / fabs(P->mu[m]);
       w0[r] = 0.5 * P->w_mu[m] * P->w_nu[p];
+      w0[nray + r] = w0[r] * P->t201[m];       // the J20 weights of I and Q
+      w0[2 * nray + r] = w0[r] * P->t202[m];
     }
   double *d_dtau = nullptr, *d_rs = nullptr;
   // the two temporaries are returned on every path (in an arena a leaked
@@ -508,21 +521,19 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
   const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu;
   switch (mode) {
     case AM_PLAIN:
-      k_moments<double, double, KM_PLAIN><<<Ns, kMomThreads, 0, st>>>(x, nullptr, P->wI2, P->wQ2, P->t201d,
-                                                                       P->t202d, nullptr, Ns, Nmu, Nnu, P->xi, xiW2,
-                                                                       P->S, kstop, step); RT_COUNT(1);
+      k_moments64<KM_PLAIN><<<Ns, kMom64Threads, 0, st>>>(x, nullptr, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu,
+                                                          P->nray, P->xi, xiW2, P->S, kstop, step); RT_COUNT(1);
       launch_formal64<KM_PLAIN>(P, x, y, P->S, st, kstop, step);
       break;
     case AM_JACOBI:
-      k_moments<double, double, KM_JACOBI><<<Ns, kMomThreads, 0, st>>>(x, P->dinv, P->wI2, P->wQ2,
-                                                                        P->t201d, P->t202d, nullptr, Ns, Nmu, Nnu,
-                                                                        P->xi, xiW2, P->S, kstop, step); RT_COUNT(1);
+      k_moments64<KM_JACOBI><<<Ns, kMom64Threads, 0, st>>>(x, P->dinv, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu,
+                                                           P->nray, P->xi, xiW2, P->S, kstop, step); RT_COUNT(1);
       launch_formal64<KM_JACOBI>(P, x, y, P->S, st, kstop, step);
       break;
     case AM_LOCAL_LAMBDA:
-      k_moments<double, double, KM_LOCAL_LAMBDA><<<Ns, kMomThreads, 0, st>>>(
-          x, nullptr, P->wI2, P->wQ2, P->t201d, P->t202d, P->Minv, Ns, Nmu, Nnu, P->xi, xiW2, P->S, kstop,
-          step); RT_COUNT(1);
+      k_moments64<KM_LOCAL_LAMBDA><<<Ns, kMom64Threads, 0, st>>>(x, nullptr, P->wray, P->t201d, P->t202d, P->Minv,
+                                                                 Ns, Nmu, P->nray, P->xi, xiW2, P->S, kstop, step);
+      RT_COUNT(1);
       launch_formal64<KM_LOCAL_LAMBDA>(P, x, y, P->S, st, kstop, step);
       break;
     default:
@@ -609,9 +620,9 @@ rt_status op_rhs(Problem* P, double* b, cudaStream_t st) {
 rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop, int step) {
   if (P->form == RT_FORM_SIGMA) return op_precond_sigma(P, v, z, st, kstop, step);
   const double xiW2 = P->xi * P->W2;
-  k_moments<double, double, KM_LOCAL_LAMBDA><<<P->Ns, kMomThreads, 0, st>>>(
-      v, nullptr, P->wI2, P->wQ2, P->t201d, P->t202d, P->Minv, P->Ns, P->Nmu, P->Nnu, P->xi, xiW2, P->S2,
-      kstop, step); RT_COUNT(1);
+  k_moments64<KM_LOCAL_LAMBDA><<<P->Ns, kMom64Threads, 0, st>>>(v, nullptr, P->wray, P->t201d, P->t202d, P->Minv,
+                                                                P->Ns, P->Nmu, P->nray, P->xi, xiW2, P->S2, kstop,
+                                                                step); RT_COUNT(1);
   k_add_local<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(v, P->cb, P->ce, P->cg, P->S2, P->Ns, P->Nmu,
                                                                     P->Nnu, z, kstop, step); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
