@@ -133,6 +133,8 @@ struct Problem {
   double* ca = nullptr;    // ... alpha (coefficient of the upwind S)
   double* cb = nullptr;    // ... beta  (coefficient of S at the new node)
   double* cg = nullptr;    // ... gamma (DELO-parabolic only: coefficient of S at the downwind node)
+  double* Etile = nullptr; // [ntile64-1][nray] FP64 formal solver: slope of each depth tile's map
+  double* Bmap = nullptr;  // [2*ngroups][ntile64-1][32] FP64 formal solver: offsets of the tile maps
   double* wray = nullptr;  // [3][nray] hat-w_m * hat-w_p, the same times T201_m, times T202_m
   double* wI2 = nullptr;   // [Nnu] spectral weights hat-w_p
   double* wQ2 = nullptr;   // [Nmu] angular weights hat-w_m = w_m / 2

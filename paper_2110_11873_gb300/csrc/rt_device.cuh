@@ -10,7 +10,7 @@ namespace {
 
 constexpr int kMomThreads = 256;
 constexpr int kMaxTiles = 8;     // FP32 kernel: up to 256 threads per CTA (255 registers a lane)
-constexpr int kMaxTiles64 = 8;   // FP64 kernel: up to 256 threads, so each lane may hold 255 registers
+constexpr int kMaxTiles64 = 16;  // FP64 formal solver: depth tiles per ray group (one warp each)
 constexpr int kRing = 8;         // prefetch depth of the FP64 formal-solver kernel (steps)
 constexpr int kRing32 = 16;      // prefetch depth of the FP32 kernel (one lane carries I and Q)
 
@@ -241,7 +241,8 @@ struct FormalArgs {
 // One lane: NS Stokes parameters (s0 .. s0+NS-1) of ray r, depth steps
 // [j0, j1) in marching order (node index j; height k = j for downward rays,
 // Ns-1-j for upward rays).  PHASE 0 composes the tile map (E, B) with zero
-// inflow; PHASE 1 sweeps from the inflow I and writes the output.
+// inflow; PHASE 2 composes only B (E, a product of the e coefficients, comes
+// from a table); PHASE 1 sweeps from the inflow I and writes the output.
 // FP64 with FS = RT_FS_DELO_PARABOLIC: each step also takes gamma times S at
 // the downwind node (read from the ring, which then holds one node past the
 // tile; gamma is 0 on the last interval of a ray).
@@ -321,7 +322,7 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
       const TC sk = rsv[u][q];
       // beta S_k, plus gamma S_next for DELO-parabolic
       const TC cur = PARA ? fma(be, sk, rg[u] * rsv[(u + 1) % RING][q]) : be * sk;
-      if (PHASE == 0) {
+      if (PHASE != 1) {
         I[q] = fma(e, I[q], fma(al, sp[q], cur));
       } else if (MODE == KM_LOCAL_LAMBDA) {
         // y = (x + beta* S) - I.  DELO-linear: x - (e I_prev + alpha S_prev).

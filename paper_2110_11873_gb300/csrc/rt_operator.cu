@@ -5,6 +5,12 @@
 //              reduces the Nmu*Nnu rays of I and Q to J00_k and J20_k with
 //              precomputed per-ray weights (w, w T201, w T202), forms sigma_k
 //              and writes the source functions S_I(k,m), S_Q(k,m).
+//   k_fmap,    FP64 formal solver: the units of the affine scan below --
+//   k_fsweep   (ray group, Stokes parameter, depth tile) -- are one warp and
+//              one CTA each, so they spread evenly over the SMs: k_fmap
+//              composes the B of every tile but the last, k_fsweep chains
+//              the maps of the tiles before its own (the slopes E are a
+//              setup table) and sweeps its tile with the output.
 //   k_formal   formal solver Lambda (Eq. 9-10) along every ray, writing
 //              y_k = z_k - I_k on the fly.  A CTA owns one group of 32 rays of
 //              the same direction sign (so the 32 lanes of a warp read one
@@ -25,6 +31,9 @@
 // coefficients are recomputed from Delta in FP32, so the apply streams only
 // x and y.
 #include <math.h>
+
+#include <algorithm>
+#include <cstdlib>
 
 #include "rt_device.cuh"
 
@@ -316,7 +325,8 @@ void free_device(Problem* P) {
   void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wray,   P->wI2,  P->wQ2,   P->t201d, P->t202d,
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
-                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf, P->cg};
+                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf, P->cg,
+                  P->Etile, P->Bmap};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
@@ -327,7 +337,7 @@ void free_device(Problem* P) {
   P->bc = nullptr;
   P->dev_err = nullptr;
   P->qw = P->St = P->qpart = nullptr;
-  P->Mdiag = P->Ibuf = P->cg = nullptr;
+  P->Mdiag = P->Ibuf = P->cg = P->Etile = P->Bmap = nullptr;
   P->staged = 0;
 }
 
@@ -338,27 +348,110 @@ static rt_status upload(Problem* P, T** dst, const std::vector<T>& src, cudaStre
   return RT_OK;
 }
 
-// Depth tiles per ray group.  FP64: the kernel is bound by FP64 issue, one
-// warp per SM sub-partition at a time; a tiled sweep costs 8 FP64 operations
-// per step (tile map, then the re-sweep) against 4 untiled, so choose the T
-// minimising waves x steps-per-tile x cost.  FP32: tiles are cheap, so aim at
-// about 16 warps per SM with tiles of at least 2*kRing steps.
+// Depth tiles per ray group.  FP64: the formal solver's warp units spread
+// evenly over the SMs, so an SM carries ceil(units / SMs) of them.  A step
+// costs a unit 3 FP64 operations in the map kernel and 4 in the sweep; an SM
+// retires one FP64 warp operation in about kFp64OpCycles, while one warp
+// alone needs about kFp64StepCycles per step (the dependent chain through I;
+// both measured on GB300).  Each kernel takes the longer of its pipe time
+// and its latency, and T minimises the sum.  FP32: tiles are cheap, so aim
+// at about 16 warps per SM with tiles of at least 2*kRing steps.
+constexpr double kFp64OpCycles = 20.0, kFp64StepCycles = 600.0;
 static int choose_tiles64(const Problem* P) {
-  const int64_t slots = 4LL * P->num_sms;
+  const int64_t sms = P->num_sms, groups = 2LL * P->ngroups;
+  auto kernel = [&](int64_t units, double ops) {
+    return std::max((double)((units + sms - 1) / sms) * ops * kFp64OpCycles, kFp64StepCycles);
+  };
   int best = 1;
   double best_cost = 1e300;
   for (int T = 1; T <= kMaxTiles64; ++T) {
     const int L = (P->Ns - 1 + T - 1) / T;
     if (T > 1 && L < 2 * kRing) break;
-    const int64_t warps = 2LL * P->ngroups * T;
-    const double waves = (double)((warps + slots - 1) / slots);
-    const double cost = waves * L * (T == 1 ? 4.0 : 8.0);
+    const double cost = L * (kernel(groups * T, 4.0) + (T > 1 ? kernel(groups * (T - 1), 3.0) : 0.0));
     if (cost < best_cost * 0.97) {
       best_cost = cost;
       best = T;
     }
   }
   return best;
+}
+
+// the ray of lane `lane` in ray group g (groups 0..ngd-1 downward); lanes
+// past the direction's last ray take that ray and are inactive
+__device__ __forceinline__ void group_ray(const FormalArgs& A, int g, int lane, int64_t& r, int& m, bool& down,
+                                          bool& active) {
+  down = g < A.ngd;
+  const int64_t base = down ? (int64_t)g * 32 : A.nd + (int64_t)(g - A.ngd) * 32;
+  const int64_t end = down ? A.nd : A.nray;
+  active = base + lane < end;
+  r = active ? base + lane : end - 1;
+  m = (int)(r / A.Nnu);
+}
+
+// slope of tile t's map for every ray, E = product of the e coefficients of
+// its steps in marching order: Etile[t][r], t < T-1 (setup)
+__global__ void k_etile(const double* __restrict__ ce, int Ns, int64_t nray, int64_t nd, int T,
+                        double* __restrict__ Etile) {
+  const int L = (Ns - 1 + T - 1) / T;
+  const int64_t n = (int64_t)(T - 1) * nray;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(i / nray);
+    const int64_t r = i % nray;
+    const bool down = r < nd;
+    const int j0 = 1 + t * L, j1 = min(Ns, j0 + L);
+    double E = 1.0;
+    for (int j = j0; j < j1; ++j) E *= ce[(int64_t)(down ? j - 1 : Ns - 1 - j) * nray + r];
+    Etile[i] = E;
+  }
+}
+
+// B of the map of tile t < T-1 (zero inflow), unit u = (g * 2 + s) * (T-1) + t
+template <int FS, int MODE>
+__global__ void __launch_bounds__(32, FS == RT_FS_DELO_PARABOLIC ? 12 : 16) k_fmap(const FormalArgs A, double* __restrict__ Bmap) {
+  if (A.kstop && A.step >= *A.kstop) return;
+  const int T = A.ntile, L = (A.Ns - 1 + T - 1) / T;
+  const int u = blockIdx.x, lane = threadIdx.x;
+  const int t = u % (T - 1), gs = u / (T - 1);
+  int64_t r;
+  int m;
+  bool down, active;
+  group_ray(A, gs >> 1, lane, r, m, down, active);
+  const int j0 = 1 + t * L, j1 = min(A.Ns, j0 + L);
+  double B[1] = {0.0}, E = 1.0;
+  if (j0 < j1) sweep<double, double, FS, MODE, 2, 1, kRing>(A, gs & 1, down, r, m, active, j0, j1, B, E);
+  Bmap[(size_t)u * 32 + lane] = B[0];
+}
+
+// tile t of ray group g, Stokes s: inflow from the boundary through the maps
+// of tiles 0..t-1, then the sweep with the output; unit u = (g * 2 + s) * T + t
+template <int FS, int MODE>
+__global__ void __launch_bounds__(32, FS == RT_FS_DELO_PARABOLIC ? 12 : 16) k_fsweep(const FormalArgs A, const double* __restrict__ Bmap,
+                                               const double* __restrict__ Etile) {
+  if (A.kstop && A.step >= *A.kstop) return;
+  const int T = A.ntile, L = (A.Ns - 1 + T - 1) / T;
+  const int u = blockIdx.x, lane = threadIdx.x;
+  const int t = u % T, gs = u / T, s0 = gs & 1;
+  int64_t r;
+  int m;
+  bool down, active;
+  group_ray(A, gs >> 1, lane, r, m, down, active);
+  const int Ns = A.Ns;
+  double I[1] = {(MODE == KM_RHS && !down && s0 == 0) ? A.inflow_bottom : 0.0};
+  for (int tt = 0; tt < t; ++tt)
+    I[0] = fma(Etile[(size_t)tt * A.nray + r], I[0], Bmap[((size_t)gs * (T - 1) + tt) * 32 + lane]);
+  if (t == 0 && active) {   // entry node: the inflow itself
+    const int64_t o = (int64_t)s0 * Ns * A.nray + (int64_t)(down ? 0 : Ns - 1) * A.nray + r;
+    const double* __restrict__ x = reinterpret_cast<const double*>(A.x);
+    double* __restrict__ y = reinterpret_cast<double*>(A.y);
+    if (MODE == KM_RHS) y[o] = I[0];
+    else if (MODE == KM_JACOBI) y[o] = x[o] * A.dinv[o];
+    else y[o] = x[o];
+  }
+  const int j0 = 1 + t * L, j1 = min(Ns, j0 + L);
+  if (j0 < j1) {
+    double E = 1.0;
+    sweep<double, double, FS, MODE, 1, 1, kRing>(A, s0, down, r, m, active, j0, j1, I, E);
+  }
 }
 
 static int choose_tiles32(const Problem* P) {
@@ -375,6 +468,9 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   const int ngd = (int)((P->nd + 31) / 32);
   P->ngroups = 2 * ngd;
   P->ntile64 = choose_tiles64(P);
+#ifdef RT_EXPERIMENT
+  if (const char* t = std::getenv("RT_TILES64")) P->ntile64 = std::min(kMaxTiles64, std::max(1, std::atoi(t)));
+#endif
   P->ntile32 = choose_tiles32(P);
   std::vector<double> dtau(Ns - 1), rscale(nray), w0(3 * nray), wnu(P->w_nu), wmu(Nmu);
   for (int m = 0; m < Nmu; ++m) wmu[m] = 0.5 * P->w_mu[m];
@@ -420,6 +516,14 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_rs, Ns, nray, Nh, Nnu, P->fs,
                                                                          P->ce, P->ca, P->cb, P->cg); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
+  if (P->ntile64 > 1) {   // the FP64 formal solver's tile slopes and map buffer
+    const int T = P->ntile64;
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Etile, (size_t)(T - 1) * nray * sizeof(double)));
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Bmap, (size_t)2 * P->ngroups * (T - 1) * 32 * sizeof(double)));
+    k_etile<<<grid_for((int64_t)(T - 1) * nray, 256, 8 * P->num_sms), 256, 0, st>>>(P->ce, Ns, nray, P->nd, T,
+                                                                                     P->Etile); RT_COUNT(1);
+    RT_TRY_CUDA(cudaGetLastError());
+  }
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mdiag, (size_t)Ns * 2 * sizeof(double)));
   k_local_blocks<<<Ns, kMomThreads, 0, st>>>(P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d, Ns, Nmu, Nnu, P->xi,
                                              P->W2, P->Minv, P->Mdiag); RT_COUNT(1);
@@ -475,28 +579,31 @@ static FormalArgs formal_args(const Problem* P, const void* x, void* y, const vo
   return A;
 }
 
+template <int FS, int MODE>
+static void formal64_units(const Problem* P, const FormalArgs& A, cudaStream_t st) {
+  const int T = P->ntile64, groups = 2 * P->ngroups;
+  if (T > 1) {
+    k_fmap<FS, MODE><<<groups * (T - 1), 32, 0, st>>>(A, P->Bmap);
+    RT_COUNT(1);
+  }
+  k_fsweep<FS, MODE><<<groups * T, 32, 0, st>>>(A, P->Bmap, P->Etile);
+  RT_COUNT(1);
+}
+
 template <int MODE>
 static void launch_formal64(const Problem* P, const double* x, double* y, const double* S, cudaStream_t st,
                             const int* kstop, int step) {
   const FormalArgs A = formal_args(P, x, y, S, P->ntile64, kstop, step);
-  if (P->fs == RT_FS_DELO_PARABOLIC)
-    k_formal<double, double, RT_FS_DELO_PARABOLIC, MODE, 2, kRing, kMaxTiles64>
-        <<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
-  else
-    k_formal<double, double, 0, MODE, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
-  RT_COUNT(1);
+  if (P->fs == RT_FS_DELO_PARABOLIC) formal64_units<RT_FS_DELO_PARABOLIC, MODE>(P, A, st);
+  else formal64_units<0, MODE>(P, A, st);
 }
 
 void formal64_lambda(Problem* P, const double* S, double* I_out, double inflow_bottom, cudaStream_t st,
                      const int* kstop, int step) {
   FormalArgs A = formal_args(P, nullptr, I_out, S, P->ntile64, kstop, step);
   A.inflow_bottom = inflow_bottom;
-  if (P->fs == RT_FS_DELO_PARABOLIC)
-    k_formal<double, double, RT_FS_DELO_PARABOLIC, KM_RHS, 2, kRing, kMaxTiles64>
-        <<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
-  else
-    k_formal<double, double, 0, KM_RHS, 2, kRing, kMaxTiles64><<<2 * P->ngroups, 32 * P->ntile64, 0, st>>>(A);
-  RT_COUNT(1);
+  if (P->fs == RT_FS_DELO_PARABOLIC) formal64_units<RT_FS_DELO_PARABOLIC, KM_RHS>(P, A, st);
+  else formal64_units<0, KM_RHS>(P, A, st);
 }
 
 template <typename TV, int MODE>
@@ -518,7 +625,7 @@ static void launch_formal32(const Problem* P, const TV* x, TV* y, cudaStream_t s
 rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st, const int* kstop, int step) {
   if (P->form == RT_FORM_SIGMA) return op_apply_sigma(P, x, y, mode, st, kstop, step);
   const double xiW2 = P->xi * P->W2;
-  const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu;
+  const int Ns = P->Ns, Nmu = P->Nmu;
   switch (mode) {
     case AM_PLAIN:
       k_moments64<KM_PLAIN><<<Ns, kMom64Threads, 0, st>>>(x, nullptr, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu,
