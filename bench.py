@@ -33,6 +33,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "operator applies/s & HBM GB/s; batched solves/s at resid 1e-8; p50/p99 latency"
 FP64_PEAK_TFLOPS = 1.25   # 2 FLOP x 2 FP64 lanes/clk/SM x 152 SMs x 2.06 GHz
+# DRAM bytes (read + write) of one block-MGS step at j = 15 on slab300: the
+# sum over its six launches in one ncu capture of `bench.py --probe bmgs
+# --probe-ns 300` (k_bdot 78.4 MB, 3 x k_bmgs<4,4> 147-148 MB, k_bmgs<4,0>
+# 78.6 MB, k_bscale 15.6 MB); retaken whenever these kernels change
+MGS_STEP_DRAM_BYTES = 616.3e6
 WORKLOAD = "slab300: Ns=300 Nmu=32 Nnu=101 (1,939,200 unknowns), line-centre tau 1e-4..1e8, x in [-8,8], " \
            "eps=1e-4 a=1e-3 W2=1, DELO-linear; Jacobi-GMRES(30) to 1e-8"
 
@@ -52,7 +57,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=400)
-    ap.add_argument("--probe", choices=["apply32", "apply64", "gmres32", "gmres64"],
+    ap.add_argument("--probe", choices=["apply32", "apply64", "gmres32", "gmres64", "bmgs"],
                     help="run only a short sequence of one operation (the target of ncu captures) and exit")
     ap.add_argument("--probe-ns", type=int, default=1000, help="N_s of the sweep atmosphere (300: slab300)")
     ap.add_argument("--probe-reps", type=int, default=4)
@@ -61,8 +66,10 @@ def parse():
 
 def probe_main(args):
     """A few operations on one atmosphere, for profilers: FP32 / FP64 applies
-    (apply32, apply64) or one Jacobi-GMRES(30) solve (gmres32: FP32 operator
-    with FP64 refinement, gmres64: FP64), 60 iterations at most."""
+    (apply32, apply64), one Jacobi-GMRES(30) solve (gmres32: FP32 operator
+    with FP64 refinement, gmres64: FP64), 60 iterations at most, or the
+    block-MGS Arnoldi step at j = 15 (bmgs: the bench's roofline object, on a
+    random 17-vector basis, w restored before each step)."""
     import torch
 
     import rt_workloads as W
@@ -72,7 +79,18 @@ def probe_main(args):
     B.build()
     at = W.slab300() if args.probe_ns == 300 else W.sweep(args.probe_ns)
     P = Problem(at)
-    if args.probe.startswith("apply"):
+    if args.probe == "bmgs":
+        jm = 15
+        g = torch.Generator("cuda").manual_seed(1)
+        V = torch.randn((jm + 2) * P.N, dtype=torch.float64, device="cuda", generator=g)
+        w0 = torch.randn(P.N, dtype=torch.float64, device="cuda", generator=g)
+        w = torch.empty_like(w0)
+        gram = torch.zeros((jm + 2) * 4, dtype=torch.float64, device="cuda")
+        h = torch.empty(jm + 2, dtype=torch.float64, device="cuda")
+        for _ in range(args.probe_reps):
+            w.copy_(w0)
+            P.arnoldi_bmgs(V, jm, w, gram, h)
+    elif args.probe.startswith("apply"):
         dt = torch.float32 if args.probe == "apply32" else torch.float64
         x = torch.rand(P.N, dtype=dt, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
         y = torch.empty_like(x)
@@ -475,7 +493,7 @@ def main():
         deep_ms = timed(lambda: Pd.apply_f32(xd, out=yd), 20, True)
         deep = {"workload": "sweep: Ns=2000 Nmu=64 Nnu=201 (51,456,000 unknowns), FP32 operator",
                 "kernels": "k_quad + k_sigma + k_staged (TMA-staged formal solver)" if Pd.staged_formal
-                else "k_moments + k_formal",
+                else "k_moments + k_formal (register-ring FP32 kernels)",
                 "ms": deep_ms, "alg_gbs": 2 * Pd.N * 4 / (deep_ms * 1e-3) / 1e9,
                 "two_pass_gbs": 3 * Pd.N * 4 / (deep_ms * 1e-3) / 1e9,
                 "note": "alg_gbs counts x read + y written (2*N*4 B); two_pass_gbs adds the quadrature's read of x "
@@ -577,14 +595,14 @@ def main():
             "size_sweep": sweep,
             "batched": batch,
             "served": served,
-            "roofline": {"kernel": "block-MGS Arnoldi step (k_bdot + 4 x k_bmgs + k_bnorm + k_gram_fold, j=15)",
+            "roofline": {"kernel": "block-MGS Arnoldi step (k_bdot + 4 x k_bmgs + k_bscale, j=15)",
                          "bound": "alu", "achieved": mgs_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": mgs_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                         "frac": mgs_tflops / FP64_PEAK_TFLOPS, "traffic": MGS_STEP_DRAM_BYTES,
                          "hbm_gbs": mgs_gbs, "hbm_frac": mgs_gbs / hbm_peak,
                          "note": "FP64-pipe bound: peak = 2 FLOP x 2 FP64 lanes/clk/SM x 152 SMs x 2.06 GHz "
                                  "(the 1.25 TFLOP/s FP64 rate of this GPU); algorithmic FLOP per step "
-                                 "(2(2(j+1)+1)+1)*N of the MGS loop; hbm_gbs counts (2(j+1)+6)*N*8 bytes "
-                                 "against the measured copy bandwidth"},
+                                 "(2(2(j+1)+1)+1)*N of the MGS loop; hbm_gbs counts "
+                                 "(2(j+1)+2*ceil((j+1)/4)+3)*N*8 bytes against the measured copy bandwidth"},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": "applies/s", "h2d_bytes_per_step": N * 8,
                     "d2h_bytes_per_step": N * 8},
