@@ -19,6 +19,8 @@ Modules
               operators, right-hand sides, Jacobi diagonals, assembly and the
               exact LU solution (Algorithm 1, Sect. 3.3, Sect. 4.4)
   krylov   -- textbook GMRES(m), BiCGSTAB, CGS and Richardson (Sect. 2)
+  stationary -- SOR and SSOR preconditioners of the assembled sigma-form
+              matrix (Sect. 2.3, with the readings that reproduce Tables 4-5)
 
 Parity status of each function is stated in its docstring; every function is
 pinned by ``tests/test_oracle_*.py`` except where a docstring says
