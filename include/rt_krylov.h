@@ -170,6 +170,17 @@ rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream);
    v_dev, z_dev: N doubles. */
 rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double* z_dev, void* stream);
 
+/* z = P^-1 v for the sigma-form SOR (kind RT_PREC_SOR) or SSOR
+   (RT_PREC_SSOR) preconditioner with relaxation omega, 0 < omega < 2: the
+   operators the solvers use with those preconditioners (defined with the
+   RT_PREC_* values below; Sect. 2.3).  The first call for a problem
+   assembles A (2*Ns applies), a call with a new (kind, omega) forms P^-1
+   (stream-ordered, synchronising once); each call then does one dense
+   matrix-vector product.  v_dev, z_dev: 2*Ns doubles, distinct.
+   RT_EINVAL for the I-form or more than 8192 unknowns. */
+rt_status rt_precond_stationary(rt_problem* prob, int32_t kind, double omega, const double* v_dev, double* z_dev,
+                                void* stream);
+
 /* One Arnoldi orthogonalisation step by modified Gram-Schmidt (Sect. 2.1:
    the O(nN) nested loop of GMRES), on the problem's vector length N:
      for i = 0..j: h_i = <w, v_i>; w -= h_i v_i;   h_{j+1} = ||w||;  v_{j+1} = w / h_{j+1}
@@ -228,8 +239,30 @@ rt_status rt_arnoldi_mgs_static(double* V_dev, int64_t N, int32_t j, double* w_d
    D^-1 A x = D^-1 b and stops on the preconditioned residual, as the
    paper's experiments do (Sect. 4.2, Table 3).  For the sigma-form, JACOBI
    uses the diagonal of A (Eq. 18) and LOCAL_LAMBDA the inverse 2x2 blocks
-   M_k = Id - J_k Lambda*_k T_k per height. */
-enum { RT_PREC_NONE = 0, RT_PREC_JACOBI = 1, RT_PREC_LOCAL_LAMBDA = 2, RT_PREC_JACOBI_LEFT = 3 };
+   M_k = Id - J_k Lambda*_k T_k per height.
+
+   SOR and SSOR (sigma-form only, FP64, 2*Ns <= 8192; Sect. 2.3): with
+   A = D + L + U the assembled sigma-form matrix (unknowns interleaved per
+   height, heights from the top), the upper SOR variant P = D/omega + U the
+   paper's experiments use (Sect. 4.2), and the SSOR preconditioner
+   P = omega/(2-omega) (D/omega + U) D^-1 (D/omega + L), whose inverse is a
+   backward relaxation sweep followed by a forward one.  These readings
+   reproduce Tables 4 and 5.  The first solve with a given (kind, omega)
+   assembles A (2*Ns operator applies) and forms P^-1 densely on the device;
+   each application is then one matrix-vector product, as the paper
+   precomputes the action of P^-1.  SOR and SSOR are applied from the right
+   (GMRES, BiCGSTAB, CGS) or as x <- x + P^-1 r (Richardson); SOR_LEFT and
+   SSOR_LEFT precondition GMRES from the left, like JACOBI_LEFT. */
+enum {
+  RT_PREC_NONE = 0,
+  RT_PREC_JACOBI = 1,
+  RT_PREC_LOCAL_LAMBDA = 2,
+  RT_PREC_JACOBI_LEFT = 3,
+  RT_PREC_SOR = 4,
+  RT_PREC_SSOR = 5,
+  RT_PREC_SOR_LEFT = 6,
+  RT_PREC_SSOR_LEFT = 7
+};
 enum { RT_X0_ZERO = 0, RT_X0_USER = 1 };
 enum { RT_ORTHO_MGS = 0, RT_ORTHO_CGS2 = 1 };
 enum { RT_PRECISION_FP64 = 0, RT_PRECISION_FP32_REFINE = 1 };
@@ -246,6 +279,7 @@ typedef struct {
   int32_t max_refine;    /* FP32_REFINE: cap on refinement steps */
   double* resid_hist;    /* optional host array: relative residual estimate per iteration */
   int32_t hist_cap;      /* its capacity */
+  double omega;          /* SOR / SSOR relaxation parameter, 0 < omega < 2 (Sect. 2.3) */
 } rt_solver_opts;
 
 typedef struct {
@@ -260,23 +294,24 @@ typedef struct {
 } rt_solve_info;
 
 /* Fill opts with defaults: restart 30, maxit 10000, Jacobi, x0 = 0, MGS,
-   FP64, rtol 1e-8, inner_rtol 1e-4, max_refine 20, no history. */
+   FP64, rtol 1e-8, inner_rtol 1e-4, max_refine 20, no history, omega 1. */
 void rt_solver_opts_default(rt_solver_opts* opts);
 
 /* Right-preconditioned restarted GMRES(m) (Sect. 2.1; Saad & Schultz 1986),
-   left-preconditioned with RT_PREC_JACOBI_LEFT (then FP64 only; rel_resid is
-   the preconditioned residual).  A cycle with m >= the steps needed is the
+   left-preconditioned with RT_PREC_JACOBI_LEFT, RT_PREC_SOR_LEFT or
+   RT_PREC_SSOR_LEFT (then FP64 only; rel_resid is the preconditioned
+   residual).  A cycle with m >= the steps needed is the
    paper's unrestarted GMRES.  b_dev, x_dev: N doubles.  Returns RT_OK when
    converged, RT_ENOTCONV at maxit, RT_EBREAKDOWN, RT_ENUMERIC; in each case
    x_dev holds the iterate. */
 rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                          double* x_dev, rt_solve_info* info, void* stream);
 /* Right-preconditioned BiCGSTAB (Sect. 2.2; van der Vorst 1992); not with
-   RT_PREC_JACOBI_LEFT. */
+   the left preconditioners. */
 rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                             double* x_dev, rt_solve_info* info, void* stream);
-/* Right-preconditioned CGS (Sect. 2.2; Sonneveld 1989); not with
-   RT_PREC_JACOBI_LEFT. */
+/* Right-preconditioned CGS (Sect. 2.2; Sonneveld 1989); not with the left
+   preconditioners. */
 rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                        double* x_dev, rt_solve_info* info, void* stream);
 
@@ -285,7 +320,8 @@ rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const doubl
    paper compares the Krylov solvers with (Sect. 2.3, Table 3).  Stops when
    ||b - A x|| / ||b|| < rtol (the unpreconditioned residual, computed every
    iteration) or after maxit updates; iters counts the updates.  FP64;
-   preconditioners NONE, JACOBI, LOCAL_LAMBDA; either form. */
+   preconditioners NONE, JACOBI, LOCAL_LAMBDA (either form), SOR and SSOR
+   (sigma-form; the paper's SOR- and SSOR-Richardson rows of Tables 4-5). */
 rt_status rt_solve_richardson(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                               double* x_dev, rt_solve_info* info, void* stream);
 

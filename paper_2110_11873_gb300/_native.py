@@ -19,6 +19,7 @@ RT_TAU_LINE_CENTER, RT_TAU_FREQ_INTEGRATED = 0, 1
 RT_MU_GL_HALF, RT_MU_GL_FULL = 0, 1
 RT_FS_DELO_LINEAR, RT_FS_IMPLICIT_EULER, RT_FS_TRAPEZOIDAL = 0, 1, 2
 RT_PREC_NONE, RT_PREC_JACOBI, RT_PREC_LOCAL_LAMBDA, RT_PREC_JACOBI_LEFT = 0, 1, 2, 3
+RT_PREC_SOR, RT_PREC_SSOR, RT_PREC_SOR_LEFT, RT_PREC_SSOR_LEFT = 4, 5, 6, 7
 RT_FORM_I, RT_FORM_SIGMA = 0, 1
 RT_X0_ZERO, RT_X0_USER = 0, 1
 RT_ORTHO_MGS, RT_ORTHO_CGS2 = 0, 1
@@ -41,6 +42,7 @@ class SolverOpts(C.Structure):
         ("restart", C.c_int32), ("maxit", C.c_int32), ("precond", C.c_int32), ("x0_kind", C.c_int32),
         ("ortho", C.c_int32), ("precision", C.c_int32), ("rtol", C.c_double), ("inner_rtol", C.c_double),
         ("max_refine", C.c_int32), ("resid_hist", C.POINTER(C.c_double)), ("hist_cap", C.c_int32),
+        ("omega", C.c_double),
     ]
 
 
@@ -81,6 +83,7 @@ SIGNATURES = [
     ("rt_rhs", C.c_int, [_P, _P, _P]),
     ("rt_jacobi_diag", C.c_int, [_P, _P, _P]),
     ("rt_precond_local_lambda", C.c_int, [_P, _P, _P, _P]),
+    ("rt_precond_stationary", C.c_int, [_P, C.c_int32, C.c_double, _P, _P, _P]),
     ("rt_arnoldi_mgs", C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
     ("rt_arnoldi_bmgs", C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P]),
     ("rt_arnoldi_mgs_static", C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P]),

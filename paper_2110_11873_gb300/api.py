@@ -242,6 +242,17 @@ class Problem:
                 "rt_precond_local_lambda")
         return z
 
+    def precond_stationary(self, v: torch.Tensor, kind: str = "ssor", omega: float = 1.0,
+                           out: Optional[torch.Tensor] = None, stream=None):
+        """z = P^-1 v for the sigma-form SOR ("sor") or SSOR ("ssor") preconditioner."""
+        v = self._vec(v)
+        z = self._vec(out)
+        k = {"sor": N.RT_PREC_SOR, "ssor": N.RT_PREC_SSOR}[kind]
+        N.check(self.lib.rt_precond_stationary(self.handle, k, float(omega), C.c_void_p(v.data_ptr()),
+                                               C.c_void_p(z.data_ptr()), _stream_handle(stream)),
+                "rt_precond_stationary")
+        return z
+
     def arnoldi_mgs(self, V: torch.Tensor, j: int, w: torch.Tensor, h: Optional[torch.Tensor] = None,
                     stream=None) -> torch.Tensor:
         """One MGS Arnoldi step: orthogonalise w against V[0..j], write
@@ -274,15 +285,20 @@ class Problem:
     def solve(self, b: torch.Tensor, method: str = "gmres", x: Optional[torch.Tensor] = None, *,
               restart: int = 30, maxit: int = 10000, precond: str = "jacobi", rtol: float = 1e-8,
               x0: bool = False, precision: str = "fp64", inner_rtol: float = 1e-4, max_refine: int = 20,
-              hist_cap: int = 0, raise_on_error: bool = True, stream=None):
-        """Solve A x = b; returns (x, SolveResult).  ``x0=True`` uses ``x`` as initial guess."""
+              hist_cap: int = 0, omega: float = 1.0, raise_on_error: bool = True, stream=None):
+        """Solve A x = b; returns (x, SolveResult).  ``x0=True`` uses ``x`` as initial guess.
+        ``precond``: "none", "jacobi", "local_lambda", "jacobi_left" (GMRES), and for the
+        sigma-form "sor", "ssor", "sor_left", "ssor_left" (GMRES) with relaxation ``omega``."""
         b = self._vec(b)
         x = self._vec(x) if x is not None else torch.zeros(self.N, dtype=torch.float64, device=self.device)
         o = N.SolverOpts()
         self.lib.rt_solver_opts_default(C.byref(o))
         o.restart, o.maxit, o.rtol = restart, maxit, rtol
         o.precond = {"none": N.RT_PREC_NONE, "jacobi": N.RT_PREC_JACOBI,
-                     "local_lambda": N.RT_PREC_LOCAL_LAMBDA, "jacobi_left": N.RT_PREC_JACOBI_LEFT}[precond]
+                     "local_lambda": N.RT_PREC_LOCAL_LAMBDA, "jacobi_left": N.RT_PREC_JACOBI_LEFT,
+                     "sor": N.RT_PREC_SOR, "ssor": N.RT_PREC_SSOR, "sor_left": N.RT_PREC_SOR_LEFT,
+                     "ssor_left": N.RT_PREC_SSOR_LEFT}[precond]
+        o.omega = omega
         o.x0_kind = N.RT_X0_USER if x0 else N.RT_X0_ZERO
         o.precision = {"fp64": N.RT_PRECISION_FP64, "fp32_refine": N.RT_PRECISION_FP32_REFINE}[precision]
         o.inner_rtol, o.max_refine = inner_rtol, max_refine

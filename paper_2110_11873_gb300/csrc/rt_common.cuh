@@ -134,6 +134,11 @@ struct Problem {
   double* cb = nullptr;    // ... beta  (coefficient of S at the new node)
   double* cg = nullptr;    // ... gamma (DELO-parabolic only: coefficient of S at the downwind node)
   double* Etile = nullptr; // [ntile64-1][nray] FP64 formal solver: slope of each depth tile's map
+  // sigma-form SOR / SSOR: the assembled matrix A (row-major n x n, n = Nop),
+  // the dense P^-1 (row-major), a triangular-inverse scratch and a vector
+  double *Asig = nullptr, *Mpre = nullptr, *Mtri = nullptr, *Mscr = nullptr;
+  int mpre_kind = 0;         // RT_PREC_SOR / RT_PREC_SSOR that Mpre holds (0: none)
+  double mpre_omega = 0.0;
   double* Bmap = nullptr;  // [2*ngroups][ntile64-1][32] FP64 formal solver: offsets of the tile maps
   double* wray = nullptr;  // [3][nray] hat-w_m * hat-w_p, the same times T201_m, times T202_m
   double* wI2 = nullptr;   // [Nnu] spectral weights hat-w_p
@@ -168,18 +173,7 @@ struct Problem {
   double* hist = nullptr;     // device history
   int hist_cap_dev = 0;
   int vec_grid = 0;           // blocks of the reduction kernels
-  // the formal solver alone (Eq. 9-10): I = Lambda S with the given inflow at
-// the bottom for Stokes I (zero elsewhere), FP64, written to I_out [2][Ns][nray]
-void formal64_lambda(Problem* P, const double* S, double* I_out, double inflow_bottom, cudaStream_t st,
-                     const int* kstop = nullptr, int step = 0);
-// sigma-form operator and its companions (rt_sigma.cu); vectors of 2*Ns
-rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaStream_t st,
-                         const int* kstop = nullptr, int step = 0);
-rt_status op_rhs_sigma(Problem* P, double* b, cudaStream_t st);
-rt_status op_jacobi_sigma(Problem* P, double* d, int inverse, cudaStream_t st);
-rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop = nullptr,
-                           int step = 0);
-// fast FP32 apply (rt_tma.cu): usable for this problem, its tables, and
+  // fast FP32 apply (rt_tma.cu): usable for this problem, its tables, and
   // the device flag its bounded waits set when they give up
   int staged = 0;
   int ntile_st = 1;            // depth tiles per ray group of the staged formal solver
@@ -213,6 +207,13 @@ rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaS
                          const int* kstop = nullptr, int step = 0);
 rt_status op_rhs_sigma(Problem* P, double* b, cudaStream_t st);
 rt_status op_jacobi_sigma(Problem* P, double* d, int inverse, cudaStream_t st);
+// sigma-form SOR / SSOR (kind RT_PREC_SOR or RT_PREC_SSOR, with or without
+// _LEFT): assemble A on first use, form P^-1 for (kind, omega) in Mpre
+rt_status op_dense_precond_build(Problem* P, int kind, double omega, cudaStream_t st);
+// z = P^-1 v with the Mpre of the last build (one GEMV)
+rt_status op_dense_precond_apply(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop = nullptr,
+                                 int step = 0);
+constexpr int kMaxDenseN = 8192;   // largest sigma-form system with a dense SOR / SSOR inverse
 rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop = nullptr,
                            int step = 0);
 // fast FP32 apply (rt_tma.cu)

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kVecThreads) k_mgs(double* __restrict__ w, con
                                                      const double* __restrict__ vnext, int64_t N,
                                                      const double* __restrict__ part_in, double* __restrict__ part_out,
                                                      double* __restrict__ hslot, const int* kstop, int step) {
-  if (step >= *kstop) return;
+  if (kstop && step >= *kstop) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const double* __restrict__ vn = vnext ? vnext : w;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bdot(const double* __restric
                                                         int64_t N, double* __restrict__ part_out, int j, int rev,
                                                         const int* kstop) {
   constexpr int nk = NK;
-  if (j >= *kstop) return;
+  if (kstop && j >= *kstop) return;
   pdl_launch_dependents();
   pdl_wait();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w,
                                                         const int* kstop) {
   static_assert(NB >= 1 && NB <= kB && NN >= 0 && NN <= kB && (NN == 0 || NB == kB), "block shape");
   constexpr int nb = NB, nn = NN, ng = NN == 0 && NB < kB ? NB : 0;
-  if (j >= *kstop) return;
+  if (kstop && j >= *kstop) return;
   pdl_launch_dependents();
   const int G = gridDim.x;
   const double* __restrict__ vb = V + (size_t)i0 * N;
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kVecThreads, 3) k_bscale(const double* __restr
                                                            int ng, double* __restrict__ hcol, double* __restrict__ gram,
                                                            GmresDev* gm, int m, int j, double* hist, int hist_cap,
                                                            int rev, const int* kstop) {
-  if (j >= *kstop) return;
+  if (kstop && j >= *kstop) return;
   pdl_wait();
   if (blockIdx.x == 0) {
     __shared__ double sets[kB];
@@ -781,7 +781,7 @@ __global__ void k_rich_begin(GmresDev* gm) { gm->kstop = kRichSteps; }
 __global__ void __launch_bounds__(kVecThreads) k_rich_update(double* __restrict__ x, const double* __restrict__ z,
                                                              const double* __restrict__ d, int64_t N,
                                                              const int* kstop, int step) {
-  if (step >= *kstop) return;
+  if (kstop && step >= *kstop) return;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
     x[n] += d ? d[n] * z[n] : z[n];
 }
@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(kVecThreads) k_rich_resid(const double* __rest
                                                             const double* __restrict__ Ax, double* __restrict__ r,
                                                             int64_t N, double* __restrict__ part, const int* kstop,
                                                             int step) {
-  if (step >= *kstop) return;
+  if (kstop && step >= *kstop) return;
   double s = 0.0;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
     const double v = b[n] - Ax[n];
@@ -826,7 +826,7 @@ __global__ void k_rich_check(const double* __restrict__ part, int G, GmresDev* g
 __global__ void __launch_bounds__(kVecThreads) k_mul_gated(const double* __restrict__ x,
                                                            const double* __restrict__ d, double* __restrict__ y,
                                                            int64_t N, const int* kstop, int step) {
-  if (step >= *kstop) return;
+  if (kstop && step >= *kstop) return;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
     y[n] = x[n] * d[n];
 }
@@ -871,16 +871,37 @@ static inline double* partb(Problem* P, int i) { return P->partials + (size_t)i 
 // block-pass partials: buffers 0 and 1 ping-pong, 2 holds the Gram partials
 static inline double* bpartb(Problem* P, int i) { return P->bpart + (size_t)i * kGramB * kMaxPartials; }
 
+// the dense sigma-form SOR / SSOR preconditioners, and the left ones
+static inline bool prec_dense(int pc) {
+  return pc == RT_PREC_SOR || pc == RT_PREC_SSOR || pc == RT_PREC_SOR_LEFT || pc == RT_PREC_SSOR_LEFT;
+}
+static inline bool prec_left(int pc) {
+  return pc == RT_PREC_JACOBI_LEFT || pc == RT_PREC_SOR_LEFT || pc == RT_PREC_SSOR_LEFT;
+}
+
+// y = M x for a left preconditioner M (D^-1 or the dense P^-1)
+static rt_status left_apply(Problem* P, int pc, const double* x, double* y, cudaStream_t st,
+                            const int* kstop = nullptr, int step = 0) {
+  if (pc == RT_PREC_JACOBI_LEFT) {
+    k_mul_gated<<<P->vec_grid, kVecThreads, 0, st>>>(x, P->dinv, y, P->Nop, kstop, step); RT_COUNT(1);
+    RT_TRY_CUDA(cudaGetLastError());
+    return RT_OK;
+  }
+  return op_dense_precond_apply(P, x, y, st, kstop, step);
+}
+
 // A M^{-1} v with the chosen preconditioner and operator precision
 static rt_status apply_prec(Problem* P, const double* v, double* y, int precond, int fp32, cudaStream_t st,
                             const int* kstop = nullptr, int step = 0) {
-  if (precond == RT_PREC_JACOBI_LEFT) {
-    // D^-1 A v: the FP64 apply into the scratch vector wk(6), then the scaling
-    double* t = P->work + (size_t)6 * P->Nop;
+  if (prec_left(precond)) {
+    // M A v: the FP64 apply into a scratch vector, then M
+    double* t = precond == RT_PREC_JACOBI_LEFT ? P->work + (size_t)6 * P->Nop : P->Mscr + P->Nop;
     RT_TRY(op_apply64(P, v, t, AM_PLAIN, st, kstop, step));
-    k_mul_gated<<<P->vec_grid, kVecThreads, 0, st>>>(t, P->dinv, y, P->Nop, kstop, step); RT_COUNT(1);
-    RT_TRY_CUDA(cudaGetLastError());
-    return RT_OK;
+    return left_apply(P, precond, t, y, st, kstop, step);
+  }
+  if (prec_dense(precond)) {   // right SOR / SSOR: A (P^-1 v)
+    RT_TRY(op_dense_precond_apply(P, v, P->Mscr, st, kstop, step));
+    return op_apply64(P, P->Mscr, y, AM_PLAIN, st, kstop, step);
   }
   const int mode = precond == RT_PREC_JACOBI ? AM_JACOBI : precond == RT_PREC_LOCAL_LAMBDA ? AM_LOCAL_LAMBDA : AM_PLAIN;
   if (fp32) return op_apply32_f64io(P, v, y, mode, st, kstop, step);
@@ -894,6 +915,9 @@ static rt_status add_precond(Problem* P, double* x, double* t, int precond, doub
     k_axpy1<<<G, kVecThreads, 0, st>>>(x, t, P->Nop); RT_COUNT(1);
   } else if (precond == RT_PREC_JACOBI) {
     k_mul<<<G, kVecThreads, 0, st>>>(t, P->dinv, tmp, P->Nop); RT_COUNT(1);
+    k_axpy1<<<G, kVecThreads, 0, st>>>(x, tmp, P->Nop); RT_COUNT(1);
+  } else if (prec_dense(precond)) {
+    RT_TRY(op_dense_precond_apply(P, t, tmp, st));
     k_axpy1<<<G, kVecThreads, 0, st>>>(x, tmp, P->Nop); RT_COUNT(1);
   } else {
     RT_TRY(op_precond_ll(P, t, tmp, st));
@@ -962,10 +986,12 @@ struct GmresGraphKey {
   }
 };
 
+constexpr int kNumPrec = RT_PREC_SSOR_LEFT + 1;
+
 struct GraphCache {
   std::map<GmresGraphKey, cudaGraphExec_t> gmres;
-  cudaGraphExec_t bicg[2][3][2] = {};  // [method][precond][fp32]
-  cudaGraphExec_t rich[3] = {};         // [precond]
+  cudaGraphExec_t bicg[2][kNumPrec][2] = {};  // [method][precond][fp32]
+  cudaGraphExec_t rich[kNumPrec] = {};         // [precond]
   std::map<cudaGraphExec_t, long long> kernels;  // kernel nodes per executable graph
   cudaStream_t cap = nullptr;
   ~GraphCache() {
@@ -1029,16 +1055,17 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
   k_lsq<<<1, 1, 0, st>>>(gm, m); RT_COUNT(1);
   double* x = wk(P, 0);
   double* t = wk(P, 4);
-  if (precond == RT_PREC_LOCAL_LAMBDA) {
+  if (precond == RT_PREC_LOCAL_LAMBDA || precond == RT_PREC_SOR || precond == RT_PREC_SSOR) {
     k_combine<<<G, kVecThreads, 0, st>>>(P->V, N, gm, x, P->dinv, t, 2); RT_COUNT(1);
-    RT_TRY(op_precond_ll(P, t, wk(P, 6), st));
+    if (precond == RT_PREC_LOCAL_LAMBDA) RT_TRY(op_precond_ll(P, t, wk(P, 6), st));
+    else RT_TRY(op_dense_precond_apply(P, t, wk(P, 6), st));
     k_axpy1<<<G, kVecThreads, 0, st>>>(x, wk(P, 6), N); RT_COUNT(1);
   } else {
     k_combine<<<G, kVecThreads, 0, st>>>(P->V, N, gm, x, P->dinv, t, precond == RT_PREC_JACOBI ? 1 : 0); RT_COUNT(1);
   }
   RT_TRY(op_apply64(P, x, wk(P, 5), AM_PLAIN, st));
-  if (precond == RT_PREC_JACOBI_LEFT) {   // the residual of D^-1 A x = D^-1 b
-    k_mul<<<G, kVecThreads, 0, st>>>(wk(P, 5), P->dinv, wk(P, 6), N); RT_COUNT(1);
+  if (prec_left(precond)) {   // the residual of M A x = M b
+    RT_TRY(left_apply(P, precond, wk(P, 5), wk(P, 6), st));
     k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 6), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
   } else {
     k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
@@ -1142,8 +1169,8 @@ static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, doubl
   } else {
     RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
     const double* ax = wk(P, 5);
-    if (o->precond == RT_PREC_JACOBI_LEFT) {
-      k_mul<<<G, kVecThreads, 0, st>>>(wk(P, 5), P->dinv, wk(P, 6), N); RT_COUNT(1);
+    if (prec_left(o->precond)) {
+      RT_TRY(left_apply(P, o->precond, wk(P, 5), wk(P, 6), st));
       ax = wk(P, 6);
     }
     k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), ax, wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
@@ -1174,6 +1201,7 @@ static rt_status prepare(Problem* P, const rt_solver_opts* o, int restart, cudaS
   RT_TRY(ensure_workspace(P, restart, st));
   if (o->resid_hist && o->hist_cap > 0) RT_TRY(ensure_hist(P, o->hist_cap));
   if (o->precond == RT_PREC_JACOBI || o->precond == RT_PREC_JACOBI_LEFT) RT_TRY(op_jacobi_inv(P, P->dinv, st));
+  if (prec_dense(o->precond)) RT_TRY(op_dense_precond_build(P, o->precond, o->omega, st));
   return RT_OK;
 }
 
@@ -1181,7 +1209,15 @@ static rt_status check_opts(const rt_solver_opts* o, const double* b, const doub
   if (!o || !b || !x) { set_error("opts, b_dev and x_dev are required"); return RT_EINVAL; }
   if (o->restart < 1 || o->restart > kMaxRestart) { set_error("restart must be in [1,%d]", kMaxRestart); return RT_EINVAL; }
   if (o->maxit < 1) { set_error("maxit must be >= 1"); return RT_EINVAL; }
-  if (o->precond < RT_PREC_NONE || o->precond > RT_PREC_JACOBI_LEFT) { set_error("bad precond"); return RT_EINVAL; }
+  if (o->precond < RT_PREC_NONE || o->precond > RT_PREC_SSOR_LEFT) { set_error("bad precond"); return RT_EINVAL; }
+  if (prec_dense(o->precond) && !(o->omega > 0.0 && o->omega < 2.0)) {
+    set_error("SOR / SSOR: omega must be in (0, 2)");
+    return RT_EINVAL;
+  }
+  if (prec_dense(o->precond) && o->precision != RT_PRECISION_FP64) {
+    set_error("SOR / SSOR need RT_PRECISION_FP64");
+    return RT_EINVAL;
+  }
   if (o->x0_kind != RT_X0_ZERO && o->x0_kind != RT_X0_USER) { set_error("bad x0_kind"); return RT_EINVAL; }
   if (o->ortho != RT_ORTHO_MGS) { set_error("only RT_ORTHO_MGS is implemented"); return RT_EINVAL; }
   if (o->precision != RT_PRECISION_FP64 && o->precision != RT_PRECISION_FP32_REFINE) { set_error("bad precision"); return RT_EINVAL; }
@@ -1222,15 +1258,14 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
                              cudaStream_t st) {
   const double t0 = now_ms();
   if (info) memset(info, 0, sizeof *info);
-  if (o->precond == RT_PREC_JACOBI_LEFT && o->precision != RT_PRECISION_FP64) {
-    set_error("RT_PREC_JACOBI_LEFT needs RT_PRECISION_FP64");
+  if (prec_left(o->precond) && o->precision != RT_PRECISION_FP64) {
+    set_error("the left preconditioners need RT_PRECISION_FP64");
     return finish_info(info, RT_EINVAL, t0);
   }
   RT_TRY(prepare(P, o, o->restart, st));
   const size_t bytes = (size_t)P->Nop * sizeof(double);
-  if (o->precond == RT_PREC_JACOBI_LEFT) {   // the system D^-1 A x = D^-1 b
-    k_mul<<<P->vec_grid, kVecThreads, 0, st>>>(b, P->dinv, wk(P, 1), P->Nop); RT_COUNT(1);
-    RT_TRY_CUDA(cudaGetLastError());
+  if (prec_left(o->precond)) {   // the system M A x = M b
+    RT_TRY(left_apply(P, o->precond, b, wk(P, 1), st));
   } else {
     RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
   }
@@ -1357,8 +1392,9 @@ static rt_status enqueue_rich(Problem* P, int precond, cudaStream_t st) {
   const int* kstop = &gm->kstop;
   k_rich_begin<<<1, 1, 0, st>>>(gm); RT_COUNT(1);
   for (int s = 0; s < kRichSteps; ++s) {
-    if (precond == RT_PREC_LOCAL_LAMBDA) {
-      RT_TRY(op_precond_ll(P, wk(P, 2), wk(P, 6), st, kstop, s));
+    if (precond == RT_PREC_LOCAL_LAMBDA || prec_dense(precond)) {
+      if (precond == RT_PREC_LOCAL_LAMBDA) RT_TRY(op_precond_ll(P, wk(P, 2), wk(P, 6), st, kstop, s));
+      else RT_TRY(op_dense_precond_apply(P, wk(P, 2), wk(P, 6), st, kstop, s));
       k_rich_update<<<G, kVecThreads, 0, st>>>(wk(P, 0), wk(P, 6), nullptr, N, kstop, s); RT_COUNT(1);
     } else {
       k_rich_update<<<G, kVecThreads, 0, st>>>(wk(P, 0), wk(P, 2), precond == RT_PREC_JACOBI ? P->dinv : nullptr, N,
@@ -1376,8 +1412,8 @@ static rt_status solve_richardson(Problem* P, const rt_solver_opts* o, const dou
                                   rt_solve_info* info, cudaStream_t st) {
   const double t0 = now_ms();
   if (info) memset(info, 0, sizeof *info);
-  if (o->precision != RT_PRECISION_FP64 || o->precond == RT_PREC_JACOBI_LEFT) {
-    set_error("Richardson: FP64, preconditioned from the right (NONE, JACOBI, LOCAL_LAMBDA)");
+  if (o->precision != RT_PRECISION_FP64 || prec_left(o->precond)) {
+    set_error("Richardson: FP64, with NONE, JACOBI, LOCAL_LAMBDA, SOR or SSOR");
     return finish_info(info, RT_EINVAL, t0);
   }
   RT_TRY(prepare(P, o, 1, st));
@@ -1456,7 +1492,7 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
     set_error("BiCGSTAB/CGS support FP64 only");
     return finish_info(info, RT_EINVAL, t0);
   }
-  if (o->precond == RT_PREC_JACOBI_LEFT) {
+  if (prec_left(o->precond)) {
     set_error("BiCGSTAB/CGS are preconditioned from the right only");
     return finish_info(info, RT_EINVAL, t0);
   }
@@ -1561,6 +1597,7 @@ void rt_solver_opts_default(rt_solver_opts* o) {
   o->rtol = 1e-8;
   o->inner_rtol = 1e-4;
   o->max_refine = 20;
+  o->omega = 1.0;
 }
 
 rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* h_dev, void* stream) {

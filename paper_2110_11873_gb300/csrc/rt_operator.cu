@@ -326,7 +326,7 @@ void free_device(Problem* P) {
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
                   P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf, P->cg,
-                  P->Etile, P->Bmap};
+                  P->Etile, P->Bmap, P->Asig, P->Mpre, P->Mtri, P->Mscr};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
@@ -338,6 +338,8 @@ void free_device(Problem* P) {
   P->dev_err = nullptr;
   P->qw = P->St = P->qpart = nullptr;
   P->Mdiag = P->Ibuf = P->cg = P->Etile = P->Bmap = nullptr;
+  P->Asig = P->Mpre = P->Mtri = P->Mscr = nullptr;
+  P->mpre_kind = 0;
   P->staged = 0;
 }
 
@@ -799,6 +801,21 @@ rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double*
     return RT_EINVAL;
   }
   return op_precond_ll(&prob->P, v_dev, z_dev, as_stream(stream));
+}
+
+rt_status rt_precond_stationary(rt_problem* prob, int32_t kind, double omega, const double* v_dev, double* z_dev,
+                                void* stream) {
+  RT_TRY(check_prob(prob));
+  if (!v_dev || !z_dev || v_dev == z_dev) {
+    set_error("v_dev and z_dev must be distinct non-NULL device buffers");
+    return RT_EINVAL;
+  }
+  if (kind != RT_PREC_SOR && kind != RT_PREC_SSOR) {
+    set_error("kind must be RT_PREC_SOR or RT_PREC_SSOR");
+    return RT_EINVAL;
+  }
+  RT_TRY(op_dense_precond_build(&prob->P, kind, omega, as_stream(stream)));
+  return op_dense_precond_apply(&prob->P, v_dev, z_dev, as_stream(stream));
 }
 
 }  // extern "C"

@@ -127,6 +127,77 @@ __global__ void k_sig_block(const double* __restrict__ v, const double* __restri
   }
 }
 
+// ------------------------------------------- SOR and SSOR (Sect. 2.3)
+// The sigma-form matrix is small (n = 2*Ns), so the paper's SOR and SSOR
+// preconditioners are formed densely from the assembled A = D + L + U and
+// applied as one matrix-vector product (the paper precomputes the action of
+// P^-1, Sect. 4.2).  Readings: the upper SOR variant P = D/omega + U, and
+// SSOR P = omega/(2-omega) (D/omega + U) D^-1 (D/omega + L).
+
+// e = unit vector j
+__global__ void k_unit(double* __restrict__ e, int n, int j) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) e[i] = i == j ? 1.0 : 0.0;
+}
+
+// row-major A from column-major C (C[j*n + i] = A_ij)
+__global__ void k_transpose(const double* __restrict__ C, int n, double* __restrict__ A) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    A[t] = C[(int64_t)j * n + i];
+  }
+}
+
+// X = (D/omega + U)^-1 (UPPER) or (D/omega + L)^-1, row-major: column j
+// by back (forward) substitution in one thread; the threads of a warp read
+// the same row of A and consecutive entries of a row of X
+template <bool UPPER>
+__global__ void k_tri_inverse(const double* __restrict__ A, int n, double omega, double* __restrict__ X) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int s = 0; s < n; ++s) {
+    const int i = UPPER ? n - 1 - s : s;
+    double x = 0.0;
+    if (UPPER ? i <= j : i >= j) {
+      double r = i == j ? 1.0 : 0.0;
+      if (UPPER)
+        for (int k = i + 1; k <= j; ++k) r = fma(-A[(int64_t)i * n + k], X[(int64_t)k * n + j], r);
+      else
+        for (int k = j; k < i; ++k) r = fma(-A[(int64_t)i * n + k], X[(int64_t)k * n + j], r);
+      x = r * omega / A[(int64_t)i * n + i];
+    }
+    X[(int64_t)i * n + j] = x;
+  }
+}
+
+// M = c * Li * diag(A) * Ui with Li lower and Ui upper triangular (SSOR)
+__global__ void k_ssor_product(const double* __restrict__ Li, const double* __restrict__ Ui,
+                               const double* __restrict__ A, int n, double c, double* __restrict__ M) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    const int kmax = i < j ? i : j;
+    double s = 0.0;
+    for (int k = 0; k <= kmax; ++k) s = fma(Li[(int64_t)i * n + k] * A[(int64_t)k * n + k], Ui[(int64_t)k * n + j], s);
+    M[t] = c * s;
+  }
+}
+
+// z = M v (row-major n x n), one warp per row
+__global__ void k_gemv(const double* __restrict__ M, const double* __restrict__ v, int n, double* __restrict__ z,
+                       const int* kstop, int step) {
+  if (kstop && step >= *kstop) return;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const double* __restrict__ row = M + (int64_t)i * n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s = fma(row[j], v[j], s);
+    s = warp_sum(s);
+    if (lane == 0) z[i] = s;
+  }
+}
+
 inline int blocks_for(int64_t n, int threads, int cap) {
   int64_t g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -144,6 +215,68 @@ void launch_sigma(Problem* P, const double* v, double* y, cudaStream_t st, const
 }
 
 }  // namespace
+
+rt_status op_dense_precond_build(Problem* P, int kind, double omega, cudaStream_t st) {
+  if (P->form != RT_FORM_SIGMA) {
+    set_error("SOR and SSOR need the sigma-form (RT_FORM_SIGMA)");
+    return RT_EINVAL;
+  }
+  const int n = (int)P->Nop;
+  if (n > kMaxDenseN) {
+    set_error("SOR and SSOR: the sigma-form system has %d > %d unknowns", n, kMaxDenseN);
+    return RT_EINVAL;
+  }
+  if (!(omega > 0.0 && omega < 2.0)) {
+    set_error("omega must be in (0, 2)");
+    return RT_EINVAL;
+  }
+  const size_t nn = (size_t)n * n;
+  if (!P->Asig) {
+    // the columns A e_j (one sigma-form apply each) into Mtri, then row-major
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Asig, nn * sizeof(double)));
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mpre, nn * sizeof(double)));
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mtri, nn * sizeof(double)));
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mscr, 2 * (size_t)n * sizeof(double)));
+    for (int j = 0; j < n; ++j) {
+      k_unit<<<blocks_for(n, 256, 64), 256, 0, st>>>(P->Mscr, n, j); RT_COUNT(1);
+      RT_TRY(op_apply_sigma(P, P->Mscr, P->Mtri + (size_t)j * n, AM_PLAIN, st, nullptr, 0));
+    }
+    k_transpose<<<blocks_for((int64_t)nn, 256, 8 * P->num_sms), 256, 0, st>>>(P->Mtri, n, P->Asig); RT_COUNT(1);
+    RT_TRY_CUDA(cudaGetLastError());
+    P->mpre_kind = 0;
+  }
+  const int base = (kind == RT_PREC_SOR || kind == RT_PREC_SOR_LEFT) ? RT_PREC_SOR : RT_PREC_SSOR;
+  if (P->mpre_kind == base && P->mpre_omega == omega) return RT_OK;
+  const int tb = 128, gb = (n + tb - 1) / tb;
+  if (base == RT_PREC_SOR) {
+    k_tri_inverse<true><<<gb, tb, 0, st>>>(P->Asig, n, omega, P->Mpre); RT_COUNT(1);
+  } else {
+    // P^-1 = (2-omega)/omega (D/omega + L)^-1 D (D/omega + U)^-1
+    double* Li = nullptr;
+    RT_TRY_CUDA(dev_alloc(P, (void**)&Li, nn * sizeof(double)));
+    k_tri_inverse<true><<<gb, tb, 0, st>>>(P->Asig, n, omega, P->Mtri); RT_COUNT(1);
+    k_tri_inverse<false><<<gb, tb, 0, st>>>(P->Asig, n, omega, Li); RT_COUNT(1);
+    k_ssor_product<<<blocks_for((int64_t)nn, 256, 16 * P->num_sms), 256, 0, st>>>(Li, P->Mtri, P->Asig, n,
+                                                                                (2.0 - omega) / omega, P->Mpre);
+    RT_COUNT(1);
+    const cudaError_t e = cudaStreamSynchronize(st);   // Li is freed on return
+    dev_free(P, Li);
+    RT_TRY_CUDA(e);
+  }
+  RT_TRY_CUDA(cudaGetLastError());
+  P->mpre_kind = base;
+  P->mpre_omega = omega;
+  return RT_OK;
+}
+
+rt_status op_dense_precond_apply(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop,
+                                 int step) {
+  const int n = (int)P->Nop;
+  k_gemv<<<blocks_for((int64_t)n * 32, 256, 8 * P->num_sms), 256, 0, st>>>(P->Mpre, v, n, z, kstop, step);
+  RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
 
 rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaStream_t st, const int* kstop,
                          int step) {

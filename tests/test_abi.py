@@ -54,6 +54,7 @@ int main(void) {
   F(rt_problem_desc, tau); F(rt_problem_desc, phi_center); F(rt_problem_desc, W2);
   F(rt_problem_desc, freq_norm); F(rt_problem_desc, form);
   F(rt_solver_opts, rtol); F(rt_solver_opts, resid_hist); F(rt_solver_opts, hist_cap);
+  F(rt_solver_opts, omega);
   F(rt_solve_info, rel_resid); F(rt_solve_info, t_total_ms);
   return 0;
 }
@@ -114,7 +115,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.rt_problem_destroy(None) == N.RT_OK
     o = N.SolverOpts()
     lib.rt_solver_opts_default(C.byref(o))
-    assert (o.restart, o.maxit, o.precond, o.rtol) == (30, 10000, N.RT_PREC_JACOBI, 1e-8)
+    assert (o.restart, o.maxit, o.precond, o.rtol, o.omega) == (30, 10000, N.RT_PREC_JACOBI, 1e-8, 1.0)
     info = N.SolveInfo()
     assert lib.rt_solve_gmres(None, C.byref(o), None, None, C.byref(info), None) == N.RT_EINVAL
     so = N.ServerOpts()
