@@ -76,6 +76,31 @@ struct GmresDev {
 };
 constexpr size_t kGmresHeader = offsetof(GmresDev, H);
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl may start
+// while the stream's previous kernel drains; before it touches anything that
+// kernel wrote it waits in pdl_wait (griddepcontrol.wait: the previous grid
+// has completed and its writes are visible).  pdl_launch_dependents lets the
+// next such kernel start; a kernel that never calls it releases its
+// dependents as its CTAs exit.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// launch as a programmatic dependent of the stream's previous kernel
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // transposing warp reduction of four FP64 values (6 additions a lane instead
 // of 20): lane l gets the warp sum of s[2*((l>>4)&1) + ((l>>3)&1)], so lanes
 // 0, 8, 16 and 24 hold the sums of s[0], s[1], s[2] and s[3]; fixed order

@@ -244,12 +244,15 @@ __global__ void __launch_bounds__(kVecThreads) k_norm_out(const double* __restri
 // transposing warp reduction of the four accumulators (6 FP64 additions per
 // thread instead of 20).
 constexpr int kB = kGramB;
+// shape of the block-pass kernels: one wave of kMgsCtasPerSm CTAs of
+// kMgsThreads per SM (64 registers a thread)
+constexpr int kMgsThreads = 512, kMgsCtasPerSm = 2;
 
 // block sums of s[0..kB-1] in a fixed order; sum k < n goes to
-// out[k * gridDim.x + blockIdx.x].  Launch with kVecThreads threads.
+// out[k * gridDim.x + blockIdx.x].  Launch with kMgsThreads threads.
 __device__ __forceinline__ void block_sum4_out(const double* s, int n, double* __restrict__ out) {
-  constexpr int NW = kVecThreads / 32;
-  static_assert(kB == 4 && kB * NW <= 64 && (NW & (NW - 1)) == 0, "reduction layout");
+  constexpr int NW = kMgsThreads / 32;
+  static_assert(kB == 4 && kB * NW <= 128 && (NW & (NW - 1)) == 0, "reduction layout");
   __shared__ double red[kB][NW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double t = warp_sum4(s);
@@ -280,9 +283,8 @@ __device__ __forceinline__ void sum_sets(const double* __restrict__ part, int G,
 // first element, the Gram entries), then waits in griddepcontrol.wait until
 // that grid has finished and its writes are visible.  The gate counter is
 // written only by the scaling kernel of the step before, which completed
-// before the operator apply between them started.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// before the operator apply between them started (the apply's kernels are
+// ordinary launches: as programmatic dependents they measured slower).
 
 // Each pass sweeps the vectors in the opposite direction to the pass before
 // (rev): it starts on the elements the previous pass touched last, which are
@@ -295,7 +297,7 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 
 // first kernel of Arnoldi step j: partial dots <w, v_k>, k < NK
 template <int NK>
-__global__ void __launch_bounds__(kVecThreads, 2) k_bdot(const double* __restrict__ w, const double* __restrict__ V,
+__global__ void __launch_bounds__(kMgsThreads, kMgsCtasPerSm) k_bdot(const double* __restrict__ w, const double* __restrict__ V,
                                                         int64_t N, double* __restrict__ part_out, int j, int rev,
                                                         const int* kstop) {
   constexpr int nk = NK;
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_bdot(const double* __restric
 // block) ||w||^2 and the Gram dots <w, v_{i0+k}>, k < ng (= NB when v_{j+1}
 // shares the block, else 0)
 template <int NB, int NN>
-__global__ void __launch_bounds__(kVecThreads, 2) k_bmgs(double* __restrict__ w, const double* __restrict__ V,
+__global__ void __launch_bounds__(kMgsThreads, kMgsCtasPerSm) k_bmgs(double* __restrict__ w, const double* __restrict__ V,
                                                         int64_t N, int i0, const double* __restrict__ part_in,
                                                         double* __restrict__ part_out, double* __restrict__ hcol,
                                                         const double* __restrict__ gram, int j, int rev,
@@ -478,8 +480,8 @@ __global__ void __launch_bounds__(kVecThreads, 3) k_bscale(const double* __restr
 
 // the grid of the block-MGS passes: one CTA per resident slot
 inline int mgs_grid(const Problem* P) {
-  int64_t g = (P->Nop + kVecThreads - 1) / kVecThreads;
-  const int cap = std::min(2 * P->num_sms, kMaxPartials);
+  int64_t g = (P->Nop + kMgsThreads - 1) / kMgsThreads;
+  const int cap = std::min(kMgsCtasPerSm * P->num_sms, kMaxPartials);
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
@@ -927,21 +929,6 @@ static rt_status add_precond(Problem* P, double* x, double* t, int precond, doub
   return RT_OK;
 }
 
-// launch as a programmatic dependent of the stream's previous kernel
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kVecThreads);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
 
 // One block-MGS Arnoldi step on w against V[0..j] (see k_bmgs): h_0..h_j
 // and h_{j+1} = ||w|| to hcol, v_{j+1} to V, the Gram row j+1 to gram; with
@@ -958,7 +945,7 @@ static rt_status enqueue_bmgs(Problem* P, double* V, double* w, int j, double* h
   static const BmgsFn last[kGramB] = {k_bmgs<1, 0>, k_bmgs<2, 0>, k_bmgs<3, 0>, k_bmgs<4, 0>};
   static_assert(kGramB == 4, "kernel tables");
   int pb = 0, rev = 0;
-  RT_TRY_CUDA(launch_pdl(bdot[std::min(kGramB, j + 1) - 1], Gm, st, (const double*)w, (const double*)V, N,
+  RT_TRY_CUDA(launch_pdl(bdot[std::min(kGramB, j + 1) - 1], Gm, kMgsThreads, st, (const double*)w, (const double*)V, N,
                          bpartb(P, 0), j, rev, kstop)); RT_COUNT(1);
   int ng = 0;
   for (int i0 = 0; i0 <= j; i0 += kGramB) {
@@ -966,13 +953,13 @@ static rt_status enqueue_bmgs(Problem* P, double* V, double* w, int j, double* h
     const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
     if (nn == 0) ng = nb < kGramB ? nb : 0;
     rev ^= 1;
-    RT_TRY_CUDA(launch_pdl(nn ? pass[nn - 1] : last[nb - 1], Gm, st, w, (const double*)V, N, i0,
+    RT_TRY_CUDA(launch_pdl(nn ? pass[nn - 1] : last[nb - 1], Gm, kMgsThreads, st, w, (const double*)V, N, i0,
                            (const double*)bpartb(P, pb), bpartb(P, pb ^ 1), hcol, (const double*)gram, j, rev,
                            kstop)); RT_COUNT(1);
     pb ^= 1;
   }
   rev ^= 1;
-  RT_TRY_CUDA(launch_pdl(k_bscale, Gm + 1, st, (const double*)w, V, N, (const double*)bpartb(P, pb), Gm, ng,
+  RT_TRY_CUDA(launch_pdl(k_bscale, std::min(Gm, 2 * P->num_sms) + 1, kVecThreads, st, (const double*)w, V, N, (const double*)bpartb(P, pb), Gm, ng,
                          hcol, gram, gm, m, j, hist, hcap, rev, kstop)); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
