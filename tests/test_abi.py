@@ -125,4 +125,6 @@ def test_null_arguments_are_rejected(lib):
     h = C.c_void_p()
     assert lib.rt_server_create(C.byref(so), C.byref(h)) == N.RT_EINVAL and not h.value
     assert lib.rt_poll(None, 1, None, None) == N.RT_EINVAL
+    assert lib.rt_precond_stationary(None, N.RT_PREC_SOR, 1.0, None, None, None) == N.RT_EINVAL
+    assert lib.rt_precond_local_lambda(None, None, None, None) == N.RT_EINVAL
     assert lib.rt_server_destroy(None) == N.RT_OK
