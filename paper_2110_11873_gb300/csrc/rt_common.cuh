@@ -166,6 +166,7 @@ struct Problem {
   double mpre_omega = 0.0;
   double* Bmap = nullptr;  // [2*ngroups][ntile64-1][32] FP64 formal solver: offsets of the tile maps
   double* wray = nullptr;  // [3][nray] hat-w_m * hat-w_p, the same times T201_m, times T202_m
+  double* wjac = nullptr;  // [3][Ns][nray] wray times the Jacobi inverse diagonal (I, I, Q), once a solver set it
   double* wI2 = nullptr;   // [Nnu] spectral weights hat-w_p
   double* wQ2 = nullptr;   // [Nmu] angular weights hat-w_m = w_m / 2
   double* t201d = nullptr; // [Nmu]
@@ -221,6 +222,9 @@ rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cud
 rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop = nullptr,
                         int step = 0);
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st);
+// the Jacobi-mode quadrature weights from P->dinv (I-form; the apply in
+// Jacobi mode uses them once they exist)
+rt_status op_jacobi_weights(Problem* P, cudaStream_t st);
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st);
 void release_graphs(Problem* P);
 // the formal solver alone (Eq. 9-10): I = Lambda S with the given inflow at

@@ -124,7 +124,10 @@ __device__ __forceinline__ void moments_height(
 // then S as in moments_height.  Every FP64 operation is useful work: no
 // lane idles on a short row and there is one reduction per height (the FP64
 // pipe bounds this kernel).  Any block size that is a multiple of 32.
-template <int MODE>
+// WJ (Jacobi mode): wray holds per-element weights [3][Ns][nray], the
+// per-ray weights times the inverse diagonal of the element (I, I, Q), so
+// the scaling of x costs no operation here.
+template <int MODE, bool WJ = false>
 __device__ __forceinline__ void moments_flat64(const double* __restrict__ x, const double* __restrict__ dinv,
                                                const double* __restrict__ wray, const double* __restrict__ t201,
                                                const double* __restrict__ t202, const double* __restrict__ Minv,
@@ -132,19 +135,23 @@ __device__ __forceinline__ void moments_flat64(const double* __restrict__ x, con
                                                double* __restrict__ S, int k) {
   const double* __restrict__ xI = x + (int64_t)k * nray;
   const double* __restrict__ xQ = x + ((int64_t)Ns + k) * nray;
-  const double* __restrict__ dI = MODE == KM_JACOBI ? dinv + (int64_t)k * nray : nullptr;
-  const double* __restrict__ dQ = MODE == KM_JACOBI ? dinv + ((int64_t)Ns + k) * nray : nullptr;
+  const double* __restrict__ dI = MODE == KM_JACOBI && !WJ ? dinv + (int64_t)k * nray : nullptr;
+  const double* __restrict__ dQ = MODE == KM_JACOBI && !WJ ? dinv + ((int64_t)Ns + k) * nray : nullptr;
+  const int64_t plane = (int64_t)Ns * nray;
+  const double* __restrict__ w0 = WJ ? wray + (int64_t)k * nray : wray;
+  const double* __restrict__ w1 = WJ ? w0 + plane : wray + nray;
+  const double* __restrict__ w2 = WJ ? w0 + 2 * plane : wray + 2 * nray;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
 #pragma unroll 2
   for (int64_t r = threadIdx.x; r < nray; r += blockDim.x) {
     double vI = xI[r], vQ = xQ[r];
-    if (MODE == KM_JACOBI) {
+    if (MODE == KM_JACOBI && !WJ) {
       vI *= dI[r];
       vQ *= dQ[r];
     }
-    a0 = fma(wray[r], vI, a0);
-    a1 = fma(wray[nray + r], vI, a1);
-    a2 = fma(wray[2 * nray + r], vQ, a2);
+    a0 = fma(w0[r], vI, a0);
+    a1 = fma(w1[r], vI, a1);
+    a2 = fma(w2[r], vQ, a2);
   }
   a1 += a2;
   // transposed warp sum: lanes 0-15 get the sum of a0, lanes 16-31 of a1

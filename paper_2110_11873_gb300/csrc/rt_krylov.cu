@@ -1188,6 +1188,7 @@ static rt_status prepare(Problem* P, const rt_solver_opts* o, int restart, cudaS
   RT_TRY(ensure_workspace(P, restart, st));
   if (o->resid_hist && o->hist_cap > 0) RT_TRY(ensure_hist(P, o->hist_cap));
   if (o->precond == RT_PREC_JACOBI || o->precond == RT_PREC_JACOBI_LEFT) RT_TRY(op_jacobi_inv(P, P->dinv, st));
+  if (o->precond == RT_PREC_JACOBI) RT_TRY(op_jacobi_weights(P, st));
   if (prec_dense(o->precond)) RT_TRY(op_dense_precond_build(P, o->precond, o->omega, st));
   return RT_OK;
 }

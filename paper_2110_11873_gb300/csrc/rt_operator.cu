@@ -214,15 +214,29 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(
   moments_height<TI, TC, MODE>(x, dinv, wnu, wmu, t201, t202, Minv, Ns, Nmu, Nnu, xi, xiW2, S, blockIdx.x);
 }
 
-// FP64 quadrature, one CTA per height (flat over the rays)
+// FP64 quadrature, one CTA per height (flat over the rays); WJ: Jacobi mode
+// with the per-element weights of k_jacobi_weights in place of wray
 constexpr int kMom64Threads = 512;
-template <int MODE>
+template <int MODE, bool WJ = false>
 __global__ void __launch_bounds__(kMom64Threads) k_moments64(
     const double* __restrict__ x, const double* __restrict__ dinv, const double* __restrict__ wray,
     const double* __restrict__ t201, const double* __restrict__ t202, const double* __restrict__ Minv, int Ns,
     int Nmu, int64_t nray, double xi, double xiW2, double* __restrict__ S, const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
-  moments_flat64<MODE>(x, dinv, wray, t201, t202, Minv, Ns, Nmu, nray, xi, xiW2, S, blockIdx.x);
+  moments_flat64<MODE, WJ>(x, dinv, wray, t201, t202, Minv, Ns, Nmu, nray, xi, xiW2, S, blockIdx.x);
+}
+
+// wjac[q][k][r] = wray[q][r] * D^-1 of element (k, r): Stokes I for q = 0, 1
+// and Q for q = 2 (the quadrature weights of the Jacobi-mode apply)
+__global__ void k_jacobi_weights(const double* __restrict__ wray, const double* __restrict__ dinv, int Ns,
+                                 int64_t nray, double* __restrict__ wjac) {
+  const int64_t plane = (int64_t)Ns * nray;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i % nray;
+    wjac[i] = wray[r] * dinv[i];
+    wjac[plane + i] = wray[nray + r] * dinv[i];
+    wjac[2 * plane + i] = wray[2 * nray + r] * dinv[plane + i];
+  }
 }
 
 // grid: NSPLIT * ngroups CTAs (ray group g, and with NSPLIT = 2 the Stokes
@@ -326,7 +340,7 @@ void free_device(Problem* P) {
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
                   P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf, P->cg,
-                  P->Etile, P->Bmap, P->Asig, P->Mpre, P->Mtri, P->Mscr};
+                  P->Etile, P->Bmap, P->Asig, P->Mpre, P->Mtri, P->Mscr, P->wjac};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
@@ -338,7 +352,7 @@ void free_device(Problem* P) {
   P->dev_err = nullptr;
   P->qw = P->St = P->qpart = nullptr;
   P->Mdiag = P->Ibuf = P->cg = P->Etile = P->Bmap = nullptr;
-  P->Asig = P->Mpre = P->Mtri = P->Mscr = nullptr;
+  P->Asig = P->Mpre = P->Mtri = P->Mscr = P->wjac = nullptr;
   P->mpre_kind = 0;
   P->staged = 0;
 }
@@ -635,8 +649,13 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
       launch_formal64<KM_PLAIN>(P, x, y, P->S, st, kstop, step);
       break;
     case AM_JACOBI:
-      k_moments64<KM_JACOBI><<<Ns, kMom64Threads, 0, st>>>(x, P->dinv, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu,
-                                                           P->nray, P->xi, xiW2, P->S, kstop, step); RT_COUNT(1);
+      if (P->wjac)
+        k_moments64<KM_JACOBI, true><<<Ns, kMom64Threads, 0, st>>>(x, nullptr, P->wjac, P->t201d, P->t202d, nullptr,
+                                                                   Ns, Nmu, P->nray, P->xi, xiW2, P->S, kstop, step);
+      else
+        k_moments64<KM_JACOBI><<<Ns, kMom64Threads, 0, st>>>(x, P->dinv, P->wray, P->t201d, P->t202d, nullptr, Ns,
+                                                             Nmu, P->nray, P->xi, xiW2, P->S, kstop, step);
+      RT_COUNT(1);
       launch_formal64<KM_JACOBI>(P, x, y, P->S, st, kstop, step);
       break;
     case AM_LOCAL_LAMBDA:
@@ -711,6 +730,16 @@ rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st) {
   if (P->form == RT_FORM_SIGMA) return op_jacobi_sigma(P, dinv, 1, st);
   k_jacobi<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d,
                                                                  P->Ns, P->Nmu, P->Nnu, P->xi, P->W2, 1, dinv);
+  RT_COUNT(1);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status op_jacobi_weights(Problem* P, cudaStream_t st) {
+  if (P->form != RT_FORM_I) return RT_OK;
+  const int64_t plane = (int64_t)P->Ns * P->nray;
+  if (!P->wjac) RT_TRY_CUDA(dev_alloc(P, (void**)&P->wjac, 3 * (size_t)plane * sizeof(double)));
+  k_jacobi_weights<<<grid_for(plane, 256, 8 * P->num_sms), 256, 0, st>>>(P->wray, P->dinv, P->Ns, P->nray, P->wjac);
   RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
