@@ -101,6 +101,88 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cud
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// sum of G partials in a fixed order (lane-strided, then a fixed shuffle
+// tree); every lane of the calling warp gets the result
+__device__ __forceinline__ double partials_sum_warp(const double* __restrict__ part, int G) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < G; i += 32) s += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Givens rotations on column j of the Hessenberg matrix and the residual
+// estimate of GMRES (one thread)
+__device__ inline void givens_step(GmresDev* gm, int m, int j, double* hist, int hist_cap) {
+  double* Hc = gm->H + j * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double t = gm->cs[i] * Hc[i] + gm->sn[i] * Hc[i + 1];
+    Hc[i + 1] = -gm->sn[i] * Hc[i] + gm->cs[i] * Hc[i + 1];
+    Hc[i] = t;
+  }
+  const double a = Hc[j], b = Hc[j + 1];
+  const double hn = hypot(a, b);
+  if (hn == 0.0) {
+    gm->breakdown = 1;
+    gm->kstop = j;
+    return;
+  }
+  const double c = a / hn, s = b / hn;
+  gm->cs[j] = c;
+  gm->sn[j] = s;
+  Hc[j] = hn;
+  Hc[j + 1] = 0.0;
+  gm->g[j + 1] = -s * gm->g[j];
+  gm->g[j] = c * gm->g[j];
+  gm->iters += 1;
+  gm->kdone = j + 1;
+  const double est = fabs(gm->g[j + 1]) / gm->bnorm;
+  if (hist && gm->hist_len < hist_cap) hist[gm->hist_len++] = est;
+  if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
+}
+
+// End of Arnoldi step j from the last block pass's partials (Gp per set; set
+// 0: ||w||^2, set 1+k: <w, v_{i0+k}>, k < ng): h_{j+1,j} = ||w|| to
+// hcol[j+1], the Gram row j+1 (<v_{j+1}, v_{j+1-d}>, d = ng - k), and with
+// gm set the Givens rotations of column j.  One CTA of at least 32*(1+ng)
+// threads; thread 0 does the scalar work.
+__device__ inline void arnoldi_fold(const double* __restrict__ part, int Gp, int ng, double* __restrict__ hcol,
+                                    double* __restrict__ gram, GmresDev* gm, int m, int j, double* hist,
+                                    int hist_cap) {
+  __shared__ double sets[kGramB];
+  const int warp = threadIdx.x >> 5;
+  if (warp <= ng) {
+    const double s = partials_sum_warp(part + (size_t)warp * Gp, Gp);
+    if ((threadIdx.x & 31) == 0) sets[warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(sets[0]);
+    const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+    hcol[j + 1] = hn;
+    for (int d = 1; d <= ng; ++d) gram[(j + 1) * kGramB + d] = sets[1 + ng - d] * inv;
+    if (gm) givens_step(gm, m, j, hist, hist_cap);
+  }
+}
+
+// 1 / ||w|| from set 0 of the same partials, in the same summation order as
+// arnoldi_fold (0 for a zero norm), broadcast to the CTA
+__device__ inline double arnoldi_inv_norm(const double* __restrict__ part, int Gp) {
+  __shared__ double inv_s;
+  if (threadIdx.x < 32) {
+    const double s = partials_sum_warp(part, Gp);
+    if (threadIdx.x == 0) {
+      const double h = sqrt(s);
+      inv_s = h > 0.0 ? 1.0 / h : 0.0;
+    }
+  }
+  __syncthreads();
+  const double inv = inv_s;
+  __syncthreads();
+  return inv;
+}
+
 // transposing warp reduction of four FP64 values (6 additions a lane instead
 // of 20): lane l gets the warp sum of s[2*((l>>4)&1) + ((l>>3)&1)], so lanes
 // 0, 8, 16 and 24 hold the sums of s[0], s[1], s[2] and s[3]; fixed order
@@ -214,8 +296,24 @@ struct Problem {
 enum ApplyMode { AM_PLAIN = 0, AM_JACOBI = 1, AM_LOCAL_LAMBDA = 2 };
 // kstop/step: inside a captured GMRES cycle the kernels of Arnoldi step
 // `step` return at once when step >= *kstop (NULL: always run)
+// GMRES, FP64 I-form: the normalisation that ends Arnoldi step jprev done by
+// the apply of step jprev + 1.  Its quadrature kernel reads u (the last block
+// pass's w), writes x = u / ||u|| as it goes, and one CTA folds h and the
+// Gram row and applies the Givens rotations of column jprev (arnoldi_fold).
+struct NormIn {
+  const double* u;
+  const double* part;   // the last pass's partials: set 0 ||u||^2, sets 1..ng the Gram dots
+  int Gp, ng;
+  double* hcol;         // column jprev of the Hessenberg matrix
+  double* gram;
+  GmresDev* gm;
+  int m, jprev;
+  double* hist;
+  int hist_cap;
+  const int* kstop;     // the kernel runs while jprev < *kstop
+};
 rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st,
-                     const int* kstop = nullptr, int step = 0);
+                     const int* kstop = nullptr, int step = 0, const NormIn* nin = nullptr);
 rt_status op_apply32(Problem* P, const float* x, float* y, int mode, cudaStream_t st);
 rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cudaStream_t st,
                            const int* kstop = nullptr, int step = 0);

@@ -126,13 +126,15 @@ __device__ __forceinline__ void moments_height(
 // pipe bounds this kernel).  Any block size that is a multiple of 32.
 // WJ (Jacobi mode): wray holds per-element weights [3][Ns][nray], the
 // per-ray weights times the inverse diagonal of the element (I, I, Q), so
-// the scaling of x costs no operation here.
-template <int MODE, bool WJ = false>
+// the scaling of x costs no operation here.  NORM: the input is x * inv,
+// also written to xout (the GMRES normalisation of NormIn).
+template <int MODE, bool WJ = false, bool NORM = false>
 __device__ __forceinline__ void moments_flat64(const double* __restrict__ x, const double* __restrict__ dinv,
                                                const double* __restrict__ wray, const double* __restrict__ t201,
                                                const double* __restrict__ t202, const double* __restrict__ Minv,
                                                int Ns, int Nmu, int64_t nray, double xi, double xiW2,
-                                               double* __restrict__ S, int k) {
+                                               double* __restrict__ S, int k, double inv = 1.0,
+                                               double* __restrict__ xout = nullptr) {
   const double* __restrict__ xI = x + (int64_t)k * nray;
   const double* __restrict__ xQ = x + ((int64_t)Ns + k) * nray;
   const double* __restrict__ dI = MODE == KM_JACOBI && !WJ ? dinv + (int64_t)k * nray : nullptr;
@@ -145,6 +147,12 @@ __device__ __forceinline__ void moments_flat64(const double* __restrict__ x, con
 #pragma unroll 2
   for (int64_t r = threadIdx.x; r < nray; r += blockDim.x) {
     double vI = xI[r], vQ = xQ[r];
+    if (NORM) {
+      vI *= inv;
+      vQ *= inv;
+      xout[(int64_t)k * nray + r] = vI;
+      xout[((int64_t)Ns + k) * nray + r] = vQ;
+    }
     if (MODE == KM_JACOBI && !WJ) {
       vI *= dI[r];
       vQ *= dQ[r];

@@ -57,10 +57,7 @@ __device__ __forceinline__ double block_sum(double v) {
 // sum of G partials in a fixed order (lane-strided, then a fixed shuffle tree);
 // every thread of the calling warp gets the result
 __device__ __forceinline__ double sum_partials_warp(const double* __restrict__ part, int G) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int i = lane; i < G; i += 32) s += part[i];
-  return wsum(s);
+  return partials_sum_warp(part, G);
 }
 
 // broadcast of sum_partials to the whole block
@@ -399,36 +396,6 @@ __global__ void __launch_bounds__(kMgsThreads, kMgsCtasPerSm) k_bmgs(double* __r
   block_sum4_out(s, nn ? nn : 1 + ng, part_out);
 }
 
-// Givens rotations on column j of the Hessenberg matrix and the residual
-// estimate (one thread)
-__device__ void givens_step(GmresDev* gm, int m, int j, double* hist, int hist_cap) {
-  double* Hc = gm->H + j * (m + 1);
-  for (int i = 0; i < j; ++i) {
-    const double t = gm->cs[i] * Hc[i] + gm->sn[i] * Hc[i + 1];
-    Hc[i + 1] = -gm->sn[i] * Hc[i] + gm->cs[i] * Hc[i + 1];
-    Hc[i] = t;
-  }
-  const double a = Hc[j], b = Hc[j + 1];
-  const double hn = hypot(a, b);
-  if (hn == 0.0) {
-    gm->breakdown = 1;
-    gm->kstop = j;
-    return;
-  }
-  const double c = a / hn, s = b / hn;
-  gm->cs[j] = c;
-  gm->sn[j] = s;
-  Hc[j] = hn;
-  Hc[j + 1] = 0.0;
-  gm->g[j + 1] = -s * gm->g[j];
-  gm->g[j] = c * gm->g[j];
-  gm->iters += 1;
-  gm->kdone = j + 1;
-  const double est = fabs(gm->g[j + 1]) / gm->bnorm;
-  if (hist && gm->hist_len < hist_cap) hist[gm->hist_len++] = est;
-  if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
-}
-
 // v_{j+1} = w / ||w|| by blocks 1..gridDim.x-1 (||w||^2 is set 0 of the last
 // pass's partials, over Gp blocks).  Block 0, scheduled first, writes
 // h_{j+1} = ||w|| to hcol[j+1] and the Gram row j+1: <v_{j+1}, v_{j+1-d}> =
@@ -445,15 +412,7 @@ __global__ void __launch_bounds__(kVecThreads, 3) k_bscale(const double* __restr
   if (kstop && j >= *kstop) return;
   pdl_wait();
   if (blockIdx.x == 0) {
-    __shared__ double sets[kB];
-    sum_sets(part_in, Gp, 1 + ng, sets);
-    if (threadIdx.x == 0) {
-      const double hn = sqrt(sets[0]);
-      const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-      hcol[j + 1] = hn;
-      for (int d = 1; d <= ng; ++d) gram[(j + 1) * kB + d] = sets[1 + ng - d] * inv;
-      if (gm) givens_step(gm, m, j, hist, hist_cap);
-    }
+    arnoldi_fold(part_in, Gp, ng, hcol, gram, gm, m, j, hist, hist_cap);
     return;
   }
   double* __restrict__ vo = V + (size_t)(j + 1) * N;
@@ -476,6 +435,15 @@ __global__ void __launch_bounds__(kVecThreads, 3) k_bscale(const double* __restr
     const int64_t e = rev ? N - 1 - i : i;
     vo[e] = w[e] * inv;
   }
+}
+
+// the end of the last Arnoldi step of a cycle whose normalisations are done
+// by the next step's apply (NormIn): the fold and the Givens rotations only
+__global__ void k_arnoldi_tail(const double* __restrict__ part, int Gp, int ng, double* __restrict__ hcol,
+                               double* __restrict__ gram, GmresDev* gm, int m, int j, double* hist, int hist_cap,
+                               const int* kstop) {
+  if (kstop && j >= *kstop) return;
+  arnoldi_fold(part, Gp, ng, hcol, gram, gm, m, j, hist, hist_cap);
 }
 
 // the grid of the block-MGS passes: one CTA per resident slot
@@ -893,12 +861,14 @@ static rt_status left_apply(Problem* P, int pc, const double* x, double* y, cuda
 }
 
 // A M^{-1} v with the chosen preconditioner and operator precision
+// (nin: GMRES, FP64 I-form; the apply's input v is formed from nin->u, see
+// NormIn)
 static rt_status apply_prec(Problem* P, const double* v, double* y, int precond, int fp32, cudaStream_t st,
-                            const int* kstop = nullptr, int step = 0) {
+                            const int* kstop = nullptr, int step = 0, const NormIn* nin = nullptr) {
   if (prec_left(precond)) {
     // M A v: the FP64 apply into a scratch vector, then M
     double* t = precond == RT_PREC_JACOBI_LEFT ? P->work + (size_t)6 * P->Nop : P->Mscr + P->Nop;
-    RT_TRY(op_apply64(P, v, t, AM_PLAIN, st, kstop, step));
+    RT_TRY(op_apply64(P, v, t, AM_PLAIN, st, kstop, step, nin));
     return left_apply(P, precond, t, y, st, kstop, step);
   }
   if (prec_dense(precond)) {   // right SOR / SSOR: A (P^-1 v)
@@ -907,7 +877,7 @@ static rt_status apply_prec(Problem* P, const double* v, double* y, int precond,
   }
   const int mode = precond == RT_PREC_JACOBI ? AM_JACOBI : precond == RT_PREC_LOCAL_LAMBDA ? AM_LOCAL_LAMBDA : AM_PLAIN;
   if (fp32) return op_apply32_f64io(P, v, y, mode, st, kstop, step);
-  return op_apply64(P, v, y, mode, st, kstop, step);
+  return op_apply64(P, v, y, mode, st, kstop, step, nin);
 }
 
 // x += M^{-1} t  (t may be overwritten)
@@ -933,8 +903,12 @@ static rt_status add_precond(Problem* P, double* x, double* t, int precond, doub
 // One block-MGS Arnoldi step on w against V[0..j] (see k_bmgs): h_0..h_j
 // and h_{j+1} = ||w|| to hcol, v_{j+1} to V, the Gram row j+1 to gram; with
 // gm set, the Givens rotations of column j (GMRES).
+// scale == false: the normalisation and the fold are left to the next apply
+// (NormIn); *pb_out and *ng_out then name the last pass's partial buffer and
+// Gram-set count.
 static rt_status enqueue_bmgs(Problem* P, double* V, double* w, int j, double* hcol, double* gram, GmresDev* gm,
-                              int m, double* hist, int hcap, const int* kstop, cudaStream_t st) {
+                              int m, double* hist, int hcap, const int* kstop, cudaStream_t st, bool scale = true,
+                              int* pb_out = nullptr, int* ng_out = nullptr) {
   const int Gm = mgs_grid(P);
   const int64_t N = P->Nop;
   using BdotFn = void (*)(const double*, const double*, int64_t, double*, int, int, const int*);
@@ -957,6 +931,12 @@ static rt_status enqueue_bmgs(Problem* P, double* V, double* w, int j, double* h
                            (const double*)bpartb(P, pb), bpartb(P, pb ^ 1), hcol, (const double*)gram, j, rev,
                            kstop)); RT_COUNT(1);
     pb ^= 1;
+  }
+  if (pb_out) *pb_out = pb;
+  if (ng_out) *ng_out = ng;
+  if (!scale) {
+    RT_TRY_CUDA(cudaGetLastError());
+    return RT_OK;
   }
   rev ^= 1;
   RT_TRY_CUDA(launch_pdl(k_bscale, std::min(Gm, 2 * P->num_sms) + 1, kVecThreads, st, (const double*)w, V, N, (const double*)bpartb(P, pb), Gm, ng,
@@ -1030,13 +1010,28 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
   double* w = wk(P, 3);
   double* hist = P->hist;
   const int hcap = P->hist_cap_dev;
+  // FP64 I-form: the normalisation of v_{j+1} and the Givens rotations of
+  // column j run inside the next step's first operator kernel (NormIn)
+  const bool fuse = !fp32 && P->form == RT_FORM_I && !prec_dense(precond);
+  int pb = 0, ng = 0;
   for (int j = 0; j < m; ++j) {
     double* vj = P->V + (size_t)j * N;
-    RT_TRY(apply_prec(P, vj, w, precond, fp32, st, kstop, j));
+    if (fuse && j > 0) {
+      const NormIn nin{w, bpartb(P, pb), mgs_grid(P), ng, &gm->H[(j - 1) * (m + 1)], gm->gram, gm, m, j - 1, hist,
+                       hcap, kstop};
+      RT_TRY(apply_prec(P, vj, w, precond, fp32, st, kstop, j, &nin));
+    } else {
+      RT_TRY(apply_prec(P, vj, w, precond, fp32, st, kstop, j));
+    }
     // block MGS: dots with the first block, one pass per block of kGramB
     // basis vectors (the last with ||w|| and the Gram dots of v_{j+1}), then
-    // the normalisation with the Givens rotations of column j
-    RT_TRY(enqueue_bmgs(P, P->V, w, j, &gm->H[j * (m + 1)], gm->gram, gm, m, hist, hcap, kstop, st));
+    // (unless fused) the normalisation with the Givens rotations of column j
+    RT_TRY(enqueue_bmgs(P, P->V, w, j, &gm->H[j * (m + 1)], gm->gram, gm, m, hist, hcap, kstop, st, !fuse, &pb,
+                        &ng));
+  }
+  if (fuse) {
+    k_arnoldi_tail<<<1, 32 * kGramB, 0, st>>>(bpartb(P, pb), mgs_grid(P), ng, &gm->H[(m - 1) * (m + 1)], gm->gram,
+                                              gm, m, m - 1, hist, hcap, kstop); RT_COUNT(1);
   }
   RT_TRY_CUDA(cudaGetLastError());
   k_lsq<<<1, 1, 0, st>>>(gm, m); RT_COUNT(1);

@@ -226,6 +226,24 @@ __global__ void __launch_bounds__(kMom64Threads) k_moments64(
   moments_flat64<MODE, WJ>(x, dinv, wray, t201, t202, Minv, Ns, Nmu, nray, xi, xiW2, S, blockIdx.x);
 }
 
+// GMRES (NormIn): block 0 ends Arnoldi step nin.jprev (fold and Givens
+// rotations); blocks 1..Ns normalise u into x = u / ||u|| while forming the
+// quadrature of x for height blockIdx.x - 1
+template <int MODE, bool WJ>
+__global__ void __launch_bounds__(kMom64Threads) k_moments64_norm(
+    double* __restrict__ x, const double* __restrict__ dinv, const double* __restrict__ wray,
+    const double* __restrict__ t201, const double* __restrict__ t202, const double* __restrict__ Minv, int Ns,
+    int Nmu, int64_t nray, double xi, double xiW2, double* __restrict__ S, const NormIn nin) {
+  if (nin.kstop && nin.jprev >= *nin.kstop) return;
+  if (blockIdx.x == 0) {
+    arnoldi_fold(nin.part, nin.Gp, nin.ng, nin.hcol, nin.gram, nin.gm, nin.m, nin.jprev, nin.hist, nin.hist_cap);
+    return;
+  }
+  const double inv = arnoldi_inv_norm(nin.part, nin.Gp);
+  moments_flat64<MODE, WJ, true>(nin.u, dinv, wray, t201, t202, Minv, Ns, Nmu, nray, xi, xiW2, S, blockIdx.x - 1,
+                                 inv, x);
+}
+
 // wjac[q][k][r] = wray[q][r] * D^-1 of element (k, r): Stokes I for q = 0, 1
 // and Q for q = 2 (the quadrature weights of the Jacobi-mode apply)
 __global__ void k_jacobi_weights(const double* __restrict__ wray, const double* __restrict__ dinv, int Ns,
@@ -638,10 +656,49 @@ static void launch_formal32(const Problem* P, const TV* x, TV* y, cudaStream_t s
   }
 }
 
-rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st, const int* kstop, int step) {
-  if (P->form == RT_FORM_SIGMA) return op_apply_sigma(P, x, y, mode, st, kstop, step);
+rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st, const int* kstop, int step,
+                     const NormIn* nin) {
+  if (P->form == RT_FORM_SIGMA) {
+    if (nin) {
+      set_error("the fused normalisation needs the I-form");
+      return RT_EINVAL;
+    }
+    return op_apply_sigma(P, x, y, mode, st, kstop, step);
+  }
   const double xiW2 = P->xi * P->W2;
   const int Ns = P->Ns, Nmu = P->Nmu;
+  if (nin) {   // GMRES: x = u / ||u|| formed by the quadrature kernel
+    double* xw = const_cast<double*>(x);
+    switch (mode) {
+      case AM_PLAIN:
+        k_moments64_norm<KM_PLAIN, false><<<Ns + 1, kMom64Threads, 0, st>>>(
+            xw, nullptr, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin);
+        break;
+      case AM_JACOBI:
+        if (P->wjac)
+          k_moments64_norm<KM_JACOBI, true><<<Ns + 1, kMom64Threads, 0, st>>>(
+              xw, nullptr, P->wjac, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin);
+        else
+          k_moments64_norm<KM_JACOBI, false><<<Ns + 1, kMom64Threads, 0, st>>>(
+              xw, P->dinv, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin);
+        break;
+      case AM_LOCAL_LAMBDA:
+        k_moments64_norm<KM_LOCAL_LAMBDA, false><<<Ns + 1, kMom64Threads, 0, st>>>(
+            xw, nullptr, P->wray, P->t201d, P->t202d, P->Minv, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin);
+        break;
+      default:
+        set_error("bad apply mode");
+        return RT_EINVAL;
+    }
+    RT_COUNT(1);
+    switch (mode) {
+      case AM_PLAIN: launch_formal64<KM_PLAIN>(P, x, y, P->S, st, kstop, step); break;
+      case AM_JACOBI: launch_formal64<KM_JACOBI>(P, x, y, P->S, st, kstop, step); break;
+      default: launch_formal64<KM_LOCAL_LAMBDA>(P, x, y, P->S, st, kstop, step); break;
+    }
+    RT_TRY_CUDA(cudaGetLastError());
+    return RT_OK;
+  }
   switch (mode) {
     case AM_PLAIN:
       k_moments64<KM_PLAIN><<<Ns, kMom64Threads, 0, st>>>(x, nullptr, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu,
