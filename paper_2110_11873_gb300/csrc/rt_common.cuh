@@ -247,6 +247,7 @@ struct Problem {
   int mpre_kind = 0;         // RT_PREC_SOR / RT_PREC_SSOR that Mpre holds (0: none)
   double mpre_omega = 0.0;
   double* Bmap = nullptr;  // [2*ngroups][ntile64-1][32] FP64 formal solver: offsets of the tile maps
+  double* Kmap = nullptr;  // [ntile64-1][L+2][nray] weights of the map offsets in the node source values
   double* wray = nullptr;  // [3][nray] hat-w_m * hat-w_p, the same times T201_m, times T202_m
   double* wjac = nullptr;  // [3][Ns][nray] wray times the Jacobi inverse diagonal (I, I, Q), once a solver set it
   double* wI2 = nullptr;   // [Nnu] spectral weights hat-w_p

@@ -5,12 +5,14 @@
 //              reduces the Nmu*Nnu rays of I and Q to J00_k and J20_k with
 //              precomputed per-ray weights (w, w T201, w T202), forms sigma_k
 //              and writes the source functions S_I(k,m), S_Q(k,m).
-//   k_fmap,    FP64 formal solver: the units of the affine scan below --
-//   k_fsweep   (ray group, Stokes parameter, depth tile) -- are one warp and
-//              one CTA each, so they spread evenly over the SMs: k_fmap
-//              composes the B of every tile but the last, k_fsweep chains
-//              the maps of the tiles before its own (the slopes E are a
-//              setup table) and sweeps its tile with the output.
+//   k_fmapdot, FP64 formal solver as an affine scan over depth tiles:
+//   k_fsweep   k_fmapdot forms the offset B of every tile's map but the last
+//              as a dot product of setup weights with the tile's node source
+//              values (one thread per tile and ray); the units of k_fsweep --
+//              (ray group, Stokes parameter, depth tile), one warp and one
+//              CTA each, so they spread evenly over the SMs -- chain the maps
+//              of the tiles before their own (the slopes E are a setup
+//              table) and sweep their tile with the output.
 //   k_formal   formal solver Lambda (Eq. 9-10) along every ray, writing
 //              y_k = z_k - I_k on the fly.  A CTA owns one group of 32 rays of
 //              the same direction sign (so the 32 lanes of a warp read one
@@ -358,7 +360,7 @@ void free_device(Problem* P) {
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
                   P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf, P->cg,
-                  P->Etile, P->Bmap, P->Asig, P->Mpre, P->Mtri, P->Mscr, P->wjac};
+                  P->Etile, P->Bmap, P->Asig, P->Mpre, P->Mtri, P->Mscr, P->wjac, P->Kmap};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
   P->ce = P->ca = P->cb = P->wray = P->wI2 = P->wQ2 = P->t201d = P->t202d = P->Bd = P->Minv = P->S = P->S2 = nullptr;
@@ -369,7 +371,7 @@ void free_device(Problem* P) {
   P->bc = nullptr;
   P->dev_err = nullptr;
   P->qw = P->St = P->qpart = nullptr;
-  P->Mdiag = P->Ibuf = P->cg = P->Etile = P->Bmap = nullptr;
+  P->Mdiag = P->Ibuf = P->cg = P->Etile = P->Bmap = P->Kmap = nullptr;
   P->Asig = P->Mpre = P->Mtri = P->Mscr = P->wjac = nullptr;
   P->mpre_kind = 0;
   P->staged = 0;
@@ -384,11 +386,12 @@ static rt_status upload(Problem* P, T** dst, const std::vector<T>& src, cudaStre
 
 // Depth tiles per ray group.  FP64: the formal solver's warp units spread
 // evenly over the SMs, so an SM carries ceil(units / SMs) of them.  A step
-// costs a unit 3 FP64 operations in the map kernel and 4 in the sweep; an SM
-// retires one FP64 warp operation in about kFp64OpCycles, while one warp
-// alone needs about kFp64StepCycles per step (the dependent chain through I;
-// both measured on GB300).  Each kernel takes the longer of its pipe time
-// and its latency, and T minimises the sum.  FP32: tiles are cheap, so aim
+// costs a sweep unit 4 FP64 operations; an SM retires one FP64 warp
+// operation in about kFp64OpCycles, while one warp alone needs about
+// kFp64StepCycles per step (the dependent chain through I; both measured on
+// GB300), and the sweep takes the longer of the two.  The map offsets cost 2
+// independent FMAs per tile node and ray (pipe time only).  T minimises the
+// sum.  FP32: tiles are cheap, so aim
 // at about 16 warps per SM with tiles of at least 2*kRing steps.
 constexpr double kFp64OpCycles = 20.0, kFp64StepCycles = 600.0;
 static int choose_tiles64(const Problem* P) {
@@ -401,7 +404,8 @@ static int choose_tiles64(const Problem* P) {
   for (int T = 1; T <= kMaxTiles64; ++T) {
     const int L = (P->Ns - 1 + T - 1) / T;
     if (T > 1 && L < 2 * kRing) break;
-    const double cost = L * (kernel(groups * T, 4.0) + (T > 1 ? kernel(groups * (T - 1), 3.0) : 0.0));
+    const double maps = (double)(T - 1) * P->nray * (L + 2) * 2.0 / 32.0 / (double)sms * kFp64OpCycles;
+    const double cost = L * kernel(groups * T, 4.0) + maps;
     if (cost < best_cost * 0.97) {
       best_cost = cost;
       best = T;
@@ -439,21 +443,78 @@ __global__ void k_etile(const double* __restrict__ ce, int Ns, int64_t nray, int
   }
 }
 
-// B of the map of tile t < T-1 (zero inflow), unit u = (g * 2 + s) * (T-1) + t
-template <int FS, int MODE>
-__global__ void __launch_bounds__(32, FS == RT_FS_DELO_PARABOLIC ? 12 : 16) k_fmap(const FormalArgs A, double* __restrict__ Bmap) {
+// Weights of the map offsets.  With zero inflow the tile recurrence
+// I_j = e_j I_{j-1} + alpha_j S_{j-1} + beta_j S_j (+ gamma_j S_{j+1}) ends at
+// B = sum_j P_j (alpha_j S_{j-1} + beta_j S_j + gamma_j S_{j+1}), P_j the
+// product of the e of the tile's later steps, so B is a fixed linear form in
+// the source values at the tile's nodes j0-1 .. j1:
+//     B(t, r, s) = sum_n K[t][n][r] S_s(node j0 - 1 + n, m(r)).
+// k_kmap builds K at setup (one backward pass per tile and ray); the map
+// kernel is then one independent FMA per node instead of a dependent
+// recurrence.  K[t][n][r], n < L + 2.
+__global__ void k_kmap(const double* __restrict__ ce, const double* __restrict__ ca, const double* __restrict__ cb,
+                       const double* __restrict__ cg, int Ns, int64_t nray, int64_t nd, int T,
+                       double* __restrict__ K) {
+  const int L = (Ns - 1 + T - 1) / T;
+  const int64_t n = (int64_t)(T - 1) * nray;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(i / nray);
+    const int64_t r = i % nray;
+    const bool down = r < nd;
+    const int j0 = 1 + t * L, j1 = min(Ns, j0 + L);
+    double* __restrict__ Kt = K + (int64_t)t * (L + 2) * nray + r;
+    for (int q = 0; q < L + 2; ++q) Kt[(int64_t)q * nray] = 0.0;
+    double Pj = 1.0;   // product of e over the steps after j
+    for (int j = j1 - 1; j >= j0; --j) {
+      const int64_t c = (int64_t)(down ? j - 1 : Ns - 1 - j) * nray + r;
+      const int q = j - j0 + 1;   // local index of node j
+      Kt[(int64_t)q * nray] += Pj * cb[c];
+      Kt[(int64_t)(q - 1) * nray] += Pj * ca[c];
+      if (cg) Kt[(int64_t)(q + 1) * nray] += Pj * cg[c];
+      Pj *= ce[c];
+    }
+  }
+}
+
+// the map offsets B of tiles t < T-1 for both Stokes parameters, written as
+// Bmap[g * 2 + s][t][lane] for the sweep kernel.  A CTA takes 32 rays of one
+// tile (x) and splits the tile's nodes over kMapSlices thread rows (y), so
+// many loads are in flight; the rows' partial sums are added in a fixed order.
+constexpr int kMapSlices = 8;
+__global__ void __launch_bounds__(32 * kMapSlices) k_fmapdot(const FormalArgs A, const double* __restrict__ K,
+                                                             double* __restrict__ Bmap) {
   if (A.kstop && A.step >= *A.kstop) return;
-  const int T = A.ntile, L = (A.Ns - 1 + T - 1) / T;
-  const int u = blockIdx.x, lane = threadIdx.x;
-  const int t = u % (T - 1), gs = u / (T - 1);
-  int64_t r;
-  int m;
-  bool down, active;
-  group_ray(A, gs >> 1, lane, r, m, down, active);
-  const int j0 = 1 + t * L, j1 = min(A.Ns, j0 + L);
-  double B[1] = {0.0}, E = 1.0;
-  if (j0 < j1) sweep<double, double, FS, MODE, 2, 1, kRing>(A, gs & 1, down, r, m, active, j0, j1, B, E);
-  Bmap[(size_t)u * 32 + lane] = B[0];
+  const int Ns = A.Ns, T = A.ntile, L = (Ns - 1 + T - 1) / T;
+  const int64_t nray = A.nray;
+  const int t = blockIdx.y;
+  const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const bool valid = r < nray;
+  const int64_t rc = valid ? r : nray - 1;
+  const double* __restrict__ S = reinterpret_cast<const double*>(A.S);
+  const int64_t sQ = (int64_t)Ns * A.Nmu;
+  const bool down = rc < A.nd;
+  const int m = (int)(rc / A.Nnu);
+  const int j0 = 1 + t * L, jend = min(Ns - 1, j0 + L);   // nodes j0-1 .. jend
+  const double* __restrict__ Kt = K + (int64_t)t * (L + 2) * nray + rc;
+  double bI = 0.0, bQ = 0.0;
+  for (int j = j0 - 1 + (int)threadIdx.y; j <= jend; j += kMapSlices) {
+    const double k = Kt[(int64_t)(j - j0 + 1) * nray];
+    const int64_t o = (int64_t)(down ? j : Ns - 1 - j) * A.Nmu + m;
+    bI = fma(k, S[o], bI);
+    bQ = fma(k, S[sQ + o], bQ);
+  }
+  __shared__ double red[2][kMapSlices][32];
+  red[0][threadIdx.y][threadIdx.x] = bI;
+  red[1][threadIdx.y][threadIdx.x] = bQ;
+  __syncthreads();
+  if (threadIdx.y < 2 && valid) {
+    double b = 0.0;
+#pragma unroll
+    for (int y = 0; y < kMapSlices; ++y) b += red[threadIdx.y][y][threadIdx.x];
+    const int64_t rr = down ? r : r - A.nd;
+    const int g = (int)(rr / 32) + (down ? 0 : A.ngd), lane = (int)(rr % 32);
+    Bmap[((size_t)(2 * g + threadIdx.y) * (T - 1) + t) * 32 + lane] = b;
+  }
 }
 
 // tile t of ray group g, Stokes s: inflow from the boundary through the maps
@@ -553,7 +614,15 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   if (P->ntile64 > 1) {   // the FP64 formal solver's tile slopes and map buffer
     const int T = P->ntile64;
     RT_TRY_CUDA(dev_alloc(P, (void**)&P->Etile, (size_t)(T - 1) * nray * sizeof(double)));
-    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Bmap, (size_t)2 * P->ngroups * (T - 1) * 32 * sizeof(double)));
+    const size_t nb = (size_t)2 * P->ngroups * (T - 1) * 32;
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Bmap, nb * sizeof(double)));
+    RT_TRY_CUDA(cudaMemsetAsync(P->Bmap, 0, nb * sizeof(double), st));   // lanes past a direction's last ray
+    const int L = (Ns - 1 + T - 1) / T;
+    const int64_t nk = (int64_t)(T - 1) * (L + 2) * nray;
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Kmap, (size_t)nk * sizeof(double)));
+    k_kmap<<<grid_for((int64_t)(T - 1) * nray, 256, 8 * P->num_sms), 256, 0, st>>>(P->ce, P->ca, P->cb, P->cg, Ns,
+                                                                                    nray, P->nd, T, P->Kmap);
+    RT_COUNT(1);
     k_etile<<<grid_for((int64_t)(T - 1) * nray, 256, 8 * P->num_sms), 256, 0, st>>>(P->ce, Ns, nray, P->nd, T,
                                                                                      P->Etile); RT_COUNT(1);
     RT_TRY_CUDA(cudaGetLastError());
@@ -617,7 +686,8 @@ template <int FS, int MODE>
 static void formal64_units(const Problem* P, const FormalArgs& A, cudaStream_t st) {
   const int T = P->ntile64, groups = 2 * P->ngroups;
   if (T > 1) {
-    k_fmap<FS, MODE><<<groups * (T - 1), 32, 0, st>>>(A, P->Bmap);
+    k_fmapdot<<<dim3((unsigned)((P->nray + 31) / 32), (unsigned)(T - 1)), dim3(32, kMapSlices), 0, st>>>(A, P->Kmap,
+                                                                                                     P->Bmap);
     RT_COUNT(1);
   }
   k_fsweep<FS, MODE><<<groups * T, 32, 0, st>>>(A, P->Bmap, P->Etile);
