@@ -1,16 +1,19 @@
 // Krylov solvers on the device (Sect. 2 of the paper): restarted GMRES(m)
-// with modified Gram-Schmidt Arnoldi and Givens rotations, BiCGSTAB and CGS,
-// all right-preconditioned, plus FP32-operator iterative refinement.
+// with modified Gram-Schmidt Arnoldi (in block form) and Givens rotations,
+// BiCGSTAB, CGS and preconditioned Richardson, plus FP32-operator iterative
+// refinement.
 //
 // Design:
 //  * every reduction is deterministic: a fixed grid writes one partial per
 //    block, and the consumer sums the partials in a fixed order (each block
 //    of the consumer kernel redundantly, so no extra launch is needed);
 //  * all scalars (Hessenberg matrix, rotations, alpha/omega/rho) stay in
-//    device memory and are updated by single-thread kernels, so a whole
-//    GMRES restart cycle (m Arnoldi steps, the least-squares solve, the
-//    update of x and the true residual) is one CUDA graph launch followed by
-//    one host read of the convergence state;
+//    device memory and are updated by one thread -- of a scalar kernel, or
+//    of a dedicated CTA of the kernel that needs them next (the Givens
+//    rotations run in a CTA of the scaling kernel, or of the next step's
+//    quadrature kernel) -- so a whole GMRES restart cycle (m Arnoldi steps,
+//    the least-squares solve, the update of x and the true residual) is one
+//    CUDA graph launch followed by one host read of the convergence state;
 //  * a step index baked into each kernel of the cycle graph is compared with
 //    the device counter `kstop`: once the residual estimate passes the
 //    tolerance the remaining kernels of the cycle return at once.
