@@ -774,12 +774,19 @@ rt_status autotune_grids(Server* S, int resident) {
     }
     *grid = pick;
   };
-  const int gs[] = {4, 8, 16}, hs[] = {2, 4, 8}, vs[] = {2, 4, 8};
+  const int gs[] = {4, 8, 16}, hs[] = {2, 4, 8}, vs[] = {4, 8, 16};
   auto apply = [&] { enqueue_apply(S, st, 0, VW, mode, fp32, 0); RT_COUNT(fp32 ? 4 : 2); };
   tune(&S->grid_g, gs, apply);
   tune(&S->grid_h, hs, apply);
+  // the vector grid on the kernel that dominates the cycle: a full block
+  // pass (4 updates, 4 look-ahead dots) of Arnoldi step 7; it writes only
+  // w, one partial buffer and rows 0-3 of Hessenberg column 7, all of which
+  // step 7 of the cycle recomputes before reading them
   tune(&S->grid_v, vs, [&] {
-    kb_bdot<1><<<S->grid_v, kBT, 0, st>>>(S->d_insts, S->d_wl_c, S->d_counts, 0);
+    if (S->opts.restart >= 2 * kGramB)
+      kb_pass_fn[kGramB - 1]<<<S->grid_v, kBT, 0, st>>>(S->d_insts, S->d_wl_c, S->d_counts, 2 * kGramB - 1, 0, 0);
+    else
+      kb_bdot<1><<<S->grid_v, kBT, 0, st>>>(S->d_insts, S->d_wl_c, S->d_counts, 0);
     RT_COUNT(1);
   });
   cudaEventDestroy(e0);
