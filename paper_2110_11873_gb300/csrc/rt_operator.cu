@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(kMom64Threads) k_moments64(
 }
 
 // GMRES (NormIn): block 0 ends Arnoldi step nin.jprev (fold and Givens
-// rotations); blocks 1..Ns normalise u into x = u / ||u|| while forming the
-// quadrature of x for height blockIdx.x - 1
+// rotations, Sect. 2.1); blocks 1..Ns normalise u into x = u / ||u|| while
+// forming the quadrature of x (Eq. 11-14) for height blockIdx.x - 1
 template <int MODE, bool WJ>
 __global__ void __launch_bounds__(kMom64Threads) k_moments64_norm(
     double* __restrict__ x, const double* __restrict__ dinv, const double* __restrict__ wray,
@@ -443,7 +443,8 @@ __global__ void k_etile(const double* __restrict__ ce, int Ns, int64_t nray, int
   }
 }
 
-// Weights of the map offsets.  With zero inflow the tile recurrence
+// Weights of the map offsets of the formal solver (Eq. 9-10 marched over a
+// depth tile).  With zero inflow the tile recurrence
 // I_j = e_j I_{j-1} + alpha_j S_{j-1} + beta_j S_j (+ gamma_j S_{j+1}) ends at
 // B = sum_j P_j (alpha_j S_{j-1} + beta_j S_j + gamma_j S_{j+1}), P_j the
 // product of the e of the tile's later steps, so B is a fixed linear form in
