@@ -244,6 +244,7 @@ struct Problem {
   // sigma-form SOR / SSOR: the assembled matrix A (row-major n x n, n = Nop),
   // the dense P^-1 (row-major), a triangular-inverse scratch and a vector
   double *Asig = nullptr, *Mpre = nullptr, *Mtri = nullptr, *Mscr = nullptr;
+  int asig_ready = 0;        // Asig holds the assembled matrix
   int mpre_kind = 0;         // RT_PREC_SOR / RT_PREC_SSOR that Mpre holds (0: none)
   double mpre_omega = 0.0;
   double* Bmap = nullptr;  // [2*ngroups][ntile64-1][32] FP64 formal solver: offsets of the tile maps

@@ -373,6 +373,7 @@ void free_device(Problem* P) {
   P->qw = P->St = P->qpart = nullptr;
   P->Mdiag = P->Ibuf = P->cg = P->Etile = P->Bmap = P->Kmap = nullptr;
   P->Asig = P->Mpre = P->Mtri = P->Mscr = P->wjac = nullptr;
+  P->asig_ready = 0;
   P->mpre_kind = 0;
   P->staged = 0;
 }

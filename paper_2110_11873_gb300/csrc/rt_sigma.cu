@@ -231,22 +231,26 @@ rt_status op_dense_precond_build(Problem* P, int kind, double omega, cudaStream_
     return RT_EINVAL;
   }
   const size_t nn = (size_t)n * n;
-  if (!P->Asig) {
+  // each buffer is allocated once; a failed allocation leaves the others for
+  // the next call, and A is assembled only once all of them exist
+  if (!P->Asig) RT_TRY_CUDA(dev_alloc(P, (void**)&P->Asig, nn * sizeof(double)));
+  if (!P->Mpre) RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mpre, nn * sizeof(double)));
+  if (!P->Mtri) RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mtri, nn * sizeof(double)));
+  if (!P->Mscr) RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mscr, 2 * (size_t)n * sizeof(double)));
+  if (!P->asig_ready) {
     // the columns A e_j (one sigma-form apply each) into Mtri, then row-major
-    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Asig, nn * sizeof(double)));
-    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mpre, nn * sizeof(double)));
-    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mtri, nn * sizeof(double)));
-    RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mscr, 2 * (size_t)n * sizeof(double)));
     for (int j = 0; j < n; ++j) {
       k_unit<<<blocks_for(n, 256, 64), 256, 0, st>>>(P->Mscr, n, j); RT_COUNT(1);
       RT_TRY(op_apply_sigma(P, P->Mscr, P->Mtri + (size_t)j * n, AM_PLAIN, st, nullptr, 0));
     }
     k_transpose<<<blocks_for((int64_t)nn, 256, 8 * P->num_sms), 256, 0, st>>>(P->Mtri, n, P->Asig); RT_COUNT(1);
     RT_TRY_CUDA(cudaGetLastError());
+    P->asig_ready = 1;
     P->mpre_kind = 0;
   }
   const int base = (kind == RT_PREC_SOR || kind == RT_PREC_SOR_LEFT) ? RT_PREC_SOR : RT_PREC_SSOR;
   if (P->mpre_kind == base && P->mpre_omega == omega) return RT_OK;
+  P->mpre_kind = 0;   // Mpre is rewritten below; tagged again once complete
   const int tb = 128, gb = (n + tb - 1) / tb;
   if (base == RT_PREC_SOR) {
     k_tri_inverse<true><<<gb, tb, 0, st>>>(P->Asig, n, omega, P->Mpre); RT_COUNT(1);
