@@ -456,14 +456,22 @@ inline int mgs_grid(const Problem* P) {
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-// back substitution H(0:k,0:k) y = g(0:k) (one thread)
+// back substitution H(0:k,0:k) y = g(0:k) by one warp: the reciprocals of
+// the diagonal first (independent FP64 divisions, in parallel), then per row
+// a warp-parallel dot product and one multiply
 __global__ void k_lsq(GmresDev* gm, int m) {
-  const int k = gm->kdone;
+  const int k = gm->kdone, lane = threadIdx.x;
+  __shared__ double ys[kMaxRestart], rd[kMaxRestart];
+  for (int i = lane; i < k; i += 32) rd[i] = 1.0 / gm->H[i * (m + 1) + i];
+  __syncwarp();
   for (int i = k - 1; i >= 0; --i) {
-    double s = gm->g[i];
-    for (int l = i + 1; l < k; ++l) s -= gm->H[l * (m + 1) + i] * gm->y[l];
-    gm->y[i] = s / gm->H[i * (m + 1) + i];
+    double s = 0.0;
+    for (int l = i + 1 + lane; l < k; l += 32) s = fma(gm->H[l * (m + 1) + i], ys[l], s);
+    s = wsum(s);
+    if (lane == 0) ys[i] = (gm->g[i] - s) * rd[i];
+    __syncwarp();
   }
+  for (int i = lane; i < k; i += 32) gm->y[i] = ys[i];
 }
 
 // t = sum_{i<k} y_i V_i; mode 0: x += t, 1: x += dinv*t, 2: t stored for P^{-1}
@@ -1037,7 +1045,7 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
                                               gm, m, m - 1, hist, hcap, kstop); RT_COUNT(1);
   }
   RT_TRY_CUDA(cudaGetLastError());
-  k_lsq<<<1, 1, 0, st>>>(gm, m); RT_COUNT(1);
+  k_lsq<<<1, 32, 0, st>>>(gm, m); RT_COUNT(1);
   double* x = wk(P, 0);
   double* t = wk(P, 4);
   if (precond == RT_PREC_LOCAL_LAMBDA || precond == RT_PREC_SOR || precond == RT_PREC_SSOR) {
