@@ -130,7 +130,10 @@ __device__ __forceinline__ double inst_norm_inv(const InstDev& I, int pb, double
 }
 
 // ------------------------------------------------------------ operator
-template <typename TC, int MODE>
+// NORM (Arnoldi steps after the first): the input is v_src = w / ||w||, the
+// last block pass's w scaled by the inverse norm kb_givens stored; it is
+// written to v_src as the quadrature reads it, in place of a scaling pass
+template <typename TC, int MODE, bool NORM = false>
 __global__ void __launch_bounds__(kMomThreads) kb_moments(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
                                                           const Counts* cnt, int src, int step, int useS2) {
   const int n = cnt->nh;
@@ -138,13 +141,15 @@ __global__ void __launch_bounds__(kMomThreads) kb_moments(const InstDev* __restr
     const int2 it = wl[w];
     const InstDev& I = insts[it.x];
     if (step_gated(I, step)) continue;
-    const double* x = vec(I, src);
+    const double* x = NORM ? I.w : vec(I, src);
+    double* xo = NORM ? vec(I, src) : nullptr;
+    const double inv = NORM ? I.gm->vscale : 1.0;
     if (sizeof(TC) == 8) {
-      moments_flat64<MODE>(x, I.dinv, I.wray, I.t201, I.t202, I.Minv, I.Ns, I.Nmu, I.nray, I.xi, I.xiW2,
-                           useS2 ? I.S2 : I.S, it.y);
+      moments_flat64<MODE, false, NORM>(x, I.dinv, I.wray, I.t201, I.t202, I.Minv, I.Ns, I.Nmu, I.nray, I.xi,
+                                        I.xiW2, useS2 ? I.S2 : I.S, it.y, inv, xo);
     } else {
-      moments_height<double, float, MODE>(x, I.dinv, I.wnu32, I.wmu32, I.t201f, I.t202f, I.Minv, I.Ns, I.Nmu, I.Nnu,
-                                          (float)I.xi, (float)I.xiW2, I.S32, it.y);
+      moments_height<double, float, MODE, NORM>(x, I.dinv, I.wnu32, I.wmu32, I.t201f, I.t202f, I.Minv, I.Ns, I.Nmu,
+                                                I.Nnu, (float)I.xi, (float)I.xiW2, I.S32, it.y, inv, xo);
     }
     __syncthreads();
   }
@@ -326,19 +331,6 @@ __global__ void __launch_bounds__(kBT) kb_bmgs(const InstDev* __restrict__ insts
                  for (int k = 0; k < kGramB - 1; ++k) if (k < ng) s[1 + k] = fma(wi, bv[k], s[1 + k]);
                })
     chunk_sum4(s, nn ? nn : 1 + ng, I, pb ^ 1, it.y);
-  }
-}
-
-// v_{j+1} = w / ||w|| with the inverse norm kb_givens stored
-__global__ void __launch_bounds__(kBT) kb_bscale(const InstDev* __restrict__ insts, const int2* __restrict__ wl,
-                                                 const Counts* cnt, int j) {
-  for (int w = blockIdx.x; w < cnt->nc; w += gridDim.x) {
-    const int2 it = wl[w];
-    const InstDev& I = insts[it.x];
-    if (step_gated(I, j)) continue;
-    const double inv = I.gm->vscale;
-    double* vo = I.V + (int64_t)(j + 1) * I.N;
-    CHUNK_LOOP(vo[n_] = I.w[n_] * inv;)
   }
 }
 
@@ -680,41 +672,48 @@ void formal32(Server* S, cudaStream_t st, int src, int dst, int step) {
                                                                                      S->d_counts, src, dst, step);
 }
 
-// the operator of every resident instance: w[dst] = A v[src] (quadrature,
-// then the formal solver), with the server's current grids
-void enqueue_apply(Server* S, cudaStream_t st, int src, int dst, int md, bool f32, int step) {
+template <bool NORM>
+void enqueue_apply_t(Server* S, cudaStream_t st, int src, int dst, int md, bool f32, int step) {
   const InstDev* I = S->d_insts;
   const Counts* C = S->d_counts;
   if (!f32) {
     switch (md) {
       case KM_JACOBI:
-        kb_moments<double, KM_JACOBI><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<double, KM_JACOBI, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
         kb_formal<double, 0, KM_JACOBI><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
         break;
       case KM_LOCAL_LAMBDA:
-        kb_moments<double, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<double, KM_LOCAL_LAMBDA, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
         kb_formal<double, 0, KM_LOCAL_LAMBDA><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst,
                                                                                      step);
         break;
       default:
-        kb_moments<double, KM_PLAIN><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<double, KM_PLAIN, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
         kb_formal<double, 0, KM_PLAIN><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
     }
   } else {
     switch (md) {
       case KM_JACOBI:
-        kb_moments<float, KM_JACOBI><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<float, KM_JACOBI, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
         formal32<KM_JACOBI>(S, st, src, dst, step);
         break;
       case KM_LOCAL_LAMBDA:
-        kb_moments<float, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<float, KM_LOCAL_LAMBDA, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
         formal32<KM_LOCAL_LAMBDA>(S, st, src, dst, step);
         break;
       default:
-        kb_moments<float, KM_PLAIN><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<float, KM_PLAIN, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
         formal32<KM_PLAIN>(S, st, src, dst, step);
     }
   }
+}
+
+// the operator of every resident instance: w[dst] = A v[src] (quadrature,
+// then the formal solver), with the server's current grids; norm: v[src] is
+// first formed as w / ||w|| by the quadrature kernel (see kb_moments)
+void enqueue_apply(Server* S, cudaStream_t st, int src, int dst, int md, bool f32, int step, bool norm = false) {
+  if (norm) enqueue_apply_t<true>(S, st, src, dst, md, f32, step);
+  else enqueue_apply_t<false>(S, st, src, dst, md, f32, step);
 }
 
 // Autotuner of the persistent grids: CTAs per SM of the quadrature, the
@@ -805,9 +804,9 @@ rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
   const int mode = prec == RT_PREC_JACOBI ? KM_JACOBI : prec == RT_PREC_LOCAL_LAMBDA ? KM_LOCAL_LAMBDA : KM_PLAIN;
   const InstDev* I = S->d_insts;
   const Counts* C = S->d_counts;
-  auto apply = [&](int src, int dst, int md, bool f32, int step) { enqueue_apply(S, st, src, dst, md, f32, step); };
   for (int j = 0; j < m; ++j) {
-    apply(j, VW, mode, fp32, j);
+    // steps after the first normalise v_j = w / ||w|| inside the quadrature
+    enqueue_apply(S, st, j, VW, mode, fp32, j, j > 0);
     int pb = 0;
     kb_bdot_fn[std::min(kGramB, j + 1) - 1]<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j);
     for (int i0 = 0; i0 <= j; i0 += kGramB) {
@@ -816,11 +815,11 @@ rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
       (nn ? kb_pass_fn[nn - 1] : kb_last_fn[nb - 1])<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, i0, pb);
       pb ^= 1;
     }
-    // h_{j+1,j}, the Gram row and the rotations first: the scaling pass is
-    // skipped by an instance whose Givens step broke down
+    // h_{j+1,j}, the Gram row, the rotations and the inverse norm that the
+    // next step's quadrature scales w by; an instance that stops at step j
+    // never forms v_{j+1}, which no later kernel of the cycle reads
     const int ng = (j + 1) % kGramB;
     kb_givens<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C, j, pb, ng);
-    kb_bscale<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j);
   }
   kb_lsq<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C);
   if (mode == KM_LOCAL_LAMBDA) {
@@ -830,7 +829,7 @@ rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
   } else {
     kb_combine<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, mode == KM_JACOBI ? 1 : 0);
   }
-  apply(VX, VTMP, KM_PLAIN, false, -1);   // FP64 true residual
+  enqueue_apply(S, st, VX, VTMP, KM_PLAIN, false, -1);   // FP64 true residual
   kb_residual<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C);
   kb_cycle_start<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, S->d_status);
   RT_TRY_CUDA(cudaGetLastError());

@@ -51,12 +51,15 @@ __device__ __forceinline__ double beta_star(const double* __restrict__ cb, int k
 // sigma_k <- M_k^{-1} sigma_k.  TI: input vector type, TC: arithmetic type.
 constexpr int kRowChunk = 8;   // loads per lane in flight per Stokes parameter
 
-// moments of height k by the whole block (all threads must call it)
-template <typename TI, typename TC, int MODE>
+// moments of height k by the whole block (all threads must call it).
+// NORM: the input is x * inv, written to xout in the input's precision as
+// each element is read (the GMRES normalisation of the batched solver)
+template <typename TI, typename TC, int MODE, bool NORM = false>
 __device__ __forceinline__ void moments_height(
     const TI* __restrict__ x, const double* __restrict__ dinv, const TC* __restrict__ wnu,
     const TC* __restrict__ wmu, const TC* __restrict__ t201, const TC* __restrict__ t202,
-    const double* __restrict__ Minv, int Ns, int Nmu, int Nnu, TC xi, TC xiW2, TC* __restrict__ S, int k) {
+    const double* __restrict__ Minv, int Ns, int Nmu, int Nnu, TC xi, TC xiW2, TC* __restrict__ S, int k,
+    double inv = 1.0, TI* __restrict__ xout = nullptr) {
   const int64_t nray = (int64_t)Nmu * Nnu;
   const int64_t oI = (int64_t)k * nray, oQ = ((int64_t)Ns + k) * nray;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -72,8 +75,20 @@ __device__ __forceinline__ void moments_height(
         const int p = p0 + c * 32 + lane;
         const bool ok = p < Nnu;
         const int64_t q = row + (ok ? p : 0);
-        vI[c] = ok ? (TC)x[oI + q] : (TC)0;
-        vQ[c] = ok ? (TC)x[oQ + q] : (TC)0;
+        if (NORM) {
+          TI a = 0, b = 0;
+          if (ok) {
+            a = (TI)(x[oI + q] * inv);
+            b = (TI)(x[oQ + q] * inv);
+            xout[oI + q] = a;
+            xout[oQ + q] = b;
+          }
+          vI[c] = (TC)a;
+          vQ[c] = (TC)b;
+        } else {
+          vI[c] = ok ? (TC)x[oI + q] : (TC)0;
+          vQ[c] = ok ? (TC)x[oQ + q] : (TC)0;
+        }
         wv[c] = ok ? wnu[p] : (TC)0;
         if (MODE == KM_JACOBI && ok) {
           vI[c] *= (TC)dinv[oI + q];
