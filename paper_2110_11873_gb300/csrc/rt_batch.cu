@@ -2,8 +2,9 @@
 //
 // Many atmospheres of different sizes are solved together by restarted
 // GMRES(m) in lock-step: every phase of an Arnoldi step (quadrature, formal
-// solve, each MGS pass, normalisation, Givens update) is ONE persistent
-// launch over all resident instances.  Each launch walks a device-resident
+// solve, each MGS pass, Givens update) is ONE persistent launch over all
+// resident instances; the normalisation of a new basis vector happens in
+// the next step's quadrature launch.  Each launch walks a device-resident
 // work list -- (instance, height) items for the quadrature, (instance, ray
 // group, Stokes) items for the formal solver, (instance, vector chunk) items
 // for the vector kernels, instances for the scalar updates -- so the grid is
