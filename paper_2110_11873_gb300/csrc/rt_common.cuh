@@ -318,7 +318,7 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
                      const int* kstop = nullptr, int step = 0, const NormIn* nin = nullptr);
 rt_status op_apply32(Problem* P, const float* x, float* y, int mode, cudaStream_t st);
 rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cudaStream_t st,
-                           const int* kstop = nullptr, int step = 0);
+                           const int* kstop = nullptr, int step = 0, const NormIn* nin = nullptr);
 rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st, const int* kstop = nullptr,
                         int step = 0);
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st);
@@ -348,7 +348,10 @@ rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t 
 // fast FP32 apply (rt_tma.cu)
 rt_status staged_setup(Problem* P, cudaStream_t st);
 bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cudaStream_t st, const int* kstop,
-                    int step, rt_status* status);
+                    int step, rt_status* status, const NormIn* nin = nullptr);
+// whether staged_apply32 takes FP64 vectors x (and a normalisation input u)
+// in this apply mode
+bool staged_f64io_ok(const Problem* P, int mode, const void* x, const void* u);
 // RT_ETIMEOUT (and clears the flag) when a bounded device wait gave up
 rt_status check_device_flag(Problem* P, cudaStream_t st);
 rt_status setup_device_tables(Problem* P, cudaStream_t st);

@@ -872,7 +872,7 @@ static rt_status left_apply(Problem* P, int pc, const double* x, double* y, cuda
 }
 
 // A M^{-1} v with the chosen preconditioner and operator precision
-// (nin: GMRES, FP64 I-form; the apply's input v is formed from nin->u, see
+// (nin: GMRES on the I-form; the apply's input v is formed from nin->u, see
 // NormIn)
 static rt_status apply_prec(Problem* P, const double* v, double* y, int precond, int fp32, cudaStream_t st,
                             const int* kstop = nullptr, int step = 0, const NormIn* nin = nullptr) {
@@ -887,7 +887,7 @@ static rt_status apply_prec(Problem* P, const double* v, double* y, int precond,
     return op_apply64(P, P->Mscr, y, AM_PLAIN, st, kstop, step);
   }
   const int mode = precond == RT_PREC_JACOBI ? AM_JACOBI : precond == RT_PREC_LOCAL_LAMBDA ? AM_LOCAL_LAMBDA : AM_PLAIN;
-  if (fp32) return op_apply32_f64io(P, v, y, mode, st, kstop, step);
+  if (fp32) return op_apply32_f64io(P, v, y, mode, st, kstop, step, nin);
   return op_apply64(P, v, y, mode, st, kstop, step, nin);
 }
 
@@ -1021,9 +1021,14 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
   double* w = wk(P, 3);
   double* hist = P->hist;
   const int hcap = P->hist_cap_dev;
-  // FP64 I-form: the normalisation of v_{j+1} and the Givens rotations of
-  // column j run inside the next step's first operator kernel (NormIn)
-  const bool fuse = !fp32 && P->form == RT_FORM_I && !prec_dense(precond);
+  // I-form: the normalisation of v_{j+1} and the Givens rotations of column
+  // j run inside the next step's first operator kernel (NormIn) -- the FP64
+  // quadrature, or the FP32 one where the staged FP32 apply takes the
+  // basis vectors (a right preconditioner; every v_j shares V's alignment,
+  // N being even)
+  const int amode = precond == RT_PREC_JACOBI ? AM_JACOBI : precond == RT_PREC_LOCAL_LAMBDA ? AM_LOCAL_LAMBDA : AM_PLAIN;
+  const bool fuse = P->form == RT_FORM_I && !prec_dense(precond) &&
+                    (!fp32 || (!prec_left(precond) && staged_f64io_ok(P, amode, P->V, w)));
   int pb = 0, ng = 0;
   for (int j = 0; j < m; ++j) {
     double* vj = P->V + (size_t)j * N;

@@ -802,7 +802,8 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
 }
 
 template <typename TV>
-static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStream_t st, const int* kstop, int step) {
+static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStream_t st, const int* kstop, int step,
+                              const NormIn* nin = nullptr) {
   if (P->fs == RT_FS_DELO_PARABOLIC) {
     set_error("the DELO-parabolic formal solver is FP64 only (use rt_apply, FP64 solvers)");
     return RT_EINVAL;
@@ -816,7 +817,11 @@ static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStre
     return RT_EINVAL;
   }
   rt_status s = RT_OK;
-  if (staged_apply32(P, x, y, sizeof(TV) == 8, mode, st, kstop, step, &s)) return s;
+  if (staged_apply32(P, x, y, sizeof(TV) == 8, mode, st, kstop, step, &s, nin)) return s;
+  if (nin) {
+    set_error("internal: the fused GMRES normalisation needs the staged FP32 apply");
+    return RT_EINVAL;
+  }
   const float xi = (float)P->xi, xiW2 = (float)(P->xi * P->W2);
   const int Ns = P->Ns, Nmu = P->Nmu, Nnu = P->Nnu;
   switch (mode) {
@@ -851,8 +856,8 @@ rt_status op_apply32(Problem* P, const float* x, float* y, int mode, cudaStream_
 }
 
 rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cudaStream_t st, const int* kstop,
-                           int step) {
-  return apply32_impl<double>(P, x, y, mode, st, kstop, step);
+                           int step, const NormIn* nin) {
+  return apply32_impl<double>(P, x, y, mode, st, kstop, step, nin);
 }
 
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st) {

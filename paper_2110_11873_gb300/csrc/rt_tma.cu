@@ -197,11 +197,27 @@ __device__ __forceinline__ float4 load4<double>(const double* p) {
   return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
 }
 
-template <typename TV, int MODE>
-__global__ void __launch_bounds__(kQuadThreads) k_quad(const TV* __restrict__ x, const double* __restrict__ dinv,
-                                                       const float* __restrict__ qw, int Ns, int64_t nray, int hpc,
-                                                       float* __restrict__ part, const int* kstop, int step) {
-  if (kstop && step >= *kstop) return;
+// four FP64 values of u scaled by inv: stored to xo (the GMRES normalisation
+// v = u / ||u||) and returned in FP32 for the quadrature
+__device__ __forceinline__ float4 load4_scaled(const double* u, double inv, double* xo) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(u)), b = __ldg(reinterpret_cast<const double2*>(u) + 1);
+  a.x *= inv;
+  a.y *= inv;
+  b.x *= inv;
+  b.y *= inv;
+  reinterpret_cast<double2*>(xo)[0] = a;
+  reinterpret_cast<double2*>(xo)[1] = b;
+  return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+// The partials of the heights of row ky of the grid, rays of column
+// blockIdx.x (all threads of the CTA call it).  NORM: the input is u * inv,
+// written to xo as it is read.
+template <typename TV, int MODE, bool NORM>
+__device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double* __restrict__ dinv,
+                                          const float* __restrict__ qw, int Ns, int64_t nray, int hpc,
+                                          float* __restrict__ part, int ky, const double* __restrict__ u = nullptr,
+                                          double inv = 1.0, double* __restrict__ xo = nullptr) {
   constexpr int nw = kQuadThreads / 32;
   __shared__ float red[kQuadMaxHeights][nw][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -212,7 +228,7 @@ __global__ void __launch_bounds__(kQuadThreads) k_quad(const TV* __restrict__ x,
   const float4 w0 = ok ? __ldg(reinterpret_cast<const float4*>(qw) + c) : z;
   const float4 w1 = ok ? __ldg(reinterpret_cast<const float4*>(qw + nray) + c) : z;
   const float4 w2 = ok ? __ldg(reinterpret_cast<const float4*>(qw + 2 * nray) + c) : z;
-  const int k_lo = blockIdx.y * hpc, k_hi = min(Ns, k_lo + hpc);
+  const int k_lo = ky * hpc, k_hi = min(Ns, k_lo + hpc);
   const int64_t plane = (int64_t)Ns * nray;
   for (int k = k_lo; k < k_hi; k += kQuadUnroll) {
     float4 vI[kQuadUnroll], vQ[kQuadUnroll];
@@ -222,8 +238,13 @@ __global__ void __launch_bounds__(kQuadThreads) k_quad(const TV* __restrict__ x,
       vQ[v] = z;
       if (ok && k + v < k_hi) {
         const int64_t o = (int64_t)(k + v) * nray + 4 * c;
-        vI[v] = load4<TV>(x + o);
-        vQ[v] = load4<TV>(x + plane + o);
+        if (NORM) {
+          vI[v] = load4_scaled(u + o, inv, xo + o);
+          vQ[v] = load4_scaled(u + plane + o, inv, xo + plane + o);
+        } else {
+          vI[v] = load4<TV>(x + o);
+          vQ[v] = load4<TV>(x + plane + o);
+        }
         if (MODE == KM_JACOBI) {
           const float4 dI = load4<double>(dinv + o), dQ = load4<double>(dinv + plane + o);
           vI[v] = make_float4(vI[v].x * dI.x, vI[v].y * dI.y, vI[v].z * dI.z, vI[v].w * dI.w);
@@ -265,6 +286,34 @@ __global__ void __launch_bounds__(kQuadThreads) k_quad(const TV* __restrict__ x,
     o[0] = s0;
     o[1] = s2;
   }
+}
+
+template <typename TV, int MODE>
+__global__ void __launch_bounds__(kQuadThreads) k_quad(const TV* __restrict__ x, const double* __restrict__ dinv,
+                                                       const float* __restrict__ qw, int Ns, int64_t nray, int hpc,
+                                                       float* __restrict__ part, const int* kstop, int step) {
+  if (kstop && step >= *kstop) return;
+  quad_tile<TV, MODE, false>(x, dinv, qw, Ns, nray, hpc, part, blockIdx.y);
+}
+
+// k_quad inside GMRES with FP64 vectors, fused with the end of Arnoldi step
+// nin.jprev: the first CTA of grid row 0 folds h_{j+1,j}, the Gram row and
+// the Givens rotations (Sect. 2.1); rows 1.. form 1/||u|| from the same
+// partials in the same order and write x = u / ||u|| as they read u for the
+// partials of row blockIdx.y - 1.  Gated by the previous step, since the
+// fold itself may end the cycle.
+template <int MODE>
+__global__ void __launch_bounds__(kQuadThreads) k_quad_norm(double* __restrict__ x, const double* __restrict__ dinv,
+                                                            const float* __restrict__ qw, int Ns, int64_t nray,
+                                                            int hpc, float* __restrict__ part, const NormIn nin) {
+  if (nin.kstop && nin.jprev >= *nin.kstop) return;
+  if (blockIdx.y == 0) {
+    if (blockIdx.x == 0)
+      arnoldi_fold(nin.part, nin.Gp, nin.ng, nin.hcol, nin.gram, nin.gm, nin.m, nin.jprev, nin.hist, nin.hist_cap);
+    return;
+  }
+  const double inv = arnoldi_inv_norm(nin.part, nin.Gp);
+  quad_tile<double, MODE, true>(nullptr, dinv, qw, Ns, nray, hpc, part, blockIdx.y - 1, nin.u, inv, x);
 }
 
 // --------------------------------------------------------------- k_sigma
@@ -608,7 +657,8 @@ void launch_staged(const Problem* P, const StagedArgs& A, const Maps& M, cudaStr
 }
 
 template <typename TV, int MODE>
-rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step) {
+rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step,
+                       const NormIn* nin = nullptr) {
   constexpr bool f64 = sizeof(TV) == 8;
   Maps M;
   memset(&M, 0, sizeof M);
@@ -623,8 +673,14 @@ rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const in
     return RT_ECUDA;
   }
   const float xi = (float)P->xi, xiW2 = (float)(P->xi * P->W2);
-  k_quad<TV, MODE><<<dim3(P->quad_gx, P->quad_gy), kQuadThreads, 0, st>>>(x, P->dinv, P->qw, P->Ns, P->nray,
-                                                                          P->quad_hpc, P->qpart, kstop, step);
+  if (nin) {   // FP64 vectors only (staged_apply32): x is written here as u / ||u||
+    k_quad_norm<MODE><<<dim3(P->quad_gx, P->quad_gy + 1), kQuadThreads, 0, st>>>(
+        const_cast<double*>(reinterpret_cast<const double*>(x)), P->dinv, P->qw, P->Ns, P->nray, P->quad_hpc,
+        P->qpart, *nin);
+  } else {
+    k_quad<TV, MODE><<<dim3(P->quad_gx, P->quad_gy), kQuadThreads, 0, st>>>(x, P->dinv, P->qw, P->Ns, P->nray,
+                                                                            P->quad_hpc, P->qpart, kstop, step);
+  }
   RT_COUNT(1);
   const int64_t nsig = (int64_t)P->Ns * P->Nmu;
   const int gs = (int)std::min<int64_t>((nsig + 255) / 256, 4LL * P->num_sms);
@@ -720,32 +776,36 @@ rt_status staged_setup(Problem* P, cudaStream_t st) {
   return RT_OK;
 }
 
+bool staged_f64io_ok(const Problem* P, int mode, const void* x, const void* u) {
+  if (!P->staged || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(u) & 15)) return false;
+  if (mode == AM_JACOBI) return !(reinterpret_cast<uintptr_t>(P->dinv) & 15);
+  return mode == AM_PLAIN || mode == AM_LOCAL_LAMBDA;
+}
+
 // The whole FP32 apply (quadrature, source functions, formal solve) through
-// the kernels above, for FP32 vectors or, with f64io, FP64 vectors; false
-// when they do not apply (nothing launched, *status untouched).
+// the kernels above, for FP32 vectors or, with f64io, FP64 vectors (and then,
+// with nin, the input formed as nin->u / ||nin->u||); false when they do not
+// apply (nothing launched, *status untouched).
 bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cudaStream_t st, const int* kstop,
-                    int step, rt_status* status) {
-  if (!P->staged || (reinterpret_cast<uintptr_t>(x) & 15)) return false;
+                    int step, rt_status* status, const NormIn* nin) {
   if (!f64io) {
-    if (mode != AM_PLAIN) return false;
+    if (nin || !P->staged || (reinterpret_cast<uintptr_t>(x) & 15) || mode != AM_PLAIN) return false;
     *status = staged_apply<float, KM_PLAIN>(P, static_cast<const float*>(x), static_cast<float*>(y), st, kstop, step);
     return true;
   }
+  if (!staged_f64io_ok(P, mode, x, nin ? static_cast<const void*>(nin->u) : x)) return false;
   const double* xd = static_cast<const double*>(x);
   double* yd = static_cast<double*>(y);
   switch (mode) {
     case AM_PLAIN:
-      *status = staged_apply<double, KM_PLAIN>(P, xd, yd, st, kstop, step);
+      *status = staged_apply<double, KM_PLAIN>(P, xd, yd, st, kstop, step, nin);
       return true;
     case AM_JACOBI:
-      if (reinterpret_cast<uintptr_t>(P->dinv) & 15) return false;
-      *status = staged_apply<double, KM_JACOBI>(P, xd, yd, st, kstop, step);
-      return true;
-    case AM_LOCAL_LAMBDA:
-      *status = staged_apply<double, KM_LOCAL_LAMBDA>(P, xd, yd, st, kstop, step);
+      *status = staged_apply<double, KM_JACOBI>(P, xd, yd, st, kstop, step, nin);
       return true;
     default:
-      return false;
+      *status = staged_apply<double, KM_LOCAL_LAMBDA>(P, xd, yd, st, kstop, step, nin);
+      return true;
   }
 }
 
