@@ -10,6 +10,9 @@
 //              A CTA covers 1024 rays and a range of heights; warp sums are
 //              combined in a fixed order into one partial per (height, CTA
 //              column), so the result does not depend on scheduling.
+//              k_quad_norm is the same inside GMRES with FP64 basis vectors:
+//              it also ends the previous Arnoldi step and forms its input
+//              v = u / ||u|| as it reads u.
 //   k_sigma    sums the partials of a height in a fixed order, forms sigma00,
 //              sigma20 (Eq. 7-8, with the local-Lambda block inverse in that
 //              mode) and writes the source functions transposed, S[s][m][k],
