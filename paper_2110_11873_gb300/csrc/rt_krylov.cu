@@ -456,21 +456,33 @@ inline int mgs_grid(const Problem* P) {
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-// back substitution H(0:k,0:k) y = g(0:k) by one warp: the reciprocals of
-// the diagonal first (independent FP64 divisions, in parallel), then per row
-// a warp-parallel dot product and one multiply
+// back substitution H(0:k,0:k) y = g(0:k) in the textbook order: row k-1
+// first, each row's sum running from g_i over l = i+1.. in increasing order,
+// then one division.  The warp stages the triangle in shared memory (cycles
+// of up to kLsqStage steps) and thread 0 runs the recurrence.  The order
+// matters in FP32 refinement: a warp-tree sum of the same products changed
+// the inner solves' iteration counts by up to 10%.
+constexpr int kLsqStage = 64;
 __global__ void k_lsq(GmresDev* gm, int m) {
   const int k = gm->kdone, lane = threadIdx.x;
-  __shared__ double ys[kMaxRestart], rd[kMaxRestart];
-  for (int i = lane; i < k; i += 32) rd[i] = 1.0 / gm->H[i * (m + 1) + i];
+  __shared__ double Hs[kLsqStage * kLsqStage], ys[kMaxRestart];
+  const bool staged = k <= kLsqStage;
+  if (staged)
+    for (int idx = lane; idx < k * k; idx += 32) {
+      const int l = idx / k, i = idx - l * k;
+      if (i <= l) Hs[idx] = gm->H[l * (m + 1) + i];
+    }
   __syncwarp();
-  for (int i = k - 1; i >= 0; --i) {
-    double s = 0.0;
-    for (int l = i + 1 + lane; l < k; l += 32) s = fma(gm->H[l * (m + 1) + i], ys[l], s);
-    s = wsum(s);
-    if (lane == 0) ys[i] = (gm->g[i] - s) * rd[i];
-    __syncwarp();
+  const double* H = staged ? Hs : gm->H;
+  const int ld = staged ? k : m + 1;
+  if (lane == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = gm->g[i];
+      for (int l = i + 1; l < k; ++l) s -= H[l * ld + i] * ys[l];
+      ys[i] = s / H[i * ld + i];
+    }
   }
+  __syncwarp();
   for (int i = lane; i < k; i += 32) gm->y[i] = ys[i];
 }
 
