@@ -66,8 +66,18 @@ enum { RT_MU_GL_HALF = 0, RT_MU_GL_FULL = 1 };
    interpolated by the parabola through the upwind, current and downwind
    nodes; the paper names the parabolic DELO methods without formulas).
    DELO-parabolic is FP64 only: rt_apply_f32, RT_PRECISION_FP32_REFINE and the
-   batch server reject it. */
-enum { RT_FS_DELO_LINEAR = 0, RT_FS_IMPLICIT_EULER = 1, RT_FS_TRAPEZOIDAL = 2, RT_FS_DELO_PARABOLIC = 3 };
+   batch server reject it.  RT_FS_DELOPAR names the same scheme: the paper
+   lists DELOPAR and DELO-parabolic side by side, with no formulas for
+   either, and here the propagation matrix is eta_I times the identity (no
+   dichroism), so both are read as this one parabolic exponential
+   integrator. */
+enum {
+  RT_FS_DELO_LINEAR = 0,
+  RT_FS_IMPLICIT_EULER = 1,
+  RT_FS_TRAPEZOIDAL = 2,
+  RT_FS_DELO_PARABOLIC = 3,
+  RT_FS_DELOPAR = RT_FS_DELO_PARABOLIC
+};
 /* linear system (Sect. 3.2):
    RT_FORM_I      Eq. (19): unknown I, N = 2*Ns*Nmu*Nnu values x[s][k][m][p],
                   A x = x - Lambda(T(J x)), b = Lambda T c + t;

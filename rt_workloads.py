@@ -35,6 +35,7 @@ FS_DELO_LINEAR = 0
 FS_IMPLICIT_EULER = 1
 FS_TRAPEZOIDAL = 2
 FS_DELO_PARABOLIC = 3
+FS_DELOPAR = FS_DELO_PARABOLIC   # the same scheme under the paper's other name (no dichroism here)
 
 
 @dataclasses.dataclass

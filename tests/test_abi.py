@@ -78,6 +78,28 @@ def test_struct_layouts_match_the_header(tmp_path):
             assert getattr(structs[sname], field).offset == int(val), key
 
 
+def test_header_constants_match_the_python_side(tmp_path):
+    """The descriptor enums of the header against the constants the Python
+    side writes into rt_problem_desc (rt_workloads) and the binding."""
+    import rt_workloads as W
+    names = {"RT_TAU_LINE_CENTER": W.TAU_LINE_CENTER, "RT_TAU_FREQ_INTEGRATED": W.TAU_FREQ_INTEGRATED,
+             "RT_MU_GL_HALF": W.MU_GL_HALF, "RT_MU_GL_FULL": W.MU_GL_FULL,
+             "RT_FS_DELO_LINEAR": W.FS_DELO_LINEAR, "RT_FS_IMPLICIT_EULER": W.FS_IMPLICIT_EULER,
+             "RT_FS_TRAPEZOIDAL": W.FS_TRAPEZOIDAL, "RT_FS_DELO_PARABOLIC": W.FS_DELO_PARABOLIC,
+             "RT_FS_DELOPAR": W.FS_DELOPAR}
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "rt_krylov.h"\nint main(void) {\n' +
+                   "".join(f'  printf("{n} %d\\n", (int){n});\n' for n in names) + "  return 0;\n}\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    assert {k: int(v) for k, v in got.items()} == names
+    assert (N.RT_FS_DELO_LINEAR, N.RT_FS_IMPLICIT_EULER, N.RT_FS_TRAPEZOIDAL) == tuple(
+        int(got[n]) for n in ("RT_FS_DELO_LINEAR", "RT_FS_IMPLICIT_EULER", "RT_FS_TRAPEZOIDAL"))
+    assert W.FS_DELOPAR == W.FS_DELO_PARABOLIC
+
+
 def _desc(**kw):
     tau = np.logspace(-4, 6, 10)
     keep = [tau]
