@@ -288,6 +288,7 @@ struct Problem {
   int staged = 0;
   int ntile_st = 1;            // depth tiles per ray group of the staged formal solver
   int quad_gx = 1, quad_gy = 1, quad_hpc = 1;   // quadrature grid, heights per CTA
+  int quadn_gy = 1, quadn_hpc = 1;             // the same for the fused-normalisation quadrature
   float* qw = nullptr;         // [3][nray] quadrature weights w0, w0*T201, w0*T202
   float* St = nullptr;         // [2][Nmu][Ns] source functions, transposed
   float* qpart = nullptr;      // [Ns][quad_gx][2] partial moments

@@ -677,8 +677,8 @@ rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const in
   }
   const float xi = (float)P->xi, xiW2 = (float)(P->xi * P->W2);
   if (nin) {   // FP64 vectors only (staged_apply32): x is written here as u / ||u||
-    k_quad_norm<MODE><<<dim3(P->quad_gx, P->quad_gy + 1), kQuadThreads, 0, st>>>(
-        const_cast<double*>(reinterpret_cast<const double*>(x)), P->dinv, P->qw, P->Ns, P->nray, P->quad_hpc,
+    k_quad_norm<MODE><<<dim3(P->quad_gx, P->quadn_gy + 1), kQuadThreads, 0, st>>>(
+        const_cast<double*>(reinterpret_cast<const double*>(x)), P->dinv, P->qw, P->Ns, P->nray, P->quadn_hpc,
         P->qpart, *nin);
   } else {
     k_quad<TV, MODE><<<dim3(P->quad_gx, P->quad_gy), kQuadThreads, 0, st>>>(x, P->dinv, P->qw, P->Ns, P->nray,
@@ -766,6 +766,21 @@ rt_status staged_setup(Problem* P, cudaStream_t st) {
   const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(Ns, target / P->quad_gx));
   P->quad_hpc = std::min((Ns + gy - 1) / gy, kQuadMaxHeights);
   P->quad_gy = (Ns + P->quad_hpc - 1) / P->quad_hpc;
+  // k_quad_norm: taller CTAs, so that the grid is one wave of resident CTAs
+  // (each CTA first forms 1/||u|| from the norm partials; a second wave would
+  // repeat that serially).  The partial layout depends on quad_gx only.
+  P->quadn_hpc = P->quad_hpc;
+  int resident = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_quad_norm<KM_JACOBI>, kQuadThreads, 0) ==
+          cudaSuccess &&
+      resident > 0) {
+    const int64_t rows = std::max<int64_t>(1, (int64_t)resident * P->num_sms / P->quad_gx - 1);
+    const int h = (int)std::min<int64_t>(kQuadMaxHeights, (Ns + rows - 1) / rows);
+    P->quadn_hpc = std::max(P->quad_hpc, h);
+  } else {
+    cudaGetLastError();
+  }
+  P->quadn_gy = (Ns + P->quadn_hpc - 1) / P->quadn_hpc;
   P->ntile_st = choose_tiles_staged(P);
 #ifdef RT_EXPERIMENT
   if (const char* t = std::getenv("RT_STAGED_TILES")) P->ntile_st = std::min(kMaxT, std::max(1, std::atoi(t)));
