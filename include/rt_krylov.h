@@ -36,6 +36,7 @@
 #ifndef RT_KRYLOV_H
 #define RT_KRYLOV_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -122,6 +123,36 @@ typedef struct rt_problem rt_problem;
    phi == NULL), non-increasing tau, x_min >= x_max, unknown enums. */
 rt_status rt_problem_create(const rt_problem_desc* desc, void* stream, rt_problem** out);
 rt_status rt_problem_destroy(rt_problem* prob);
+
+/* Device memory from the caller (the paper has no counterpart: this is how
+   the library's workspaces can come from another allocator, such as
+   PyTorch's caching allocator, which then accounts for them).
+     alloc(ctx, bytes, stream)   returns `bytes` of device memory on the
+                                 current device, aligned to 256 bytes or
+                                 more, or NULL when it cannot;
+     release(ctx, ptr, bytes, stream)  takes back a block alloc returned,
+                                 with the size it was asked for.
+   `stream` is the stream given to rt_problem_create_with_allocator (for a
+   server: the server's internal stream); the library uses a block only on
+   the streams of its own calls, which never overlap in time for one problem.
+   Both functions are called from the thread making the library call, and for
+   a server also from its worker thread; they must not call back into this
+   library.  A request the library cannot satisfy fails with RT_ENOMEM. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*release)(void* ctx, void* ptr, size_t bytes, void* stream);
+} rt_allocator;
+
+/* rt_problem_create with every device workspace of the problem -- the
+   tables built here, the Krylov basis, work vectors and GMRES state (taken
+   at the first solve), the residual history -- requested from `allocator`
+   instead of cudaMalloc.  The rt_allocator struct is copied; its functions
+   and ctx must stay valid until rt_problem_destroy has returned, which
+   synchronises the device and then releases every block.  allocator NULL
+   behaves as rt_problem_create; RT_EINVAL when alloc or release is NULL. */
+rt_status rt_problem_create_with_allocator(const rt_problem_desc* desc, const rt_allocator* allocator, void* stream,
+                                           rt_problem** out);
 /* Length N of the system's vectors: 2*Ns*Nmu*Nnu (RT_FORM_I) or 2*Ns
    (RT_FORM_SIGMA); -1 for NULL */
 int64_t rt_problem_size(const rt_problem* prob);
@@ -143,8 +174,10 @@ rt_status rt_apply(rt_problem* prob, const double* x_dev, double* y_dev, void* s
    aligned) the formal solver streams x through shared memory with tensor
    copies whose waits are bounded; a wait that gives up leaves y invalid and
    is reported by rt_problem_check.  Setting RT_NO_TMA=1 in the environment
-   before rt_problem_create selects the register-ring kernel instead; both
-   give bit-identical results. */
+   before rt_problem_create selects the register-ring kernel instead.  The two
+   kernels agree to FP32 rounding accumulated along the rays, not bit for bit:
+   they split the depth scan into different tiles, sum the quadrature in
+   different orders and carry the recurrence in different variables. */
 rt_status rt_apply_f32(rt_problem* prob, const float* x_dev, float* y_dev, void* stream);
 
 /* Synchronises `stream` and reports RT_ETIMEOUT (then clears the condition)
@@ -158,6 +191,15 @@ rt_status rt_problem_check(rt_problem* prob, void* stream);
    counterpart in the paper): 1 = shared-memory tensor-copy staging, 0 = the
    register-ring kernel, -1 for NULL.  Host only. */
 int rt_problem_formal_kernel(const rt_problem* prob);
+
+/* Failure injection for the bounded waits (no counterpart in the paper; it
+   exercises this library's error path without a device fault): the next
+   `count` calls of rt_apply_f32 on this problem that take the tensor-copy
+   kernel treat the first wait of one warp as given up -- that warp flags the
+   problem, waits (bounded) for its copies in flight and skips its depth
+   tile, so y is invalid and the next rt_problem_check returns RT_ETIMEOUT.
+   count = 0 disarms it.  RT_EINVAL for NULL or count < 0.  Host only. */
+rt_status rt_problem_inject_wait_timeout(rt_problem* prob, int32_t count);
 
 /* b = Lambda T c + t of Eq. (19): one formal solve with S_I = eps B, S_Q = 0
    and the boundary radiation; for RT_FORM_SIGMA b = J t + c of Eq. (18), t
@@ -233,7 +275,9 @@ rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_
    array of 2 x 1024 doubles (16 KB) inside the library, which every GPU that
    loads the library keeps until the process exits.  The first call on a
    device looks up that array's device address (cudaGetSymbolAddress) with
-   the device current; make that first call before any stream capture.
+   the device current; make that first call before any stream capture.  The
+   address is cached per CUDA context, so after a cudaDeviceReset the next
+   call looks it up again (and that call, too, belongs outside a capture).
    All calls share the one array: calls whose work overlaps on the GPU (two
    streams, or two host threads) race and must not be issued.
    Sizes beyond the limits return RT_EINVAL with a message:
@@ -317,11 +361,14 @@ void rt_solver_opts_default(rt_solver_opts* opts);
 rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                          double* x_dev, rt_solve_info* info, void* stream);
 /* Right-preconditioned BiCGSTAB (Sect. 2.2; van der Vorst 1992); not with
-   the left preconditioners. */
+   the left preconditioners.  With RT_PRECISION_FP32_REFINE the FP32 operator
+   runs inside FP64 iterative refinement, as for GMRES: every outer step
+   forms the FP64 residual, solves with the FP32 operator to inner_rtol and
+   corrects x; iters counts the inner iterations of all steps. */
 rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                             double* x_dev, rt_solve_info* info, void* stream);
 /* Right-preconditioned CGS (Sect. 2.2; Sonneveld 1989); not with the left
-   preconditioners. */
+   preconditioners; RT_PRECISION_FP32_REFINE as for BiCGSTAB. */
 rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
                        double* x_dev, rt_solve_info* info, void* stream);
 
@@ -371,6 +418,14 @@ typedef struct rt_server rt_server;
 void rt_server_opts_default(rt_server_opts* opts);
 /* Create a server on the current device (the device stays the worker's). */
 rt_status rt_server_create(const rt_server_opts* opts, rt_server** out);
+/* rt_server_create with the server's device memory -- the arena of
+   mem_budget_bytes that holds the resident instances, and the server's work
+   lists and per-slot state -- requested from `allocator` (see rt_allocator).
+   The functions and ctx must stay valid until rt_server_destroy has
+   returned, which synchronises the device before the releases.  allocator
+   NULL behaves as rt_server_create. */
+rt_status rt_server_create_with_allocator(const rt_server_opts* opts, const rt_allocator* allocator,
+                                          rt_server** out);
 /* Queue one solve.  desc as for rt_problem_create (arrays copied; Ns <= 4096);
    opts may be NULL (rtol 1e-8, maxit 10000) -- only rtol and maxit are read.
    *ticket identifies the request for rt_poll. */
@@ -409,6 +464,17 @@ const char* rt_last_error(void);
    work): number of kernels this library has launched in the process so far.
    A kernel node of a captured CUDA graph counts once per graph launch. */
 int64_t rt_launch_count(void);
+
+/* Measurement aid (the paper has no counterpart): enqueues on `stream` one
+   kernel that performs nothing but FP64 fused multiply-adds -- `iters`
+   iterations of 8 independent chains per thread, 4 CTAs of 256 threads per
+   SM -- and returns the number of FP64 floating-point operations it does
+   (2 per fused multiply-add), or -1 (see rt_last_error) for iters < 1, a NULL
+   sink_dev or a failed launch.  The caller times the launch with CUDA events
+   on `stream`; FLOP / time is the FP64 rate that bounds the FP64 kernels of
+   this library.  sink_dev: one caller-owned device double, overwritten (it
+   keeps the chains from being optimised away). */
+int64_t rt_probe_fp64_fma(int32_t iters, double* sink_dev, void* stream);
 
 #ifdef __cplusplus
 }

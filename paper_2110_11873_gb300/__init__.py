@@ -5,6 +5,6 @@ The compute path is the C-ABI library librtkrylov.so (include/rt_krylov.h);
 this package only marshals arguments to it.
 """
 from . import _native
-from .api import Problem, Server, SolveResult
+from .api import Problem, Server, SolveResult, TorchAllocator
 
-__all__ = ["Problem", "Server", "SolveResult", "_native"]
+__all__ = ["Problem", "Server", "SolveResult", "TorchAllocator", "_native"]

@@ -69,10 +69,20 @@ class ServerStats(C.Structure):
     ]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN)]
+
+
 # (name, restype, argtypes) for every entry point of include/rt_krylov.h
 _P = C.c_void_p
 SIGNATURES = [
     ("rt_problem_create", C.c_int, [C.POINTER(ProblemDesc), _P, C.POINTER(_P)]),
+    ("rt_problem_create_with_allocator", C.c_int, [C.POINTER(ProblemDesc), C.POINTER(Allocator), _P,
+                                                    C.POINTER(_P)]),
     ("rt_problem_destroy", C.c_int, [_P]),
     ("rt_problem_size", C.c_int64, [_P]),
     ("rt_problem_grids", C.c_int, [_P] + [C.POINTER(C.c_double)] * 6),
@@ -80,6 +90,7 @@ SIGNATURES = [
     ("rt_apply_f32", C.c_int, [_P, _P, _P, _P]),
     ("rt_problem_check", C.c_int, [_P, _P]),
     ("rt_problem_formal_kernel", C.c_int, [_P]),
+    ("rt_problem_inject_wait_timeout", C.c_int, [_P, C.c_int32]),
     ("rt_rhs", C.c_int, [_P, _P, _P]),
     ("rt_jacobi_diag", C.c_int, [_P, _P, _P]),
     ("rt_precond_local_lambda", C.c_int, [_P, _P, _P, _P]),
@@ -94,12 +105,14 @@ SIGNATURES = [
     ("rt_solve_richardson", C.c_int, [_P, C.POINTER(SolverOpts), _P, _P, C.POINTER(SolveInfo), _P]),
     ("rt_server_opts_default", None, [C.POINTER(ServerOpts)]),
     ("rt_server_create", C.c_int, [C.POINTER(ServerOpts), C.POINTER(_P)]),
+    ("rt_server_create_with_allocator", C.c_int, [C.POINTER(ServerOpts), C.POINTER(Allocator), C.POINTER(_P)]),
     ("rt_batch_submit", C.c_int, [_P, C.POINTER(ProblemDesc), C.POINTER(SolverOpts), C.POINTER(C.c_uint64)]),
     ("rt_poll", C.c_int, [_P, C.c_uint64, C.POINTER(SolveInfo), C.POINTER(C.c_double)]),
     ("rt_server_stats_get", C.c_int, [_P, C.POINTER(ServerStats)]),
     ("rt_server_destroy", C.c_int, [_P]),
     ("rt_last_error", C.c_char_p, []),
     ("rt_launch_count", C.c_int64, []),
+    ("rt_probe_fp64_fma", C.c_int64, [C.c_int32, _P, _P]),
 ]
 
 _lib = None

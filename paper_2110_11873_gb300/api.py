@@ -65,12 +65,51 @@ def _desc_of(atm, keep: list, phi=None, phi_center=0.0) -> "N.ProblemDesc":
     return d
 
 
+class TorchAllocator:
+    """An rt_allocator backed by PyTorch's caching allocator: the library's
+    device workspaces are then PyTorch allocations (counted by
+    torch.cuda.memory_allocated, reused from its cache).  Keeps counts of the
+    blocks it handed out and took back.  ``fail_after``: refuse every request
+    after that many (to exercise the library's out-of-memory path)."""
+
+    def __init__(self, device=None, fail_after: Optional[int] = None):
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.fail_after = fail_after
+        self.allocs = 0
+        self.releases = 0
+        self.live = {}
+
+        def _alloc(ctx, nbytes, stream):
+            if self.fail_after is not None and self.allocs >= self.fail_after:
+                return None
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device, stream=int(stream or 0))
+            except Exception:   # out of memory: the library reports RT_ENOMEM
+                return None
+            self.allocs += 1
+            self.live[int(p)] = int(nbytes)
+            return p
+
+        def _release(ctx, ptr, nbytes, stream):
+            self.releases += 1
+            self.live.pop(int(ptr), None)
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._fa = N.ALLOC_FN(_alloc)
+        self._fr = N.RELEASE_FN(_release)
+        self.struct = N.Allocator(None, self._fa, self._fr)
+
+
 class Server:
-    """Batched / served solves (rt_server_*): submit atmospheres, poll results."""
+    """Batched / served solves (rt_server_*): submit atmospheres, poll results.
+    ``allocator``: a TorchAllocator (or any object with an rt_allocator
+    ``struct``) from which the server takes its device memory."""
 
     def __init__(self, mem_budget_bytes: int = 8 << 30, max_slots: int = 64, restart: int = 30,
-                 precond: str = "local_lambda", precision: str = "fp64", autotune: bool = True):
+                 precond: str = "local_lambda", precision: str = "fp64", autotune: bool = True,
+                 allocator=None):
         self.lib = N.load()
+        self.allocator = allocator
         o = N.ServerOpts()
         self.lib.rt_server_opts_default(C.byref(o))
         o.mem_budget_bytes, o.max_slots, o.restart = int(mem_budget_bytes), int(max_slots), int(restart)
@@ -79,7 +118,11 @@ class Server:
         o.precision = {"fp64": N.RT_PRECISION_FP64, "fp32_refine": N.RT_PRECISION_FP32_REFINE}[precision]
         o.autotune = 1 if autotune else 0
         h = C.c_void_p()
-        N.check(self.lib.rt_server_create(C.byref(o), C.byref(h)), "rt_server_create")
+        if allocator is None:
+            N.check(self.lib.rt_server_create(C.byref(o), C.byref(h)), "rt_server_create")
+        else:
+            N.check(self.lib.rt_server_create_with_allocator(C.byref(o), C.byref(allocator.struct), C.byref(h)),
+                    "rt_server_create_with_allocator")
         self.handle = h
         self.sizes = {}
 
@@ -133,12 +176,15 @@ class Problem:
     Voigt profile (with ``phi_center`` for line-centre tau).  ``form``
     selects the linear system: "I" (Eq. 19, N = 2*Ns*Nmu*Nnu) or "sigma"
     (Eq. 18, N = 2*Ns); apply, rhs, jacobi_diag, precond_local_lambda and
-    solve then work on that system.
+    solve then work on that system.  ``allocator``: a TorchAllocator (or any
+    object with an rt_allocator ``struct``) that supplies the problem's
+    device workspaces instead of cudaMalloc.
     """
 
     def __init__(self, atm, phi: Optional[np.ndarray] = None, phi_center: float = 0.0,
-                 stream: Optional[torch.cuda.Stream] = None, form: str = "I"):
+                 stream: Optional[torch.cuda.Stream] = None, form: str = "I", allocator=None):
         self.lib = N.load()
+        self.allocator = allocator
         f = {k: getattr(atm, k) for k in _DESC_FIELDS}
         self._tau = np.ascontiguousarray(f["tau"], dtype=np.float64)
         self._B = np.ascontiguousarray(f["B"], dtype=np.float64)
@@ -159,7 +205,12 @@ class Problem:
         self.Ns, self.Nmu, self.Nnu = d.Ns, d.Nmu, d.Nnu
         self.device = torch.device("cuda", torch.cuda.current_device())
         h = C.c_void_p()
-        N.check(self.lib.rt_problem_create(C.byref(d), _stream_handle(stream), C.byref(h)), "rt_problem_create")
+        if allocator is None:
+            N.check(self.lib.rt_problem_create(C.byref(d), _stream_handle(stream), C.byref(h)), "rt_problem_create")
+        else:
+            N.check(self.lib.rt_problem_create_with_allocator(C.byref(d), C.byref(allocator.struct),
+                                                              _stream_handle(stream), C.byref(h)),
+                    "rt_problem_create_with_allocator")
         self.handle = h
         self.N = int(self.lib.rt_problem_size(h))
 
@@ -217,6 +268,11 @@ class Problem:
     def staged_formal(self) -> bool:
         """True when FP32 applies use the shared-memory tensor-copy kernel."""
         return self.lib.rt_problem_formal_kernel(self.handle) == 1
+
+    def inject_wait_timeout(self, count: int = 1) -> None:
+        """Arm the next `count` tensor-copy FP32 applies to give up one wait
+        (failure injection; the following check() raises RT_ETIMEOUT)."""
+        N.check(self.lib.rt_problem_inject_wait_timeout(self.handle, int(count)), "rt_problem_inject_wait_timeout")
 
     def check(self, stream=None) -> None:
         """Raise RTError(RT_ETIMEOUT) when a bounded device wait of this

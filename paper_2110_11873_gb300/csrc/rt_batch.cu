@@ -497,9 +497,11 @@ __global__ void __launch_bounds__(kBT) kb_cycle_start(const InstDev* __restrict_
 // First-fit allocator over one device allocation (256-byte granules).
 class Arena : public DevAllocator {
  public:
-  rt_status init(size_t bytes) {
+  // one block of `bytes` from src (NULL: cudaMalloc)
+  rt_status init(size_t bytes, DevAllocator* src) {
     bytes_ = (bytes + 255) & ~(size_t)255;
-    cudaError_t e = cudaMalloc(&base_, bytes_);
+    src_ = src;
+    cudaError_t e = src ? src->alloc(&base_, bytes_) : cudaMalloc(&base_, bytes_);
     if (e != cudaSuccess) {
       set_error("arena allocation of %zu bytes failed: %s", bytes_, cudaGetErrorString(e));
       base_ = nullptr;
@@ -508,9 +510,15 @@ class Arena : public DevAllocator {
     free_[0] = bytes_;
     return RT_OK;
   }
-  ~Arena() override {
-    if (base_) cudaFree(base_);
+  // gives the block back to its source (before the source goes away)
+  void teardown() {
+    if (base_) {
+      if (src_) src_->release(base_);
+      else cudaFree(base_);
+    }
+    base_ = nullptr;
   }
+  ~Arena() override { teardown(); }
   cudaError_t alloc(void** p, size_t bytes) override {
     std::lock_guard<std::mutex> lk(mu_);
     bytes = (bytes + 255) & ~(size_t)255;
@@ -568,6 +576,7 @@ class Arena : public DevAllocator {
 
  private:
   void* base_ = nullptr;
+  DevAllocator* src_ = nullptr;
   size_t bytes_ = 0, in_use_ = 0;
   std::map<size_t, size_t> free_, used_;
   std::mutex mu_;
@@ -604,6 +613,7 @@ struct Instance {
 struct Server {
   rt_server_opts opts{};
   int device = 0, sms = 0;
+  DevAllocator* hook = nullptr;   // the caller's allocator (owned), or NULL for cudaMalloc
   Arena arena;
   std::mutex mu;
   std::condition_variable cv;
@@ -639,13 +649,28 @@ struct Server {
 
 namespace {
 
+// the server's own device buffers: from the caller's allocator when given
+cudaError_t srv_alloc(Server* S, void** p, size_t bytes) {
+  return S->hook ? S->hook->alloc(p, bytes) : cudaMalloc(p, bytes);
+}
+void srv_free(Server* S, void* p) {
+  if (!p) return;
+  if (S->hook) S->hook->release(p);
+  else cudaFree(p);
+}
+
 template <typename T>
-rt_status grow(T** p, size_t* cap, size_t need) {
+rt_status grow(Server* S, T** p, size_t* cap, size_t need) {
   if (need <= *cap) return RT_OK;
-  if (*p) cudaFree(*p);
+  if (*p) {
+    // the previous cycle's kernels may still read the old list
+    RT_TRY_CUDA(cudaStreamSynchronize(S->st));
+    srv_free(S, *p);
+  }
   *p = nullptr;
+  *cap = 0;
   size_t c = need + need / 2 + 64;
-  RT_TRY_CUDA(cudaMalloc((void**)p, c * sizeof(T)));
+  RT_TRY_CUDA(srv_alloc(S, (void**)p, c * sizeof(T)));
   *cap = c;
   return RT_OK;
 }
@@ -905,10 +930,10 @@ rt_status rebuild_lists(Server* S) {
   // instances do not end up on the same SMs
   bool regrown = false;
   const size_t ch = S->cap_h, cc = S->cap_c, c64 = S->cap_g64, c32 = S->cap_g32;
-  RT_TRY(grow(&S->d_wl_h, &S->cap_h, h.size()));
-  RT_TRY(grow(&S->d_wl_c, &S->cap_c, c.size()));
-  RT_TRY(grow(&S->d_wl_g64, &S->cap_g64, g64.size()));
-  RT_TRY(grow(&S->d_wl_g32, &S->cap_g32, g32.size()));
+  RT_TRY(grow(S, &S->d_wl_h, &S->cap_h, h.size()));
+  RT_TRY(grow(S, &S->d_wl_c, &S->cap_c, c.size()));
+  RT_TRY(grow(S, &S->d_wl_g64, &S->cap_g64, g64.size()));
+  RT_TRY(grow(S, &S->d_wl_g32, &S->cap_g32, g32.size()));
   regrown = ch != S->cap_h || cc != S->cap_c || c64 != S->cap_g64 || c32 != S->cap_g32;
   if (regrown) drop_graph(S);
   if (!h.empty()) RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_h, h.data(), h.size() * sizeof(int2), cudaMemcpyHostToDevice, S->st));
@@ -935,6 +960,7 @@ rt_status make_instance(Server* S, Request* rq, Instance* in, int slot) {
   in->slot = slot;
   Problem& P = in->P;
   P.alloc = &S->arena;
+  P.in_arena = 1;
   host_grids(&rq->desc, P);
   P.device = S->device;
   P.num_sms = S->sms;
@@ -1023,7 +1049,7 @@ rt_status start_instances(Server* S, const std::vector<Instance*>& fresh) {
     wi.push_back(in->slot);
     for (int cc = 0; cc < in->dev.nchunks; ++cc) c.push_back(make_int2(in->slot, cc));
   }
-  RT_TRY(grow(&S->d_wl_new_c, &S->cap_new_c, c.size()));
+  RT_TRY(grow(S, &S->d_wl_new_c, &S->cap_new_c, c.size()));
   RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_new_c, c.data(), c.size() * sizeof(int2), cudaMemcpyHostToDevice, S->st));
   RT_TRY_CUDA(cudaMemcpyAsync(S->d_wl_new_i, wi.data(), wi.size() * sizeof(int), cudaMemcpyHostToDevice, S->st));
   Counts cn{0, 0, (int)c.size(), (int)wi.size(), {0, 0, 0}, {0, 0, 0}};
@@ -1154,6 +1180,7 @@ void worker_main(Server* S) {
       break;
     }
     // one restart cycle for every resident instance
+    RT_NVTX("server restart cycle (graph)");
     cudaError_t e = cudaGraphLaunch(S->graph, S->st);
     if (e == cudaSuccess) count_launches(S->graph_kernels);
     S->cycles.fetch_add(1);
@@ -1221,7 +1248,8 @@ void rt_server_opts_default(rt_server_opts* o) {
   o->autotune = 1;
 }
 
-rt_status rt_server_create(const rt_server_opts* opts, rt_server** out) {
+static rt_status create_server(const rt_server_opts* opts, const rt_allocator* hook, rt_server** out) {
+  RT_NVTX("rt_server_create");
   clear_error();
   if (!opts || !out) { set_error("opts and out are required"); return RT_EINVAL; }
   *out = nullptr;
@@ -1230,6 +1258,7 @@ rt_status rt_server_create(const rt_server_opts* opts, rt_server** out) {
   if (opts->precond < RT_PREC_NONE || opts->precond > RT_PREC_LOCAL_LAMBDA) { set_error("bad precond"); return RT_EINVAL; }
   if (opts->precision != RT_PRECISION_FP64 && opts->precision != RT_PRECISION_FP32_REFINE) { set_error("bad precision"); return RT_EINVAL; }
   if (opts->mem_budget_bytes < ((int64_t)1 << 20)) { set_error("mem_budget_bytes must be >= 1 MiB"); return RT_EINVAL; }
+  if (hook && (!hook->alloc || !hook->release)) { set_error("the allocator needs both alloc and release"); return RT_EINVAL; }
   rt_server* srv = new (std::nothrow) rt_server();
   if (!srv) { set_error("host allocation failed"); return RT_ENOMEM; }
   Server* S = &srv->S;
@@ -1241,9 +1270,24 @@ rt_status rt_server_create(const rt_server_opts* opts, rt_server** out) {
     delete srv;
     return RT_ECUDA;
   }
-  rt_status s = S->arena.init((size_t)opts->mem_budget_bytes);
+  e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    set_error("server stream creation failed: %s", cudaGetErrorString(e));
+    rt_server_destroy(srv);
+    return RT_ECUDA;
+  }
+  if (hook) {
+    S->hook = make_hook_allocator(hook, S->st);
+    if (!S->hook) {
+      set_error("host allocation failed");
+      rt_server_destroy(srv);
+      return RT_ENOMEM;
+    }
+  }
+  rt_status s = S->arena.init((size_t)opts->mem_budget_bytes, S->hook);
   if (s != RT_OK) {
-    delete srv;
+    rt_server_destroy(srv);
     return s;
   }
   S->slots.assign(opts->max_slots, nullptr);
@@ -1251,22 +1295,27 @@ rt_status rt_server_create(const rt_server_opts* opts, rt_server** out) {
   S->grid_g = 8 * S->sms;
   S->grid_v = 4 * S->sms;
   S->grid_i = (opts->max_slots + kInstThreads - 1) / kInstThreads;
-  e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_insts, sizeof(InstDev) * opts->max_slots);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_status, sizeof(InstStatus) * opts->max_slots);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_counts, sizeof(Counts));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_new_counts, sizeof(Counts));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_wl_i, sizeof(int) * opts->max_slots);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_wl_new_i, sizeof(int) * opts->max_slots);
+  e = srv_alloc(S, (void**)&S->d_insts, sizeof(InstDev) * opts->max_slots);
+  if (e == cudaSuccess) e = srv_alloc(S, (void**)&S->d_status, sizeof(InstStatus) * opts->max_slots);
+  if (e == cudaSuccess) e = srv_alloc(S, (void**)&S->d_counts, sizeof(Counts));
+  if (e == cudaSuccess) e = srv_alloc(S, (void**)&S->d_new_counts, sizeof(Counts));
+  if (e == cudaSuccess) e = srv_alloc(S, (void**)&S->d_wl_i, sizeof(int) * opts->max_slots);
+  if (e == cudaSuccess) e = srv_alloc(S, (void**)&S->d_wl_new_i, sizeof(int) * opts->max_slots);
   if (e != cudaSuccess) {
     set_error("server setup failed: %s", cudaGetErrorString(e));
     rt_server_destroy(srv);
-    return RT_ECUDA;
+    return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
   }
   S->worker = std::thread(worker_main, S);
   *out = srv;
   return RT_OK;
+}
+
+rt_status rt_server_create(const rt_server_opts* opts, rt_server** out) { return create_server(opts, nullptr, out); }
+
+rt_status rt_server_create_with_allocator(const rt_server_opts* opts, const rt_allocator* allocator,
+                                          rt_server** out) {
+  return create_server(opts, allocator, out);
 }
 
 rt_status rt_batch_submit(rt_server* srv, const rt_problem_desc* desc, const rt_solver_opts* opts, uint64_t* ticket) {
@@ -1370,12 +1419,16 @@ rt_status rt_server_destroy(rt_server* srv) {
   S->cv.notify_all();
   if (S->worker.joinable()) S->worker.join();
   drop_graph(S);
+  // a caller's allocator may hand a released block to its next user at once
+  if (S->hook) cudaDeviceSynchronize();
   void* ptrs[] = {S->d_insts, S->d_status, S->d_counts, S->d_new_counts, S->d_wl_i, S->d_wl_new_i, S->d_wl_h,
                   S->d_wl_c, S->d_wl_g64, S->d_wl_g32, S->d_wl_new_c};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) srv_free(S, p);
+  S->arena.teardown();
   if (S->st) cudaStreamDestroy(S->st);
   if (S->cap) cudaStreamDestroy(S->cap);
+  delete S->hook;
+  S->hook = nullptr;
   delete srv;
   return RT_OK;
 }

@@ -15,9 +15,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rt_krylov.h"
 
 namespace rt {
+
+// NVTX range over the enclosing scope: named ranges for every entry point,
+// solve phase and kernel launch, visible to profilers (no cost without one).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define RT_NVTX_CAT2(a, b) a##b
+#define RT_NVTX_CAT(a, b) RT_NVTX_CAT2(a, b)
+#define RT_NVTX(name) ::rt::NvtxRange RT_NVTX_CAT(rt_nvtx_, __LINE__)(name)
 
 void set_error(const char* fmt, ...);
 void clear_error();
@@ -209,15 +223,24 @@ struct BicgDev {
 };
 
 // Device memory source of a problem: NULL means cudaMalloc/cudaFree; the
-// batch server passes its arena.
+// batch server passes its arena; rt_problem_create_with_allocator the
+// caller's hook.
 struct DevAllocator {
   virtual ~DevAllocator() {}
   virtual cudaError_t alloc(void** p, size_t bytes) = 0;
   virtual void release(void* p) = 0;
 };
 
+// A caller-provided rt_allocator behind the DevAllocator interface: every
+// request goes to the hook with the stream the object was made with; the
+// sizes are remembered for the matching release.  Blocks must be 256-byte
+// aligned (a misaligned one is handed back and the request fails).
+DevAllocator* make_hook_allocator(const rt_allocator* hook, cudaStream_t st);
+
 struct Problem {
-  DevAllocator* alloc = nullptr;
+  DevAllocator* alloc = nullptr;     // NULL: cudaMalloc / cudaFree
+  DevAllocator* own_alloc = nullptr; // the caller's allocator hook, owned (deleted at destroy)
+  int in_arena = 0;                  // 1: an instance of the batch server, tables in its arena
   // sizes
   int Ns = 0, Nmu = 0, Nnu = 0, Nh = 0;
   int64_t nray = 0;   // Nmu*Nnu rays per Stokes parameter
@@ -290,9 +313,14 @@ struct Problem {
   int quad_gx = 1, quad_gy = 1, quad_hpc = 1;   // quadrature grid, heights per CTA
   int quadn_gy = 1, quadn_hpc = 1;             // the same for the fused-normalisation quadrature
   float* qw = nullptr;         // [3][nray] quadrature weights w0, w0*T201, w0*T202
-  float* St = nullptr;         // [2][Nmu][Ns] source functions, transposed
+  float4* stab = nullptr;      // [2][Ns + pad] node operands of the formal solver, march-indexed per
+                               // direction: (sigma00, sigma20) of the node, then the constants of the
+                               // interval a step into it crosses
   float* qpart = nullptr;      // [Ns][quad_gx][2] partial moments
+  int* qcnt = nullptr;         // [quadrature grid rows] CTAs of a row done (the last one forms sigma)
   int* dev_err = nullptr;
+  int inject_wait_fail = 0;    // standalone FP32 applies still to run with one tensor-copy wait forced to
+                               // give up (failure injection, rt_problem_inject_wait_timeout)
 };
 
 // operator entry points used by the solvers (all enqueue on `st`)

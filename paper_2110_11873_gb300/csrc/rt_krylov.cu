@@ -21,11 +21,14 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <tuple>
+
+#include <cuda.h>
 
 #include "rt_common.cuh"
 
@@ -841,18 +844,18 @@ static rt_status ensure_workspace(Problem* P, int restart, cudaStream_t st) {
     if (cap > kMaxPartials) cap = kMaxPartials;
     P->vec_grid = (int)(g < 1 ? 1 : (g > cap ? cap : g));
   }
-  if (!P->work) RT_TRY_CUDA(cudaMalloc((void**)&P->work, (size_t)kWorkVecs * P->Nop * sizeof(double)));
-  if (!P->dinv) RT_TRY_CUDA(cudaMalloc((void**)&P->dinv, (size_t)P->Nop * sizeof(double)));
-  if (!P->partials) RT_TRY_CUDA(cudaMalloc((void**)&P->partials, (size_t)2 * 2 * kMaxPartials * sizeof(double)));
-  if (!P->bpart) RT_TRY_CUDA(cudaMalloc((void**)&P->bpart, (size_t)3 * kGramB * kMaxPartials * sizeof(double)));
-  if (!P->gm) RT_TRY_CUDA(cudaMalloc((void**)&P->gm, sizeof(GmresDev)));
-  if (!P->bc) RT_TRY_CUDA(cudaMalloc((void**)&P->bc, sizeof(BicgDev)));
+  if (!P->work) RT_TRY_CUDA(dev_alloc(P, (void**)&P->work, (size_t)kWorkVecs * P->Nop * sizeof(double)));
+  if (!P->dinv) RT_TRY_CUDA(dev_alloc(P, (void**)&P->dinv, (size_t)P->Nop * sizeof(double)));
+  if (!P->partials) RT_TRY_CUDA(dev_alloc(P, (void**)&P->partials, (size_t)2 * 2 * kMaxPartials * sizeof(double)));
+  if (!P->bpart) RT_TRY_CUDA(dev_alloc(P, (void**)&P->bpart, (size_t)3 * kGramB * kMaxPartials * sizeof(double)));
+  if (!P->gm) RT_TRY_CUDA(dev_alloc(P, (void**)&P->gm, sizeof(GmresDev)));
+  if (!P->bc) RT_TRY_CUDA(dev_alloc(P, (void**)&P->bc, sizeof(BicgDev)));
   if (restart > P->ws_restart) {
     release_graphs(P);  // captured graphs hold the old basis pointer
-    if (P->V) cudaFree(P->V);
+    if (P->V) dev_free(P, P->V);
     P->V = nullptr;
     P->ws_restart = 0;
-    RT_TRY_CUDA(cudaMalloc((void**)&P->V, (size_t)(restart + 1) * P->Nop * sizeof(double)));
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->V, (size_t)(restart + 1) * P->Nop * sizeof(double)));
     P->ws_restart = restart;
   }
   (void)st;
@@ -1146,12 +1149,12 @@ static rt_status get_graph(Problem* P, GraphCache* gc, int m, int precond, int f
 
 static rt_status ensure_hist(Problem* P, int cap) {
   if (cap > P->hist_cap_dev) {
-    if (P->hist) cudaFree(P->hist);
+    if (P->hist) dev_free(P, P->hist);
     P->hist = nullptr;
     P->hist_cap_dev = 0;
     // the graphs bake the history pointer: drop them
     release_graphs(P);
-    RT_TRY_CUDA(cudaMalloc((void**)&P->hist, (size_t)cap * sizeof(double)));
+    RT_TRY_CUDA(dev_alloc(P, (void**)&P->hist, (size_t)cap * sizeof(double)));
     P->hist_cap_dev = cap;
   }
   return RT_OK;
@@ -1161,6 +1164,7 @@ static rt_status ensure_hist(Problem* P, int cap) {
 // zero).  Returns the host copy of the final device state.
 static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, double tol, int maxit, bool x0_zero,
                             GmresDev* hs, int* cycles, cudaStream_t st) {
+  RT_NVTX("GMRES cycles");
   const int G = P->vec_grid;
   const int64_t N = P->Nop;
   const int m = o->restart;
@@ -1195,6 +1199,7 @@ static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, doubl
   cudaGraphExec_t ex;
   RT_TRY(get_graph(P, gc, m, o->precond, fp32, &ex));
   for (;;) {
+    RT_NVTX("GMRES restart cycle (graph)");
     RT_TRY(launch_graph(gc, ex, st));
     RT_TRY_CUDA(cudaMemcpyAsync(hs, P->gm, kGmresHeader, cudaMemcpyDeviceToHost, st));
     RT_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1250,6 +1255,7 @@ static rt_status finish_info(rt_solve_info* info, rt_status s, double t0) {
 
 // true relative residual of x = wk(0) against b = wk(1)
 static rt_status true_residual(Problem* P, double* rel, cudaStream_t st) {
+  RT_NVTX("true residual (FP64 operator)");
   const int G = P->vec_grid;
   RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
   k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), P->Nop, partb(P, 0)); RT_COUNT(1);
@@ -1261,7 +1267,10 @@ static rt_status true_residual(Problem* P, double* rel, cudaStream_t st) {
   RT_TRY_CUDA(cudaStreamSynchronize(st));
   double rr = 0, bb = 0;
   for (int i = 0; i < G; ++i) { rr += h[i]; bb += h[G + i]; }
-  *rel = bb > 0 ? sqrt(rr / bb) : 0.0;
+  // a NaN or Inf in b or in the residual gives NaN (RT_ENUMERIC upstream); a
+  // zero b gives 0
+  if (rr != rr || bb != bb || std::isinf(rr) || std::isinf(bb)) *rel = NAN;
+  else *rel = bb > 0 ? sqrt(rr / bb) : 0.0;
   return RT_OK;
 }
 
@@ -1309,6 +1318,7 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
     while (refine < maxref && iters < o->maxit) {
       if (rel != rel) { s = RT_ENUMERIC; break; }
       if (rel < o->rtol) { s = RT_OK; break; }
+      RT_NVTX("refinement step");
       // inner solve: b <- r, x <- 0
       RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), wk(P, 2), bytes, cudaMemcpyDeviceToDevice, st));
       RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
@@ -1457,7 +1467,9 @@ static rt_status solve_richardson(Problem* P, const rt_solver_opts* o, const dou
   hs.bnorm = sqrt(bb);
   hs.tol = o->rtol;
   hs.maxit = o->maxit;
-  hs.rel = hs.bnorm > 0.0 ? sqrt(rr) / hs.bnorm : 0.0;
+  // NaN or Inf in b or x0 gives NaN (RT_ENUMERIC below); a zero b gives 0
+  if (rr != rr || bb != bb || std::isinf(rr) || std::isinf(bb)) hs.rel = NAN;
+  else hs.rel = hs.bnorm > 0.0 ? sqrt(rr) / hs.bnorm : 0.0;
   rt_status s = RT_OK;
   if (hs.bnorm > 0.0 && hs.rel >= o->rtol) {
     RT_TRY_CUDA(cudaMemcpyAsync(P->gm, &hs, kGmresHeader, cudaMemcpyHostToDevice, st));
@@ -1495,31 +1507,22 @@ static rt_status solve_richardson(Problem* P, const rt_solver_opts* o, const dou
   return finish_info(info, s, t0);
 }
 
-static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, const double* b, double* x,
-                            rt_solve_info* info, cudaStream_t st) {
-  const double t0 = now_ms();
-  if (info) memset(info, 0, sizeof *info);
-  if (o->precision != RT_PRECISION_FP64) {
-    set_error("BiCGSTAB/CGS support FP64 only");
-    return finish_info(info, RT_EINVAL, t0);
-  }
-  if (prec_left(o->precond)) {
-    set_error("BiCGSTAB/CGS are preconditioned from the right only");
-    return finish_info(info, RT_EINVAL, t0);
-  }
-  RT_TRY(prepare(P, o, 2, st));
+// BiCGSTAB (method 0) or CGS (method 1) on the internal buffers: b = wk(1);
+// x0 = wk(0) (set to zero here when x0_zero); fp32 selects the FP32 operator.
+// On return wk(0) = x0 + M^{-1} acc, *hs holds the final device state and
+// *applies counts the products with A; *zero_b is set when ||b|| = 0 (x = 0).
+static rt_status bicg_core(Problem* P, int method, const rt_solver_opts* o, int fp32, double tol, int maxit,
+                           bool x0_zero, BicgDev* hs, int* applies, bool* zero_b, cudaStream_t st) {
   const int G = P->vec_grid;
   const int64_t N = P->Nop;
   const size_t bytes = (size_t)N * sizeof(double);
   double *x0 = wk(P, 0), *bb = wk(P, 1), *r = wk(P, 2), *rhat = wk(P, 3);
   double* acc = P->V + 2 * (size_t)N;
-  RT_TRY_CUDA(cudaMemcpyAsync(bb, b, bytes, cudaMemcpyDeviceToDevice, st));
-  int applies = 0;
-  if (o->x0_kind == RT_X0_USER) {
-    RT_TRY_CUDA(cudaMemcpyAsync(x0, x, bytes, cudaMemcpyDeviceToDevice, st));
+  *zero_b = false;
+  if (!x0_zero) {
     RT_TRY(op_apply64(P, x0, wk(P, 5), AM_PLAIN, st));
     k_residual<<<G, kVecThreads, 0, st>>>(bb, wk(P, 5), r, N, partb(P, 0)); RT_COUNT(1);
-    applies = 1;
+    *applies += 1;
   } else {
     RT_TRY_CUDA(cudaMemsetAsync(x0, 0, bytes, st));
     RT_TRY_CUDA(cudaMemcpyAsync(r, bb, bytes, cudaMemcpyDeviceToDevice, st));
@@ -1529,8 +1532,8 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
   RT_TRY_CUDA(cudaMemsetAsync(acc, 0, bytes, st));
   BicgDev init;
   memset(&init, 0, sizeof init);
-  init.tol = o->rtol;
-  init.maxit = o->maxit;
+  init.tol = tol;
+  init.maxit = maxit;
   RT_TRY_CUDA(cudaMemcpyAsync(P->bc, &init, sizeof init, cudaMemcpyHostToDevice, st));
   // ||b||, then ||r||^2 and <rhat, r>
   k_dot<<<G, kVecThreads, 0, st>>>(bb, bb, N, partb(P, 1), nullptr, 0, nullptr); RT_COUNT(1);
@@ -1544,46 +1547,125 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
     for (int i = 0; i < G; ++i) s2 += h[i];
     init.bnorm = sqrt(s2);
     if (init.bnorm == 0.0) {
-      RT_TRY_CUDA(cudaMemsetAsync(x, 0, bytes, st));
-      RT_TRY_CUDA(cudaStreamSynchronize(st));
-      if (info) info->rel_resid = 0.0;
-      return finish_info(info, RT_OK, t0);
+      RT_TRY_CUDA(cudaMemsetAsync(x0, 0, bytes, st));
+      *zero_b = true;
+      memset(hs, 0, sizeof *hs);
+      hs->done = 1;
+      return RT_OK;
     }
     RT_TRY_CUDA(cudaMemcpyAsync(&P->bc->bnorm, &init.bnorm, sizeof(double), cudaMemcpyHostToDevice, st));
   }
   k_bc_init<<<1, 32, 0, st>>>(P->bc, partb(P, 0), G); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   GraphCache* gc = cache_of(P);
-  cudaGraphExec_t& ex = gc->bicg[method][o->precond][0];
+  cudaGraphExec_t& ex = gc->bicg[method][o->precond][fp32 ? 1 : 0];
   if (!ex) {
     const int prec = o->precond;
-    rt_status s = capture_graph(gc, [&](cudaStream_t cs) { return enqueue_bicg_iter(P, method, prec, 0, cs); }, &ex);
-    if (s != RT_OK) return finish_info(info, s, t0);
+    RT_TRY(capture_graph(gc, [&](cudaStream_t cs) { return enqueue_bicg_iter(P, method, prec, fp32, cs); }, &ex));
   }
-  BicgDev hs;
-  RT_TRY_CUDA(cudaMemcpyAsync(&hs, P->bc, sizeof hs, cudaMemcpyDeviceToHost, st));
+  RT_TRY_CUDA(cudaMemcpyAsync(hs, P->bc, sizeof *hs, cudaMemcpyDeviceToHost, st));
   RT_TRY_CUDA(cudaStreamSynchronize(st));
-  while (!hs.done) {
+  while (!hs->done) {
+    RT_NVTX("BiCGSTAB/CGS iteration (graph)");
     RT_TRY(launch_graph(gc, ex, st));
-    RT_TRY_CUDA(cudaMemcpyAsync(&hs, P->bc, sizeof hs, cudaMemcpyDeviceToHost, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(hs, P->bc, sizeof *hs, cudaMemcpyDeviceToHost, st));
     RT_TRY_CUDA(cudaStreamSynchronize(st));
-    applies += (hs.half ? 1 : 2);
+    *applies += (hs->half ? 1 : 2);
   }
   // x = x0 + M^{-1} acc
   RT_TRY(add_precond(P, x0, acc, o->precond, wk(P, 6), st));
-  RT_TRY_CUDA(cudaMemcpyAsync(x, x0, bytes, cudaMemcpyDeviceToDevice, st));
+  return RT_OK;
+}
+
+static rt_status bicg_status(const BicgDev& hs) {
+  return hs.done == 1 ? RT_OK : hs.done == 2 ? RT_EBREAKDOWN : hs.done == 3 ? RT_ENUMERIC : RT_ENOTCONV;
+}
+
+static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, const double* b, double* x,
+                            rt_solve_info* info, cudaStream_t st) {
+  const double t0 = now_ms();
+  if (info) memset(info, 0, sizeof *info);
+  if (prec_left(o->precond)) {
+    set_error("BiCGSTAB/CGS are preconditioned from the right only");
+    return finish_info(info, RT_EINVAL, t0);
+  }
+  const bool refine = o->precision == RT_PRECISION_FP32_REFINE;
+  // two more basis-sized vectors for the refinement: the outer iterate and b
+  RT_TRY(prepare(P, o, refine ? 4 : 2, st));
+  const int64_t N = P->Nop;
+  const size_t bytes = (size_t)N * sizeof(double);
+  RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
+  if (o->x0_kind == RT_X0_USER) RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), x, bytes, cudaMemcpyDeviceToDevice, st));
+  int applies = 0, iters = 0, refine_steps = 0;
+  BicgDev hs;
+  memset(&hs, 0, sizeof hs);
+  bool zero_b = false;
+  rt_status s = RT_OK;
   double rel = 0;
-  RT_TRY(true_residual(P, &rel, st));
+  if (!refine) {
+    RT_TRY(bicg_core(P, method, o, 0, o->rtol, o->maxit, o->x0_kind == RT_X0_ZERO, &hs, &applies, &zero_b, st));
+    iters = hs.iters;
+    if (zero_b) {
+      RT_TRY_CUDA(cudaMemsetAsync(x, 0, bytes, st));
+      RT_TRY_CUDA(cudaStreamSynchronize(st));
+      if (info) info->rel_resid = 0.0;
+      return finish_info(info, RT_OK, t0);
+    }
+    s = bicg_status(hs);
+    RT_TRY_CUDA(cudaMemcpyAsync(x, wk(P, 0), bytes, cudaMemcpyDeviceToDevice, st));
+    RT_TRY(true_residual(P, &rel, st));
+  } else {
+    // FP32 operator inside FP64 iterative refinement, as for GMRES:
+    //   r = b - A64 x (FP64);  solve A32 d = r to inner_rtol;  x += d
+    double* xb = P->V + 3 * (size_t)N;    // the outer iterate
+    double* bsave = P->V + 4 * (size_t)N;
+    if (o->x0_kind == RT_X0_ZERO) RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(xb, wk(P, 0), bytes, cudaMemcpyDeviceToDevice, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(bsave, wk(P, 1), bytes, cudaMemcpyDeviceToDevice, st));
+    RT_TRY(true_residual(P, &rel, st));   // r = wk(2)
+    applies += 1;
+    s = RT_ENOTCONV;
+    const int maxref = o->max_refine > 0 ? o->max_refine : 20;
+    while (refine_steps < maxref && iters < o->maxit) {
+      if (rel != rel) { s = RT_ENUMERIC; break; }
+      if (rel < o->rtol) { s = RT_OK; break; }
+      RT_NVTX("refinement step");
+      RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), wk(P, 2), bytes, cudaMemcpyDeviceToDevice, st));
+      RT_TRY(bicg_core(P, method, o, 1, o->inner_rtol > 0 ? o->inner_rtol : 1e-4, o->maxit - iters, true, &hs,
+                       &applies, &zero_b, st));
+      iters += hs.iters;
+      refine_steps += 1;
+      const rt_status inner = bicg_status(hs);
+      if (inner == RT_EBREAKDOWN && hs.iters == 0) { s = RT_EBREAKDOWN; break; }
+      // x + d into wk(0); keep it only if the FP64 residual went down (an
+      // inner solve that failed with the FP32 operator must not spoil x)
+      k_axpy1<<<P->vec_grid, kVecThreads, 0, st>>>(wk(P, 0), xb, N); RT_COUNT(1);
+      RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), bsave, bytes, cudaMemcpyDeviceToDevice, st));
+      const double prev = rel;
+      RT_TRY(true_residual(P, &rel, st));
+      applies += 1;
+      if (!(rel < prev)) {   // rejected: x stays the last accepted iterate, with its residual
+        rel = prev;
+        s = (inner == RT_ENUMERIC || hs.done == 3) ? RT_ENUMERIC : RT_ENOTCONV;
+        break;
+      }
+      RT_TRY_CUDA(cudaMemcpyAsync(xb, wk(P, 0), bytes, cudaMemcpyDeviceToDevice, st));
+      if (hs.iters == 0) break;
+    }
+    if (rel != rel) s = RT_ENUMERIC;
+    else if (s == RT_ENOTCONV && rel < o->rtol) s = RT_OK;
+    RT_TRY_CUDA(cudaMemcpyAsync(x, xb, bytes, cudaMemcpyDeviceToDevice, st));
+  }
   int hl = 0;
   if (o->resid_hist && o->hist_cap > 0 && P->hist) {
     hl = hs.iters < o->hist_cap ? hs.iters : o->hist_cap;
     if (hl) RT_TRY_CUDA(cudaMemcpyAsync(o->resid_hist, P->hist, hl * sizeof(double), cudaMemcpyDeviceToHost, st));
-    RT_TRY_CUDA(cudaStreamSynchronize(st));
   }
-  rt_status s = hs.done == 1 ? RT_OK : hs.done == 2 ? RT_EBREAKDOWN : hs.done == 3 ? RT_ENUMERIC : RT_ENOTCONV;
+  RT_TRY_CUDA(cudaStreamSynchronize(st));
   if (info) {
-    info->iters = hs.iters;
+    info->iters = iters;
     info->applies = applies;
+    info->refine_steps = refine_steps;
     info->rel_resid = rel;
     info->hist_len = hl;
   }
@@ -1612,6 +1694,7 @@ void rt_solver_opts_default(rt_solver_opts* o) {
 }
 
 rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* h_dev, void* stream) {
+  RT_NVTX("rt_arnoldi_mgs");
   clear_error();
   if (!prob || !V_dev || !w_dev || !h_dev) { set_error("prob, V_dev, w_dev and h_dev are required"); return RT_EINVAL; }
   if (j < 0 || j >= kMaxRestart) { set_error("j must be in [0,%d)", kMaxRestart); return RT_EINVAL; }
@@ -1639,6 +1722,7 @@ rt_status rt_arnoldi_mgs(rt_problem* prob, double* V_dev, int32_t j, double* w_d
 
 rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_dev, double* gram_dev,
                           double* h_dev, void* stream) {
+  RT_NVTX("rt_arnoldi_bmgs");
   clear_error();
   if (!prob || !V_dev || !w_dev || !gram_dev || !h_dev) {
     set_error("prob, V_dev, w_dev, gram_dev and h_dev are required");
@@ -1656,6 +1740,7 @@ rt_status rt_arnoldi_bmgs(rt_problem* prob, double* V_dev, int32_t j, double* w_
 
 rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,
                          rt_solve_info* info, void* stream) {
+  RT_NVTX("rt_solve_gmres");
   clear_error();
   if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
   RT_TRY(check_opts(opts, b_dev, x_dev));
@@ -1664,6 +1749,7 @@ rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const dou
 
 rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,
                             rt_solve_info* info, void* stream) {
+  RT_NVTX("rt_solve_bicgstab");
   clear_error();
   if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
   RT_TRY(check_opts(opts, b_dev, x_dev));
@@ -1672,6 +1758,7 @@ rt_status rt_solve_bicgstab(rt_problem* prob, const rt_solver_opts* opts, const 
 
 rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,
                        rt_solve_info* info, void* stream) {
+  RT_NVTX("rt_solve_cgs");
   clear_error();
   if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
   RT_TRY(check_opts(opts, b_dev, x_dev));
@@ -1680,6 +1767,7 @@ rt_status rt_solve_cgs(rt_problem* prob, const rt_solver_opts* opts, const doubl
 
 rt_status rt_solve_richardson(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev, double* x_dev,
                               rt_solve_info* info, void* stream) {
+  RT_NVTX("rt_solve_richardson");
   clear_error();
   if (!prob) { set_error("prob is NULL"); return RT_EINVAL; }
   RT_TRY(check_opts(opts, b_dev, x_dev));
@@ -1710,23 +1798,55 @@ struct StaticScratch {
   int grid_cap = 0;
 };
 std::mutex g_static_mu;
-std::map<int, StaticScratch> g_static_by_device;
+std::map<unsigned long long, StaticScratch> g_static_by_context;
 
-// Device addresses of the static scratch on the current device; looked up
-// once per device (cudaGetSymbolAddress) and cached.
+// Identity of the current device's context: the driver's per-context id,
+// unique for the life of the process, so a context created after a device
+// reset (which reloads the module and moves the array) gets a new entry.
+// Before the context exists (first call in a process), or where the driver
+// does not offer the id, the device ordinal is used; cudaGetSymbolAddress
+// then creates the context, and later calls key on its id (one more lookup).
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+unsigned long long current_context_key(int dev) {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<PfnCtxGetCurrent>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PfnCtxGetId>(fn);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+    return id;
+  return (1ull << 63) | (unsigned long long)dev;
+}
+
+// Device addresses of the static scratch in the current device's context;
+// looked up once per context (cudaGetSymbolAddress, with the device current)
+// and cached.
 rt_status static_scratch_for_current_device(StaticScratch* out) {
   int dev = 0;
   RT_TRY_CUDA(cudaGetDevice(&dev));
+  const unsigned long long key = current_context_key(dev);
   std::lock_guard<std::mutex> lk(g_static_mu);
-  auto it = g_static_by_device.find(dev);
-  if (it == g_static_by_device.end()) {
+  auto it = g_static_by_context.find(key);
+  if (it == g_static_by_context.end()) {
     StaticScratch s;
     RT_TRY_CUDA(cudaGetSymbolAddress((void**)&s.scratch, g_static_scratch));
     RT_TRY_CUDA(cudaGetSymbolAddress((void**)&s.gate, g_static_never_stop));
     int sms = 0;
     RT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     s.grid_cap = 4 * sms < kStaticPartials ? 4 * sms : kStaticPartials;
-    it = g_static_by_device.emplace(dev, s).first;
+    it = g_static_by_context.emplace(key, s).first;
   }
   *out = it->second;
   return RT_OK;
@@ -1737,6 +1857,7 @@ rt_status static_scratch_for_current_device(StaticScratch* out) {
 extern "C" {
 
 rt_status rt_arnoldi_mgs_static(double* V_dev, int64_t N, int32_t j, double* w_dev, double* h_dev, void* stream) {
+  RT_NVTX("rt_arnoldi_mgs_static");
   clear_error();
   if (!V_dev || !w_dev || !h_dev) { set_error("V_dev, w_dev and h_dev are required"); return RT_EINVAL; }
   if (N < 1 || N > RT_ARNOLDI_STATIC_MAX_N) {

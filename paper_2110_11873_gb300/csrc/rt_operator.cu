@@ -359,7 +359,7 @@ void free_device(Problem* P) {
   void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wray,   P->wI2,  P->wQ2,   P->t201d, P->t202d,
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
-                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->St, P->qpart, P->Mdiag, P->Ibuf, P->cg,
+                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->stab, P->qpart, P->qcnt, P->Mdiag, P->Ibuf, P->cg,
                   P->Etile, P->Bmap, P->Asig, P->Mpre, P->Mtri, P->Mscr, P->wjac, P->Kmap};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
@@ -370,7 +370,9 @@ void free_device(Problem* P) {
   P->gm = nullptr;
   P->bc = nullptr;
   P->dev_err = nullptr;
-  P->qw = P->St = P->qpart = nullptr;
+  P->qw = P->qpart = nullptr;
+  P->stab = nullptr;
+  P->qcnt = nullptr;
   P->Mdiag = P->Ibuf = P->cg = P->Etile = P->Bmap = P->Kmap = nullptr;
   P->Asig = P->Mpre = P->Mtri = P->Mscr = P->wjac = nullptr;
   P->asig_ready = 0;
@@ -730,6 +732,7 @@ static void launch_formal32(const Problem* P, const TV* x, TV* y, cudaStream_t s
 
 rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStream_t st, const int* kstop, int step,
                      const NormIn* nin) {
+  RT_NVTX("operator apply FP64");
   if (P->form == RT_FORM_SIGMA) {
     if (nin) {
       set_error("the fused normalisation needs the I-form");
@@ -804,6 +807,7 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
 template <typename TV>
 static rt_status apply32_impl(Problem* P, const TV* x, TV* y, int mode, cudaStream_t st, const int* kstop, int step,
                               const NormIn* nin = nullptr) {
+  RT_NVTX("operator apply FP32");
   if (P->fs == RT_FS_DELO_PARABOLIC) {
     set_error("the DELO-parabolic formal solver is FP64 only (use rt_apply, FP64 solvers)");
     return RT_EINVAL;
@@ -880,6 +884,7 @@ rt_status op_jacobi_weights(Problem* P, cudaStream_t st) {
 }
 
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st) {
+  RT_NVTX("right-hand side");
   if (P->form == RT_FORM_SIGMA) return op_rhs_sigma(P, b, st);
   k_rhs_source<<<grid_for((int64_t)P->Ns * P->Nmu, 256, 4 * P->num_sms), 256, 0, st>>>(P->Bd, P->Ns, P->Nmu, P->eps,
                                                                                       P->S2); RT_COUNT(1);
@@ -944,6 +949,7 @@ rt_status rt_rhs(rt_problem* prob, double* b_dev, void* stream) {
 }
 
 rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream) {
+  RT_NVTX("rt_jacobi_diag");
   RT_TRY(check_prob(prob));
   if (!d_dev) {
     set_error("d_dev is NULL");
@@ -958,6 +964,7 @@ rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream) {
 }
 
 rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double* z_dev, void* stream) {
+  RT_NVTX("rt_precond_local_lambda");
   RT_TRY(check_prob(prob));
   if (!v_dev || !z_dev || v_dev == z_dev) {
     set_error("v_dev and z_dev must be distinct non-NULL device buffers");
@@ -968,6 +975,7 @@ rt_status rt_precond_local_lambda(rt_problem* prob, const double* v_dev, double*
 
 rt_status rt_precond_stationary(rt_problem* prob, int32_t kind, double omega, const double* v_dev, double* z_dev,
                                 void* stream) {
+  RT_NVTX("rt_precond_stationary");
   RT_TRY(check_prob(prob));
   if (!v_dev || !z_dev || v_dev == z_dev) {
     set_error("v_dev and z_dev must be distinct non-NULL device buffers");

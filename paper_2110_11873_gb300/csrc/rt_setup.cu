@@ -17,6 +17,8 @@
 
 #include <atomic>
 #include <complex>
+#include <mutex>
+#include <unordered_map>
 
 #include "rt_common.cuh"
 
@@ -229,9 +231,99 @@ void host_grids(const rt_problem_desc* d, Problem& P) {
 }
 
 
+namespace {
+class HookAlloc : public DevAllocator {
+ public:
+  HookAlloc(const rt_allocator& h, cudaStream_t st) : h_(h), st_(st) {}
+  cudaError_t alloc(void** p, size_t bytes) override {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    void* q = h_.alloc(h_.ctx, bytes, reinterpret_cast<void*>(st_));
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) & 255) {   // the kernels assume 256-byte aligned blocks
+      h_.release(h_.ctx, q, bytes, reinterpret_cast<void*>(st_));
+      return cudaErrorMemoryAllocation;
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      sizes_[q] = bytes;
+    }
+    *p = q;
+    return cudaSuccess;
+  }
+  void release(void* p) override {
+    if (!p) return;
+    size_t bytes = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      auto it = sizes_.find(p);
+      if (it == sizes_.end()) return;
+      bytes = it->second;
+      sizes_.erase(it);
+    }
+    h_.release(h_.ctx, p, bytes, reinterpret_cast<void*>(st_));
+  }
+
+ private:
+  rt_allocator h_;
+  cudaStream_t st_;
+  std::mutex mu_;
+  std::unordered_map<void*, size_t> sizes_;
+};
+}  // namespace
+
+DevAllocator* make_hook_allocator(const rt_allocator* hook, cudaStream_t st) {
+  if (!hook || !hook->alloc || !hook->release) return nullptr;
+  return new (std::nothrow) HookAlloc(*hook, st);
+}
+
 }  // namespace rt
 
 using namespace rt;
+
+static rt_status create_problem(const rt_problem_desc* desc, const rt_allocator* hook, void* stream,
+                                rt_problem** out) {
+  RT_NVTX("rt_problem_create");
+  clear_error();
+  if (!out) { set_error("out is NULL"); return RT_EINVAL; }
+  *out = nullptr;
+  RT_TRY(validate_desc(desc));
+  if (hook && (!hook->alloc || !hook->release)) {
+    set_error("the allocator needs both alloc and release");
+    return RT_EINVAL;
+  }
+  rt_problem* pr = new (std::nothrow) rt_problem();
+  if (!pr) { set_error("host allocation failed"); return RT_ENOMEM; }
+  Problem& P = pr->P;
+  if (hook) {
+    P.own_alloc = make_hook_allocator(hook, as_stream(stream));
+    if (!P.own_alloc) {
+      delete pr;
+      set_error("host allocation failed");
+      return RT_ENOMEM;
+    }
+    P.alloc = P.own_alloc;
+  }
+  host_grids(desc, P);
+  cudaError_t e = cudaGetDevice(&P.device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device);
+  if (e != cudaSuccess) {
+    set_error("no CUDA device: %s", cudaGetErrorString(e));
+    delete P.own_alloc;
+    delete pr;
+    return RT_ECUDA;
+  }
+  rt_status s = setup_device_tables(&P, as_stream(stream));
+  if (s != RT_OK) {
+    if (P.own_alloc) cudaDeviceSynchronize();
+    free_device(&P);
+    delete P.own_alloc;
+    delete pr;
+    return s;
+  }
+  *out = pr;
+  return RT_OK;
+}
 
 extern "C" {
 
@@ -240,35 +332,23 @@ const char* rt_last_error(void) { return rt::g_err.c_str(); }
 int64_t rt_launch_count(void) { return (int64_t)rt::g_launch_count.load(std::memory_order_relaxed); }
 
 rt_status rt_problem_create(const rt_problem_desc* desc, void* stream, rt_problem** out) {
-  clear_error();
-  if (!out) { set_error("out is NULL"); return RT_EINVAL; }
-  *out = nullptr;
-  RT_TRY(validate_desc(desc));
-  rt_problem* pr = new (std::nothrow) rt_problem();
-  if (!pr) { set_error("host allocation failed"); return RT_ENOMEM; }
-  Problem& P = pr->P;
-  host_grids(desc, P);
-  cudaError_t e = cudaGetDevice(&P.device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device);
-  if (e != cudaSuccess) {
-    set_error("no CUDA device: %s", cudaGetErrorString(e));
-    delete pr;
-    return RT_ECUDA;
-  }
-  rt_status s = setup_device_tables(&P, as_stream(stream));
-  if (s != RT_OK) {
-    free_device(&P);
-    delete pr;
-    return s;
-  }
-  *out = pr;
-  return RT_OK;
+  return create_problem(desc, nullptr, stream, out);
+}
+
+rt_status rt_problem_create_with_allocator(const rt_problem_desc* desc, const rt_allocator* allocator, void* stream,
+                                           rt_problem** out) {
+  return create_problem(desc, allocator, stream, out);
 }
 
 rt_status rt_problem_destroy(rt_problem* prob) {
+  RT_NVTX("rt_problem_destroy");
   if (!prob) return RT_OK;
   release_graphs(&prob->P);
+  // a caller's allocator may hand a released block to its next user at once:
+  // nothing of this problem may still be running on the device
+  if (prob->P.own_alloc) cudaDeviceSynchronize();
   free_device(&prob->P);
+  delete prob->P.own_alloc;
   delete prob;
   return RT_OK;
 }
@@ -282,6 +362,16 @@ rt_status rt_problem_check(rt_problem* prob, void* stream) {
 }
 
 int rt_problem_formal_kernel(const rt_problem* prob) { return prob ? prob->P.staged : -1; }
+
+rt_status rt_problem_inject_wait_timeout(rt_problem* prob, int32_t count) {
+  clear_error();
+  if (!prob || count < 0) {
+    set_error("prob is NULL or count < 0");
+    return RT_EINVAL;
+  }
+  prob->P.inject_wait_fail = count;
+  return RT_OK;
+}
 
 rt_status rt_problem_grids(const rt_problem* prob, double* mu, double* w_mu, double* x,
                            double* phi, double* w_nu, double* phi_hat) {

@@ -1,6 +1,7 @@
 // The FP32 operator apply of single problems (sm_103a): a vectorised
-// quadrature (T then J, Eq. 11-14) and a formal solver (Eq. 9-10) whose input
-// streams through shared memory with tensor copies.
+// quadrature (J, Eq. 11-14) that also forms the multipolar components
+// (Eq. 13-14), and a formal solver (Eq. 9-10) whose input streams through
+// shared memory with tensor copies.
 //
 //   k_quad     partial moments.  Each thread owns four consecutive rays (one
 //              16-byte load per Stokes parameter and height) and keeps their
@@ -9,28 +10,32 @@
 //              J00_k = sum_r w0 x_I  and  J20_k = sum_r (w1 x_I + w2 x_Q).
 //              A CTA covers 1024 rays and a range of heights; warp sums are
 //              combined in a fixed order into one partial per (height, CTA
-//              column), so the result does not depend on scheduling.
+//              column).  The last CTA of a grid row to finish (a counter per
+//              row) sums that row's partials over the columns in column order
+//              and writes sigma00 = xi J00, sigma20 = xi W2 J20 (with the
+//              local-Lambda block inverse in that mode) into the operand
+//              tables of the formal solver.  Which CTA finishes last does not
+//              change the sums, so the result does not depend on scheduling.
 //              k_quad_norm is the same inside GMRES with FP64 basis vectors:
 //              it also ends the previous Arnoldi step and forms its input
 //              v = u / ||u|| as it reads u.
-//   k_sigma    sums the partials of a height in a fixed order, forms sigma00,
-//              sigma20 (Eq. 7-8, with the local-Lambda block inverse in that
-//              mode) and writes the source functions transposed, S[s][m][k],
-//              so that a lane walking along a ray reads consecutive words.
-//   k_staged   the formal solve.  A CTA takes 32 rays of one direction sign
-//              and splits the depth into `ntile` tiles, one warp each; the
-//              depth recurrence I_k = e I_prev + alpha S_prev + beta S_k is
-//              solved as an affine scan (tile maps, chained inflows, re-sweep).
-//              In the re-sweep every warp streams its rows of x (and of the
-//              Jacobi diagonal) into a ring of shared-memory stages with
-//              cp.async.bulk.tensor, one 3D box (rays x heights x Stokes) per
-//              stage completing on an mbarrier, so the recurrence never waits
-//              on HBM.  The two Stokes parameters of a lane share the step
-//              coefficients and are updated as one packed FP32x2 operation; the
-//              two Taylor polynomials of the DELO-linear coefficients are
-//              evaluated as one packed pair as well.  The sweep direction is a
-//              template parameter, so operand offsets inside an unrolled round
-//              are compile-time constants.
+//   k_staged   the formal solve (a programmatic dependent of the quadrature:
+//              its set-up, and in a standalone apply its first tensor copies
+//              of x, overlap the quadrature's tail).  A CTA takes 32 rays of
+//              one direction sign and splits the depth into `ntile` tiles,
+//              one warp each; the depth recurrence
+//              I_k = e I_prev + alpha S_prev + beta S_k is solved as an affine
+//              scan (tile maps, chained inflows, re-sweep).  The step
+//              coefficients are recomputed in FP32 from the node table and
+//              the ray's scale; where Delta is small, alpha and beta come from
+//              one Taylor series.  In the re-sweep every warp streams its rows of x (and
+//              of the Jacobi diagonal) into a ring of shared-memory stages
+//              with cp.async.bulk.tensor, one 3D box (rays x heights x Stokes)
+//              per stage completing on an mbarrier, so the recurrence never
+//              waits on HBM.  The per-node operands (sigma00, sigma20 and the
+//              interval's optical depth) come from a table indexed along the
+//              march, so both directions read it forwards; S_I and S_Q follow
+//              from the lane's T201_m, T202_m (Eq. 7-8).
 //
 // Every mbarrier wait is bounded (kWaitNs of wall time): a warp whose copy
 // does not arrive sets the problem's device error flag, waits (again
@@ -43,6 +48,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -68,13 +74,11 @@ namespace {
 #ifndef RT_STAGED_MINB
 #define RT_STAGED_MINB 2
 #endif
-#ifndef RT_STAGED_WARPS_PER_SM
-#define RT_STAGED_WARPS_PER_SM 48
-#endif
 
 constexpr int kNST = RT_STAGED_NST;            // stages per warp
-constexpr int kRS = RT_STAGED_RS;              // prefetch distance of dtau and S (steps)
+constexpr int kRS = RT_STAGED_RS;              // prefetch distance of the node operands (steps)
 constexpr int kMaxT = RT_STAGED_MAXT;          // warps per CTA (depth tiles of a ray group)
+constexpr int kTabPad = 2 * kRS;               // table entries past the last node (prefetch reads them)
 constexpr unsigned long long kWaitNs = 1000000000ull;   // bound of one wait
 constexpr int kQuadThreads = 256;
 constexpr int kQuadMaxHeights = 64;            // heights per CTA of k_quad
@@ -149,41 +153,75 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
-// ------------------------------------------------------- packed FP32 pairs
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 neg2(float2 a) { return f2(-a.x, -a.y); }
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* tm) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
+}
 
-// The step coefficients of coeffs32 (same values, bit for bit): the Taylor
-// polynomials of beta and alpha run as one packed pair.
+// 2^a by the hardware's approximate exponential (a <= 0 here)
+__device__ __forceinline__ float ex2_approx(float a) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
+// ------------------------------------------------------ step coefficients
+// The coefficients of I_k = e I_prev + alpha S_prev + beta S_k from the node
+// operand op (op.z, op.w: the interval constants of the table) and the ray's
+// scale rsc = phi_hat_p / |mu_m| (irsc = 1 / rsc); Delta = dtau * rsc.
+//   DELO-linear: op.z = dtau / ln 2, op.w = 1 / dtau; D2 = Delta / ln 2 and
+//     e = 2^(-D2) = exp(-Delta).  With q = (1 - e) / Delta, beta = 1 - q and
+//     alpha = q - e.  For Delta < 1/2 those differences cancel, so there
+//       h = beta / Delta = sum_n (-Delta)^n / (n+2)!   (from the series of
+//       e^-Delta), truncated after n = 7 (relative error below 1e-8),
+//       beta = Delta h,   alpha = Delta (1 - (1 + Delta) h),
+//     the last from 1 - e = Delta g, g = 1 - Delta h, alpha = (1 - e) - beta;
+//     1 - (1 + Delta) h stays near 1/2, so alpha keeps its relative accuracy.
+//     Both branches are evaluated and one is selected (no divergence).
+//     Above 1/2, q's rounding error is below 2e-7.
+//   implicit Euler: op.z = dtau; e = 1 / (1 + Delta), alpha = 0, beta = Delta e.
+//   trapezoidal: op.z = dtau; h = Delta / 2, q = 1 / (1 + h), e = (1 - h) q,
+//     alpha = beta = h q.
+//   (reciprocals by the hardware approximation, within 2 ulp)
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr float kSeriesD2 = (float)(0.5 / kLn2);
+
+// (-1)^n ln2^(n+1) / (n+2)!: the series of beta / D2 in powers of D2
+constexpr double pow_ln2(int k) { return k == 0 ? 1.0 : kLn2 * pow_ln2(k - 1); }
+constexpr double fact(int k) { return k <= 1 ? 1.0 : k * fact(k - 1); }
+constexpr float kB(int n) { return (float)((n % 2 ? -1.0 : 1.0) * pow_ln2(n + 1) / fact(n + 2)); }
+
 template <int FS>
-__device__ __forceinline__ void coeffs_packed(float D, float& e, float& al, float& be) {
+__device__ __forceinline__ void step_coeffs(const float4& op, float rsc, float irsc, float& e, float& al, float& be) {
   if (FS == RT_FS_DELO_LINEAR) {
-    e = __expf(-D);
-    if (D < 0.5f) {
-      const float2 DD = f2(D, D);
-      float2 ba = f2(-1.0f / 3628800.0f, -9.0f / 3628800.0f);
-      ba = fma2(ba, DD, f2(1.0f / 362880.0f, 8.0f / 362880.0f));
-      ba = fma2(ba, DD, f2(-1.0f / 40320.0f, -7.0f / 40320.0f));
-      ba = fma2(ba, DD, f2(1.0f / 5040.0f, 6.0f / 5040.0f));
-      ba = fma2(ba, DD, f2(-1.0f / 720.0f, -5.0f / 720.0f));
-      ba = fma2(ba, DD, f2(1.0f / 120.0f, 4.0f / 120.0f));
-      ba = fma2(ba, DD, f2(-1.0f / 24.0f, -3.0f / 24.0f));
-      ba = fma2(ba, DD, f2(1.0f / 6.0f, 2.0f / 6.0f));
-      ba = fma2(ba, DD, f2(-0.5f, -0.5f));
-      const float2 r = mul2(ba, f2(-D, -D));
-      be = r.x;
-      al = r.y;
-    } else {
-      const float q = __fdividef(1.0f - e, D);
-      const float2 r = add2(f2(1.0f, q), f2(-q, -e));
-      be = r.x;
-      al = r.y;
-    }
+    const float D2 = op.z * rsc;
+    e = ex2_approx(-D2);
+    float hb = kB(7);
+    hb = fmaf(hb, D2, kB(6));
+    hb = fmaf(hb, D2, kB(5));
+    hb = fmaf(hb, D2, kB(4));
+    hb = fmaf(hb, D2, kB(3));
+    hb = fmaf(hb, D2, kB(2));
+    hb = fmaf(hb, D2, kB(1));
+    hb = fmaf(hb, D2, kB(0));
+    const float bs = hb * D2;
+    const float onep = fmaf(D2, (float)kLn2, 1.0f);
+    const float as = D2 * fmaf(-onep, hb, (float)kLn2);
+    const float iD = op.w * irsc;
+    const float q = fmaf(-e, iD, iD);
+    const bool thin = D2 < kSeriesD2;
+    be = thin ? bs : 1.0f - q;
+    al = thin ? as : q - e;
+  } else if (FS == RT_FS_IMPLICIT_EULER) {
+    const float D = op.z * rsc;
+    e = __fdividef(1.0f, 1.0f + D);
+    al = 0.0f;
+    be = D * e;
   } else {
-    coeffs32<FS>(D, e, al, be);
+    const float h = 0.5f * op.z * rsc;
+    const float q = __fdividef(1.0f, 1.0f + h);
+    e = (1.0f - h) * q;
+    al = h * q;
+    be = al;
   }
 }
 
@@ -213,16 +251,31 @@ __device__ __forceinline__ float4 load4_scaled(const double* u, double inv, doub
   return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
 }
 
+// Where the quadrature puts its result: the multipolar components of every
+// height go into the .xy of the formal solver's node tables, march-indexed
+// per direction (tab[k] downward, tab[Ns + kTabPad + Ns-1-k] upward).
+struct QuadOut {
+  float* part;          // [Ns][gridDim.x][2] partial moments
+  int* cnt;             // [rows] CTAs of a grid row done (reset by the last one)
+  float4* tab;          // [2][Ns + kTabPad] node operands
+  const double* Minv;   // [Ns][4] local-Lambda block inverses (KM_LOCAL_LAMBDA)
+  float xi, xiW2;
+  int Ns;
+};
+
 // The partials of the heights of row ky of the grid, rays of column
-// blockIdx.x (all threads of the CTA call it).  NORM: the input is u * inv,
+// blockIdx.x (all threads of the CTA call it); the last CTA of the row then
+// forms sigma00, sigma20 of the row's heights.  NORM: the input is u * inv,
 // written to xo as it is read.
 template <typename TV, int MODE, bool NORM>
 __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double* __restrict__ dinv,
-                                          const float* __restrict__ qw, int Ns, int64_t nray, int hpc,
-                                          float* __restrict__ part, int ky, const double* __restrict__ u = nullptr,
-                                          double inv = 1.0, double* __restrict__ xo = nullptr) {
+                                          const float* __restrict__ qw, int64_t nray, int hpc, const QuadOut& Q,
+                                          int ky, const double* __restrict__ u = nullptr, double inv = 1.0,
+                                          double* __restrict__ xo = nullptr) {
   constexpr int nw = kQuadThreads / 32;
   __shared__ float red[kQuadMaxHeights][nw][2];
+  __shared__ int last;
+  const int Ns = Q.Ns;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nc = nray / 4;
   const int64_t c = (int64_t)blockIdx.x * kQuadThreads + threadIdx.x;
@@ -285,18 +338,48 @@ __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double
       s0 += red[i][w][0];
       s2 += red[i][w][1];
     }
-    float* o = part + ((int64_t)(k_lo + i) * gridDim.x + blockIdx.x) * 2;
+    float* o = Q.part + ((int64_t)(k_lo + i) * gridDim.x + blockIdx.x) * 2;
     o[0] = s0;
     o[1] = s2;
   }
+  // publish the partials, then count this CTA in its row
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(Q.cnt + ky, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int gx = gridDim.x;
+  for (int i = threadIdx.x; i < k_hi - k_lo; i += kQuadThreads) {
+    const int k = k_lo + i;
+    const float* p = Q.part + (int64_t)k * gx * 2;
+    float a = 0.f, b = 0.f;
+    for (int j = 0; j < gx; ++j) {   // column order, whichever CTA came last
+      a += __ldcg(p + 2 * j);
+      b += __ldcg(p + 2 * j + 1);
+    }
+    float s0 = Q.xi * a, s2 = Q.xiW2 * b;
+    if (MODE == KM_LOCAL_LAMBDA) {
+      const double* Mi = Q.Minv + 4 * k;
+      const float u0 = fmaf((float)Mi[0], s0, (float)Mi[1] * s2);
+      const float u2 = fmaf((float)Mi[2], s0, (float)Mi[3] * s2);
+      s0 = u0;
+      s2 = u2;
+    }
+    const float2 sg = make_float2(s0, s2);
+    reinterpret_cast<float2*>(Q.tab + k)[0] = sg;
+    reinterpret_cast<float2*>(Q.tab + (Ns + kTabPad) + (Ns - 1 - k))[0] = sg;
+  }
+  if (threadIdx.x == 0) Q.cnt[ky] = 0;   // ready for the next launch (stream-ordered)
 }
 
 template <typename TV, int MODE>
-__global__ void __launch_bounds__(kQuadThreads) k_quad(const TV* __restrict__ x, const double* __restrict__ dinv,
-                                                       const float* __restrict__ qw, int Ns, int64_t nray, int hpc,
-                                                       float* __restrict__ part, const int* kstop, int step) {
+__global__ void __launch_bounds__(kQuadThreads, sizeof(TV) == 4 ? 8 : 4) k_quad(const TV* __restrict__ x, const double* __restrict__ dinv,
+                                                       const float* __restrict__ qw, int64_t nray, int hpc,
+                                                       const QuadOut Q, const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
-  quad_tile<TV, MODE, false>(x, dinv, qw, Ns, nray, hpc, part, blockIdx.y);
+  pdl_launch_dependents();
+  quad_tile<TV, MODE, false>(x, dinv, qw, nray, hpc, Q, blockIdx.y);
 }
 
 // k_quad inside GMRES with FP64 vectors, fused with the end of Arnoldi step
@@ -307,59 +390,33 @@ __global__ void __launch_bounds__(kQuadThreads) k_quad(const TV* __restrict__ x,
 // fold itself may end the cycle.
 template <int MODE>
 __global__ void __launch_bounds__(kQuadThreads) k_quad_norm(double* __restrict__ x, const double* __restrict__ dinv,
-                                                            const float* __restrict__ qw, int Ns, int64_t nray,
-                                                            int hpc, float* __restrict__ part, const NormIn nin) {
+                                                            const float* __restrict__ qw, int64_t nray, int hpc,
+                                                            const QuadOut Q, const NormIn nin) {
   if (nin.kstop && nin.jprev >= *nin.kstop) return;
+  pdl_launch_dependents();
   if (blockIdx.y == 0) {
     if (blockIdx.x == 0)
       arnoldi_fold(nin.part, nin.Gp, nin.ng, nin.hcol, nin.gram, nin.gm, nin.m, nin.jprev, nin.hist, nin.hist_cap);
     return;
   }
   const double inv = arnoldi_inv_norm(nin.part, nin.Gp);
-  quad_tile<double, MODE, true>(nullptr, dinv, qw, Ns, nray, hpc, part, blockIdx.y - 1, nin.u, inv, x);
-}
-
-// --------------------------------------------------------------- k_sigma
-// One thread per (m, k): sum the gx partials of height k in order, then
-// S_I = sigma00 + T201_m sigma20, S_Q = T202_m sigma20 into St[s][m][k].
-template <int MODE>
-__global__ void k_sigma(const float* __restrict__ part, int gx, const float* __restrict__ t201,
-                        const float* __restrict__ t202, const double* __restrict__ Minv, int Ns, int Nmu, float xi,
-                        float xiW2, float* __restrict__ St, const int* kstop, int step) {
-  if (kstop && step >= *kstop) return;
-  const int64_t n = (int64_t)Ns * Nmu;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(i % Ns), m = (int)(i / Ns);
-    const float* p = part + (int64_t)k * gx * 2;
-    float a = 0.f, b = 0.f;
-    for (int j = 0; j < gx; ++j) {
-      a += p[2 * j];
-      b += p[2 * j + 1];
-    }
-    float s0 = xi * a, s2 = xiW2 * b;
-    if (MODE == KM_LOCAL_LAMBDA) {
-      const double* Mi = Minv + 4 * k;
-      const float u0 = (float)Mi[0] * s0 + (float)Mi[1] * s2;
-      const float u2 = (float)Mi[2] * s0 + (float)Mi[3] * s2;
-      s0 = u0;
-      s2 = u2;
-    }
-    St[i] = s0 + t201[m] * s2;
-    St[n + i] = t202[m] * s2;
-  }
+  quad_tile<double, MODE, true>(nullptr, dinv, qw, nray, hpc, Q, blockIdx.y - 1, nin.u, inv, x);
 }
 
 // -------------------------------------------------------------- k_staged
 struct StagedArgs {
-  const void* x;          // input (TV), [2][Ns][nray]
-  void* y;                // output (TV)
+  void* y;                // output (TV), [2][Ns][nray]
+  const void* x;          // input (TV): read through the tensor maps; the entry node directly
   const double* dinv;     // Jacobi diagonal (KM_JACOBI)
-  const float* dtau;      // [Ns-1]
+  const float4* tab;      // [2][Ns + kTabPad] node operands, march-indexed per direction
   const float* r32;       // [nray] phi_hat / |mu|
-  const float* St;        // source functions [2][Nmu][Ns]
-  int Ns, Nmu, Nnu;
+  const float* t201;      // [Nmu]
+  const float* t202;      // [Nmu]
+  int Ns, Nnu;
   int64_t nray, nd;
-  int ngd, ntile;
+  int ngd, ntile, L;      // downward ray groups, tiles per group, steps per tile
+  int early;              // 1: x is ready before the quadrature ends (copies may start at once)
+  int fail_wait;          // 1: the first wait of CTA 0, warp 0 gives up (failure injection)
   const int* kstop;
   int step;
   int* err;
@@ -372,82 +429,19 @@ struct Maps {
   CUtensorMap d[2];
 };
 
-template <bool DOWN>
-__device__ __forceinline__ constexpr int dir(int v) {
-  return DOWN ? v : -v;
-}
-
-// ring of the next kRS steps' dtau and S (both Stokes parameters)
-struct Operands {
-  const float* dt;   // dtau of the interval of the ring's first step
-  const float* sI;   // S_I at the height of the ring's first step
-  int64_t sq;        // S_Q - S_I
-  float re[kRS];
-  float2 ss[kRS];
-};
-
-template <bool DOWN>
-__device__ __forceinline__ void opload(Operands& O, int u, int ahead) {
-  O.re[u] = O.dt[dir<DOWN>(ahead)];
-  O.ss[u] = f2(O.sI[dir<DOWN>(ahead)], O.sI[O.sq + dir<DOWN>(ahead)]);
-}
-
-template <bool DOWN>
-__device__ __forceinline__ void opadvance(Operands& O) {
-  O.dt += dir<DOWN>(kRS);
-  O.sI += dir<DOWN>(kRS);
-}
-
-// phase A: map I_out = E I_in + B of n1 steps with zero inflow
-template <int FS, bool DOWN>
-__device__ __forceinline__ void tile_map(Operands O, float rsc, float2 sp, int n1, float& E, float2& B) {
-#pragma unroll
-  for (int u = 0; u < kRS; ++u)
-    if (u < n1) opload<DOWN>(O, u, u);
-  auto step = [&](int u) {
-    float e, al, be;
-    coeffs_packed<FS>(O.re[u] * rsc, e, al, be);
-    E *= e;
-    B = fma2(f2(e, e), B, fma2(f2(al, al), sp, mul2(f2(be, be), O.ss[u])));
-    sp = O.ss[u];
-  };
-  int n = 0;
-  for (; n + 2 * kRS <= n1; n += kRS) {
-#pragma unroll
-    for (int u = 0; u < kRS; ++u) {
-      step(u);
-      opload<DOWN>(O, u, u + kRS);
-    }
-    opadvance<DOWN>(O);
-  }
-  for (; n < n1; n += kRS) {
-#pragma unroll
-    for (int u = 0; u < kRS; ++u) {
-      if (n + u < n1) {
-        step(u);
-        if (n + u + kRS < n1) opload<DOWN>(O, u, u + kRS);
-      }
-    }
-    opadvance<DOWN>(O);
-  }
-}
-
 template <typename TV, int FS, int MODE, bool DOWN>
 __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, unsigned char* dsm,
                                             float (*sh)[kMaxT][32], int g, int t, int lane) {
   using C = Cfg<TV, MODE>;
   constexpr int DK = C::DK;
-  const int T = A.ntile, Ns = A.Ns;
+  const int T = A.ntile, Ns = A.Ns, L = A.L;
   const int h = DOWN ? 0 : 1;
   const int64_t hbase = DOWN ? 0 : A.nd;
   const int64_t hext = DOWN ? A.nd : A.nray - A.nd;
   const int c0 = (DOWN ? g : g - A.ngd) * 32;   // first ray of the group within its half
   const bool active = c0 + lane < hext;
   const int64_t r = hbase + (active ? c0 + lane : hext - 1);
-  const int m = (int)(r / A.Nnu);
-  const float rsc = A.r32[r];
-  const int L = (Ns - 1 + T - 1) / T;   // steps per tile
-  const int j0 = 1 + t * L;
+  const int j0 = 1 + t * L;                     // first step of the tile (march index)
   const int n1 = max(min(Ns, j0 + L) - j0, 0);
   const int nst = (n1 + DK - 1) / DK;
   unsigned char* wbase = dsm + (size_t)t * kNST * C::STAGE;
@@ -463,28 +457,60 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
   if (lane == 0 && nst > 0) {
     for (int s = 0; s < kNST; ++s) mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int q = 0; q < kNST && q < nst; ++q) issue(q);   // they land while the tile maps are composed
+    if (A.early)   // x is not written by the kernels before this one
+      for (int q = 0; q < kNST && q < nst; ++q) issue(q);
   }
+  const int m = (int)(r / A.Nnu);
+  const float rsc = __ldg(A.r32 + r);
+  const float irsc = 1.0f / rsc;
+  const float t201 = __ldg(A.t201 + m), t202 = __ldg(A.t202 + m);
+  // the node operands (sigma, written by the quadrature) are read after this
+  pdl_wait();
   __syncwarp();
-  // operands at the tile's first step; upwind S at the node before it
-  Operands O;
-  O.sq = (int64_t)A.Nmu * Ns;
-  O.dt = A.dtau + (DOWN ? j0 - 1 : Ns - 1 - j0);
-  O.sI = A.St + (int64_t)m * Ns + (DOWN ? j0 : Ns - 1 - j0);
-  float2 sp0 = f2(0.f, 0.f);
-  if (n1 > 0) sp0 = f2(O.sI[dir<DOWN>(-1)], O.sI[O.sq + dir<DOWN>(-1)]);
-  float2 I = f2(0.f, 0.f);
+  if (lane == 0 && nst > 0 && !A.early)
+    for (int q = 0; q < kNST && q < nst; ++q) issue(q);   // they land while the tile maps are composed
+  __syncwarp();
+  const float4* tab = A.tab + (size_t)h * (Ns + kTabPad);
+  float II = 0.f, IQ = 0.f;   // I at the tile's inflow node (zero inflow at the entry node)
   if (T > 1) {
+    // phase A: the tile's map I_out = E I_in + B (zero inflow gives B)
     if (t < T - 1 && n1 > 0) {
-      float E = 1.f;
-      float2 B = f2(0.f, 0.f);
-      tile_map<FS, DOWN>(O, rsc, sp0, n1, E, B);
+      float4 ring[kRS];
+      const float4* pn = tab + j0;
+#pragma unroll
+      for (int u = 0; u < kRS; ++u) ring[u] = __ldg(pn + u);
+      const float4 pp = __ldg(tab + j0 - 1);
+      float sIp = fmaf(t201, pp.y, pp.x), sQp = t202 * pp.y;
+      float E = 1.f, BI = 0.f, BQ = 0.f;
+      auto stepA = [&](const float4& op) {
+        float e, al, be;
+        step_coeffs<FS>(op, rsc, irsc, e, al, be);
+        const float sI = fmaf(t201, op.y, op.x), sQ = t202 * op.y;
+        BI = fmaf(e, BI, fmaf(al, sIp, be * sI));
+        BQ = fmaf(e, BQ, fmaf(al, sQp, be * sQ));
+        E *= e;
+        sIp = sI;
+        sQp = sQ;
+      };
+      int n = 0;
+      for (; n + kRS <= n1; n += kRS) {
+#pragma unroll
+        for (int u = 0; u < kRS; ++u) {
+          const float4 op = ring[u];
+          ring[u] = __ldg(pn + kRS + u);   // the table is padded past the last node
+          stepA(op);
+        }
+        pn += kRS;
+      }
+#pragma unroll
+      for (int u = 0; u < kRS; ++u)
+        if (n + u < n1) stepA(ring[u]);
       sh[0][t][lane] = E;
-      sh[1][t][lane] = B.x;
-      sh[2][t][lane] = B.y;
+      sh[1][t][lane] = BI;
+      sh[2][t][lane] = BQ;
     }
     __syncthreads();
-    if (t == 0) {
+    if (t == 0) {   // phase B: chain the maps into every tile's inflow
       float in0 = 0.f, in1 = 0.f;
       for (int u = 0; u < T; ++u) {
         const bool has = u < T - 1 && 1 + u * L < Ns;
@@ -499,10 +525,11 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
       }
     }
     __syncthreads();
-    I = f2(sh[1][t][lane], sh[2][t][lane]);
+    II = sh[1][t][lane];
+    IQ = sh[2][t][lane];
   }
   const int64_t plane = (int64_t)Ns * A.nray;
-  // entry node (tile 0): zero inflow
+  // entry node (tile 0): zero inflow, so y = x there
   if (t == 0 && active) {
     const int64_t o = (int64_t)(DOWN ? 0 : Ns - 1) * A.nray + r;
     const TV* x = reinterpret_cast<const TV*>(A.x);
@@ -516,14 +543,22 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
   // phase C: re-sweep from the tile's inflow, x from the staged ring
   TV* yI = reinterpret_cast<TV*>(A.y) + (int64_t)(DOWN ? j0 : Ns - 1 - j0) * A.nray + r;
   const int64_t dy = DOWN ? A.nray : -A.nray;
-  float2 sp = sp0;
+  float4 ring[kRS];
+  const float4* pn = tab + j0;
 #pragma unroll
-  for (int u = 0; u < kRS; ++u)
-    if (u < n1) opload<DOWN>(O, u, u);
+  for (int u = 0; u < kRS; ++u) ring[u] = __ldg(pn + u);
+  float sIp, sQp;
+  {
+    const float4 pp = __ldg(tab + j0 - 1);
+    sIp = fmaf(t201, pp.y, pp.x);
+    sQp = t202 * pp.y;
+  }
   int qfail = -1;
   for (int q = 0; q < nst; ++q) {
     const int slot = q % kNST;
-    const bool ok = mbar_wait(&bar[slot], (uint32_t)((q / kNST) & 1));
+    bool ok;
+    if (A.fail_wait && q == 0 && t == 0 && blockIdx.x == 0) ok = false;   // injected: the wait gives up
+    else ok = mbar_wait(&bar[slot], (uint32_t)((q / kNST) & 1));
     if (!__all_sync(0xffffffffu, ok)) {
       qfail = q;
       break;
@@ -531,44 +566,50 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
     const TV* xs = reinterpret_cast<const TV*>(wbase + slot * C::STAGE);
     const double* ds = reinterpret_cast<const double*>(wbase + slot * C::STAGE + C::XBYTES);
     const int nb = q * DK;
-    auto step = [&](int u, bool guard) {
+    auto step = [&](int u) {
       const int ru = u % kRS;
       const int row = DOWN ? u : DK - 1 - u;   // the box runs up in height
+      const float4 op = ring[ru];
+      ring[ru] = __ldg(pn + kRS + ru);
+      if (ru == kRS - 1) pn += kRS;
       float e, al, be;
-      coeffs_packed<FS>(O.re[ru] * rsc, e, al, be);
-      const float2 xv = f2((float)xs[row * 32 + lane], (float)xs[(DK + row) * 32 + lane]);
-      const float2 ss = O.ss[ru];
-      float2 yv;
+      step_coeffs<FS>(op, rsc, irsc, e, al, be);
+      const float sI = fmaf(t201, op.y, op.x), sQ = t202 * op.y;
+      const float xI = (float)xs[row * 32 + lane], xQ = (float)xs[(DK + row) * 32 + lane];
+      float yvI, yvQ;
       if (MODE == KM_LOCAL_LAMBDA) {
-        const float2 tt = fma2(f2(e, e), I, mul2(f2(al, al), sp));
-        yv = add2(xv, neg2(tt));
-        I = fma2(f2(be, be), ss, tt);
+        // y = x - (I - beta S): the step without its beta S_k term
+        const float tI = fmaf(e, II, al * sIp), tQ = fmaf(e, IQ, al * sQp);
+        yvI = xI - tI;
+        yvQ = xQ - tQ;
+        II = fmaf(be, sI, tI);
+        IQ = fmaf(be, sQ, tQ);
       } else {
-        I = fma2(f2(e, e), I, fma2(f2(al, al), sp, mul2(f2(be, be), ss)));
+        II = fmaf(e, II, fmaf(al, sIp, be * sI));
+        IQ = fmaf(e, IQ, fmaf(al, sQp, be * sQ));
         if (MODE == KM_JACOBI) {
-          const float2 dv = f2((float)ds[row * 32 + lane], (float)ds[(DK + row) * 32 + lane]);
-          yv = fma2(xv, dv, neg2(I));
+          yvI = fmaf(xI, (float)ds[row * 32 + lane], -II);
+          yvQ = fmaf(xQ, (float)ds[(DK + row) * 32 + lane], -IQ);
         } else {
-          yv = add2(xv, neg2(I));
+          yvI = xI - II;
+          yvQ = xQ - IQ;
         }
       }
-      sp = ss;
+      sIp = sI;
+      sQp = sQ;
       if (active) {
-        yI[0] = (TV)yv.x;
-        yI[plane] = (TV)yv.y;
+        yI[0] = (TV)yvI;
+        yI[plane] = (TV)yvQ;
       }
       yI += dy;
-      // refill this ring slot with the operands kRS steps ahead
-      if (!guard || nb + u + kRS < n1) opload<DOWN>(O, ru, kRS + ru);
-      if (ru == kRS - 1) opadvance<DOWN>(O);
     };
-    if (nb + DK + kRS <= n1) {
+    if (nb + DK <= n1) {
 #pragma unroll
-      for (int u = 0; u < DK; ++u) step(u, false);
+      for (int u = 0; u < DK; ++u) step(u);
     } else {
 #pragma unroll
       for (int u = 0; u < DK; ++u)
-        if (nb + u < n1) step(u, true);
+        if (nb + u < n1) step(u);
     }
     __syncwarp();
     if (lane == 0 && q + kNST < nst) {
@@ -579,8 +620,9 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
     __syncwarp();
   }
   if (qfail >= 0) {
-    // a copy did not arrive: flag it and wait (bounded) for the copies
-    // still in flight before the CTA's shared memory is released
+    // a copy did not arrive (or the wait was told to give up): flag it and
+    // wait (bounded) for the copies still in flight before the CTA's shared
+    // memory is released
     if (lane == 0) atomicExch(A.err, 1);
     const int last = min(nst, qfail + kNST);
     for (int q = qfail; q < last; ++q) mbar_wait(&bar[q % kNST], (uint32_t)((q / kNST) & 1));
@@ -590,12 +632,22 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
 template <typename TV, int FS, int MODE>
 __global__ void __launch_bounds__(32 * kMaxT, RT_STAGED_MINB)
     k_staged(const StagedArgs A, const __grid_constant__ Maps M) {
-  if (A.kstop && A.step >= *A.kstop) return;
   extern __shared__ unsigned char dsm_raw[];
   unsigned char* dsm = dsm_raw + ((128 - (smem_u32(dsm_raw) & 127)) & 127);   // 128-byte aligned stages
   __shared__ float sh[3][kMaxT][32];   // per tile: E and B, then the tile's inflow
+  __shared__ int gate;
   const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
   const int g = blockIdx.x;
+  if (threadIdx.x == 0) {
+    prefetch_tensormap(&M.x[g < A.ngd ? 0 : 1]);
+    if (MODE == KM_JACOBI) prefetch_tensormap(&M.d[g < A.ngd ? 0 : 1]);
+  }
+  if (A.kstop) {   // inside a captured cycle: the step counter is written by the kernels before
+    pdl_wait();
+    if (threadIdx.x == 0) gate = A.step >= *A.kstop;
+    __syncthreads();
+    if (gate) return;
+  }
   if (g < A.ngd) staged_body<TV, FS, MODE, true>(A, M, dsm, sh, g, t, lane);
   else staged_body<TV, FS, MODE, false>(A, M, dsm, sh, g, t, lane);
 }
@@ -643,26 +695,40 @@ bool encode_half(CUtensorMap* tm, const void* base, int64_t first_ray, int64_t n
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// the formal solver as a programmatic dependent of the quadrature
+template <typename TV, int FS, int MODE>
+cudaError_t launch_staged_fs(const Problem* P, const StagedArgs& A, const Maps& M, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P->ngroups);
+  cfg.blockDim = dim3(32 * P->ntile_st);
+  cfg.dynamicSmemBytes = smem_bytes(Cfg<TV, MODE>::WARP, P->ntile_st);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_staged<TV, FS, MODE>, A, M);
+}
+
 template <typename TV, int MODE>
-void launch_staged(const Problem* P, const StagedArgs& A, const Maps& M, cudaStream_t st) {
-  const dim3 grid(P->ngroups), block(32 * P->ntile_st);
-  const size_t sm = smem_bytes(Cfg<TV, MODE>::WARP, P->ntile_st);
+cudaError_t launch_staged(const Problem* P, const StagedArgs& A, const Maps& M, cudaStream_t st) {
+  RT_COUNT(1);
   switch (P->fs) {
     case RT_FS_DELO_LINEAR:
-      k_staged<TV, RT_FS_DELO_LINEAR, MODE><<<grid, block, sm, st>>>(A, M); RT_COUNT(1);
-      break;
+      return launch_staged_fs<TV, RT_FS_DELO_LINEAR, MODE>(P, A, M, st);
     case RT_FS_IMPLICIT_EULER:
-      k_staged<TV, RT_FS_IMPLICIT_EULER, MODE><<<grid, block, sm, st>>>(A, M); RT_COUNT(1);
-      break;
+      return launch_staged_fs<TV, RT_FS_IMPLICIT_EULER, MODE>(P, A, M, st);
     default:
-      k_staged<TV, RT_FS_TRAPEZOIDAL, MODE><<<grid, block, sm, st>>>(A, M); RT_COUNT(1);
+      return launch_staged_fs<TV, RT_FS_TRAPEZOIDAL, MODE>(P, A, M, st);
   }
 }
 
 template <typename TV, int MODE>
 rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step,
-                       const NormIn* nin = nullptr) {
+                       const NormIn* nin = nullptr, int fail_wait = 0) {
   constexpr bool f64 = sizeof(TV) == 8;
+  RT_NVTX("FP32 apply: k_quad + k_staged");
   Maps M;
   memset(&M, 0, sizeof M);
   const int dk = Cfg<TV, MODE>::DK;
@@ -675,62 +741,84 @@ rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const in
     set_error("cuTensorMapEncodeTiled failed for the Jacobi diagonal");
     return RT_ECUDA;
   }
-  const float xi = (float)P->xi, xiW2 = (float)(P->xi * P->W2);
+  QuadOut Q;
+  Q.part = P->qpart;
+  Q.cnt = P->qcnt;
+  Q.tab = P->stab;
+  Q.Minv = P->Minv;
+  Q.xi = (float)P->xi;
+  Q.xiW2 = (float)(P->xi * P->W2);
+  Q.Ns = P->Ns;
   if (nin) {   // FP64 vectors only (staged_apply32): x is written here as u / ||u||
     k_quad_norm<MODE><<<dim3(P->quad_gx, P->quadn_gy + 1), kQuadThreads, 0, st>>>(
-        const_cast<double*>(reinterpret_cast<const double*>(x)), P->dinv, P->qw, P->Ns, P->nray, P->quadn_hpc,
-        P->qpart, *nin);
+        const_cast<double*>(reinterpret_cast<const double*>(x)), P->dinv, P->qw, P->nray, P->quadn_hpc, Q, *nin);
   } else {
-    k_quad<TV, MODE><<<dim3(P->quad_gx, P->quad_gy), kQuadThreads, 0, st>>>(x, P->dinv, P->qw, P->Ns, P->nray,
-                                                                            P->quad_hpc, P->qpart, kstop, step);
+    k_quad<TV, MODE><<<dim3(P->quad_gx, P->quad_gy), kQuadThreads, 0, st>>>(x, P->dinv, P->qw, P->nray,
+                                                                             P->quad_hpc, Q, kstop, step);
   }
-  RT_COUNT(1);
-  const int64_t nsig = (int64_t)P->Ns * P->Nmu;
-  const int gs = (int)std::min<int64_t>((nsig + 255) / 256, 4LL * P->num_sms);
-  k_sigma<MODE == KM_LOCAL_LAMBDA ? KM_LOCAL_LAMBDA : KM_PLAIN><<<gs, 256, 0, st>>>(
-      P->qpart, P->quad_gx, P->t201f, P->t202f, P->Minv, P->Ns, P->Nmu, xi, xiW2, P->St, kstop, step);
   RT_COUNT(1);
   StagedArgs A;
   A.x = x;
   A.y = y;
   A.dinv = P->dinv;
-  A.dtau = P->dtau32;
+  A.tab = P->stab;
   A.r32 = P->r32;
-  A.St = P->St;
+  A.t201 = P->t201f;
+  A.t202 = P->t202f;
   A.Ns = P->Ns;
-  A.Nmu = P->Nmu;
   A.Nnu = P->Nnu;
   A.nray = P->nray;
   A.nd = P->nd;
   A.ngd = P->ngroups / 2;
   A.ntile = P->ntile_st;
+  A.L = (P->Ns - 1 + P->ntile_st - 1) / P->ntile_st;
+  A.early = (!nin && !kstop) ? 1 : 0;
+  A.fail_wait = fail_wait;
   A.kstop = kstop;
   A.step = step;
   A.err = P->dev_err;
-  launch_staged<TV, MODE>(P, A, M, st);
+  RT_TRY_CUDA((launch_staged<TV, MODE>(P, A, M, st)));
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
 
-// depth tiles of the staged kernel: about RT_STAGED_WARPS_PER_SM warps per
-// SM, tiles of at least two stages
+// Depth tiles of the staged kernel: the most tiles (up to kMaxT, each at
+// least two stages long) whose grid of ray-group CTAs is one wave of
+// resident CTAs; when even one tile does not give one wave, the tile count
+// that gives the most resident warps.
 int choose_tiles_staged(const Problem* P) {
-  const int64_t want = ((int64_t)RT_STAGED_WARPS_PER_SM * P->num_sms + P->ngroups - 1) / P->ngroups;
-  int T = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxT, want));
-  while (T > 1 && (P->Ns - 1) / T < 2 * RT_STAGED_DK) --T;
-  return T;
+  int best = 1;
+  long long best_warps = -1;
+  for (int T = kMaxT; T >= 1; --T) {
+    if (T > 1 && (P->Ns - 1) / T < 2 * RT_STAGED_DK) continue;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_staged<float, RT_FS_DELO_LINEAR, KM_PLAIN>, 32 * T,
+                                                      smem_bytes(Cfg<float, KM_PLAIN>::WARP, T)) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 0;
+    }
+    if (occ <= 0) continue;
+    if ((long long)occ * P->num_sms >= P->ngroups) return T;
+    const long long warps = std::min<long long>((long long)occ * P->num_sms, P->ngroups) * T;
+    if (warps > best_warps) {
+      best_warps = warps;
+      best = T;
+    }
+  }
+  return best;
 }
 
 }  // namespace
 
-// Prepares the fast FP32 apply of a single problem: quadrature weights,
-// transposed source functions, partial sums, the tile count, the kernels'
-// shared-memory opt-in.  Leaves it off (P->staged = 0) when the layout does
-// not allow the vector loads and tensor copies, when the problem lives in a
-// batch arena, or when RT_NO_TMA=1 is set in the environment.
+// Prepares the fast FP32 apply of a single problem: quadrature weights, the
+// formal solver's node tables, partial sums and row counters, the tile
+// count, the kernels' shared-memory opt-in.  Leaves it off (P->staged = 0)
+// when the layout does not allow the vector loads and tensor copies, when
+// the problem lives in a batch arena, or when RT_NO_TMA=1 is set in the
+// environment.
 rt_status staged_setup(Problem* P, cudaStream_t st) {
   P->staged = 0;
-  if (P->alloc || P->form == RT_FORM_SIGMA || P->fs == RT_FS_DELO_PARABOLIC) return RT_OK;
+  if (P->in_arena || P->form == RT_FORM_SIGMA || P->fs == RT_FS_DELO_PARABOLIC) return RT_OK;
   const char* off = std::getenv("RT_NO_TMA");
   if (off && off[0] && off[0] != '0') return RT_OK;
   if ((P->nray % 4) || (P->nd % 4) || !P->dev_err) return RT_OK;
@@ -760,6 +848,23 @@ rt_status staged_setup(Problem* P, cudaStream_t st) {
       qw[nray + r] = (float)(w0 * P->t201[m]);
       qw[2 * nray + r] = (float)(w0 * P->t202[m]);
     }
+  // node tables, march-indexed: entry j of direction h is node(j) (j downward,
+  // Ns-1-j upward) with the interval a step into it crosses; .xy (sigma) are
+  // written by the quadrature of every apply
+  const int tn = Ns + kTabPad;
+  std::vector<float4> tab(2 * (size_t)tn, make_float4(0.f, 0.f, 0.f, 0.f));
+  for (int h = 0; h < 2; ++h)
+    for (int j = 1; j < Ns; ++j) {
+      const int k = h == 0 ? j : Ns - 1 - j;   // node reached by step j
+      const double dt = h == 0 ? P->tau[k] - P->tau[k - 1] : P->tau[k + 1] - P->tau[k];
+      float4& o = tab[(size_t)h * tn + j];
+      if (P->fs == RT_FS_DELO_LINEAR) {
+        o.z = (float)(dt / kLn2);
+        o.w = (float)(1.0 / dt);
+      } else {
+        o.z = (float)dt;
+      }
+    }
   const int64_t nc = nray / 4;
   P->quad_gx = (int)((nc + kQuadThreads - 1) / kQuadThreads);
   const int64_t target = 8LL * P->num_sms;   // CTAs of k_quad
@@ -768,27 +873,43 @@ rt_status staged_setup(Problem* P, cudaStream_t st) {
   P->quad_gy = (Ns + P->quad_hpc - 1) / P->quad_hpc;
   // k_quad_norm: taller CTAs, so that the grid is one wave of resident CTAs
   // (each CTA first forms 1/||u|| from the norm partials; a second wave would
-  // repeat that serially).  The partial layout depends on quad_gx only.
+  // repeat that serially).  The resident count is the smallest over the
+  // three instantiations the solvers launch.  The partial layout depends on
+  // quad_gx only.
   P->quadn_hpc = P->quad_hpc;
-  int resident = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_quad_norm<KM_JACOBI>, kQuadThreads, 0) ==
-          cudaSuccess &&
-      resident > 0) {
+  int resident = 1 << 30;
+  {
+    int o[3] = {0, 0, 0};
+    bool okq = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], k_quad_norm<KM_PLAIN>, kQuadThreads, 0) ==
+                   cudaSuccess &&
+               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], k_quad_norm<KM_JACOBI>, kQuadThreads, 0) ==
+                   cudaSuccess &&
+               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], k_quad_norm<KM_LOCAL_LAMBDA>, kQuadThreads, 0) ==
+                   cudaSuccess;
+    if (!okq) {
+      cudaGetLastError();
+      resident = 0;
+    }
+    for (int i = 0; i < 3 && okq; ++i) resident = std::min(resident, o[i]);
+  }
+  if (resident > 0) {
     const int64_t rows = std::max<int64_t>(1, (int64_t)resident * P->num_sms / P->quad_gx - 1);
     const int h = (int)std::min<int64_t>(kQuadMaxHeights, (Ns + rows - 1) / rows);
     P->quadn_hpc = std::max(P->quad_hpc, h);
-  } else {
-    cudaGetLastError();
   }
   P->quadn_gy = (Ns + P->quadn_hpc - 1) / P->quadn_hpc;
   P->ntile_st = choose_tiles_staged(P);
 #ifdef RT_EXPERIMENT
   if (const char* t = std::getenv("RT_STAGED_TILES")) P->ntile_st = std::min(kMaxT, std::max(1, std::atoi(t)));
 #endif
+  const int rows = std::max(P->quad_gy, P->quadn_gy);
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->qw, qw.size() * sizeof(float)));
   RT_TRY_CUDA(cudaMemcpyAsync(P->qw, qw.data(), qw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  RT_TRY_CUDA(dev_alloc(P, (void**)&P->St, (size_t)2 * Ns * Nmu * sizeof(float)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->stab, tab.size() * sizeof(float4)));
+  RT_TRY_CUDA(cudaMemcpyAsync(P->stab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->qpart, (size_t)Ns * P->quad_gx * 2 * sizeof(float)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->qcnt, (size_t)rows * sizeof(int)));
+  RT_TRY_CUDA(cudaMemsetAsync(P->qcnt, 0, (size_t)rows * sizeof(int), st));
   RT_TRY_CUDA(cudaStreamSynchronize(st));
   P->staged = 1;
   return RT_OK;
@@ -800,15 +921,21 @@ bool staged_f64io_ok(const Problem* P, int mode, const void* x, const void* u) {
   return mode == AM_PLAIN || mode == AM_LOCAL_LAMBDA;
 }
 
-// The whole FP32 apply (quadrature, source functions, formal solve) through
-// the kernels above, for FP32 vectors or, with f64io, FP64 vectors (and then,
-// with nin, the input formed as nin->u / ||nin->u||); false when they do not
-// apply (nothing launched, *status untouched).
+// The whole FP32 apply (quadrature with the multipolar components, formal
+// solve) through the kernels above, for FP32 vectors or, with f64io, FP64
+// vectors (and then, with nin, the input formed as nin->u / ||nin->u||);
+// false when they do not apply (nothing launched, *status untouched).
 bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cudaStream_t st, const int* kstop,
                     int step, rt_status* status, const NormIn* nin) {
   if (!f64io) {
     if (nin || !P->staged || (reinterpret_cast<uintptr_t>(x) & 15) || mode != AM_PLAIN) return false;
-    *status = staged_apply<float, KM_PLAIN>(P, static_cast<const float*>(x), static_cast<float*>(y), st, kstop, step);
+    int fail = 0;
+    if (!kstop && P->inject_wait_fail > 0) {   // a standalone apply consumes one armed injection
+      fail = 1;
+      P->inject_wait_fail -= 1;
+    }
+    *status = staged_apply<float, KM_PLAIN>(P, static_cast<const float*>(x), static_cast<float*>(y), st, kstop,
+                                            step, nullptr, fail);
     return true;
   }
   if (!staged_f64io_ok(P, mode, x, nin ? static_cast<const void*>(nin->u) : x)) return false;

@@ -24,12 +24,41 @@ def to_host(x: torch.Tensor) -> np.ndarray:
     return x.detach().double().cpu().numpy()
 
 
-def assert_close_scaled(got, ref, tol, what=""):
-    """max_i |got_i - ref_i| <= tol * max_i |ref_i| (elementwise, scaled by the vector's size)."""
+def stokes_blocks(n: int, layout: str):
+    """Index sets of the Stokes I and Q parts of a vector of length n:
+    "I" the I-form layout x[s][k][m][p] (first half I, second half Q),
+    "sigma" the sigma-form layout (sigma00, sigma20 interleaved per height),
+    "flat" the whole vector as one block."""
+    if layout == "flat":
+        return [("all", slice(None))]
+    assert n % 2 == 0, f"a {layout}-form vector has even length, got {n}"
+    if layout == "I":
+        return [("I", slice(0, n // 2)), ("Q", slice(n // 2, n))]
+    if layout == "sigma":
+        return [("sigma00", slice(0, n, 2)), ("sigma20", slice(1, n, 2))]
+    raise ValueError(layout)
+
+
+def assert_close_scaled(got, ref, tol, what="", layout="I"):
+    """Per Stokes block b: max_{i in b} |got_i - ref_i| <= tol * max_{i in b} |ref_i|.
+
+    Each block is scaled by its own largest reference entry, so a Q part
+    that is orders of magnitude below the I part is checked at the same
+    relative accuracy.  A block whose reference is exactly zero is scaled
+    by the whole vector's largest entry.  Returns the worst scaled error."""
     got = np.asarray(got)
     ref = np.asarray(ref)
     assert got.shape == ref.shape, (got.shape, ref.shape)
-    scale = max(np.max(np.abs(ref)), 1e-300)
-    err = np.max(np.abs(got - ref))
-    assert err <= tol * scale, f"{what}: max err {err:.3e} > {tol:.1e} * {scale:.3e}"
-    return err / scale
+    whole = max(float(np.max(np.abs(ref))), 1e-300) if ref.size else 1.0
+    worst = 0.0
+    for name, ix in stokes_blocks(ref.size, layout):
+        r, g = ref.reshape(-1)[ix], got.reshape(-1)[ix]
+        if r.size == 0:
+            continue
+        scale = float(np.max(np.abs(r)))
+        if scale == 0.0:
+            scale = whole
+        err = float(np.max(np.abs(g - r)))
+        assert err <= tol * scale, f"{what} [{name}]: max err {err:.3e} > {tol:.1e} * {scale:.3e}"
+        worst = max(worst, err / scale)
+    return worst

@@ -56,6 +56,8 @@ int main(void) {
   F(rt_solver_opts, rtol); F(rt_solver_opts, resid_hist); F(rt_solver_opts, hist_cap);
   F(rt_solver_opts, omega);
   F(rt_solve_info, rel_resid); F(rt_solve_info, t_total_ms);
+  printf("rt_allocator %zu\n", sizeof(rt_allocator));
+  F(rt_allocator, ctx); F(rt_allocator, alloc); F(rt_allocator, release);
   return 0;
 }
 """
@@ -69,7 +71,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                                check=True).stdout.split("\n") if line)
     structs = {"rt_problem_desc": N.ProblemDesc, "rt_solver_opts": N.SolverOpts, "rt_solve_info": N.SolveInfo,
-               "rt_server_opts": N.ServerOpts, "rt_server_stats": N.ServerStats}
+               "rt_server_opts": N.ServerOpts, "rt_server_stats": N.ServerStats, "rt_allocator": N.Allocator}
     for name, cls in structs.items():
         assert int(got[name]) == C.sizeof(cls), name
     for key, val in got.items():
@@ -150,3 +152,24 @@ def test_null_arguments_are_rejected(lib):
     assert lib.rt_precond_stationary(None, N.RT_PREC_SOR, 1.0, None, None, None) == N.RT_EINVAL
     assert lib.rt_precond_local_lambda(None, None, None, None) == N.RT_EINVAL
     assert lib.rt_server_destroy(None) == N.RT_OK
+
+
+def test_allocator_hook_probe_and_injection_arguments_are_checked_on_the_host(lib):
+    """rt_problem_create_with_allocator and rt_server_create_with_allocator
+    refuse a hook without alloc or release before touching a device; the
+    FP64 probe refuses iters < 1 or a NULL sink; the wait-timeout injection
+    refuses a NULL problem or a negative count."""
+    d, keep = _desc()
+    half = N.Allocator()
+    half.alloc = N.ALLOC_FN(lambda ctx, n, st: None)   # release left NULL
+    h = C.c_void_p()
+    assert lib.rt_problem_create_with_allocator(C.byref(d), C.byref(half), None, C.byref(h)) == N.RT_EINVAL
+    assert not h.value and "alloc and release" in N.last_error()
+    so = N.ServerOpts()
+    lib.rt_server_opts_default(C.byref(so))
+    assert lib.rt_server_create_with_allocator(C.byref(so), C.byref(half), C.byref(h)) == N.RT_EINVAL
+    bad, keep2 = _desc(Ns=1)
+    assert lib.rt_problem_create_with_allocator(C.byref(bad), None, None, C.byref(h)) == N.RT_EINVAL
+    assert lib.rt_probe_fp64_fma(0, C.c_void_p(16), None) == -1
+    assert lib.rt_probe_fp64_fma(10, None, None) == -1
+    assert lib.rt_problem_inject_wait_timeout(None, 1) == N.RT_EINVAL

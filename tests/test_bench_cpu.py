@@ -41,3 +41,28 @@ def test_reference_arm_two_ranks_gloo():
     assert r.returncode == 0, r.stderr[-3000:]
     lines = _json_lines(r.stdout)
     assert len(lines) == 1 and lines[0]["n_gpus"] == 2
+
+
+def test_oracle_per_solve_check_of_saved_solutions(tmp_path):
+    """The CPU leg's per-solve check: a saved solution is identified by its
+    distribution (seed), index and count; the oracle recomputes b, the true
+    residual and (small N_s) the distance from its exact solution.  The
+    oracle's own exact solution passes with residual and error at rounding
+    level; a perturbed copy shows the perturbation."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import rt_workloads as W
+    from oracle.transfer import Transfer
+
+    at = W.batch_instances(512)[379]
+    assert at.Ns <= 120
+    xs = Transfer(at).exact_I()
+    path = str(tmp_path / "s.npz")
+    np.savez(path, **{f"batched__{W.BATCH_SEED}__379__512": xs,
+                      f"served200__{W.BATCH_SEED}__379__512": xs * (1 + 1e-6)})
+    out = bench.oracle_errors(path)
+    assert "error" not in out, out
+    assert out["batched"]["true_resid_max"] < 1e-12 and out["batched"]["err_vs_lu_max"] < 1e-12
+    assert 5e-7 < out["served200"]["err_vs_lu_max"] < 2e-6

@@ -57,8 +57,10 @@ def test_sigma_form_apply_matches_the_oracle(pair):
     name, at, _, tr = pair
     Ps = problem(at, form="sigma")
     s = W.random_vector(2 * at.Ns, 8)
-    assert_close_scaled(to_host(Ps.apply(to_dev(s))), tr.apply_sigma(s), TOL64, name + " sigma")
-    assert_close_scaled(to_host(Ps.rhs()), tr.rhs_sigma(), TOL64, name + " sigma rhs")
+    assert_close_scaled(to_host(Ps.apply(to_dev(s))), tr.apply_sigma(s), TOL64, name + " sigma", layout="sigma")
+    # the sigma20 part of b = J t + c is a near cancellation (T201 integrates to zero over a
+    # hemisphere of isotropic radiation): it is checked on the scale of the whole vector
+    assert_close_scaled(to_host(Ps.rhs()), tr.rhs_sigma(), TOL64, name + " sigma rhs", layout="flat")
 
 
 @pytest.mark.parametrize("precond", ["jacobi", "local_lambda"])

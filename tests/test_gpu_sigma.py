@@ -61,17 +61,19 @@ def test_sigma_apply_matches_the_oracle(pair):
     for seed in (3, 4):
         s = W.random_vector(2 * at.Ns, seed)
         y = to_host(P.apply(to_dev(s)))
-        assert_close_scaled(y, tr.apply_sigma(s), TOL64, name)
+        assert_close_scaled(y, tr.apply_sigma(s), TOL64, name, layout="sigma")
 
 
 def test_sigma_rhs_diagonal_and_blocks_match_the_oracle(pair):
     name, at, P, tr = pair
-    assert_close_scaled(to_host(P.rhs()), tr.rhs_sigma(), TOL64, name + " rhs")
-    assert_close_scaled(to_host(P.jacobi_diag()), tr.jacobi_sigma(), TOL64, name + " diag")
+    # the sigma20 part of b = J t + c is a near cancellation (T201 integrates to zero over a
+    # hemisphere of isotropic radiation): it is checked on the scale of the whole vector
+    assert_close_scaled(to_host(P.rhs()), tr.rhs_sigma(), TOL64, name + " rhs", layout="flat")
+    assert_close_scaled(to_host(P.jacobi_diag()), tr.jacobi_sigma(), TOL64, name + " diag", layout="sigma")
     v = W.random_vector(2 * at.Ns, 5)
     M = tr.local_blocks_sigma()
     z_ref = np.linalg.solve(M, v.reshape(at.Ns, 2, 1)).reshape(-1)
-    assert_close_scaled(to_host(P.precond_local_lambda(to_dev(v))), z_ref, TOL64, name + " blocks")
+    assert_close_scaled(to_host(P.precond_local_lambda(to_dev(v))), z_ref, TOL64, name + " blocks", layout="sigma")
 
 
 @pytest.mark.parametrize("method,precond", [("gmres", "local_lambda"), ("gmres", "jacobi"), ("gmres", "none"),

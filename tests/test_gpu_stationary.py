@@ -48,7 +48,7 @@ def test_preconditioner_matches_the_oracle(name, at):
     for kind, build in (("sor", St.sor_matrix), ("ssor", St.ssor_matrix)):
         for omega in (1.0, 1.5, 0.8):
             z = to_host(P.precond_stationary(to_dev(v), kind, omega))
-            assert_close_scaled(z, St.inverse_action(build(A, omega))(v), TOL64, f"{name} {kind} {omega}")
+            assert_close_scaled(z, St.inverse_action(build(A, omega))(v), TOL64, f"{name} {kind} {omega}", layout="sigma")
 
 
 @pytest.mark.parametrize("method,precond,omega", [
