@@ -319,6 +319,8 @@ struct Problem {
   float* qpart = nullptr;      // [Ns][quad_gx][2] partial moments
   int* qcnt = nullptr;         // [quadrature grid rows] CTAs of a row done (the last one forms sigma)
   int* dev_err = nullptr;
+  float* tile_dt = nullptr;    // [2][ntile_st] DELO-linear: the sum of dtau / ln 2 over each depth tile
+  void* tma_cache = nullptr;   // host: recently encoded tensor maps of the FP32 apply (rt_tma.cu)
   int inject_wait_fail = 0;    // standalone FP32 applies still to run with one tensor-copy wait forced to
                                // give up (failure injection, rt_problem_inject_wait_timeout)
 };
@@ -376,6 +378,7 @@ rt_status op_precond_sigma(Problem* P, const double* v, double* z, cudaStream_t 
                            int step = 0);
 // fast FP32 apply (rt_tma.cu)
 rt_status staged_setup(Problem* P, cudaStream_t st);
+void staged_release(Problem* P);   // host state of the fast FP32 apply
 bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cudaStream_t st, const int* kstop,
                     int step, rt_status* status, const NormIn* nin = nullptr);
 // whether staged_apply32 takes FP64 vectors x (and a normalisation input u)

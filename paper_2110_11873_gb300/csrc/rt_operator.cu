@@ -359,7 +359,7 @@ void free_device(Problem* P) {
   void* ptrs[] = {P->ce,     P->ca,    P->cb,     P->wray,   P->wI2,  P->wQ2,   P->t201d, P->t202d,
                   P->Bd,     P->Minv,  P->S,      P->S2,     P->dtau32, P->r32, P->wray32, P->wI2f,
                   P->wQ2f,   P->t201f, P->t202f,  P->S32,    P->V,    P->work,  P->dinv,  P->work32,
-                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->stab, P->qpart, P->qcnt, P->Mdiag, P->Ibuf, P->cg,
+                  P->partials, P->gm,  P->bc,     P->hist,  P->dev_err, P->bpart, P->qw, P->stab, P->qpart, P->qcnt, P->tile_dt, P->Mdiag, P->Ibuf, P->cg,
                   P->Etile, P->Bmap, P->Asig, P->Mpre, P->Mtri, P->Mscr, P->wjac, P->Kmap};
   for (void* p : ptrs)
     if (p) dev_free(P, p);
@@ -373,6 +373,8 @@ void free_device(Problem* P) {
   P->qw = P->qpart = nullptr;
   P->stab = nullptr;
   P->qcnt = nullptr;
+  P->tile_dt = nullptr;
+  staged_release(P);
   P->Mdiag = P->Ibuf = P->cg = P->Etile = P->Bmap = P->Kmap = nullptr;
   P->Asig = P->Mpre = P->Mtri = P->Mscr = P->wjac = nullptr;
   P->asig_ready = 0;

@@ -66,7 +66,7 @@ namespace {
 #define RT_STAGED_NST 2
 #endif
 #ifndef RT_STAGED_RS
-#define RT_STAGED_RS 4
+#define RT_STAGED_RS 2
 #endif
 #ifndef RT_STAGED_MAXT
 #define RT_STAGED_MAXT 16
@@ -82,7 +82,7 @@ constexpr int kTabPad = 2 * kRS;               // table entries past the last no
 constexpr unsigned long long kWaitNs = 1000000000ull;   // bound of one wait
 constexpr int kQuadThreads = 256;
 constexpr int kQuadMaxHeights = 64;            // heights per CTA of k_quad
-constexpr int kQuadUnroll = 4;                 // heights in flight per thread
+constexpr int kQuadBatch = 2;                  // heights per batch of loads (two batches in flight)
 
 template <typename TV, int MODE>
 struct Cfg {
@@ -263,16 +263,35 @@ struct QuadOut {
   int Ns;
 };
 
+// Transposing warp sum of four FP32 values (7 shuffles and additions a lane
+// instead of 20): lanes 0, 8, 16 and 24 end with the warp sums of v[0],
+// v[1], v[2] and v[3]; fixed order.
+__device__ __forceinline__ float warp_sum4f(const float* v) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const float r0 = (h16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, h16 ? v[0] : v[2], 16);
+  const float r1 = (h16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, h16 ? v[1] : v[3], 16);
+  float t = (h8 ? r1 : r0) + __shfl_xor_sync(0xffffffffu, h8 ? r0 : r1, 8);
+  t += __shfl_xor_sync(0xffffffffu, t, 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
 // The partials of the heights of row ky of the grid, rays of column
 // blockIdx.x (all threads of the CTA call it); the last CTA of the row then
-// forms sigma00, sigma20 of the row's heights.  NORM: the input is u * inv,
-// written to xo as it is read.
+// forms sigma00, sigma20 of the row's heights.  Loads run one batch of
+// kQuadBatch heights ahead of the sums, so the memory system always has
+// this CTA's next rows in flight.  NORM: the input is u * inv, written to xo
+// as it is read.
 template <typename TV, int MODE, bool NORM>
 __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double* __restrict__ dinv,
                                           const float* __restrict__ qw, int64_t nray, int hpc, const QuadOut& Q,
                                           int ky, const double* __restrict__ u = nullptr, double inv = 1.0,
                                           double* __restrict__ xo = nullptr) {
   constexpr int nw = kQuadThreads / 32;
+  constexpr int U = kQuadBatch;
+  static_assert(U == 2, "the transposing reduction takes two heights of two values");
   __shared__ float red[kQuadMaxHeights][nw][2];
   __shared__ int last;
   const int Ns = Q.Ns;
@@ -286,10 +305,9 @@ __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double
   const float4 w2 = ok ? __ldg(reinterpret_cast<const float4*>(qw + 2 * nray) + c) : z;
   const int k_lo = ky * hpc, k_hi = min(Ns, k_lo + hpc);
   const int64_t plane = (int64_t)Ns * nray;
-  for (int k = k_lo; k < k_hi; k += kQuadUnroll) {
-    float4 vI[kQuadUnroll], vQ[kQuadUnroll];
+  auto load = [&](int k, float4* vI, float4* vQ) {
 #pragma unroll
-    for (int v = 0; v < kQuadUnroll; ++v) {
+    for (int v = 0; v < U; ++v) {
       vI[v] = z;
       vQ[v] = z;
       if (ok && k + v < k_hi) {
@@ -308,8 +326,11 @@ __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double
         }
       }
     }
+  };
+  auto reduce = [&](int k, const float4* vI, const float4* vQ) {
+    float a[2 * U];
 #pragma unroll
-    for (int v = 0; v < kQuadUnroll; ++v) {
+    for (int v = 0; v < U; ++v) {
       float a0 = w0.x * vI[v].x;
       a0 = fmaf(w0.y, vI[v].y, a0);
       a0 = fmaf(w0.z, vI[v].z, a0);
@@ -322,13 +343,23 @@ __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double
       a2 = fmaf(w2.y, vQ[v].y, a2);
       a2 = fmaf(w2.z, vQ[v].z, a2);
       a2 = fmaf(w2.w, vQ[v].w, a2);
-      a0 = warp_sum(a0);
-      a2 = warp_sum(a2);
-      if (lane == 0 && k + v < k_hi) {
-        red[k + v - k_lo][warp][0] = a0;
-        red[k + v - k_lo][warp][1] = a2;
-      }
+      a[2 * v] = a0;
+      a[2 * v + 1] = a2;
     }
+    const float t = warp_sum4f(a);   // lane 8*i holds the sum of a[i]
+    if ((lane & 7) == 0) {
+      const int i = lane >> 3, v = i >> 1;
+      if (k + v < k_hi) red[k + v - k_lo][warp][i & 1] = t;
+    }
+  };
+  float4 aI[U], aQ[U], bI[U], bQ[U];
+  load(k_lo, aI, aQ);
+  for (int k = k_lo; k < k_hi; k += 2 * U) {
+    load(k + U, bI, bQ);
+    reduce(k, aI, aQ);
+    if (k + U >= k_hi) break;
+    load(k + 2 * U, aI, aQ);
+    reduce(k + U, bI, bQ);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < k_hi - k_lo; i += kQuadThreads) {
@@ -349,32 +380,39 @@ __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the row's last CTA: one warp per height sums the columns' partials
+  // (lane-strided, then the fixed shuffle tree: the order does not depend on
+  // which CTA came last)
   const int gx = gridDim.x;
-  for (int i = threadIdx.x; i < k_hi - k_lo; i += kQuadThreads) {
+  for (int i = warp; i < k_hi - k_lo; i += nw) {
     const int k = k_lo + i;
     const float* p = Q.part + (int64_t)k * gx * 2;
     float a = 0.f, b = 0.f;
-    for (int j = 0; j < gx; ++j) {   // column order, whichever CTA came last
+    for (int j = lane; j < gx; j += 32) {
       a += __ldcg(p + 2 * j);
       b += __ldcg(p + 2 * j + 1);
     }
-    float s0 = Q.xi * a, s2 = Q.xiW2 * b;
-    if (MODE == KM_LOCAL_LAMBDA) {
-      const double* Mi = Q.Minv + 4 * k;
-      const float u0 = fmaf((float)Mi[0], s0, (float)Mi[1] * s2);
-      const float u2 = fmaf((float)Mi[2], s0, (float)Mi[3] * s2);
-      s0 = u0;
-      s2 = u2;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+      float s0 = Q.xi * a, s2 = Q.xiW2 * b;
+      if (MODE == KM_LOCAL_LAMBDA) {
+        const double* Mi = Q.Minv + 4 * k;
+        const float u0 = fmaf((float)Mi[0], s0, (float)Mi[1] * s2);
+        const float u2 = fmaf((float)Mi[2], s0, (float)Mi[3] * s2);
+        s0 = u0;
+        s2 = u2;
+      }
+      const float2 sg = make_float2(s0, s2);
+      reinterpret_cast<float2*>(Q.tab + k)[0] = sg;
+      reinterpret_cast<float2*>(Q.tab + (Ns + kTabPad) + (Ns - 1 - k))[0] = sg;
     }
-    const float2 sg = make_float2(s0, s2);
-    reinterpret_cast<float2*>(Q.tab + k)[0] = sg;
-    reinterpret_cast<float2*>(Q.tab + (Ns + kTabPad) + (Ns - 1 - k))[0] = sg;
   }
   if (threadIdx.x == 0) Q.cnt[ky] = 0;   // ready for the next launch (stream-ordered)
 }
 
 template <typename TV, int MODE>
-__global__ void __launch_bounds__(kQuadThreads, sizeof(TV) == 4 ? 8 : 4) k_quad(const TV* __restrict__ x, const double* __restrict__ dinv,
+__global__ void __launch_bounds__(kQuadThreads, 4) k_quad(const TV* __restrict__ x, const double* __restrict__ dinv,
                                                        const float* __restrict__ qw, int64_t nray, int hpc,
                                                        const QuadOut Q, const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
@@ -412,6 +450,7 @@ struct StagedArgs {
   const float* r32;       // [nray] phi_hat / |mu|
   const float* t201;      // [Nmu]
   const float* t202;      // [Nmu]
+  const float* tile_dt;   // [2][ntile] DELO-linear: sum of dtau / ln 2 over each tile (the tile's slope is 2^-(rsc sum))
   int Ns, Nnu;
   int64_t nray, nd;
   int ngd, ntile, L;      // downward ray groups, tiles per group, steps per tile
@@ -471,26 +510,29 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
     for (int q = 0; q < kNST && q < nst; ++q) issue(q);   // they land while the tile maps are composed
   __syncwarp();
   const float4* tab = A.tab + (size_t)h * (Ns + kTabPad);
-  float II = 0.f, IQ = 0.f;   // I at the tile's inflow node (zero inflow at the entry node)
+  // The recurrence runs on the multipolar components: with S_I = sigma00 +
+  // T201 sigma20 and S_Q = T202 sigma20 (Eq. 7-8) and Lambda linear, the
+  // formal solution of the ray is I_I = U0 + T201 U2, I_Q = T202 U2, where U0
+  // and U2 solve the same recurrence with sigma00 and sigma20 as the source.
+  float U0 = 0.f, U2 = 0.f;   // at the tile's inflow node (zero inflow at the entry node)
   if (T > 1) {
-    // phase A: the tile's map I_out = E I_in + B (zero inflow gives B)
+    // phase A: the tile's map U_out = E U_in + B (zero inflow gives B)
     if (t < T - 1 && n1 > 0) {
       float4 ring[kRS];
       const float4* pn = tab + j0;
 #pragma unroll
       for (int u = 0; u < kRS; ++u) ring[u] = __ldg(pn + u);
       const float4 pp = __ldg(tab + j0 - 1);
-      float sIp = fmaf(t201, pp.y, pp.x), sQp = t202 * pp.y;
-      float E = 1.f, BI = 0.f, BQ = 0.f;
+      float s0p = pp.x, s2p = pp.y;
+      float E = 1.f, B0 = 0.f, B2 = 0.f;
       auto stepA = [&](const float4& op) {
         float e, al, be;
         step_coeffs<FS>(op, rsc, irsc, e, al, be);
-        const float sI = fmaf(t201, op.y, op.x), sQ = t202 * op.y;
-        BI = fmaf(e, BI, fmaf(al, sIp, be * sI));
-        BQ = fmaf(e, BQ, fmaf(al, sQp, be * sQ));
-        E *= e;
-        sIp = sI;
-        sQp = sQ;
+        B0 = fmaf(e, B0, fmaf(al, s0p, be * op.x));
+        B2 = fmaf(e, B2, fmaf(al, s2p, be * op.y));
+        if (FS != RT_FS_DELO_LINEAR) E *= e;
+        s0p = op.x;
+        s2p = op.y;
       };
       int n = 0;
       for (; n + kRS <= n1; n += kRS) {
@@ -505,9 +547,11 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
 #pragma unroll
       for (int u = 0; u < kRS; ++u)
         if (n + u < n1) stepA(ring[u]);
+      // DELO-linear: the product of the tile's e is exp(-Delta summed over the tile)
+      if (FS == RT_FS_DELO_LINEAR) E = ex2_approx(-rsc * __ldg(A.tile_dt + h * T + t));
       sh[0][t][lane] = E;
-      sh[1][t][lane] = BI;
-      sh[2][t][lane] = BQ;
+      sh[1][t][lane] = B0;
+      sh[2][t][lane] = B2;
     }
     __syncthreads();
     if (t == 0) {   // phase B: chain the maps into every tile's inflow
@@ -525,8 +569,8 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
       }
     }
     __syncthreads();
-    II = sh[1][t][lane];
-    IQ = sh[2][t][lane];
+    U0 = sh[1][t][lane];
+    U2 = sh[2][t][lane];
   }
   const int64_t plane = (int64_t)Ns * A.nray;
   // entry node (tile 0): zero inflow, so y = x there
@@ -547,11 +591,11 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
   const float4* pn = tab + j0;
 #pragma unroll
   for (int u = 0; u < kRS; ++u) ring[u] = __ldg(pn + u);
-  float sIp, sQp;
+  float s0p, s2p;
   {
     const float4 pp = __ldg(tab + j0 - 1);
-    sIp = fmaf(t201, pp.y, pp.x);
-    sQp = t202 * pp.y;
+    s0p = pp.x;
+    s2p = pp.y;
   }
   int qfail = -1;
   for (int q = 0; q < nst; ++q) {
@@ -574,32 +618,32 @@ __device__ __forceinline__ void staged_body(const StagedArgs& A, const Maps& M, 
       if (ru == kRS - 1) pn += kRS;
       float e, al, be;
       step_coeffs<FS>(op, rsc, irsc, e, al, be);
-      const float sI = fmaf(t201, op.y, op.x), sQ = t202 * op.y;
       const float xI = (float)xs[row * 32 + lane], xQ = (float)xs[(DK + row) * 32 + lane];
       float yvI, yvQ;
       if (MODE == KM_LOCAL_LAMBDA) {
         // y = x - (I - beta S): the step without its beta S_k term
-        const float tI = fmaf(e, II, al * sIp), tQ = fmaf(e, IQ, al * sQp);
-        yvI = xI - tI;
-        yvQ = xQ - tQ;
-        II = fmaf(be, sI, tI);
-        IQ = fmaf(be, sQ, tQ);
+        const float t0 = fmaf(e, U0, al * s0p), t2 = fmaf(e, U2, al * s2p);
+        yvI = xI - fmaf(t201, t2, t0);
+        yvQ = fmaf(-t202, t2, xQ);
+        U0 = fmaf(be, op.x, t0);
+        U2 = fmaf(be, op.y, t2);
       } else {
-        II = fmaf(e, II, fmaf(al, sIp, be * sI));
-        IQ = fmaf(e, IQ, fmaf(al, sQp, be * sQ));
+        U0 = fmaf(e, U0, fmaf(al, s0p, be * op.x));
+        U2 = fmaf(e, U2, fmaf(al, s2p, be * op.y));
         if (MODE == KM_JACOBI) {
-          yvI = fmaf(xI, (float)ds[row * 32 + lane], -II);
-          yvQ = fmaf(xQ, (float)ds[(DK + row) * 32 + lane], -IQ);
+          yvI = fmaf(xI, (float)ds[row * 32 + lane], -fmaf(t201, U2, U0));
+          yvQ = fmaf(xQ, (float)ds[(DK + row) * 32 + lane], -(t202 * U2));
         } else {
-          yvI = xI - II;
-          yvQ = xQ - IQ;
+          yvI = xI - fmaf(t201, U2, U0);
+          yvQ = fmaf(-t202, U2, xQ);
         }
       }
-      sIp = sI;
-      sQp = sQ;
-      if (active) {
-        yI[0] = (TV)yvI;
-        yI[plane] = (TV)yvQ;
+      s0p = op.x;
+      s2p = op.y;
+      if (active) {   // evict-first stores: in a large apply, y would push out of L2 the lines of x
+                      // that the quadrature left there and other warps have still to read
+        __stcs(yI, (TV)yvI);
+        __stcs(yI + plane, (TV)yvQ);
       }
       yI += dy;
     };
@@ -724,14 +768,43 @@ cudaError_t launch_staged(const Problem* P, const StagedArgs& A, const Maps& M, 
   }
 }
 
+// The last few tensor-map sets a problem encoded, keyed by the vector
+// addresses: encoding costs a few microseconds of host time per apply, which
+// a standalone apply would otherwise spend before its first kernel starts.
+// A map holds the address and the dimensions only, so an entry stays valid
+// for any buffer at that address.
+struct MapCache {
+  static constexpr int kEntries = 8;
+  struct Entry {
+    const void* x = nullptr;
+    const void* d = nullptr;
+    int dk = 0;
+    bool f64 = false;
+    Maps M;
+  } e[kEntries];
+  int next = 0;
+};
+
 template <typename TV, int MODE>
-rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step,
-                       const NormIn* nin = nullptr, int fail_wait = 0) {
+rt_status staged_maps(Problem* P, const TV* x, Maps* out) {
   constexpr bool f64 = sizeof(TV) == 8;
-  RT_NVTX("FP32 apply: k_quad + k_staged");
+  const int dk = Cfg<TV, MODE>::DK;
+  const void* d = MODE == KM_JACOBI ? static_cast<const void*>(P->dinv) : nullptr;
+  if (!P->tma_cache) {
+    P->tma_cache = new (std::nothrow) MapCache();
+    if (!P->tma_cache) {
+      set_error("host allocation failed");
+      return RT_ENOMEM;
+    }
+  }
+  MapCache* C = static_cast<MapCache*>(P->tma_cache);
+  for (const auto& en : C->e)
+    if (en.x == x && en.d == d && en.dk == dk && en.f64 == f64) {
+      *out = en.M;
+      return RT_OK;
+    }
   Maps M;
   memset(&M, 0, sizeof M);
-  const int dk = Cfg<TV, MODE>::DK;
   if (!encode_half(&M.x[0], x, 0, P->nd, P, f64, dk) || !encode_half(&M.x[1], x, P->nd, P->nray - P->nd, P, f64, dk)) {
     set_error("cuTensorMapEncodeTiled failed for the FP32 apply");
     return RT_ECUDA;
@@ -741,6 +814,23 @@ rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const in
     set_error("cuTensorMapEncodeTiled failed for the Jacobi diagonal");
     return RT_ECUDA;
   }
+  MapCache::Entry& en = C->e[C->next];
+  C->next = (C->next + 1) % MapCache::kEntries;
+  en.x = x;
+  en.d = d;
+  en.dk = dk;
+  en.f64 = f64;
+  en.M = M;
+  *out = M;
+  return RT_OK;
+}
+
+template <typename TV, int MODE>
+rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const int* kstop, int step,
+                       const NormIn* nin = nullptr, int fail_wait = 0) {
+  RT_NVTX("FP32 apply: k_quad + k_staged");
+  Maps M;
+  RT_TRY((staged_maps<TV, MODE>(P, x, &M)));
   QuadOut Q;
   Q.part = P->qpart;
   Q.cnt = P->qcnt;
@@ -765,6 +855,7 @@ rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const in
   A.r32 = P->r32;
   A.t201 = P->t201f;
   A.t202 = P->t202f;
+  A.tile_dt = P->tile_dt;
   A.Ns = P->Ns;
   A.Nnu = P->Nnu;
   A.nray = P->nray;
@@ -782,10 +873,12 @@ rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const in
   return RT_OK;
 }
 
-// Depth tiles of the staged kernel: the most tiles (up to kMaxT, each at
-// least two stages long) whose grid of ray-group CTAs is one wave of
-// resident CTAs; when even one tile does not give one wave, the tile count
-// that gives the most resident warps.
+// Depth tiles of the staged kernel: the tile count (up to kMaxT, each tile
+// at least two stages long) that puts the most warps on the SMs at once,
+// min(resident CTAs, ray groups) x tiles; the recurrence is latency-bound,
+// so more resident warps beat a grid that fits one wave (measured on the
+// N_s = 2000 sweep atmosphere: 16 tiles in 1.3 waves 133 us, 10 tiles in one
+// wave 140 us).
 int choose_tiles_staged(const Problem* P) {
   int best = 1;
   long long best_warps = -1;
@@ -798,7 +891,6 @@ int choose_tiles_staged(const Problem* P) {
       occ = 0;
     }
     if (occ <= 0) continue;
-    if ((long long)occ * P->num_sms >= P->ngroups) return T;
     const long long warps = std::min<long long>((long long)occ * P->num_sms, P->ngroups) * T;
     if (warps > best_warps) {
       best_warps = warps;
@@ -867,7 +959,7 @@ rt_status staged_setup(Problem* P, cudaStream_t st) {
     }
   const int64_t nc = nray / 4;
   P->quad_gx = (int)((nc + kQuadThreads - 1) / kQuadThreads);
-  const int64_t target = 8LL * P->num_sms;   // CTAs of k_quad
+  const int64_t target = 4LL * P->num_sms;   // CTAs of k_quad: one wave at 4 resident per SM
   const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(Ns, target / P->quad_gx));
   P->quad_hpc = std::min((Ns + gy - 1) / gy, kQuadMaxHeights);
   P->quad_gy = (Ns + P->quad_hpc - 1) / P->quad_hpc;
@@ -902,12 +994,26 @@ rt_status staged_setup(Problem* P, cudaStream_t st) {
 #ifdef RT_EXPERIMENT
   if (const char* t = std::getenv("RT_STAGED_TILES")) P->ntile_st = std::min(kMaxT, std::max(1, std::atoi(t)));
 #endif
+  // per depth tile and direction, the sum of the steps' dtau / ln 2 (DELO-linear tile slopes)
+  const int T = P->ntile_st, L = (Ns - 1 + T - 1) / T;
+  std::vector<float> tdt(2 * (size_t)T, 0.f);
+  for (int h = 0; h < 2; ++h)
+    for (int t = 0; t < T; ++t) {
+      double sum = 0.0;
+      for (int j = 1 + t * L; j < std::min(Ns, 1 + (t + 1) * L); ++j) {
+        const int k = h == 0 ? j : Ns - 1 - j;
+        sum += (h == 0 ? P->tau[k] - P->tau[k - 1] : P->tau[k + 1] - P->tau[k]) / kLn2;
+      }
+      tdt[(size_t)h * T + t] = (float)sum;
+    }
   const int rows = std::max(P->quad_gy, P->quadn_gy);
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->qw, qw.size() * sizeof(float)));
   RT_TRY_CUDA(cudaMemcpyAsync(P->qw, qw.data(), qw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->stab, tab.size() * sizeof(float4)));
   RT_TRY_CUDA(cudaMemcpyAsync(P->stab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->qpart, (size_t)Ns * P->quad_gx * 2 * sizeof(float)));
+  RT_TRY_CUDA(dev_alloc(P, (void**)&P->tile_dt, tdt.size() * sizeof(float)));
+  RT_TRY_CUDA(cudaMemcpyAsync(P->tile_dt, tdt.data(), tdt.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->qcnt, (size_t)rows * sizeof(int)));
   RT_TRY_CUDA(cudaMemsetAsync(P->qcnt, 0, (size_t)rows * sizeof(int), st));
   RT_TRY_CUDA(cudaStreamSynchronize(st));
@@ -952,6 +1058,11 @@ bool staged_apply32(Problem* P, const void* x, void* y, bool f64io, int mode, cu
       *status = staged_apply<double, KM_LOCAL_LAMBDA>(P, xd, yd, st, kstop, step, nin);
       return true;
   }
+}
+
+void staged_release(Problem* P) {
+  delete static_cast<MapCache*>(P->tma_cache);
+  P->tma_cache = nullptr;
 }
 
 rt_status check_device_flag(Problem* P, cudaStream_t st) {
