@@ -53,6 +53,8 @@ enum VecId { VX = 100, VB, VR, VW, VT, VTMP };
 struct InstDev {
   int Ns, Nmu, Nnu, Nh, ngd, ngroups, fs, nchunks, chunk, m;
   int64_t nray, nd, N;
+  int64_t cstride;   // columns of the FP64 tables (coef_col)
+  int cshare;
   double xi, xiW2, inflow_bottom;
   const double *ce, *ca, *cb, *wnu, *wmu, *wray, *t201, *t202, *Minv;
   const float *dtau32, *r32, *wnu32, *wmu32, *t201f, *t202f;
@@ -165,6 +167,9 @@ __device__ __forceinline__ void formal_item(const InstDev& I, int g, int s0, int
   A.ce = I.ce;
   A.ca = I.ca;
   A.cb = I.cb;
+  A.cg = nullptr;
+  A.cstride = I.cstride;
+  A.cshare = I.cshare;
   A.dtau32 = I.dtau32;
   A.r32 = I.r32;
   A.S = sizeof(TC) == 8 ? (const void*)I.S : (const void*)I.S32;
@@ -434,7 +439,8 @@ __global__ void __launch_bounds__(kBT) kb_add_local(const InstDev* __restrict__ 
     const InstDev& I = insts[it.x];
     CHUNK_LOOP(const int64_t rr = n_ % I.nray; const int64_t sk = n_ / I.nray; const int k = (int)(sk % I.Ns);
                const int s = (int)(sk / I.Ns); const int m = (int)(rr / I.Nnu);
-               I.x[n_] += I.t[n_] + beta_star(I.cb, k, m, rr, I.Ns, I.Nh, I.nray) *
+               I.x[n_] += I.t[n_] + beta_star(I.cb, k, m, coef_col(rr, I.Nh, I.Nnu, I.cshare), I.cstride, I.Ns,
+                                              I.Nh) *
                                          I.S2[((int64_t)s * I.Ns + k) * I.Nmu + m];)
   }
 }
@@ -1008,6 +1014,8 @@ rt_status make_instance(Server* S, Request* rq, Instance* in, int slot) {
   D.ce = P.ce;
   D.ca = P.ca;
   D.cb = P.cb;
+  D.cstride = P.cstride;
+  D.cshare = P.cshare;
   D.wnu = P.wI2;
   D.wmu = P.wQ2;
   D.wray = P.wray;

@@ -222,6 +222,19 @@ struct BicgDev {
   int half;        // BiCGSTAB converged at the half step
 };
 
+// Column of the FP64 step-coefficient tables for ray r = m*Nnu + p.  Without
+// a downwind term the coefficients of a step depend on |mu| only, so the
+// tables hold one column per (|mu|, p) that both directions share (shared =
+// 1, nray/2 columns): m < Nh (mu < 0) reads column (Nh-1-m)*Nnu + p, m >= Nh
+// column (m-Nh)*Nnu + p.  DELO-parabolic's coefficients include the downwind
+// interval, which differs between the directions: one column per ray.
+__host__ __device__ __forceinline__ int64_t coef_col(int64_t r, int Nh, int Nnu, int shared) {
+  if (!shared) return r;
+  const int m = (int)(r / Nnu);
+  const int64_t p = r - (int64_t)m * Nnu;
+  return (int64_t)(m < Nh ? Nh - 1 - m : m - Nh) * Nnu + p;
+}
+
 // Device memory source of a problem: NULL means cudaMalloc/cudaFree; the
 // batch server passes its arena; rt_problem_create_with_allocator the
 // caller's hook.
@@ -259,7 +272,9 @@ struct Problem {
   int ngroups = 0;
   int ntile64 = 1, ntile32 = 1;   // depth tiles per ray group (FP64 / FP32 kernels)
   // FP64 device tables
-  double* ce = nullptr;    // [(Ns-1)][nray] step factor e of the interval (i, i+1) on ray r
+  int cshare = 0;          // 1: the FP64 tables hold one column per (|mu|, p), shared by both directions
+  int64_t cstride = 0;     // columns of the FP64 tables: nray/2 (shared) or nray (DELO-parabolic)
+  double* ce = nullptr;    // [(Ns-1)][cstride] step factor e of the interval (i, i+1), column coef_col(r)
   double* ca = nullptr;    // ... alpha (coefficient of the upwind S)
   double* cb = nullptr;    // ... beta  (coefficient of S at the new node)
   double* cg = nullptr;    // ... gamma (DELO-parabolic only: coefficient of S at the downwind node)

@@ -26,19 +26,21 @@ __device__ __forceinline__ T warp_sum(T v) {
 // beta* (coefficient of S_k in I_k) of ray r = m*Nnu + p at height k: the
 // beta of the step ending at k; with the DELO-parabolic downwind coefficients
 // cg (else NULL) also e_k times the gamma of the step before, whose downwind
-// node is k.
-__device__ __forceinline__ double beta_star(const double* __restrict__ cb, int k, int m, int64_t r, int Ns,
-                                            int Nh, int64_t nray, const double* __restrict__ ce = nullptr,
+// node is k.  col = coef_col(r, ...) and cstride: the table column and row
+// length (coef_col).
+__device__ __forceinline__ double beta_star(const double* __restrict__ cb, int k, int m, int64_t col,
+                                            int64_t cstride, int Ns, int Nh,
+                                            const double* __restrict__ ce = nullptr,
                                             const double* __restrict__ cg = nullptr) {
   if (m < Nh) {
     if (k == 0) return 0.0;
-    double b = cb[(int64_t)(k - 1) * nray + r];
-    if (cg && k >= 2) b += ce[(int64_t)(k - 1) * nray + r] * cg[(int64_t)(k - 2) * nray + r];
+    double b = cb[(int64_t)(k - 1) * cstride + col];
+    if (cg && k >= 2) b += ce[(int64_t)(k - 1) * cstride + col] * cg[(int64_t)(k - 2) * cstride + col];
     return b;
   }
   if (k == Ns - 1) return 0.0;
-  double b = cb[(int64_t)k * nray + r];
-  if (cg && k <= Ns - 3) b += ce[(int64_t)k * nray + r] * cg[(int64_t)(k + 1) * nray + r];
+  double b = cb[(int64_t)k * cstride + col];
+  if (cg && k <= Ns - 3) b += ce[(int64_t)k * cstride + col] * cg[(int64_t)(k + 1) * cstride + col];
   return b;
 }
 
@@ -255,6 +257,8 @@ struct FormalArgs {
   const double* ca;
   const double* cb;
   const double* cg;       // DELO-parabolic: downwind coefficient table (else NULL)
+  int64_t cstride;        // columns of the FP64 tables (coef_col)
+  int cshare;             // 1: one column per (|mu|, p) shared by both directions
   const float* dtau32;    // FP32: interval optical depths
   const float* r32;       // FP32: per-ray scale phi_hat/|mu|
   const void* S;          // source functions (TC) [2][Ns][Nmu]
@@ -289,6 +293,7 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
   TV* __restrict__ y = reinterpret_cast<TV*>(A.y) + (int64_t)s0 * plane;
   const double* __restrict__ dinv = A.dinv + (int64_t)s0 * plane;
   const float rs = (sizeof(TC) == 4) ? A.r32[r] : 0.0f;
+  const int64_t col = coef_col(r, A.Nmu / 2, A.Nnu, A.cshare), cstride = A.cstride;
   auto height = [&](int j) { return down ? j : Ns - 1 - j; };
   auto interval = [&](int j) { return down ? j - 1 : Ns - 1 - j; };
   TC sp[NS];
@@ -296,7 +301,7 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
   for (int q = 0; q < NS; ++q) sp[q] = Sm[q * sstride + (int64_t)height(j0 - 1) * A.Nmu];  // upwind source
   // gamma of the step before j0 (its downwind node is the tile's first node)
   TC gp = 0;
-  if (PARA && j0 >= 2) gp = (TC)A.cg[(int64_t)interval(j0 - 1) * nray + r];
+  if (PARA && j0 >= 2) gp = (TC)A.cg[(int64_t)interval(j0 - 1) * cstride + col];
   // register ring of the next RING steps
   TC re[RING], ra[RING], rb[RING], rg[RING], rsv[RING][NS], rx[RING][NS], rd[RING][NS];
   if (PARA) {
@@ -309,7 +314,7 @@ __device__ __forceinline__ void sweep(const FormalArgs& A, int s0, bool down, in
     if (j < j1) {
       const int k = height(j), i = interval(j);
       if (sizeof(TC) == 8) {
-        const int64_t c = (int64_t)i * nray + r;
+        const int64_t c = (int64_t)i * cstride + col;
         re[u] = (TC)A.ce[c];
         ra[u] = (TC)A.ca[c];
         rb[u] = (TC)A.cb[c];

@@ -52,12 +52,14 @@ namespace {
 // interval of a ray, where the step stays DELO-linear):
 //   alpha += q / (D (D + Dn)),  beta -= q / (D Dn),  gamma = q / (Dn (D + Dn)).
 __global__ void k_coeffs64(const double* __restrict__ dtau, const double* __restrict__ rscale, int Ns,
-                           int64_t nray, int Nh, int Nnu, int fs, double* __restrict__ ce, double* __restrict__ ca,
-                           double* __restrict__ cb, double* __restrict__ cg) {
-  const int64_t n = (int64_t)(Ns - 1) * nray;
+                           int64_t cstride, int shared, int Nh, int Nnu, int fs, double* __restrict__ ce,
+                           double* __restrict__ ca, double* __restrict__ cb, double* __restrict__ cg) {
+  const int64_t n = (int64_t)(Ns - 1) * cstride;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t % nray;
-    const int i = (int)(t / nray);
+    const int64_t c = t % cstride;
+    const int i = (int)(t / cstride);
+    // the ray this column stands for (shared columns: the upward ray of that |mu| and p)
+    const int64_t r = shared ? ((int64_t)Nh + c / Nnu) * Nnu + c % Nnu : c;
     const double D = dtau[i] * rscale[r];
     double e, al, be;
     if (fs == RT_FS_DELO_LINEAR || fs == RT_FS_DELO_PARABOLIC) {
@@ -128,8 +130,8 @@ __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __re
                                                              const double* __restrict__ wray,
                                                              const double* __restrict__ t201,
                                                              const double* __restrict__ t202, int Ns, int Nmu,
-                                                             int Nnu, double xi, double W2,
-                                                             double* __restrict__ Minv,
+                                                             int Nnu, int64_t cstride, int shared, double xi,
+                                                             double W2, double* __restrict__ Minv,
                                                              double* __restrict__ Mdiag) {
   const int k = blockIdx.x;
   const int Nh = Nmu / 2;
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __re
   double a0 = 0, a1 = 0, a2 = 0;
   for (int64_t r = threadIdx.x; r < nray; r += blockDim.x) {
     const int m = (int)(r / Nnu);
-    const double s = wray[r] * beta_star(cb, k, m, r, Ns, Nh, nray, ce, cg);
+    const double s = wray[r] * beta_star(cb, k, m, coef_col(r, Nh, Nnu, shared), cstride, Ns, Nh, ce, cg);
     a0 += s;
     a1 += t201[m] * s;
     a2 += (t201[m] * t201[m] + t202[m] * t202[m]) * s;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(kMomThreads) k_local_blocks(const double* __re
 __global__ void k_jacobi(const double* __restrict__ cb, const double* __restrict__ ce, const double* __restrict__ cg,
                          const double* __restrict__ wray,
                          const double* __restrict__ t201, const double* __restrict__ t202, int Ns, int Nmu, int Nnu,
-                         double xi, double W2, int inverse, double* __restrict__ d) {
+                         int64_t cstride, int shared, double xi, double W2, int inverse, double* __restrict__ d) {
   const int Nh = Nmu / 2;
   const int64_t nray = (int64_t)Nmu * Nnu, N = 2 * (int64_t)Ns * nray;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -175,7 +177,7 @@ __global__ void k_jacobi(const double* __restrict__ cb, const double* __restrict
     const int64_t sk = t / nray;
     const int k = (int)(sk % Ns), s = (int)(sk / Ns);
     const int m = (int)(r / Nnu);
-    const double bw = beta_star(cb, k, m, r, Ns, Nh, nray, ce, cg) * wray[r];
+    const double bw = beta_star(cb, k, m, coef_col(r, Nh, Nnu, shared), cstride, Ns, Nh, ce, cg) * wray[r];
     const double v = s == 0 ? 1.0 - xi * bw * (1.0 + W2 * t201[m] * t201[m]) : 1.0 - xi * W2 * bw * t202[m] * t202[m];
     d[t] = inverse ? 1.0 / v : v;
   }
@@ -193,7 +195,8 @@ __global__ void k_rhs_source(const double* __restrict__ B, int Ns, int Nmu, doub
 // z = v + beta* S (the Lambda* T M^{-1} J part of P^{-1} v, S = T M^{-1} J v)
 __global__ void k_add_local(const double* __restrict__ v, const double* __restrict__ cb, const double* __restrict__ ce,
                             const double* __restrict__ cg, const double* __restrict__ S,
-                            int Ns, int Nmu, int Nnu, double* __restrict__ z, const int* kstop, int step) {
+                            int Ns, int Nmu, int Nnu, int64_t cstride, int shared, double* __restrict__ z,
+                            const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
   const int Nh = Nmu / 2;
   const int64_t nray = (int64_t)Nmu * Nnu, N = 2 * (int64_t)Ns * nray;
@@ -201,7 +204,8 @@ __global__ void k_add_local(const double* __restrict__ v, const double* __restri
     const int64_t r = t % nray, sk = t / nray;
     const int k = (int)(sk % Ns), s = (int)(sk / Ns);
     const int m = (int)(r / Nnu);
-    z[t] = v[t] + beta_star(cb, k, m, r, Ns, Nh, nray, ce, cg) * S[((int64_t)s * Ns + k) * Nmu + m];
+    z[t] = v[t] + beta_star(cb, k, m, coef_col(r, Nh, Nnu, shared), cstride, Ns, Nh, ce, cg) *
+                      S[((int64_t)s * Ns + k) * Nmu + m];
   }
 }
 
@@ -433,8 +437,8 @@ __device__ __forceinline__ void group_ray(const FormalArgs& A, int g, int lane, 
 
 // slope of tile t's map for every ray, E = product of the e coefficients of
 // its steps in marching order: Etile[t][r], t < T-1 (setup)
-__global__ void k_etile(const double* __restrict__ ce, int Ns, int64_t nray, int64_t nd, int T,
-                        double* __restrict__ Etile) {
+__global__ void k_etile(const double* __restrict__ ce, int Ns, int64_t nray, int64_t nd, int T, int64_t cstride,
+                        int shared, int Nh, int Nnu, double* __restrict__ Etile) {
   const int L = (Ns - 1 + T - 1) / T;
   const int64_t n = (int64_t)(T - 1) * nray;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -442,8 +446,9 @@ __global__ void k_etile(const double* __restrict__ ce, int Ns, int64_t nray, int
     const int64_t r = i % nray;
     const bool down = r < nd;
     const int j0 = 1 + t * L, j1 = min(Ns, j0 + L);
+    const int64_t col = coef_col(r, Nh, Nnu, shared);
     double E = 1.0;
-    for (int j = j0; j < j1; ++j) E *= ce[(int64_t)(down ? j - 1 : Ns - 1 - j) * nray + r];
+    for (int j = j0; j < j1; ++j) E *= ce[(int64_t)(down ? j - 1 : Ns - 1 - j) * cstride + col];
     Etile[i] = E;
   }
 }
@@ -459,8 +464,8 @@ __global__ void k_etile(const double* __restrict__ ce, int Ns, int64_t nray, int
 // kernel is then one independent FMA per node instead of a dependent
 // recurrence.  K[t][n][r], n < L + 2.
 __global__ void k_kmap(const double* __restrict__ ce, const double* __restrict__ ca, const double* __restrict__ cb,
-                       const double* __restrict__ cg, int Ns, int64_t nray, int64_t nd, int T,
-                       double* __restrict__ K) {
+                       const double* __restrict__ cg, int Ns, int64_t nray, int64_t nd, int T, int64_t cstride,
+                       int shared, int Nh, int Nnu, double* __restrict__ K) {
   const int L = (Ns - 1 + T - 1) / T;
   const int64_t n = (int64_t)(T - 1) * nray;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -470,9 +475,10 @@ __global__ void k_kmap(const double* __restrict__ ce, const double* __restrict__
     const int j0 = 1 + t * L, j1 = min(Ns, j0 + L);
     double* __restrict__ Kt = K + (int64_t)t * (L + 2) * nray + r;
     for (int q = 0; q < L + 2; ++q) Kt[(int64_t)q * nray] = 0.0;
+    const int64_t col = coef_col(r, Nh, Nnu, shared);
     double Pj = 1.0;   // product of e over the steps after j
     for (int j = j1 - 1; j >= j0; --j) {
-      const int64_t c = (int64_t)(down ? j - 1 : Ns - 1 - j) * nray + r;
+      const int64_t c = (int64_t)(down ? j - 1 : Ns - 1 - j) * cstride + col;
       const int q = j - j0 + 1;   // local index of node j
       Kt[(int64_t)q * nray] += Pj * cb[c];
       Kt[(int64_t)(q - 1) * nray] += Pj * ca[c];
@@ -606,7 +612,11 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   RT_TRY(upload(P, &P->t201d, P->t201, st));
   RT_TRY(upload(P, &P->t202d, P->t202, st));
   RT_TRY(upload(P, &P->Bd, P->B, st));
-  const size_t nc = (size_t)(Ns - 1) * nray;
+  // the step coefficients depend on |mu| only unless the scheme has a
+  // downwind term: one table column per (|mu|, p) then serves both directions
+  P->cshare = P->fs != RT_FS_DELO_PARABOLIC;
+  P->cstride = P->cshare ? nray / 2 : nray;
+  const size_t nc = (size_t)(Ns - 1) * P->cstride;
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->ce, nc * sizeof(double)));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->ca, nc * sizeof(double)));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->cb, nc * sizeof(double)));
@@ -614,8 +624,9 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->S, (size_t)2 * Ns * Nmu * sizeof(double)));
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->S2, (size_t)2 * Ns * Nmu * sizeof(double)));
   if (P->fs == RT_FS_DELO_PARABOLIC) RT_TRY_CUDA(dev_alloc(P, (void**)&P->cg, nc * sizeof(double)));
-  k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_rs, Ns, nray, Nh, Nnu, P->fs,
-                                                                         P->ce, P->ca, P->cb, P->cg); RT_COUNT(1);
+  k_coeffs64<<<grid_for((int64_t)nc, 256, 8 * P->num_sms), 256, 0, st>>>(d_dtau, d_rs, Ns, P->cstride, P->cshare,
+                                                                         Nh, Nnu, P->fs, P->ce, P->ca, P->cb, P->cg);
+  RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   if (P->ntile64 > 1) {   // the FP64 formal solver's tile slopes and map buffer
     const int T = P->ntile64;
@@ -626,16 +637,18 @@ rt_status setup_device_tables(Problem* P, cudaStream_t st) {
     const int L = (Ns - 1 + T - 1) / T;
     const int64_t nk = (int64_t)(T - 1) * (L + 2) * nray;
     RT_TRY_CUDA(dev_alloc(P, (void**)&P->Kmap, (size_t)nk * sizeof(double)));
-    k_kmap<<<grid_for((int64_t)(T - 1) * nray, 256, 8 * P->num_sms), 256, 0, st>>>(P->ce, P->ca, P->cb, P->cg, Ns,
-                                                                                    nray, P->nd, T, P->Kmap);
+    k_kmap<<<grid_for((int64_t)(T - 1) * nray, 256, 8 * P->num_sms), 256, 0, st>>>(
+        P->ce, P->ca, P->cb, P->cg, Ns, nray, P->nd, T, P->cstride, P->cshare, Nh, Nnu, P->Kmap);
     RT_COUNT(1);
-    k_etile<<<grid_for((int64_t)(T - 1) * nray, 256, 8 * P->num_sms), 256, 0, st>>>(P->ce, Ns, nray, P->nd, T,
-                                                                                     P->Etile); RT_COUNT(1);
+    k_etile<<<grid_for((int64_t)(T - 1) * nray, 256, 8 * P->num_sms), 256, 0, st>>>(
+        P->ce, Ns, nray, P->nd, T, P->cstride, P->cshare, Nh, Nnu, P->Etile);
+    RT_COUNT(1);
     RT_TRY_CUDA(cudaGetLastError());
   }
   RT_TRY_CUDA(dev_alloc(P, (void**)&P->Mdiag, (size_t)Ns * 2 * sizeof(double)));
-  k_local_blocks<<<Ns, kMomThreads, 0, st>>>(P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d, Ns, Nmu, Nnu, P->xi,
-                                             P->W2, P->Minv, P->Mdiag); RT_COUNT(1);
+  k_local_blocks<<<Ns, kMomThreads, 0, st>>>(P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d, Ns, Nmu, Nnu,
+                                             P->cstride, P->cshare, P->xi, P->W2, P->Minv, P->Mdiag);
+  RT_COUNT(1);
   if (P->form == RT_FORM_SIGMA) RT_TRY_CUDA(dev_alloc(P, (void**)&P->Ibuf, (size_t)P->N * sizeof(double)));
   RT_TRY_CUDA(cudaGetLastError());
   // FP32 tables
@@ -671,6 +684,8 @@ static FormalArgs formal_args(const Problem* P, const void* x, void* y, const vo
   A.ca = P->ca;
   A.cb = P->cb;
   A.cg = P->cg;
+  A.cstride = P->cstride;
+  A.cshare = P->cshare;
   A.dtau32 = P->dtau32;
   A.r32 = P->r32;
   A.S = S;
@@ -869,7 +884,8 @@ rt_status op_apply32_f64io(Problem* P, const double* x, double* y, int mode, cud
 rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st) {
   if (P->form == RT_FORM_SIGMA) return op_jacobi_sigma(P, dinv, 1, st);
   k_jacobi<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d,
-                                                                 P->Ns, P->Nmu, P->Nnu, P->xi, P->W2, 1, dinv);
+                                                                 P->Ns, P->Nmu, P->Nnu, P->cstride, P->cshare, P->xi,
+                                                                 P->W2, 1, dinv);
   RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
@@ -903,7 +919,8 @@ rt_status op_precond_ll(Problem* P, const double* v, double* z, cudaStream_t st,
                                                                 P->Ns, P->Nmu, P->nray, P->xi, xiW2, P->S2, kstop,
                                                                 step); RT_COUNT(1);
   k_add_local<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, st>>>(v, P->cb, P->ce, P->cg, P->S2, P->Ns, P->Nmu,
-                                                                    P->Nnu, z, kstop, step); RT_COUNT(1);
+                                                                    P->Nnu, P->cstride, P->cshare, z, kstop, step);
+  RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
@@ -960,7 +977,9 @@ rt_status rt_jacobi_diag(rt_problem* prob, double* d_dev, void* stream) {
   Problem* P = &prob->P;
   if (P->form == RT_FORM_SIGMA) return op_jacobi_sigma(P, d_dev, 0, as_stream(stream));
   k_jacobi<<<grid_for(P->N, 256, 8 * P->num_sms), 256, 0, as_stream(stream)>>>(
-      P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d, P->Ns, P->Nmu, P->Nnu, P->xi, P->W2, 0, d_dev); RT_COUNT(1);
+      P->cb, P->ce, P->cg, P->wray, P->t201d, P->t202d, P->Ns, P->Nmu, P->Nnu, P->cstride, P->cshare, P->xi, P->W2, 0,
+      d_dev);
+  RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
