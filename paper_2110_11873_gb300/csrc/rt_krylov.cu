@@ -461,28 +461,27 @@ inline int mgs_grid(const Problem* P) {
 
 // back substitution H(0:k,0:k) y = g(0:k) in the textbook order: row k-1
 // first, each row's sum running from g_i over l = i+1.. in increasing order,
-// then one division.  The warp stages the triangle in shared memory (cycles
-// of up to kLsqStage steps) and thread 0 runs the recurrence.  The order
-// matters in FP32 refinement: a warp-tree sum of the same products changed
-// the inner solves' iteration counts by up to 10%.
-constexpr int kLsqStage = 64;
+// then one division.  The warp stages the triangle in shared memory (packed
+// by columns; 103 KB for the longest cycle, 160 steps) and thread 0 runs the
+// recurrence from there.  The order matters in FP32 refinement: a warp-tree
+// sum of the same products changed the inner solves' iteration counts by up
+// to 10%.  Dynamic shared memory for cycles of up to m steps: the packed
+// triangle, then y.
+inline size_t lsq_smem(int m) { return ((size_t)m * (m + 1) / 2 + (size_t)m) * sizeof(double); }
+
 __global__ void k_lsq(GmresDev* gm, int m) {
   const int k = gm->kdone, lane = threadIdx.x;
-  __shared__ double Hs[kLsqStage * kLsqStage], ys[kMaxRestart];
-  const bool staged = k <= kLsqStage;
-  if (staged)
-    for (int idx = lane; idx < k * k; idx += 32) {
-      const int l = idx / k, i = idx - l * k;
-      if (i <= l) Hs[idx] = gm->H[l * (m + 1) + i];
-    }
+  extern __shared__ double lsq_sm[];
+  double* Hs = lsq_sm;                          // column l (rows 0..l) at l (l + 1) / 2
+  double* ys = lsq_sm + (size_t)m * (m + 1) / 2;
+  for (int l = 0; l < k; ++l)
+    for (int i = lane; i <= l; i += 32) Hs[l * (l + 1) / 2 + i] = gm->H[l * (m + 1) + i];
   __syncwarp();
-  const double* H = staged ? Hs : gm->H;
-  const int ld = staged ? k : m + 1;
   if (lane == 0) {
     for (int i = k - 1; i >= 0; --i) {
       double s = gm->g[i];
-      for (int l = i + 1; l < k; ++l) s -= H[l * ld + i] * ys[l];
-      ys[i] = s / H[i * ld + i];
+      for (int l = i + 1; l < k; ++l) s -= Hs[l * (l + 1) / 2 + i] * ys[l];
+      ys[i] = s / Hs[i * (i + 1) / 2 + i];
     }
   }
   __syncwarp();
@@ -838,6 +837,16 @@ struct Workspace {
 };
 
 static rt_status ensure_workspace(Problem* P, int restart, cudaStream_t st) {
+  {
+    // k_lsq's shared triangle of the longest cycle (103 KB) needs the opt-in;
+    // set here, outside any stream capture
+    static std::once_flag lsq_attr;
+    static cudaError_t lsq_err = cudaSuccess;
+    std::call_once(lsq_attr, [] {
+      lsq_err = cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsq_smem(kMaxRestart));
+    });
+    RT_TRY_CUDA(lsq_err);
+  }
   if (!P->vec_grid) {
     int64_t g = (P->Nop + 2 * kVecThreads - 1) / (2 * kVecThreads);
     int cap = 4 * P->num_sms;
@@ -1065,7 +1074,7 @@ static rt_status enqueue_cycle(Problem* P, int m, int precond, int fp32, cudaStr
                                               gm, m, m - 1, hist, hcap, kstop); RT_COUNT(1);
   }
   RT_TRY_CUDA(cudaGetLastError());
-  k_lsq<<<1, 32, 0, st>>>(gm, m); RT_COUNT(1);
+  k_lsq<<<1, 32, lsq_smem(m), st>>>(gm, m); RT_COUNT(1);
   double* x = wk(P, 0);
   double* t = wk(P, 4);
   if (precond == RT_PREC_LOCAL_LAMBDA || precond == RT_PREC_SOR || precond == RT_PREC_SSOR) {

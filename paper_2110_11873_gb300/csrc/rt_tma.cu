@@ -83,6 +83,7 @@ constexpr unsigned long long kWaitNs = 1000000000ull;   // bound of one wait
 constexpr int kQuadThreads = 256;
 constexpr int kQuadMaxHeights = 64;            // heights per CTA of k_quad
 constexpr int kQuadBatch = 2;                  // heights per batch of loads (two batches in flight)
+constexpr int kQuadFinal = 4096;               // partials a row's last CTA stages in shared memory
 
 template <typename TV, int MODE>
 struct Cfg {
@@ -293,6 +294,7 @@ __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double
   constexpr int U = kQuadBatch;
   static_assert(U == 2, "the transposing reduction takes two heights of two values");
   __shared__ float red[kQuadMaxHeights][nw][2];
+  __shared__ float fin[kQuadFinal];
   __shared__ int last;
   const int Ns = Q.Ns;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -382,15 +384,24 @@ __device__ __forceinline__ void quad_tile(const TV* __restrict__ x, const double
   __threadfence();
   // the row's last CTA: one warp per height sums the columns' partials
   // (lane-strided, then the fixed shuffle tree: the order does not depend on
-  // which CTA came last)
+  // which CTA came last).  The row's partials are one contiguous block; when
+  // it fits, the whole CTA first copies it to shared memory, so the block
+  // costs one round trip to L2 instead of one per height.
   const int gx = gridDim.x;
+  const int nrow = (k_hi - k_lo) * gx * 2;
+  const float* prow = Q.part + (int64_t)k_lo * gx * 2;
+  const bool staged = nrow <= kQuadFinal;
+  if (staged) {
+    for (int i = threadIdx.x; i < nrow; i += kQuadThreads) fin[i] = __ldcg(prow + i);
+    __syncthreads();
+  }
   for (int i = warp; i < k_hi - k_lo; i += nw) {
     const int k = k_lo + i;
-    const float* p = Q.part + (int64_t)k * gx * 2;
+    const float* p = staged ? fin + i * gx * 2 : Q.part + (int64_t)k * gx * 2;
     float a = 0.f, b = 0.f;
     for (int j = lane; j < gx; j += 32) {
-      a += __ldcg(p + 2 * j);
-      b += __ldcg(p + 2 * j + 1);
+      a += staged ? p[2 * j] : __ldcg(p + 2 * j);
+      b += staged ? p[2 * j + 1] : __ldcg(p + 2 * j + 1);
     }
     a = warp_sum(a);
     b = warp_sum(b);
