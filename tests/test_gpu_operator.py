@@ -159,12 +159,14 @@ def test_arnoldi_mgs_step_against_plain_mgs():
     np.testing.assert_allclose(to_host(wd), w, rtol=1e-11, atol=1e-14)
 
 
-@pytest.mark.parametrize("j", [0, 3, 4, 6, 9, 31])
+@pytest.mark.parametrize("j", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 15, 31, 63, 158, 159])
 def test_arnoldi_block_mgs_step_against_plain_mgs(j):
     """rt_arnoldi_bmgs (the GMRES orthogonalisation): blocks of 4 basis vectors
     with the Gram correction give the MGS coefficients of the same loop in
     numpy, on a basis that is orthonormal only to rounding (its Gram rows
-    computed in numpy), and write the Gram row of the new vector."""
+    computed in numpy), and write the Gram row of the new vector.  j covers
+    every size of the last block, with and without a full block before it,
+    and the last steps of the longest cycle (160)."""
     at = W.slab(37, 6, 33, 1e-4, 1e6, 6.0)
     P = problem(at)
     N = P.N
