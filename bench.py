@@ -41,9 +41,16 @@ METRIC = "operator applies/s & HBM GB/s; batched solves/s at resid 1e-8; p50/p99
 FP64_NOMINAL_TFLOPS = 1.25   # 2 FLOP x 2 FP64 lanes/clk/SM x 152 SMs x 2.06 GHz (context only)
 # DRAM bytes (read + write) of one block-MGS step at j = 15 on slab300: the
 # sum over its six launches in one ncu capture of `bench.py --probe bmgs
-# --probe-ns 300` (k_bdot 78.4 MB, 3 x k_bmgs<4,4> 147-148 MB, k_bmgs<4,0>
-# 78.6 MB, k_bscale 15.6 MB); retaken whenever these kernels change
-MGS_STEP_DRAM_BYTES = 616.3e6
+# --probe-ns 300` (k_bdot 78.7 MB, 3 x k_bmgs<4,4> 146.7-147.0 MB,
+# k_bmgs<4,0> 78.7 MB, k_bscale 15.6 MB); retaken whenever these kernels change
+MGS_STEP_DRAM_BYTES = 613.3e6
+# GMRES restart length of the batched and served solves (local-Lambda, FP32
+# operator inside FP64 refinement).  The Arnoldi step's FP64 work grows with
+# the cycle length, the step count falls with it; on the 512-atmosphere batch
+# restart 6-12 gave 274-294 solves/s against 214 at 30 (5: 224, 15: 267,
+# 20: 248), so the served cycles are 10 steps long.  The single-instance
+# FP64 comparison runs at the same restart.
+BATCH_RESTART = 10
 WORKLOAD = "slab300: Ns=300 Nmu=32 Nnu=101 (1,939,200 unknowns), line-centre tau 1e-4..1e8, x in [-8,8], " \
            "eps=1e-4 a=1e-3 W2=1, DELO-linear; Jacobi-GMRES(30) to 1e-8"
 
@@ -333,7 +340,8 @@ def batch_bench(W, Server, Problem, torch, count, keep=24):
     ats = W.batch_instances(count)
     n1 = min(16, count)
     keep = min(keep, count)
-    srv = Server(mem_budget_bytes=160 << 30, max_slots=count, precond="local_lambda", precision="fp32_refine")
+    srv = Server(mem_budget_bytes=160 << 30, max_slots=count, restart=BATCH_RESTART, precond="local_lambda",
+                 precision="fp32_refine")
     t0 = _t.perf_counter()
     tickets = [srv.submit(a) for a in ats]
     res = _drain(srv, tickets, want_x=set(tickets[:max(n1, keep)]))
@@ -350,7 +358,7 @@ def batch_bench(W, Server, Problem, torch, count, keep=24):
     for a in ats[:n1]:
         P = Problem(a)
         b = P.rhs()
-        xs, info = P.solve(b, "gmres", restart=30, precond="local_lambda", rtol=1e-8)
+        xs, info = P.solve(b, "gmres", restart=BATCH_RESTART, precond="local_lambda", rtol=1e-8)
         xref.append(xs.cpu().numpy())
         P.close()
     torch.cuda.synchronize()
@@ -364,7 +372,7 @@ def batch_bench(W, Server, Problem, torch, count, keep=24):
                        "Nnu~U{21..101} odd, Nmu in {8,16,32}, eps log-U[1e-6,1e-2], a log-U[1e-4,1e-2], "
                        "B=1+c log10(1+tau)",
            "precision": "FP32 operator, FP64 Arnoldi and FP64 restart residual (refinement)",
-           "solves": len(ok), "failed": count - len(ok), "wall_s": wall, "solves_per_s": len(ok) / wall,
+           "restart": BATCH_RESTART, "solves": len(ok), "failed": count - len(ok), "wall_s": wall, "solves_per_s": len(ok) / wall,
            "iters_mean": sum(its) / max(len(its), 1), "rel_resid_max": max(rel) if rel else None,
            "cycles": stats["cycles"],
            "grids_ctas": {"quadrature": stats["grid_quad"], "formal": stats["grid_formal"],
@@ -384,7 +392,8 @@ def serve_bench(W, Server, rates, nreq, keep=8):
     out, kept = {}, {}
     for rate in rates:
         arr = W.poisson_arrivals(rate, nreq)
-        srv = Server(mem_budget_bytes=64 << 30, max_slots=512, precond="local_lambda", precision="fp32_refine")
+        srv = Server(mem_budget_bytes=64 << 30, max_slots=512, restart=BATCH_RESTART, precond="local_lambda",
+                     precision="fp32_refine")
         pending, lat, done_t = {}, [], []
         kept[rate] = {}
         t0 = _t.perf_counter()
@@ -409,7 +418,7 @@ def serve_bench(W, Server, rates, nreq, keep=8):
         srv.close()
         lat.sort()
         span = max(done_t) - float(arr[0])
-        out[str(rate)] = {"offered_req_per_s": rate, "requests": nreq,
+        out[str(rate)] = {"offered_req_per_s": rate, "requests": nreq, "restart": BATCH_RESTART,
                           "achieved_solves_per_s": nreq / span,
                           "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
     return out, kept

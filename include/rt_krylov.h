@@ -317,7 +317,13 @@ enum {
   RT_PREC_SOR_LEFT = 6,
   RT_PREC_SSOR_LEFT = 7
 };
-enum { RT_X0_ZERO = 0, RT_X0_USER = 1 };
+/* Initial guess: zero, the caller's x_dev, or the paper's (Sect. 4.2: sigma
+   = [1, 0, 1, 0, ...], i.e. sigma^0_0 = 1 and sigma^2_0 = 0 at every
+   height).  For RT_FORM_SIGMA RT_X0_PAPER is that vector; for the I-form it
+   is the radiation field that sigma produces, Lambda(T sigma) + t (Eq. 19):
+   one formal solve with S_I = 1, S_Q = 0 and the boundary radiation.  The
+   batch server always starts from zero. */
+enum { RT_X0_ZERO = 0, RT_X0_USER = 1, RT_X0_PAPER = 2 };
 enum { RT_ORTHO_MGS = 0, RT_ORTHO_CGS2 = 1 };
 enum { RT_PRECISION_FP64 = 0, RT_PRECISION_FP32_REFINE = 1 };
 
@@ -325,7 +331,7 @@ typedef struct {
   int32_t restart;       /* GMRES restart length m, 1..160 (Sect. 2.1) */
   int32_t maxit;         /* cap on iterations (Arnoldi steps / BiCGSTAB-CGS iterations) */
   int32_t precond;       /* RT_PREC_*, applied from the right */
-  int32_t x0_kind;       /* RT_X0_ZERO, or RT_X0_USER: x_dev holds the initial guess */
+  int32_t x0_kind;       /* RT_X0_ZERO, RT_X0_USER (x_dev holds the initial guess) or RT_X0_PAPER */
   int32_t ortho;         /* GMRES Arnoldi: RT_ORTHO_MGS (default) or RT_ORTHO_CGS2 */
   int32_t precision;     /* RT_PRECISION_FP64, or FP32 operator inside FP64 iterative refinement */
   double rtol;           /* stop when ||b - A x||_2 / ||b||_2 < rtol (Sect. 4.2) */
@@ -344,6 +350,12 @@ typedef struct {
   int32_t refine_steps;  /* FP32_REFINE outer steps */
   int32_t hist_len;      /* entries written to resid_hist */
   double rel_resid;      /* final ||b - A x|| / ||b||, FP64 operator */
+  double err_est;        /* the solver's own estimate of the same quantity when it stopped, without an
+                            extra product: GMRES |g_{j+1}| / ||b|| of the last Arnoldi step (Givens
+                            rotations, Sect. 2.1), BiCGSTAB / CGS the recursively updated residual,
+                            Richardson the residual it formed; FP32_REFINE the last inner solve's
+                            estimate times the outer relative residual it started from (what the FP64
+                            residual would be with an exact FP32 operator); rel_resid when no step ran */
   double t_total_ms;     /* wall time of the call */
 } rt_solve_info;
 

@@ -21,7 +21,7 @@ RT_FS_DELO_LINEAR, RT_FS_IMPLICIT_EULER, RT_FS_TRAPEZOIDAL = 0, 1, 2
 RT_PREC_NONE, RT_PREC_JACOBI, RT_PREC_LOCAL_LAMBDA, RT_PREC_JACOBI_LEFT = 0, 1, 2, 3
 RT_PREC_SOR, RT_PREC_SSOR, RT_PREC_SOR_LEFT, RT_PREC_SSOR_LEFT = 4, 5, 6, 7
 RT_FORM_I, RT_FORM_SIGMA = 0, 1
-RT_X0_ZERO, RT_X0_USER = 0, 1
+RT_X0_ZERO, RT_X0_USER, RT_X0_PAPER = 0, 1, 2
 RT_ORTHO_MGS, RT_ORTHO_CGS2 = 0, 1
 RT_PRECISION_FP64, RT_PRECISION_FP32_REFINE = 0, 1
 
@@ -50,7 +50,7 @@ class SolveInfo(C.Structure):
     _fields_ = [
         ("status", C.c_int32), ("iters", C.c_int32), ("restarts", C.c_int32), ("applies", C.c_int32),
         ("refine_steps", C.c_int32), ("hist_len", C.c_int32), ("rel_resid", C.c_double),
-        ("t_total_ms", C.c_double),
+        ("err_est", C.c_double), ("t_total_ms", C.c_double),
     ]
 
 

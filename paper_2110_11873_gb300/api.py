@@ -32,6 +32,7 @@ class SolveResult:
     applies: int
     refine_steps: int
     rel_resid: float
+    err_est: float
     t_total_ms: float
     history: np.ndarray
 
@@ -147,7 +148,7 @@ class Server:
             return None
         self.sizes.pop(ticket, None)
         res = SolveResult(info.status, info.iters, info.restarts, info.applies, info.refine_steps,
-                          info.rel_resid, info.t_total_ms, np.zeros(0))
+                          info.rel_resid, info.err_est, info.t_total_ms, np.zeros(0))
         return st, res, x
 
     def stats(self) -> dict:
@@ -340,9 +341,10 @@ class Problem:
     # --------------------------------------------------------------- solvers
     def solve(self, b: torch.Tensor, method: str = "gmres", x: Optional[torch.Tensor] = None, *,
               restart: int = 30, maxit: int = 10000, precond: str = "jacobi", rtol: float = 1e-8,
-              x0: bool = False, precision: str = "fp64", inner_rtol: float = 1e-4, max_refine: int = 20,
+              x0=False, precision: str = "fp64", inner_rtol: float = 1e-4, max_refine: int = 20,
               hist_cap: int = 0, omega: float = 1.0, raise_on_error: bool = True, stream=None):
-        """Solve A x = b; returns (x, SolveResult).  ``x0=True`` uses ``x`` as initial guess.
+        """Solve A x = b; returns (x, SolveResult).  ``x0=True`` uses ``x`` as initial guess,
+        ``x0="paper"`` the paper's (sigma = [1, 0, 1, 0, ...], lifted to the I-form).
         ``precond``: "none", "jacobi", "local_lambda", "jacobi_left" (GMRES), and for the
         sigma-form "sor", "ssor", "sor_left", "ssor_left" (GMRES) with relaxation ``omega``."""
         b = self._vec(b)
@@ -355,7 +357,7 @@ class Problem:
                      "sor": N.RT_PREC_SOR, "ssor": N.RT_PREC_SSOR, "sor_left": N.RT_PREC_SOR_LEFT,
                      "ssor_left": N.RT_PREC_SSOR_LEFT}[precond]
         o.omega = omega
-        o.x0_kind = N.RT_X0_USER if x0 else N.RT_X0_ZERO
+        o.x0_kind = N.RT_X0_PAPER if x0 == "paper" else (N.RT_X0_USER if x0 else N.RT_X0_ZERO)
         o.precision = {"fp64": N.RT_PRECISION_FP64, "fp32_refine": N.RT_PRECISION_FP32_REFINE}[precision]
         o.inner_rtol, o.max_refine = inner_rtol, max_refine
         hist = np.zeros(max(hist_cap, 1))
@@ -367,7 +369,7 @@ class Problem:
         st = fn(self.handle, C.byref(o), C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), C.byref(info),
                 _stream_handle(stream))
         res = SolveResult(info.status, info.iters, info.restarts, info.applies, info.refine_steps,
-                          info.rel_resid, info.t_total_ms, hist[: info.hist_len].copy())
+                          info.rel_resid, info.err_est, info.t_total_ms, hist[: info.hist_len].copy())
         if raise_on_error and st not in (N.RT_OK, N.RT_ENOTCONV, N.RT_EBREAKDOWN):
             raise N.RTError(st, f"rt_solve_{method}")
         return x, res

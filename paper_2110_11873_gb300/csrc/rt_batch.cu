@@ -66,6 +66,7 @@ struct InstDev {
 
 struct InstStatus {
   double rel;
+  double est;   // |g_{j+1}| / ||b|| of the instance's last Arnoldi step (rel before any)
   int iters, kstop, kdone, breakdown;
 };
 
@@ -391,6 +392,7 @@ __global__ void kb_givens(const InstDev* __restrict__ insts, const int* __restri
   gm->iters += 1;
   gm->kdone = j + 1;
   const double est = fabs(gm->g[j + 1]) / gm->bnorm;
+  gm->est = est;
   if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
 }
 
@@ -488,6 +490,7 @@ __global__ void __launch_bounds__(kBT) kb_cycle_start(const InstDev* __restrict_
       if (!(gm->rel >= gm->tol)) gm->kstop = 0;
       InstStatus st;
       st.rel = gm->rel;
+      st.est = gm->iters > 0 ? gm->est : gm->rel;
       st.iters = gm->iters;
       st.kstop = gm->kstop;
       st.kdone = gm->kdone;
@@ -657,7 +660,8 @@ namespace {
 
 // the server's own device buffers: from the caller's allocator when given
 cudaError_t srv_alloc(Server* S, void** p, size_t bytes) {
-  return S->hook ? S->hook->alloc(p, bytes) : cudaMalloc(p, bytes);
+  const cudaError_t e = S->hook ? S->hook->alloc(p, bytes) : cudaMalloc(p, bytes);
+  return e == cudaSuccess ? poison_fill(*p, bytes) : e;
 }
 void srv_free(Server* S, void* p) {
   if (!p) return;
@@ -1081,6 +1085,7 @@ void finish_request(Server* S, Instance* in, const InstStatus& st, rt_status sta
   rq->info.applies = st.iters + in->cycles;
   rq->info.refine_steps = S->opts.precision == RT_PRECISION_FP32_REFINE ? in->cycles : 0;
   rq->info.rel_resid = st.rel;
+  rq->info.err_est = st.est;
   rq->t_done = wall_ms();
   rq->info.t_total_ms = rq->t_done - rq->t_submit;
   std::lock_guard<std::mutex> lk(S->mu);

@@ -76,6 +76,7 @@ constexpr int kGramB = 4;                // basis vectors per block pass of the 
 struct GmresDev {
   double bnorm, tol, rnorm, rel;   // ||b||, rtol, last true residual norm, rnorm/bnorm
   double vscale;                   // 1 / ||w|| of the current Arnoldi step (batched solver)
+  double est;                      // |g_{j+1}| / ||b|| of the last Arnoldi step (Givens rotations)
   int kstop;                       // steps this cycle may take (set at cycle start)
   int kdone;                       // steps completed this cycle
   int iters;                       // Arnoldi steps over all cycles
@@ -152,6 +153,7 @@ __device__ inline void givens_step(GmresDev* gm, int m, int j, double* hist, int
   gm->iters += 1;
   gm->kdone = j + 1;
   const double est = fabs(gm->g[j + 1]) / gm->bnorm;
+  gm->est = est;
   if (hist && gm->hist_len < hist_cap) hist[gm->hist_len++] = est;
   if (!(est >= gm->tol) || gm->iters >= gm->maxit || b == 0.0) gm->kstop = j + 1;
 }
@@ -372,6 +374,9 @@ rt_status op_jacobi_inv(Problem* P, double* dinv, cudaStream_t st);
 // Jacobi mode uses them once they exist)
 rt_status op_jacobi_weights(Problem* P, cudaStream_t st);
 rt_status op_rhs(Problem* P, double* b, cudaStream_t st);
+// the paper's initial guess (Sect. 4.2) in the problem's form: sigma =
+// [1, 0, 1, 0, ...], or for the I-form Lambda(T sigma) + t
+rt_status op_x0_paper(Problem* P, double* x, cudaStream_t st);
 void release_graphs(Problem* P);
 // the formal solver alone (Eq. 9-10): I = Lambda S with the given inflow at
 // the bottom for Stokes I (zero elsewhere), FP64, written to I_out [2][Ns][nray]
@@ -381,6 +386,7 @@ void formal64_lambda(Problem* P, const double* S, double* I_out, double inflow_b
 rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaStream_t st,
                          const int* kstop = nullptr, int step = 0);
 rt_status op_rhs_sigma(Problem* P, double* b, cudaStream_t st);
+rt_status op_x0_paper_sigma(Problem* P, double* x, cudaStream_t st);   // [1, 0, 1, 0, ...]
 rt_status op_jacobi_sigma(Problem* P, double* d, int inverse, cudaStream_t st);
 // sigma-form SOR / SSOR (kind RT_PREC_SOR or RT_PREC_SSOR, with or without
 // _LEFT): assemble A on first use, form P^-1 for (kind, omega) in Mpre
@@ -406,6 +412,13 @@ void free_device(Problem* P);
 rt_status validate_desc(const rt_problem_desc* d);
 void host_grids(const rt_problem_desc* d, Problem& P);
 cudaError_t dev_alloc(Problem* P, void** p, size_t bytes);
+// Debug aid: with RT_POISON=1 in the environment every new workspace (of a
+// problem, of the batch server, and every block the server's arena hands
+// out) is filled with 0xFF bytes -- NaN in FP64 and FP32, -1 in integers --
+// before it is returned, so a kernel that reads memory nothing has written
+// yet produces NaN instead of a plausible stale value.  Off by default; not
+// inside a stream capture.
+cudaError_t poison_fill(void* p, size_t bytes);
 void dev_free(Problem* P, void* p);
 
 }  // namespace rt

@@ -377,11 +377,20 @@ __global__ void __launch_bounds__(kMgsThreads, kMgsCtasPerSm) k_bmgs(double* __r
 #pragma unroll
   for (int k = 0; k < kB; ++k) h[k] = k < nb ? hs[k] : 0.0;
   double s[kB] = {0.0, 0.0, 0.0, 0.0};
-  for (bool loaded = true; i < N; i += stride, loaded = false) {
+  for (; i < N; i += stride) {
     const int64_t e = rev ? N - 1 - i : i;
-    if (!loaded) {
-      wv = w[e];
-      load_v(e);
+    // software pipeline: the next element's loads are issued before this
+    // element's FP64 work
+    const int64_t i2 = i + stride;
+    double wv2 = 0.0, bv2[kB], nv2[kB];
+    if (i2 < N) {
+      const int64_t e2 = rev ? N - 1 - i2 : i2;
+      wv2 = w[e2];
+#pragma unroll
+      for (int k = 0; k < kB; ++k) {
+        if (k < nb) bv2[k] = vb[(size_t)k * N + e2];
+        if (k < nn) nv2[k] = vn[(size_t)k * N + e2];
+      }
     }
     double wi = wv;
 #pragma unroll
@@ -397,6 +406,12 @@ __global__ void __launch_bounds__(kMgsThreads, kMgsCtasPerSm) k_bmgs(double* __r
 #pragma unroll
       for (int k = 0; k < kB - 1; ++k)
         if (k < ng) s[1 + k] = fma(wi, bv[k], s[1 + k]);
+    }
+    wv = wv2;
+#pragma unroll
+    for (int k = 0; k < kB; ++k) {
+      if (k < nb) bv[k] = bv2[k];
+      if (k < nn) nv[k] = nv2[k];
     }
   }
   block_sum4_out(s, nn ? nn : 1 + ng, part_out);
@@ -1243,7 +1258,10 @@ static rt_status check_opts(const rt_solver_opts* o, const double* b, const doub
     set_error("SOR / SSOR need RT_PRECISION_FP64");
     return RT_EINVAL;
   }
-  if (o->x0_kind != RT_X0_ZERO && o->x0_kind != RT_X0_USER) { set_error("bad x0_kind"); return RT_EINVAL; }
+  if (o->x0_kind != RT_X0_ZERO && o->x0_kind != RT_X0_USER && o->x0_kind != RT_X0_PAPER) {
+    set_error("bad x0_kind");
+    return RT_EINVAL;
+  }
   if (o->ortho != RT_ORTHO_MGS) { set_error("only RT_ORTHO_MGS is implemented"); return RT_EINVAL; }
   if (o->precision != RT_PRECISION_FP64 && o->precision != RT_PRECISION_FP32_REFINE) { set_error("bad precision"); return RT_EINVAL; }
   if (!(o->rtol > 0.0)) { set_error("rtol must be > 0"); return RT_EINVAL; }
@@ -1260,6 +1278,15 @@ static rt_status finish_info(rt_solve_info* info, rt_status s, double t0) {
     info->t_total_ms = now_ms() - t0;
   }
   return s;
+}
+
+// the initial guess into wk(0): zero, the caller's x, or the paper's (Sect. 4.2)
+static rt_status load_x0(Problem* P, const rt_solver_opts* o, const double* x, cudaStream_t st) {
+  const size_t bytes = (size_t)P->Nop * sizeof(double);
+  if (o->x0_kind == RT_X0_USER) RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), x, bytes, cudaMemcpyDeviceToDevice, st));
+  else if (o->x0_kind == RT_X0_PAPER) RT_TRY(op_x0_paper(P, wk(P, 0), st));
+  else RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
+  return RT_OK;
 }
 
 // true relative residual of x = wk(0) against b = wk(1)
@@ -1298,19 +1325,19 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
   } else {
     RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
   }
-  if (o->x0_kind == RT_X0_USER) RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), x, bytes, cudaMemcpyDeviceToDevice, st));
-  else RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
+  RT_TRY(load_x0(P, o, x, st));
   std::unique_ptr<GmresDev> hsp(new GmresDev);   // only its header is read back
   GmresDev& hs = *hsp;
   int cycles = 0;
   rt_status s = RT_OK;
   int iters = 0, applies = 0, refine = 0;
-  double rel = 0.0;
+  double rel = 0.0, est = -1.0;
   if (o->precision == RT_PRECISION_FP64) {
     RT_TRY(gmres_core(P, o, 0, o->rtol, o->maxit, o->x0_kind == RT_X0_ZERO, &hs, &cycles, st));
     iters = hs.iters;
-    applies = hs.iters + cycles + (o->x0_kind == RT_X0_USER ? 1 : 0);
+    applies = hs.iters + cycles + (o->x0_kind != RT_X0_ZERO ? 1 : 0);
     rel = hs.bnorm == 0.0 ? 0.0 : hs.rel;
+    if (hs.iters > 0 && hs.bnorm != 0.0) est = hs.est;
     if (rel != rel) s = RT_ENUMERIC;
     else if (!(rel < o->rtol) && hs.bnorm != 0.0) s = (hs.breakdown && hs.kdone == 0) ? RT_EBREAKDOWN : RT_ENOTCONV;
   } else {
@@ -1332,6 +1359,7 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
       RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), wk(P, 2), bytes, cudaMemcpyDeviceToDevice, st));
       RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
       RT_TRY(gmres_core(P, o, 1, o->inner_rtol > 0 ? o->inner_rtol : 1e-4, o->maxit - iters, true, &hs, &cycles, st));
+      if (hs.iters > 0) est = hs.est * rel;   // relative to the inner b = r, which is rel * ||b||
       iters += hs.iters;
       applies += hs.iters + cycles;
       refine += 1;
@@ -1363,6 +1391,7 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
     info->applies = applies;
     info->refine_steps = refine;
     info->rel_resid = rel;
+    info->err_est = est >= 0.0 ? est : rel;
     info->hist_len = hl;
   }
   return finish_info(info, s, t0);
@@ -1452,8 +1481,8 @@ static rt_status solve_richardson(Problem* P, const rt_solver_opts* o, const dou
   const size_t bytes = (size_t)N * sizeof(double);
   RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
   int applies = 0;
-  if (o->x0_kind == RT_X0_USER) {
-    RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), x, bytes, cudaMemcpyDeviceToDevice, st));
+  if (o->x0_kind != RT_X0_ZERO) {
+    RT_TRY(load_x0(P, o, x, st));
     RT_TRY(op_apply64(P, wk(P, 0), wk(P, 5), AM_PLAIN, st));
     k_residual<<<G, kVecThreads, 0, st>>>(wk(P, 1), wk(P, 5), wk(P, 2), N, partb(P, 0)); RT_COUNT(1);
     applies = 1;
@@ -1511,6 +1540,7 @@ static rt_status solve_richardson(Problem* P, const rt_solver_opts* o, const dou
     info->iters = hs.iters;
     info->applies = applies + hs.iters;
     info->rel_resid = hs.rel;
+    info->err_est = hs.rel;   // every step forms the FP64 residual itself
     info->hist_len = hl;
   }
   return finish_info(info, s, t0);
@@ -1604,23 +1634,24 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
   const int64_t N = P->Nop;
   const size_t bytes = (size_t)N * sizeof(double);
   RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), b, bytes, cudaMemcpyDeviceToDevice, st));
-  if (o->x0_kind == RT_X0_USER) RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 0), x, bytes, cudaMemcpyDeviceToDevice, st));
+  if (o->x0_kind != RT_X0_ZERO) RT_TRY(load_x0(P, o, x, st));
   int applies = 0, iters = 0, refine_steps = 0;
   BicgDev hs;
   memset(&hs, 0, sizeof hs);
   bool zero_b = false;
   rt_status s = RT_OK;
-  double rel = 0;
+  double rel = 0, est = -1.0;
   if (!refine) {
     RT_TRY(bicg_core(P, method, o, 0, o->rtol, o->maxit, o->x0_kind == RT_X0_ZERO, &hs, &applies, &zero_b, st));
     iters = hs.iters;
     if (zero_b) {
       RT_TRY_CUDA(cudaMemsetAsync(x, 0, bytes, st));
       RT_TRY_CUDA(cudaStreamSynchronize(st));
-      if (info) info->rel_resid = 0.0;
+      if (info) info->rel_resid = info->err_est = 0.0;
       return finish_info(info, RT_OK, t0);
     }
     s = bicg_status(hs);
+    est = hs.rel;   // the recursively updated residual
     RT_TRY_CUDA(cudaMemcpyAsync(x, wk(P, 0), bytes, cudaMemcpyDeviceToDevice, st));
     RT_TRY(true_residual(P, &rel, st));
   } else {
@@ -1653,8 +1684,10 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
       const double prev = rel;
       RT_TRY(true_residual(P, &rel, st));
       applies += 1;
+      est = hs.rel * prev;   // the inner estimate, relative to its b = r (prev * ||b||)
       if (!(rel < prev)) {   // rejected: x stays the last accepted iterate, with its residual
         rel = prev;
+        est = prev;
         s = (inner == RT_ENUMERIC || hs.done == 3) ? RT_ENUMERIC : RT_ENOTCONV;
         break;
       }
@@ -1676,6 +1709,7 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
     info->applies = applies;
     info->refine_steps = refine_steps;
     info->rel_resid = rel;
+    info->err_est = est >= 0.0 && est == est ? est : rel;
     info->hist_len = hl;
   }
   return finish_info(info, s, t0);

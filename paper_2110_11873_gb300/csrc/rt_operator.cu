@@ -192,6 +192,16 @@ __global__ void k_rhs_source(const double* __restrict__ B, int Ns, int Nmu, doub
   }
 }
 
+// source functions of the paper's initial guess sigma^0_0 = 1, sigma^2_0 = 0
+// (Sect. 4.2): S_I = 1, S_Q = 0
+__global__ void k_unit_source(int Ns, int Nmu, double* __restrict__ S) {
+  const int64_t n = (int64_t)Ns * Nmu;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    S[t] = 1.0;
+    S[n + t] = 0.0;
+  }
+}
+
 // z = v + beta* S (the Lambda* T M^{-1} J part of P^{-1} v, S = T M^{-1} J v)
 __global__ void k_add_local(const double* __restrict__ v, const double* __restrict__ cb, const double* __restrict__ ce,
                             const double* __restrict__ cg, const double* __restrict__ S,
@@ -349,8 +359,17 @@ inline int grid_for(int64_t n, int threads, int cap) {
 }  // namespace
 
 // --------------------------------------------------------------- host side
+cudaError_t poison_fill(void* p, size_t bytes) {
+  const char* e = std::getenv("RT_POISON");
+  if (!e || e[0] != '1' || g_capturing || !p || !bytes) return cudaSuccess;
+  cudaError_t r = cudaMemset(p, 0xFF, bytes);
+  if (r == cudaSuccess) r = cudaDeviceSynchronize();
+  return r;
+}
+
 cudaError_t dev_alloc(Problem* P, void** p, size_t bytes) {
-  return P->alloc ? P->alloc->alloc(p, bytes) : cudaMalloc(p, bytes);
+  cudaError_t e = P->alloc ? P->alloc->alloc(p, bytes) : cudaMalloc(p, bytes);
+  return e == cudaSuccess ? poison_fill(*p, bytes) : e;
 }
 
 void dev_free(Problem* P, void* p) {
@@ -907,6 +926,18 @@ rt_status op_rhs(Problem* P, double* b, cudaStream_t st) {
   k_rhs_source<<<grid_for((int64_t)P->Ns * P->Nmu, 256, 4 * P->num_sms), 256, 0, st>>>(P->Bd, P->Ns, P->Nmu, P->eps,
                                                                                       P->S2); RT_COUNT(1);
   launch_formal64<KM_RHS>(P, nullptr, b, P->S2, st, nullptr, 0);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status op_x0_paper(Problem* P, double* x, cudaStream_t st) {
+  RT_NVTX("initial guess of the paper");
+  if (P->form == RT_FORM_SIGMA) return op_x0_paper_sigma(P, x, st);
+  // I = Lambda(T sigma) + t: the formal solve of the right-hand side with
+  // S_I = 1 in place of eps B
+  k_unit_source<<<grid_for((int64_t)P->Ns * P->Nmu, 256, 4 * P->num_sms), 256, 0, st>>>(P->Ns, P->Nmu, P->S2);
+  RT_COUNT(1);
+  launch_formal64<KM_RHS>(P, nullptr, x, P->S2, st, nullptr, 0);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }

@@ -109,6 +109,12 @@ __global__ void __launch_bounds__(kSigThreads) k_sig_moments(
   }
 }
 
+// the paper's initial guess (Sect. 4.2): sigma^0_0 = 1, sigma^2_0 = 0 at every
+// height, interleaved per height as the sigma-form vectors are
+__global__ void k_sig_unit(int n, double* __restrict__ x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = (i & 1) ? 0.0 : 1.0;
+}
+
 // Jacobi diagonal of Eq. (18) (the diagonals of the blocks M_k), or its inverse
 __global__ void k_sig_jacobi(const double* __restrict__ Mdiag, int n, int inverse, double* __restrict__ d) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -304,6 +310,13 @@ rt_status op_apply_sigma(Problem* P, const double* v, double* y, int mode, cudaS
 
 rt_status op_rhs_sigma(Problem* P, double* b, cudaStream_t st) {
   launch_sigma<KM_RHS>(P, nullptr, b, st, nullptr, 0);
+  RT_TRY_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status op_x0_paper_sigma(Problem* P, double* x, cudaStream_t st) {
+  k_sig_unit<<<blocks_for(2 * (int64_t)P->Ns, 256, 4 * P->num_sms), 256, 0, st>>>(2 * P->Ns, x);
+  RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }

@@ -62,3 +62,22 @@ def assert_close_scaled(got, ref, tol, what="", layout="I"):
         assert err <= tol * scale, f"{what} [{name}]: max err {err:.3e} > {tol:.1e} * {scale:.3e}"
         worst = max(worst, err / scale)
     return worst
+
+
+def perturbed(b, seed):
+    """b with every entry moved by about 1e-15 relative (seeded)."""
+    return b * (1.0 + 1e-15 * np.random.default_rng(seed).standard_normal(b.size))
+
+
+def assert_iterate(got, xo, xp, what, floor=1e-10):
+    """Per Stokes block (I, then Q): max|got - xo| <= tol * max|xo| with
+    tol = max(floor, 20 * the oracle's own change when b is perturbed by
+    1e-15 relative, xp).  The Q part of a solution is about 1e-3 of the I
+    part, so each block is scaled by its own largest entry."""
+    n = xo.size // 2
+    for name, sl in (("I", slice(0, n)), ("Q", slice(n, None))):
+        scale = np.max(np.abs(xo[sl]))
+        own = np.max(np.abs(xp[sl] - xo[sl])) / scale
+        tol = max(floor, 20 * own)
+        assert_close_scaled(got[sl], xo[sl], tol, f"{what} [{name}] (oracle's own change {own:.1e})",
+                            layout="flat")

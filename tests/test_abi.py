@@ -55,7 +55,7 @@ int main(void) {
   F(rt_problem_desc, freq_norm); F(rt_problem_desc, form);
   F(rt_solver_opts, rtol); F(rt_solver_opts, resid_hist); F(rt_solver_opts, hist_cap);
   F(rt_solver_opts, omega);
-  F(rt_solve_info, rel_resid); F(rt_solve_info, t_total_ms);
+  F(rt_solve_info, rel_resid); F(rt_solve_info, err_est); F(rt_solve_info, t_total_ms);
   printf("rt_allocator %zu\n", sizeof(rt_allocator));
   F(rt_allocator, ctx); F(rt_allocator, alloc); F(rt_allocator, release);
   return 0;

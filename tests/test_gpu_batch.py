@@ -75,6 +75,8 @@ def test_batch_solutions(cases, precision, tol_exact):
         rel = np.linalg.norm(b - tr.apply_I(x)) / np.linalg.norm(b)
         assert rel < 1e-8, (at.name, rel)
         assert np.linalg.norm(x - x_ex) / np.linalg.norm(x_ex) < tol_exact
+        # the Givens estimate of the instance's last Arnoldi step, relative to ||b||
+        assert np.isfinite(info.err_est) and 0.0 < info.err_est < 1e-4, (at.name, info)
         if precision == "fp64":
             P = problem(at)
             _, si = P.solve(to_dev(b), "gmres", restart=30, precond="local_lambda", rtol=1e-8)

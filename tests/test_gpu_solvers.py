@@ -26,7 +26,7 @@ from oracle import krylov as K
 from oracle.transfer import Transfer
 from paper_2110_11873_gb300 import _native as N
 
-from gpu_util import assert_close_scaled, problem, to_dev, to_host
+from gpu_util import assert_close_scaled, assert_iterate as _assert_iterate, perturbed as _perturbed, problem, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -43,10 +43,6 @@ def _oracle_solve(tr, b, method, prec, **kw):
     Minv = {"none": None, "jacobi": lambda v: v / d, "local_lambda": tr.local_lambda_I_inverse}[prec]
     fn = {"gmres": K.gmres, "bicgstab": K.bicgstab, "cgs": K.cgs}[method]
     return fn(tr.apply_I, b, M_inv=Minv, **kw)
-
-
-def _perturbed(b, seed):
-    return b * (1.0 + 1e-15 * np.random.default_rng(seed).standard_normal(b.size))
 
 
 def _oracle_count_range(tr, b, method, prec, copies=2, **kw):
@@ -86,20 +82,6 @@ def test_gmres_slab70(slab70, prec):
     eo = np.linalg.norm(xo - xs) / np.linalg.norm(xs)
     eg = np.linalg.norm(x - xs) / np.linalg.norm(xs)
     assert eg < 5 * eo + 1e-12, (eg, eo)
-
-
-def _assert_iterate(got, xo, xp, what, floor=1e-10):
-    """Per Stokes block (I, then Q): max|got - xo| <= tol * max|xo| with
-    tol = max(floor, 20 * the oracle's own change when b is perturbed by
-    1e-15 relative, xp).  The Q part of a solution is about 1e-3 of the I
-    part, so each block is scaled by its own largest entry."""
-    n = xo.size // 2
-    for name, sl in (("I", slice(0, n)), ("Q", slice(n, None))):
-        scale = np.max(np.abs(xo[sl]))
-        own = np.max(np.abs(xp[sl] - xo[sl])) / scale
-        tol = max(floor, 20 * own)
-        assert_close_scaled(got[sl], xo[sl], tol, f"{what} [{name}] (oracle's own change {own:.1e})",
-                            layout="flat")
 
 
 @pytest.mark.parametrize("prec,iters", [("local_lambda", 12), ("jacobi", 75)])
