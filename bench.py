@@ -76,6 +76,9 @@ def parse():
                     help="run only a short sequence of one operation (the target of ncu captures) and exit")
     ap.add_argument("--probe-ns", type=int, default=1000, help="N_s of the sweep atmosphere (300: slab300)")
     ap.add_argument("--probe-reps", type=int, default=4)
+    ap.add_argument("--probe-budget-gb", type=int, default=160,
+                    help="device-memory budget of the batch probe's server (its arena is allocated at once; "
+                         "keep it to a few GB for multi-pass ncu captures)")
     return ap.parse_args()
 
 
@@ -96,8 +99,8 @@ def probe_main(args):
     if args.probe == "batch":
         from paper_2110_11873_gb300 import Server
         ats = W.batch_instances(args.batch_count)
-        srv = Server(mem_budget_bytes=160 << 30, max_slots=len(ats), precond="local_lambda",
-                     precision="fp32_refine")
+        srv = Server(mem_budget_bytes=args.probe_budget_gb << 30, max_slots=len(ats), restart=BATCH_RESTART,
+                     precond="local_lambda", precision="fp32_refine")
         tickets = [srv.submit(a) for a in ats]
         res = _drain(srv, tickets)
         st = srv.stats()
