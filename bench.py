@@ -427,6 +427,19 @@ def serve_bench(W, Server, rates, nreq, keep=8):
     return out, kept
 
 
+def solve_alg_bytes(info, N: int, m: int = 30) -> float:
+    """Algorithmic bytes of one GMRES(m) solve with info.iters Arnoldi steps in
+    info.restarts cycles: (2j+6)*N*8 for step j of a cycle, 2*N*8 more per
+    cycle for the restart residual's apply."""
+    steps, total = info.iters, 0.0
+    for c in range(max(info.restarts, 1)):
+        k = min(m, steps - c * m)
+        if k <= 0:
+            break
+        total += sum((2 * j + 6) for j in range(k)) * N * 8 + 2 * N * 8
+    return total
+
+
 def bench_config(precond: str, world: int) -> dict:
     """The `config` object of both arms' JSON lines."""
     return {"workload": WORKLOAD, "precond": precond, "restart": 30, "rtol": 1e-8,
@@ -797,6 +810,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": bench_config(args.precond, world),
             "solves_per_s": solves_all / (ms_max / 1000.0),
+            "solve_alg_gbs": solve_alg_bytes(info, N) * solves_all / (ms_max * 1e-3) / 1e9,
+            "solve_alg_gbs_note": "algorithmic bytes of a solve over its time: per Arnoldi step j of a cycle "
+                                  "(2j+6)*N*8 (the apply's x and y, each basis vector read twice by the "
+                                  "orthogonalisation, w written and read), per cycle one more apply",
             "iters_per_solve": info.iters, "applies_per_solve": info.applies,
             "apply_fp64": {"ms": apply_ms, "applies_per_s": 1000.0 / apply_ms, "alg_gbs": apply_gbs,
                            "tflops": apply64_flop / (apply_ms * 1e-3) / 1e12,

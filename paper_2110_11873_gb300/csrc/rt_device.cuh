@@ -161,7 +161,7 @@ __device__ __forceinline__ void moments_flat64(const double* __restrict__ x, con
   const double* __restrict__ w1 = WJ ? w0 + plane : wray + nray;
   const double* __restrict__ w2 = WJ ? w0 + 2 * plane : wray + 2 * nray;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-#pragma unroll 2
+#pragma unroll 4
   for (int64_t r = threadIdx.x; r < nray; r += blockDim.x) {
     double vI = xI[r], vQ = xQ[r];
     if (NORM) {
