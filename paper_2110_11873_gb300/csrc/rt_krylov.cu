@@ -489,8 +489,28 @@ __global__ void k_lsq(GmresDev* gm, int m) {
   extern __shared__ double lsq_sm[];
   double* Hs = lsq_sm;                          // column l (rows 0..l) at l (l + 1) / 2
   double* ys = lsq_sm + (size_t)m * (m + 1) / 2;
-  for (int l = 0; l < k; ++l)
-    for (int i = lane; i <= l; i += 32) Hs[l * (l + 1) / 2 + i] = gm->H[l * (m + 1) + i];
+  // the packed triangle, q = l (l + 1) / 2 + i, in rounds of 8 loads a lane
+  // issued before any store (a column-by-column copy waited for each load)
+  const int total = k * (k + 1) / 2;
+  constexpr int U = 8;
+  for (int q0 = 0; q0 < total; q0 += 32 * U) {
+    double v[U];
+    int dst[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u * 32 + lane;
+      dst[u] = q < total ? q : -1;
+      if (q < total) {
+        int l = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+        while (l * (l + 1) / 2 > q) --l;           // exact column of q despite the rounding of sqrtf
+        while ((l + 1) * (l + 2) / 2 <= q) ++l;
+        v[u] = gm->H[l * (m + 1) + (q - l * (l + 1) / 2)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (dst[u] >= 0) Hs[dst[u]] = v[u];
+  }
   __syncwarp();
   if (lane == 0) {
     for (int i = k - 1; i >= 0; --i) {
