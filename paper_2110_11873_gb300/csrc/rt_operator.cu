@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(kMom64Threads) k_moments64_norm(
     const double* __restrict__ t201, const double* __restrict__ t202, const double* __restrict__ Minv, int Ns,
     int Nmu, int64_t nray, double xi, double xiW2, double* __restrict__ S, const NormIn nin) {
   if (nin.kstop && nin.jprev >= *nin.kstop) return;
+  pdl_wait();   // the last block pass's w and partials
   if (blockIdx.x == 0) {
     arnoldi_fold(nin.part, nin.Gp, nin.ng, nin.hcol, nin.gram, nin.gm, nin.m, nin.jprev, nin.hist, nin.hist_cap);
     return;
@@ -348,6 +349,22 @@ __global__ void __launch_bounds__(32 * MAXT) k_formal(const FormalArgs A) {
     TC E = 1;
     sweep<TC, TV, FS, MODE, 1, NS, RING>(A, s0, down, r, m, active, j0, j1, I, E);
   }
+}
+
+// launch_pdl with a multi-dimensional grid and block
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl_shape(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                                    Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 inline int grid_for(int64_t n, int threads, int cap) {
@@ -515,6 +532,7 @@ constexpr int kMapSlices = 8;
 __global__ void __launch_bounds__(32 * kMapSlices) k_fmapdot(const FormalArgs A, const double* __restrict__ K,
                                                              double* __restrict__ Bmap) {
   if (A.kstop && A.step >= *A.kstop) return;
+  pdl_wait();   // the source values of the quadrature before
   const int Ns = A.Ns, T = A.ntile, L = (Ns - 1 + T - 1) / T;
   const int64_t nray = A.nray;
   const int t = blockIdx.y;
@@ -726,8 +744,8 @@ template <int FS, int MODE>
 static void formal64_units(const Problem* P, const FormalArgs& A, cudaStream_t st) {
   const int T = P->ntile64, groups = 2 * P->ngroups;
   if (T > 1) {
-    k_fmapdot<<<dim3((unsigned)((P->nray + 31) / 32), (unsigned)(T - 1)), dim3(32, kMapSlices), 0, st>>>(A, P->Kmap,
-                                                                                                     P->Bmap);
+    launch_pdl_shape(k_fmapdot, dim3((unsigned)((P->nray + 31) / 32), (unsigned)(T - 1)), dim3(32, kMapSlices), st,
+                     A, (const double*)P->Kmap, P->Bmap);
     RT_COUNT(1);
   }
   k_fsweep<FS, MODE><<<groups * T, 32, 0, st>>>(A, P->Bmap, P->Etile);
@@ -782,20 +800,20 @@ rt_status op_apply64(Problem* P, const double* x, double* y, int mode, cudaStrea
     double* xw = const_cast<double*>(x);
     switch (mode) {
       case AM_PLAIN:
-        k_moments64_norm<KM_PLAIN, false><<<Ns + 1, kMom64Threads, 0, st>>>(
-            xw, nullptr, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin);
+        RT_TRY_CUDA(launch_pdl(k_moments64_norm<KM_PLAIN, false>, Ns + 1, kMom64Threads, st,
+            xw, nullptr, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin));
         break;
       case AM_JACOBI:
         if (P->wjac)
-          k_moments64_norm<KM_JACOBI, true><<<Ns + 1, kMom64Threads, 0, st>>>(
-              xw, nullptr, P->wjac, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin);
+          RT_TRY_CUDA(launch_pdl(k_moments64_norm<KM_JACOBI, true>, Ns + 1, kMom64Threads, st,
+              xw, nullptr, P->wjac, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin));
         else
-          k_moments64_norm<KM_JACOBI, false><<<Ns + 1, kMom64Threads, 0, st>>>(
-              xw, P->dinv, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin);
+          RT_TRY_CUDA(launch_pdl(k_moments64_norm<KM_JACOBI, false>, Ns + 1, kMom64Threads, st,
+              xw, P->dinv, P->wray, P->t201d, P->t202d, nullptr, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin));
         break;
       case AM_LOCAL_LAMBDA:
-        k_moments64_norm<KM_LOCAL_LAMBDA, false><<<Ns + 1, kMom64Threads, 0, st>>>(
-            xw, nullptr, P->wray, P->t201d, P->t202d, P->Minv, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin);
+        RT_TRY_CUDA(launch_pdl(k_moments64_norm<KM_LOCAL_LAMBDA, false>, Ns + 1, kMom64Threads, st,
+            xw, nullptr, P->wray, P->t201d, P->t202d, P->Minv, Ns, Nmu, P->nray, P->xi, xiW2, P->S, *nin));
         break;
       default:
         set_error("bad apply mode");
