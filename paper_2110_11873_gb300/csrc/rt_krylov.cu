@@ -285,9 +285,13 @@ __device__ __forceinline__ void sum_sets(const double* __restrict__ part, int G,
 // runs what does not depend on it (the gate, the basis-vector loads of its
 // first element, the Gram entries), then waits in griddepcontrol.wait until
 // that grid has finished and its writes are visible.  The gate counter is
-// written only by the scaling kernel of the step before, which completed
-// before the operator apply between them started (the apply's kernels are
-// ordinary launches: as programmatic dependents they measured slower).
+// read before that wait.  It is written only by the Givens update of the step
+// before (the scaling kernel, or the first CTA of this step's quadrature
+// kernel), which finished before the kernels of this step's apply passed
+// their own waits.  The counter only falls within a cycle (at convergence),
+// so a read that still saw its earlier value would run a block pass of a
+// step past convergence: work on the discarded part of the basis and of the
+// Hessenberg matrix, which nothing of the cycle reads afterwards.
 
 // Each pass sweeps the vectors in the opposite direction to the pass before
 // (rev): it starts on the elements the previous pass touched last, which are

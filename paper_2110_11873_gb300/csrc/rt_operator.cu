@@ -572,6 +572,7 @@ template <int FS, int MODE>
 __global__ void __launch_bounds__(32, FS == RT_FS_DELO_PARABOLIC ? 12 : 16) k_fsweep(const FormalArgs A, const double* __restrict__ Bmap,
                                                const double* __restrict__ Etile) {
   if (A.kstop && A.step >= *A.kstop) return;
+  pdl_wait();   // the tile maps and source values of the kernels before
   const int T = A.ntile, L = (A.Ns - 1 + T - 1) / T;
   const int u = blockIdx.x, lane = threadIdx.x;
   const int t = u % T, gs = u / T, s0 = gs & 1;
@@ -748,7 +749,8 @@ static void formal64_units(const Problem* P, const FormalArgs& A, cudaStream_t s
                      A, (const double*)P->Kmap, P->Bmap);
     RT_COUNT(1);
   }
-  k_fsweep<FS, MODE><<<groups * T, 32, 0, st>>>(A, P->Bmap, P->Etile);
+  launch_pdl_shape(k_fsweep<FS, MODE>, dim3(groups * T), dim3(32), st, A, (const double*)P->Bmap,
+                   (const double*)P->Etile);
   RT_COUNT(1);
 }
 
