@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(kQuadThreads, 4) k_quad(const TV* __restrict__
                                                        const QuadOut Q, const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
   pdl_launch_dependents();
+  pdl_wait();   // x (and the node table the formal solver before may still read)
   quad_tile<TV, MODE, false>(x, dinv, qw, nray, hpc, Q, blockIdx.y);
 }
 
@@ -854,8 +855,19 @@ rt_status staged_apply(Problem* P, const TV* x, TV* y, cudaStream_t st, const in
     k_quad_norm<MODE><<<dim3(P->quad_gx, P->quadn_gy + 1), kQuadThreads, 0, st>>>(
         const_cast<double*>(reinterpret_cast<const double*>(x)), P->dinv, P->qw, P->nray, P->quadn_hpc, Q, *nin);
   } else {
-    k_quad<TV, MODE><<<dim3(P->quad_gx, P->quad_gy), kQuadThreads, 0, st>>>(x, P->dinv, P->qw, P->nray,
-                                                                             P->quad_hpc, Q, kstop, step);
+    {   // a programmatic dependent of the kernel before
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(P->quad_gx, P->quad_gy);
+      cfg.blockDim = dim3(kQuadThreads);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      RT_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_quad<TV, MODE>, x, (const double*)P->dinv, (const float*)P->qw, P->nray,
+                                     P->quad_hpc, Q, kstop, step));
+    }
   }
   RT_COUNT(1);
   StagedArgs A;
