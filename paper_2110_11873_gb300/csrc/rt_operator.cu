@@ -572,7 +572,12 @@ template <int FS, int MODE>
 __global__ void __launch_bounds__(32, FS == RT_FS_DELO_PARABOLIC ? 12 : 16) k_fsweep(const FormalArgs A, const double* __restrict__ Bmap,
                                                const double* __restrict__ Etile) {
   if (A.kstop && A.step >= *A.kstop) return;
-  pdl_wait();   // the tile maps and source values of the kernels before
+  // A programmatic dependent of k_fmapdot.  It never releases its own
+  // dependents early: the block passes after it read the basis vector v_j,
+  // which this apply's quadrature wrote, before their wait, and that is safe
+  // because they start only once every CTA here has exited -- after this
+  // wait, hence after the quadrature and the tile maps finished.
+  pdl_wait();
   const int T = A.ntile, L = (A.Ns - 1 + T - 1) / T;
   const int u = blockIdx.x, lane = threadIdx.x;
   const int t = u % T, gs = u / T, s0 = gs & 1;

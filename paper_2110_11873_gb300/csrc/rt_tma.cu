@@ -427,8 +427,11 @@ __global__ void __launch_bounds__(kQuadThreads, 4) k_quad(const TV* __restrict__
                                                        const float* __restrict__ qw, int64_t nray, int hpc,
                                                        const QuadOut Q, const int* kstop, int step) {
   if (kstop && step >= *kstop) return;
+  // x (and the node table the formal solver before may still read) only
+  // after the kernel before has finished; the formal solver may start only
+  // then too, because in a standalone apply it copies x before its own wait
+  pdl_wait();
   pdl_launch_dependents();
-  pdl_wait();   // x (and the node table the formal solver before may still read)
   quad_tile<TV, MODE, false>(x, dinv, qw, nray, hpc, Q, blockIdx.y);
 }
 
