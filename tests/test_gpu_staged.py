@@ -171,3 +171,30 @@ def test_deep_atmosphere_with_few_rays_through_the_fused_normalisation():
     x64, r64 = P.solve(b, "gmres", restart=30, precond="local_lambda", rtol=1e-11)
     assert r64.status == 0, r64
     assert_close_scaled(xh, to_host(x64), 1e-6, "fp32-refine vs fp64")
+
+
+@pytest.mark.parametrize("name,at", [("slab300", W.slab300()), ("sweep500", W.sweep(500))])
+def test_chained_applies_back_to_back_equal_synchronised_ones(name, at):
+    """Each apply's output is the next one's input, eight in a row on one
+    stream with no host synchronisation between them, FP32 (staged path)
+    and FP64.  The kernels of an apply are programmatic dependents of the
+    kernels before them, and the staged formal solver copies x before its
+    own wait; the chain must give bit for bit what the same chain gives with
+    a device synchronisation after every apply."""
+    P = problem(at)
+    assert P.staged_formal
+    g = torch.Generator(device="cuda").manual_seed(11)
+    for dt, fn in ((torch.float32, P.apply_f32), (torch.float64, P.apply)):
+        x0 = torch.rand(P.N, dtype=dt, device="cuda", generator=g)
+        bufs = [x0.clone()] + [torch.empty_like(x0) for _ in range(8)]
+        for i in range(8):
+            fn(bufs[i], out=bufs[i + 1])
+        chained = to_host(bufs[8])
+        ref = x0.clone()
+        for _ in range(8):
+            nxt = torch.empty_like(ref)
+            fn(ref, out=nxt)
+            torch.cuda.synchronize()
+            ref = nxt
+        P.check()
+        np.testing.assert_array_equal(chained, to_host(ref), err_msg=f"{name} {dt}")
