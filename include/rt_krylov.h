@@ -424,11 +424,15 @@ typedef struct {
                                 kernels (quadrature, formal solver, vector passes) on the resident
                                 instances and keep the fastest; 0: fixed grids.  Results do not
                                 depend on the grids. */
+  int32_t graphs;            /* 1: each restart cycle is one launch of a captured CUDA graph; 0: the
+                                cycle's kernels are launched one by one on the server's stream (for
+                                debugging and for tools that do not follow graphs).  Results are
+                                the same either way. */
 } rt_server_opts;
 
 typedef struct rt_server rt_server;
 
-/* defaults: 8 GiB budget, 64 slots, restart 30, local-Lambda, FP64, autotune on */
+/* defaults: 8 GiB budget, 64 slots, restart 30, local-Lambda, FP64, autotune on, graphs on */
 void rt_server_opts_default(rt_server_opts* opts);
 /* Create a server on the current device (the device stays the worker's). */
 rt_status rt_server_create(const rt_server_opts* opts, rt_server** out);

@@ -57,7 +57,7 @@ class SolveInfo(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [
         ("mem_budget_bytes", C.c_int64), ("max_slots", C.c_int32), ("restart", C.c_int32),
-        ("precond", C.c_int32), ("precision", C.c_int32), ("autotune", C.c_int32),
+        ("precond", C.c_int32), ("precision", C.c_int32), ("autotune", C.c_int32), ("graphs", C.c_int32),
     ]
 
 

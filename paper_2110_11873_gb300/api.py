@@ -107,7 +107,7 @@ class Server:
     ``struct``) from which the server takes its device memory."""
 
     def __init__(self, mem_budget_bytes: int = 8 << 30, max_slots: int = 64, restart: int = 30,
-                 precond: str = "local_lambda", precision: str = "fp64", autotune: bool = True,
+                 precond: str = "local_lambda", precision: str = "fp64", autotune: bool = True, graphs: bool = True,
                  allocator=None):
         self.lib = N.load()
         self.allocator = allocator
@@ -118,6 +118,7 @@ class Server:
                      "local_lambda": N.RT_PREC_LOCAL_LAMBDA}[precond]
         o.precision = {"fp64": N.RT_PRECISION_FP64, "fp32_refine": N.RT_PRECISION_FP32_REFINE}[precision]
         o.autotune = 1 if autotune else 0
+        o.graphs = 1 if graphs else 0
         h = C.c_void_p()
         if allocator is None:
             N.check(self.lib.rt_server_create(C.byref(o), C.byref(h)), "rt_server_create")

@@ -701,11 +701,11 @@ int64_t chunk_for(int64_t N) {
 template <int MODE>
 void formal32(Server* S, cudaStream_t st, int src, int dst, int step) {
   kb_formal<float, RT_FS_DELO_LINEAR, MODE><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(S->d_insts, S->d_wl_g32,
-                                                                                     S->d_counts, src, dst, step);
+                                                                                     S->d_counts, src, dst, step); RT_COUNT(1);
   kb_formal<float, RT_FS_IMPLICIT_EULER, MODE><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(S->d_insts, S->d_wl_g32,
-                                                                                        S->d_counts, src, dst, step);
+                                                                                        S->d_counts, src, dst, step); RT_COUNT(1);
   kb_formal<float, RT_FS_TRAPEZOIDAL, MODE><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(S->d_insts, S->d_wl_g32,
-                                                                                     S->d_counts, src, dst, step);
+                                                                                     S->d_counts, src, dst, step); RT_COUNT(1);
 }
 
 template <bool NORM>
@@ -715,30 +715,30 @@ void enqueue_apply_t(Server* S, cudaStream_t st, int src, int dst, int md, bool 
   if (!f32) {
     switch (md) {
       case KM_JACOBI:
-        kb_moments<double, KM_JACOBI, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
-        kb_formal<double, 0, KM_JACOBI><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
+        kb_moments<double, KM_JACOBI, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0); RT_COUNT(1);
+        kb_formal<double, 0, KM_JACOBI><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step); RT_COUNT(1);
         break;
       case KM_LOCAL_LAMBDA:
-        kb_moments<double, KM_LOCAL_LAMBDA, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<double, KM_LOCAL_LAMBDA, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0); RT_COUNT(1);
         kb_formal<double, 0, KM_LOCAL_LAMBDA><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst,
-                                                                                     step);
+                                                                                     step); RT_COUNT(1);
         break;
       default:
-        kb_moments<double, KM_PLAIN, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
-        kb_formal<double, 0, KM_PLAIN><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step);
+        kb_moments<double, KM_PLAIN, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0); RT_COUNT(1);
+        kb_formal<double, 0, KM_PLAIN><<<S->grid_g, 32 * kFormalWarps, 0, st>>>(I, S->d_wl_g64, C, src, dst, step); RT_COUNT(1);
     }
   } else {
     switch (md) {
       case KM_JACOBI:
-        kb_moments<float, KM_JACOBI, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<float, KM_JACOBI, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0); RT_COUNT(1);
         formal32<KM_JACOBI>(S, st, src, dst, step);
         break;
       case KM_LOCAL_LAMBDA:
-        kb_moments<float, KM_LOCAL_LAMBDA, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<float, KM_LOCAL_LAMBDA, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0); RT_COUNT(1);
         formal32<KM_LOCAL_LAMBDA>(S, st, src, dst, step);
         break;
       default:
-        kb_moments<float, KM_PLAIN, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0);
+        kb_moments<float, KM_PLAIN, NORM><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, src, step, 0); RT_COUNT(1);
         formal32<KM_PLAIN>(S, st, src, dst, step);
     }
   }
@@ -844,30 +844,30 @@ rt_status enqueue_batch_cycle(Server* S, cudaStream_t st) {
     // steps after the first normalise v_j = w / ||w|| inside the quadrature
     enqueue_apply(S, st, j, VW, mode, fp32, j, j > 0);
     int pb = 0;
-    kb_bdot_fn[std::min(kGramB, j + 1) - 1]<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j);
+    kb_bdot_fn[std::min(kGramB, j + 1) - 1]<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j); RT_COUNT(1);
     for (int i0 = 0; i0 <= j; i0 += kGramB) {
       const int nb = std::min(kGramB, j + 1 - i0);
       const int nn = std::max(0, std::min(kGramB, j + 1 - (i0 + nb)));
-      (nn ? kb_pass_fn[nn - 1] : kb_last_fn[nb - 1])<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, i0, pb);
+      (nn ? kb_pass_fn[nn - 1] : kb_last_fn[nb - 1])<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, j, i0, pb); RT_COUNT(1);
       pb ^= 1;
     }
     // h_{j+1,j}, the Gram row, the rotations and the inverse norm that the
     // next step's quadrature scales w by; an instance that stops at step j
     // never forms v_{j+1}, which no later kernel of the cycle reads
     const int ng = (j + 1) % kGramB;
-    kb_givens<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C, j, pb, ng);
+    kb_givens<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C, j, pb, ng); RT_COUNT(1);
   }
-  kb_lsq<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C);
+  kb_lsq<<<S->grid_i, kInstThreads, 0, st>>>(I, S->d_wl_i, C); RT_COUNT(1);
   if (mode == KM_LOCAL_LAMBDA) {
-    kb_combine<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, 2);
-    kb_moments<double, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, VT, -1, 1);
-    kb_add_local<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C);
+    kb_combine<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, 2); RT_COUNT(1);
+    kb_moments<double, KM_LOCAL_LAMBDA><<<S->grid_h, kMomThreads, 0, st>>>(I, S->d_wl_h, C, VT, -1, 1); RT_COUNT(1);
+    kb_add_local<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C); RT_COUNT(1);
   } else {
-    kb_combine<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, mode == KM_JACOBI ? 1 : 0);
+    kb_combine<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, mode == KM_JACOBI ? 1 : 0); RT_COUNT(1);
   }
   enqueue_apply(S, st, VX, VTMP, KM_PLAIN, false, -1);   // FP64 true residual
-  kb_residual<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C);
-  kb_cycle_start<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, S->d_status);
+  kb_residual<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C); RT_COUNT(1);
+  kb_cycle_start<<<S->grid_v, kBT, 0, st>>>(I, S->d_wl_c, C, S->d_status); RT_COUNT(1);
   RT_TRY_CUDA(cudaGetLastError());
   return RT_OK;
 }
@@ -1187,15 +1187,26 @@ void worker_main(Server* S) {
         }
       }
     }
-    if (s == RT_OK) s = capture_cycle(S);
+    if (s == RT_OK && S->opts.graphs) s = capture_cycle(S);
     if (s != RT_OK) {
       fail(s);
       break;
     }
     // one restart cycle for every resident instance
-    RT_NVTX("server restart cycle (graph)");
-    cudaError_t e = cudaGraphLaunch(S->graph, S->st);
-    if (e == cudaSuccess) count_launches(S->graph_kernels);
+    cudaError_t e = cudaSuccess;
+    if (S->opts.graphs) {
+      RT_NVTX("server restart cycle (graph)");
+      e = cudaGraphLaunch(S->graph, S->st);
+      if (e == cudaSuccess) count_launches(S->graph_kernels);
+    } else {
+      RT_NVTX("server restart cycle (direct launches)");
+      s = enqueue_batch_cycle(S, S->st);
+      if (s != RT_OK) {
+        fail(s);
+        break;
+      }
+      e = cudaGetLastError();
+    }
     S->cycles.fetch_add(1);
     hs.resize(S->slots.size());
     if (e == cudaSuccess)
@@ -1259,6 +1270,7 @@ void rt_server_opts_default(rt_server_opts* o) {
   o->precond = RT_PREC_LOCAL_LAMBDA;
   o->precision = RT_PRECISION_FP64;
   o->autotune = 1;
+  o->graphs = 1;
 }
 
 static rt_status create_server(const rt_server_opts* opts, const rt_allocator* hook, rt_server** out) {

@@ -49,7 +49,7 @@ int main(void) {
   printf("rt_problem_desc %zu\nrt_solver_opts %zu\nrt_solve_info %zu\nrt_server_opts %zu\nrt_server_stats %zu\n",
          sizeof(rt_problem_desc), sizeof(rt_solver_opts), sizeof(rt_solve_info), sizeof(rt_server_opts),
          sizeof(rt_server_stats));
-  F(rt_server_opts, precision); F(rt_server_opts, autotune);
+  F(rt_server_opts, precision); F(rt_server_opts, autotune); F(rt_server_opts, graphs);
   F(rt_server_stats, completed); F(rt_server_stats, grid_quad); F(rt_server_stats, tuned);
   F(rt_problem_desc, tau); F(rt_problem_desc, phi_center); F(rt_problem_desc, W2);
   F(rt_problem_desc, freq_norm); F(rt_problem_desc, form);

@@ -200,3 +200,30 @@ def test_config4_size_instance_in_a_mix_matches_the_exact_solution(cases):
         err = np.max(np.abs(x[sl] - x_ex[sl])) / scale
         own = np.max(np.abs(xo[sl] - x_ex[sl])) / scale
         assert err < max(1e-6, 2 * own), (name, err, own)
+
+
+def test_direct_launches_give_the_graph_results(cases):
+    """rt_server_opts.graphs = 0 launches every kernel of a restart cycle on
+    the server's stream instead of one captured graph: the same solutions
+    bit for bit, the same iteration counts, and the library's launch
+    counter advances by at least the cycles' kernels."""
+    from paper_2110_11873_gb300 import _native as NN
+    ats, trs, bs, xs = cases
+    problem(ats[0])
+    lib = NN.load()
+    out = {}
+    for graphs in (True, False):
+        srv = Server(mem_budget_bytes=1 << 30, max_slots=8, precond="local_lambda", precision="fp32_refine",
+                     graphs=graphs, autotune=False)
+        l0 = lib.rt_launch_count()
+        tickets = [srv.submit(a) for a in ats]
+        res = _wait(srv, tickets)
+        out[graphs] = ([res[t][2] for t in tickets], [res[t][1].iters for t in tickets],
+                       lib.rt_launch_count() - l0, srv.stats()["cycles"])
+        srv.close()
+    (xg, ig, lg, cg), (xd, id_, ld, cd) = out[True], out[False]
+    assert ig == id_
+    for a, b in zip(xg, xd):
+        np.testing.assert_array_equal(a, b)
+    assert ld >= cd > 0 and lg >= cg > 0, (lg, cg, ld, cd)
+
