@@ -52,7 +52,8 @@ typedef enum {
   RT_EBREAKDOWN = 5,   /* Krylov breakdown (zero denominator); x_dev holds the last iterate */
   RT_ENUMERIC = 6,     /* NaN or Inf met in a residual */
   RT_EPENDING = 7,     /* batch ticket not finished yet */
-  RT_ETIMEOUT = 8      /* a device-side bounded wait gave up */
+  RT_ETIMEOUT = 8,     /* a device-side bounded wait gave up */
+  RT_ECANCELED = 9     /* batch request cancelled (rt_batch_cancel) or past its deadline */
 } rt_status;
 
 /* optical-depth convention (reading of Sect. 4.1): the tau grid is line-centre
@@ -340,6 +341,8 @@ typedef struct {
   double* resid_hist;    /* optional host array: relative residual estimate per iteration */
   int32_t hist_cap;      /* its capacity */
   double omega;          /* SOR / SSOR relaxation parameter, 0 < omega < 2 (Sect. 2.3) */
+  double deadline_ms;    /* batch server only: a request not finished this long after its submission
+                            ends with RT_ECANCELED (checked between restart cycles); 0: none */
 } rt_solver_opts;
 
 typedef struct {
@@ -445,17 +448,27 @@ rt_status rt_server_create(const rt_server_opts* opts, rt_server** out);
 rt_status rt_server_create_with_allocator(const rt_server_opts* opts, const rt_allocator* allocator,
                                           rt_server** out);
 /* Queue one solve.  desc as for rt_problem_create (arrays copied; Ns <= 4096);
-   opts may be NULL (rtol 1e-8, maxit 10000) -- only rtol and maxit are read.
-   *ticket identifies the request for rt_poll. */
+   opts may be NULL (rtol 1e-8, maxit 10000, no deadline) -- only rtol, maxit
+   and deadline_ms are read.  *ticket identifies the request for rt_poll. */
 rt_status rt_batch_submit(rt_server* srv, const rt_problem_desc* desc, const rt_solver_opts* opts,
                           uint64_t* ticket);
 /* RT_EPENDING while the request is queued or resident; afterwards its final
    status (RT_OK, RT_ENOTCONV, RT_EBREAKDOWN, RT_ENUMERIC, RT_ENOMEM when the
-   instance cannot fit the budget even alone), with info filled (t_total_ms:
-   submission to completion) and, when x_host is not NULL, the N-vector
-   solution copied there.  A finished request is released by the poll that
-   reports it. */
+   instance cannot fit the budget even alone, RT_ECANCELED), with info filled
+   (t_total_ms: submission to completion) and, when x_host is not NULL, the
+   N-vector solution copied there (the iterate reached, for a request ended
+   by RT_ENOTCONV or RT_ECANCELED while resident; zeros for one that was
+   never admitted).  A finished request is released by the poll that reports
+   it. */
 rt_status rt_poll(rt_server* srv, uint64_t ticket, rt_solve_info* info, double* x_host);
+
+/* Cancel a request (no counterpart in the paper; a serving control).  A
+   queued request ends at once; a resident one at the end of the restart
+   cycle in progress, keeping the iterate it reached; either way rt_poll then
+   reports RT_ECANCELED.  A request that already finished is left as it is.
+   RT_OK, or RT_EINVAL for NULL or an unknown ticket (never issued, or
+   already released by rt_poll).  Host only; thread-safe. */
+rt_status rt_batch_cancel(rt_server* srv, uint64_t ticket);
 typedef struct {
   int32_t resident;          /* instances on the device now */
   int32_t queued;            /* submitted, not yet admitted */

@@ -11,9 +11,10 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librtkrylov.so")
 
-RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_EBREAKDOWN, RT_ENUMERIC, RT_EPENDING, RT_ETIMEOUT = range(9)
+(RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_EBREAKDOWN, RT_ENUMERIC, RT_EPENDING, RT_ETIMEOUT,
+ RT_ECANCELED) = range(10)
 STATUS_NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV",
-                5: "RT_EBREAKDOWN", 6: "RT_ENUMERIC", 7: "RT_EPENDING", 8: "RT_ETIMEOUT"}
+                5: "RT_EBREAKDOWN", 6: "RT_ENUMERIC", 7: "RT_EPENDING", 8: "RT_ETIMEOUT", 9: "RT_ECANCELED"}
 
 RT_TAU_LINE_CENTER, RT_TAU_FREQ_INTEGRATED = 0, 1
 RT_MU_GL_HALF, RT_MU_GL_FULL = 0, 1
@@ -42,7 +43,7 @@ class SolverOpts(C.Structure):
         ("restart", C.c_int32), ("maxit", C.c_int32), ("precond", C.c_int32), ("x0_kind", C.c_int32),
         ("ortho", C.c_int32), ("precision", C.c_int32), ("rtol", C.c_double), ("inner_rtol", C.c_double),
         ("max_refine", C.c_int32), ("resid_hist", C.POINTER(C.c_double)), ("hist_cap", C.c_int32),
-        ("omega", C.c_double),
+        ("omega", C.c_double), ("deadline_ms", C.c_double),
     ]
 
 
@@ -108,6 +109,7 @@ SIGNATURES = [
     ("rt_server_create_with_allocator", C.c_int, [C.POINTER(ServerOpts), C.POINTER(Allocator), C.POINTER(_P)]),
     ("rt_batch_submit", C.c_int, [_P, C.POINTER(ProblemDesc), C.POINTER(SolverOpts), C.POINTER(C.c_uint64)]),
     ("rt_poll", C.c_int, [_P, C.c_uint64, C.POINTER(SolveInfo), C.POINTER(C.c_double)]),
+    ("rt_batch_cancel", C.c_int, [_P, C.c_uint64]),
     ("rt_server_stats_get", C.c_int, [_P, C.POINTER(ServerStats)]),
     ("rt_server_destroy", C.c_int, [_P]),
     ("rt_last_error", C.c_char_p, []),

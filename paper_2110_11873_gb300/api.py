@@ -128,16 +128,22 @@ class Server:
         self.handle = h
         self.sizes = {}
 
-    def submit(self, atm, rtol: float = 1e-8, maxit: int = 10000) -> int:
+    def submit(self, atm, rtol: float = 1e-8, maxit: int = 10000, deadline_ms: float = 0.0) -> int:
+        """Queue one solve; deadline_ms > 0 cancels it if unfinished that long after submission."""
         keep = []
         d = _desc_of(atm, keep)
         o = N.SolverOpts()
         self.lib.rt_solver_opts_default(C.byref(o))
-        o.rtol, o.maxit = rtol, maxit
+        o.rtol, o.maxit, o.deadline_ms = rtol, maxit, deadline_ms
         t = C.c_uint64()
         N.check(self.lib.rt_batch_submit(self.handle, C.byref(d), C.byref(o), C.byref(t)), "rt_batch_submit")
         self.sizes[t.value] = 2 * d.Ns * d.Nmu * d.Nnu
         return t.value
+
+    def cancel(self, ticket: int) -> None:
+        """Cancel a request: a queued one ends at once, a resident one after the
+        restart cycle in progress; its poll then reports RT_ECANCELED."""
+        N.check(self.lib.rt_batch_cancel(self.handle, C.c_uint64(ticket)), "rt_batch_cancel")
 
     def poll(self, ticket: int, want_x: bool = True):
         """None while pending; else (status, SolveResult, x or None)."""

@@ -608,6 +608,8 @@ struct Request {
   std::vector<double> x;   // solution on completion
   rt_solve_info info{};
   bool done = false;
+  double deadline = 0;             // wall time (ms) past which the request is cancelled; 0: none
+  std::atomic<bool> cancel{false}; // set by rt_batch_cancel for a resident request
 };
 
 struct Instance {
@@ -1120,6 +1122,21 @@ void worker_main(Server* S) {
       for (Instance* in : S->slots) any_active |= in != nullptr;
       if (!any_active) S->cv.wait(lk, [&] { return S->stop || !S->pending.empty(); });
       if (S->stop) break;
+      // queued requests past their deadline (anywhere in the queue) end unadmitted
+      const double now = wall_ms();
+      for (auto q = S->pending.begin(); q != S->pending.end();) {
+        Request* rq = *q;
+        if (rq->cancel.load() || (rq->deadline > 0.0 && now > rq->deadline)) {
+          rq->info.status = RT_ECANCELED;
+          rq->t_done = now;
+          rq->info.t_total_ms = rq->t_done - rq->t_submit;
+          rq->done = true;
+          S->completed.fetch_add(1);
+          q = S->pending.erase(q);
+        } else {
+          ++q;
+        }
+      }
       int freeslots = 0;
       for (Instance* in : S->slots) freeslots += in == nullptr;
       while (!S->pending.empty() && (int)admit.size() < freeslots) {
@@ -1150,6 +1167,7 @@ void worker_main(Server* S) {
         std::lock_guard<std::mutex> lk(S->mu);
         rq->info.status = s;
         rq->done = true;
+        S->completed.fetch_add(1);
         continue;
       }
       S->slots[slot] = in;
@@ -1170,6 +1188,7 @@ void worker_main(Server* S) {
         S->pending.pop_front();
         rq->info.status = RT_ENOMEM;
         rq->done = true;
+        S->completed.fetch_add(1);
       }
       continue;
     }
@@ -1230,6 +1249,8 @@ void worker_main(Server* S) {
       else if (st.iters >= in->req->maxit) fin = RT_ENOTCONV;
       else if (st.breakdown && st.kdone == 0) fin = RT_EBREAKDOWN;
       else if (st.kstop == 0) fin = RT_ENOTCONV;
+      else if (in->req->cancel.load() || (in->req->deadline > 0.0 && wall_ms() > in->req->deadline))
+        fin = RT_ECANCELED;
       if (fin != RT_EPENDING) {
         finish_request(S, in, st, fin);
         free_instance(S, in);
@@ -1370,8 +1391,13 @@ rt_status rt_batch_submit(rt_server* srv, const rt_problem_desc* desc, const rt_
     if (!(opts->rtol > 0.0) || opts->maxit < 1) { set_error("rtol must be > 0 and maxit >= 1"); return RT_EINVAL; }
     rq->rtol = opts->rtol;
     rq->maxit = opts->maxit;
+    if (opts->deadline_ms < 0.0 || opts->deadline_ms != opts->deadline_ms) {
+      set_error("deadline_ms must be >= 0");
+      return RT_EINVAL;
+    }
   }
   rq->t_submit = wall_ms();
+  if (opts && opts->deadline_ms > 0.0) rq->deadline = rq->t_submit + opts->deadline_ms;
   rq->info.status = RT_EPENDING;
   const uint64_t t = S->next_ticket.fetch_add(1);
   rq->ticket = t;
@@ -1409,8 +1435,35 @@ rt_status rt_poll(rt_server* srv, uint64_t ticket, rt_solve_info* info, double* 
     S->requests.erase(it);
   }
   if (info) *info = done->info;
-  if (x_host && !done->x.empty()) memcpy(x_host, done->x.data(), done->x.size() * sizeof(double));
+  if (x_host) {
+    if (!done->x.empty()) memcpy(x_host, done->x.data(), done->x.size() * sizeof(double));
+    else   // never admitted (cancelled while queued, or no room in the budget): zeros
+      memset(x_host, 0, (size_t)2 * done->desc.Ns * done->desc.Nmu * done->desc.Nnu * sizeof(double));
+  }
   return done->info.status;
+}
+
+rt_status rt_batch_cancel(rt_server* srv, uint64_t ticket) {
+  clear_error();
+  if (!srv) { set_error("srv is NULL"); return RT_EINVAL; }
+  Server* S = &srv->S;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->requests.find(ticket);
+  if (it == S->requests.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return RT_EINVAL; }
+  Request* rq = it->second.get();
+  if (rq->done) return RT_OK;
+  for (auto q = S->pending.begin(); q != S->pending.end(); ++q)
+    if (*q == rq) {   // still queued: it ends now
+      S->pending.erase(q);
+      rq->info.status = RT_ECANCELED;
+      rq->t_done = wall_ms();
+      rq->info.t_total_ms = rq->t_done - rq->t_submit;
+      rq->done = true;
+      S->completed.fetch_add(1);
+      return RT_OK;
+    }
+  rq->cancel.store(true);   // admitted: the worker ends it after the current cycle
+  return RT_OK;
 }
 
 rt_status rt_server_stats_get(rt_server* srv, rt_server_stats* out) {

@@ -54,7 +54,7 @@ int main(void) {
   F(rt_problem_desc, tau); F(rt_problem_desc, phi_center); F(rt_problem_desc, W2);
   F(rt_problem_desc, freq_norm); F(rt_problem_desc, form);
   F(rt_solver_opts, rtol); F(rt_solver_opts, resid_hist); F(rt_solver_opts, hist_cap);
-  F(rt_solver_opts, omega);
+  F(rt_solver_opts, omega); F(rt_solver_opts, deadline_ms);
   F(rt_solve_info, rel_resid); F(rt_solve_info, err_est); F(rt_solve_info, t_total_ms);
   printf("rt_allocator %zu\n", sizeof(rt_allocator));
   F(rt_allocator, ctx); F(rt_allocator, alloc); F(rt_allocator, release);
@@ -173,3 +173,4 @@ def test_allocator_hook_probe_and_injection_arguments_are_checked_on_the_host(li
     assert lib.rt_probe_fp64_fma(0, C.c_void_p(16), None) == -1
     assert lib.rt_probe_fp64_fma(10, None, None) == -1
     assert lib.rt_problem_inject_wait_timeout(None, 1) == N.RT_EINVAL
+    assert lib.rt_batch_cancel(None, 1) == N.RT_EINVAL

@@ -227,3 +227,67 @@ def test_direct_launches_give_the_graph_results(cases):
         np.testing.assert_array_equal(a, b)
     assert ld >= cd > 0 and lg >= cg > 0, (lg, cg, ld, cd)
 
+
+
+def _until(cond, timeout=60.0):
+    t0 = time.time()
+    while not cond():
+        assert time.time() - t0 < timeout, "server state not reached"
+        time.sleep(0.002)
+
+
+def test_cancel_and_deadline(cases):
+    """rt_batch_cancel ends a queued request at once (x zeros) and a resident
+    one after the restart cycle in progress (x the iterate it reached); a
+    request past deadline_ms ends the same way, whether resident or still
+    queued; each reports RT_ECANCELED, and later requests on the same server
+    are solved as usual."""
+    ats, trs, bs, xs = cases
+    # unpreconditioned GMRES(10) on a thick, strongly scattering slab: thousands of cycles
+    slow = W.slab(120, 16, 41, 1e-4, 1e8, 8.0, eps=1e-6, name="slow")
+    n_slow = 2 * 120 * 16 * 41
+    srv = Server(mem_budget_bytes=1 << 30, max_slots=1, restart=10, precond="none", autotune=False)
+    t_res = srv.submit(slow, rtol=1e-14, maxit=10 ** 7)
+    t_q = srv.submit(slow, rtol=1e-14, maxit=10 ** 7)
+    _until(lambda: srv.stats()["resident"] == 1 and srv.stats()["cycles"] >= 2)
+    assert srv.stats()["queued"] == 1 and srv.poll(t_q) is None
+    srv.cancel(t_q)
+    st, info, x = srv.poll(t_q)        # finished by the cancel call itself
+    assert st == N.RT_ECANCELED and info.status == N.RT_ECANCELED and info.iters == 0
+    assert x.shape == (n_slow,) and not np.any(x)
+    with pytest.raises(N.RTError):     # released by the poll that reported it
+        srv.cancel(t_q)
+
+    srv.cancel(t_res)
+    (st, info, x), = _wait(srv, [t_res], timeout=30).values()
+    assert st == N.RT_ECANCELED and info.iters >= 20 and info.restarts >= 2, info
+    assert np.all(np.isfinite(x)) and np.any(x) and 0.0 < info.rel_resid < 1.0, info
+
+    # deadline while resident
+    t_d = srv.submit(slow, rtol=1e-14, maxit=10 ** 7, deadline_ms=300.0)
+    (st, info, x), = _wait(srv, [t_d], timeout=30).values()
+    assert st == N.RT_ECANCELED and info.t_total_ms >= 300.0 and info.iters > 0, info
+    assert np.any(x)
+
+    # deadline while queued behind a resident request
+    t_hold = srv.submit(slow, rtol=1e-14, maxit=10 ** 7)
+    _until(lambda: srv.stats()["resident"] == 1)
+    t_qd = srv.submit(slow, rtol=1e-14, maxit=10 ** 7, deadline_ms=100.0)
+    (st, info, x), = _wait(srv, [t_qd], timeout=30).values()
+    assert st == N.RT_ECANCELED and info.iters == 0 and info.t_total_ms >= 100.0, info
+    assert not np.any(x)
+    assert srv.poll(t_hold) is None    # the resident request is untouched
+    srv.cancel(t_hold)
+    (st, info, x), = _wait(srv, [t_hold], timeout=30).values()
+    assert st == N.RT_ECANCELED
+
+    # the server goes on serving
+    t_ok = srv.submit(ats[0], maxit=20000)
+    (st, info, x), = _wait(srv, [t_ok], timeout=120).values()
+    assert st == N.RT_OK, info
+    assert np.linalg.norm(bs[0] - trs[0].apply_I(x)) / np.linalg.norm(bs[0]) < 1e-8
+    s = srv.stats()
+    assert s["completed"] == 6 and s["resident"] == 0 and s["queued"] == 0, s
+    with pytest.raises(N.RTError):
+        srv.submit(slow, deadline_ms=-1.0)
+    srv.close()
