@@ -440,6 +440,19 @@ def solve_alg_bytes(info, N: int, m: int = 30) -> float:
     return total
 
 
+def reduce_over_ranks(seconds: float, counts, dist, device: str):
+    """Whole-job timing over the ranks: (the slowest rank's time, the sum of
+    each count over all ranks).  dist None: this process alone.  NCCL takes
+    device tensors, gloo host ones."""
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    c = torch.tensor([float(v) for v in counts], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(v) for v in c.tolist()]
+
+
 def bench_config(precond: str, world: int) -> dict:
     """The `config` object of both arms' JSON lines."""
     return {"workload": WORKLOAD, "precond": precond, "restart": 30, "rtol": 1e-8,
@@ -567,14 +580,7 @@ def main():
         e1.record(stream)
         barrier()
         launches1 = lib.rt_launch_count()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    cnt = torch.tensor([applies, solves], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    applies_all, solves_all = (float(v) for v in cnt.tolist())
+    ms_max, (applies_all, solves_all) = reduce_over_ranks(e0.elapsed_time(e1), (applies, solves), dist, "cuda")
     value = applies_all / (ms_max / 1000.0)
 
     peaks = {}
@@ -686,11 +692,8 @@ def main():
         x_host.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
         e2e_applies += info.applies
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = e2e_applies * world / float(te.item())
+    e2e_max, (e2e_all,) = reduce_over_ranks(time.perf_counter() - t0, (e2e_applies,), dist, "cuda")
+    e2e_value = e2e_all / e2e_max
 
     # ---- the small atmosphere: slab70, FP64 Jacobi-GMRES(30)
     small = None

@@ -43,6 +43,40 @@ def test_reference_arm_two_ranks_gloo():
     assert len(lines) == 1 and lines[0]["n_gpus"] == 2
 
 
+def _reduce_rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r: 10 (r + 1) ms, 100 (r + 1) applies, r + 1 solves
+        q.put((rank, bench.reduce_over_ranks(10.0 * (rank + 1), (100 * (rank + 1), rank + 1), dist, "cpu")))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_rank_reduction_two_ranks_gloo():
+    """The whole-job figures of an N-rank bench run: the time is the slowest
+    rank's, the applies and solves the sum over ranks (two gloo ranks on the
+    CPU; the GPU run does the same over NCCL)."""
+    import multiprocessing as mp
+
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_over_ranks(3.0, (5, 1), None, "cpu") == (3.0, [5.0, 1.0])
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_reduce_rank, args=(r, 2, 29637, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out[0] == out[1] == (20.0, [300.0, 3.0])
+
+
 def test_oracle_per_solve_check_of_saved_solutions(tmp_path):
     """The CPU leg's per-solve check: a saved solution is identified by its
     distribution (seed), index and count; the oracle recomputes b, the true
