@@ -19,8 +19,9 @@ LIB = os.path.join(HERE, "librtkrylov.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# a missing return in a non-void function is an error (device front end and host compiler)
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
-          "--expt-relaxed-constexpr", "-I" + INCLUDE]
+          "--expt-relaxed-constexpr", "--diag-error", "940", "-Xcompiler", "-Werror=return-type", "-I" + INCLUDE]
 
 
 def nvcc() -> str:

@@ -528,6 +528,8 @@ __global__ void k_lsq(GmresDev* gm, int m) {
 }
 
 // t = sum_{i<k} y_i V_i; mode 0: x += t, 1: x += dinv*t, 2: t stored for P^{-1}
+// (with no step done, t = 0, so that the x += P^{-1} t that follows adds nothing
+// rather than the previous cycle's update once more)
 __global__ void __launch_bounds__(kVecThreads) k_combine(const double* __restrict__ V, int64_t N,
                                                          const GmresDev* gm, double* __restrict__ x,
                                                          const double* __restrict__ dinv, double* __restrict__ t,
@@ -536,7 +538,12 @@ __global__ void __launch_bounds__(kVecThreads) k_combine(const double* __restric
   __shared__ double ys[kMaxRestart];
   for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = gm->y[i];
   __syncthreads();
-  if (k == 0) return;
+  if (k == 0) {
+    if (mode == 2)
+      for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        t[n] = 0.0;
+    return;
+  }
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int i = 0; i < k; ++i) s = fma(ys[i], V[(int64_t)i * N + n], s);
@@ -1029,13 +1036,23 @@ struct GmresGraphKey {
 
 constexpr int kNumPrec = RT_PREC_SSOR_LEFT + 1;
 
+// bytes of one host copy of a solver's state header (GMRES or BiCGSTAB/CGS)
+constexpr size_t kHdrBytes = ((kGmresHeader > sizeof(BicgDev) ? kGmresHeader : sizeof(BicgDev)) + 255) / 256 * 256;
+
 struct GraphCache {
   std::map<GmresGraphKey, cudaGraphExec_t> gmres;
   cudaGraphExec_t bicg[2][kNumPrec][2] = {};  // [method][precond][fp32]
   cudaGraphExec_t rich[kNumPrec] = {};         // [precond]
   std::map<cudaGraphExec_t, long long> kernels;  // kernel nodes per executable graph
   cudaStream_t cap = nullptr;
+  // two pinned host copies of the state header and the events that mark
+  // them written: the host reads one launch's copy while the next runs
+  unsigned char* hdr = nullptr;
+  cudaEvent_t hev[2] = {nullptr, nullptr};
   ~GraphCache() {
+    if (hdr) cudaFreeHost(hdr);
+    for (cudaEvent_t e : hev)
+      if (e) cudaEventDestroy(e);
     for (auto& kv : gmres) cudaGraphExecDestroy(kv.second);
     for (auto& a : bicg)
       for (auto& b : a)
@@ -1181,6 +1198,49 @@ static rt_status launch_graph(GraphCache* gc, cudaGraphExec_t ex, cudaStream_t s
   return RT_OK;
 }
 
+// Launches `ex` until `stop(header)` holds, one launch ahead of the host:
+// launch k+1 and the copy of its state header are queued before the host
+// waits for launch k's copy, so the device does not idle while the host
+// reads a header and decides.  The graphs this serves leave the state
+// unchanged when they run after a stop (their steps are gated off, or they
+// repeat a step that changes nothing), so the extra launch queued when the
+// stop is seen is waited for and not counted.  `dev` is the header's device
+// address, `out` receives the header of the stopping launch; `launches`
+// counts the launches up to it.
+template <typename Hdr, typename Stop>
+static rt_status launch_until(GraphCache* gc, cudaGraphExec_t ex, const Hdr* dev, Hdr* out, size_t bytes,
+                              cudaStream_t st, int* launches, Stop&& stop) {
+  if (bytes > kHdrBytes) {
+    set_error("internal: solver header larger than its host copy");
+    return RT_EINVAL;
+  }
+  if (!gc->hdr) {
+    RT_TRY_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&gc->hdr), 2 * kHdrBytes, cudaHostAllocDefault));
+    for (cudaEvent_t& e : gc->hev) RT_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  auto enqueue = [&](int slot) -> rt_status {
+    RT_TRY(launch_graph(gc, ex, st));
+    RT_TRY_CUDA(cudaMemcpyAsync(gc->hdr + slot * kHdrBytes, dev, bytes, cudaMemcpyDeviceToHost, st));
+    RT_TRY_CUDA(cudaEventRecord(gc->hev[slot], st));
+    return RT_OK;
+  };
+  *launches = 0;
+  RT_TRY(enqueue(0));
+  for (int k = 0;; ++k) {
+    const rt_status s = enqueue((k + 1) & 1);   // one ahead
+    if (s != RT_OK) {
+      cudaStreamSynchronize(st);
+      return s;
+    }
+    RT_TRY_CUDA(cudaEventSynchronize(gc->hev[k & 1]));
+    memcpy(static_cast<void*>(out), gc->hdr + (k & 1) * kHdrBytes, bytes);
+    *launches += 1;
+    if (stop(*out)) break;
+  }
+  RT_TRY_CUDA(cudaStreamSynchronize(st));   // the launch queued ahead (no effect)
+  return RT_OK;
+}
+
 static rt_status get_graph(Problem* P, GraphCache* gc, int m, int precond, int fp32, cudaGraphExec_t* out) {
   GmresGraphKey key{m, precond, fp32};
   auto it = gc->gmres.find(key);
@@ -1246,18 +1306,16 @@ static rt_status gmres_core(Problem* P, const rt_solver_opts* o, int fp32, doubl
   GraphCache* gc = cache_of(P);
   cudaGraphExec_t ex;
   RT_TRY(get_graph(P, gc, m, o->precond, fp32, &ex));
-  for (;;) {
-    RT_NVTX("GMRES restart cycle (graph)");
-    RT_TRY(launch_graph(gc, ex, st));
-    RT_TRY_CUDA(cudaMemcpyAsync(hs, P->gm, kGmresHeader, cudaMemcpyDeviceToHost, st));
-    RT_TRY_CUDA(cudaStreamSynchronize(st));
-    *cycles += 1;
-    if (hs->rel != hs->rel) return RT_OK;
-    if (!(hs->rel >= tol)) return RT_OK;
-    if (hs->iters >= maxit) return RT_OK;
-    if (hs->breakdown && hs->kdone == 0) return RT_OK;
-    if (hs->kstop == 0) return RT_OK;
-  }
+  // A cycle that runs after one of these stops changes nothing: k_cycle_start
+  // of the stopping cycle set kstop = 0 (converged, NaN, no steps left), so
+  // every step is gated off and the update and residual repeat exactly; or
+  // the first step broke down, which the next cycle repeats with the same
+  // result (no step done, x unchanged).
+  RT_NVTX("GMRES restart cycles (graphs)");
+  RT_TRY(launch_until(gc, ex, P->gm, hs, kGmresHeader, st, cycles, [&](const GmresDev& h) {
+    return h.rel != h.rel || !(h.rel >= tol) || h.iters >= maxit || (h.breakdown && h.kdone == 0) || h.kstop == 0;
+  }));
+  return RT_OK;
 }
 
 static rt_status prepare(Problem* P, const rt_solver_opts* o, int restart, cudaStream_t st) {
@@ -1465,7 +1523,8 @@ static rt_status enqueue_bicg_iter(Problem* P, int method, int precond, int fp32
 // a kernel that skips when done: apply_prec launches operator kernels that do
 // not look at the flag, so an iteration after convergence still computes an
 // (unused) product; the graph therefore holds one iteration and the host
-// checks the flag after every launch.
+// checks the flag after every launch (one launch behind the device,
+// launch_until).
 // Richardson iterations of one graph launch: vectors x = wk(0), b = wk(1),
 // r = wk(2), Ax = wk(5), z = wk(6)
 static rt_status enqueue_rich(Problem* P, int precond, cudaStream_t st) {
@@ -1628,12 +1687,16 @@ static rt_status bicg_core(Problem* P, int method, const rt_solver_opts* o, int 
   }
   RT_TRY_CUDA(cudaMemcpyAsync(hs, P->bc, sizeof *hs, cudaMemcpyDeviceToHost, st));
   RT_TRY_CUDA(cudaStreamSynchronize(st));
-  while (!hs->done) {
-    RT_NVTX("BiCGSTAB/CGS iteration (graph)");
-    RT_TRY(launch_graph(gc, ex, st));
-    RT_TRY_CUDA(cudaMemcpyAsync(hs, P->bc, sizeof *hs, cudaMemcpyDeviceToHost, st));
-    RT_TRY_CUDA(cudaStreamSynchronize(st));
-    *applies += (hs->half ? 1 : 2);
+  if (!hs->done) {
+    // An iteration after the stop changes nothing: its vector kernels skip
+    // (the half-step update is applied once, marked by half = 2) and its
+    // operator products are recomputed from unchanged inputs.
+    RT_NVTX("BiCGSTAB/CGS iterations (graphs)");
+    int its = 0;
+    RT_TRY(launch_until(gc, ex, P->bc, hs, sizeof *hs, st, &its, [&](const BicgDev& h) {
+      *applies += h.half ? 1 : 2;
+      return h.done != 0;
+    }));
   }
   // x = x0 + M^{-1} acc
   RT_TRY(add_precond(P, x0, acc, o->precond, wk(P, 6), st));

@@ -108,7 +108,6 @@ static double dawson(double x) {
 static double voigt_H(double a, double x) {
   typedef std::complex<double> C;
   const double rsp = 1.0 / sqrt(M_PI);
-  C wm1(0.0, 0.0);
   C w0(exp(-x * x), 2.0 * rsp * dawson(x));
   C w1 = -2.0 * x * w0 + C(0.0, 2.0 * rsp);
   C ia(0.0, a), pw(1.0, 0.0);
@@ -125,7 +124,6 @@ static double voigt_H(double a, double x) {
     wprev = wn;
     wn = wnext;
   }
-  (void)wm1;
   return sum;
 }
 
