@@ -336,7 +336,10 @@ typedef struct {
   int32_t ortho;         /* GMRES Arnoldi: RT_ORTHO_MGS (default) or RT_ORTHO_CGS2 */
   int32_t precision;     /* RT_PRECISION_FP64, or FP32 operator inside FP64 iterative refinement */
   double rtol;           /* stop when ||b - A x||_2 / ||b||_2 < rtol (Sect. 4.2) */
-  double inner_rtol;     /* FP32_REFINE: relative tolerance of each inner solve (e.g. 1e-4) */
+  double inner_rtol;     /* FP32_REFINE: relative tolerance of each inner solve; <= 0: GMRES takes
+                            rtol (each restart of its inner solve starts from the FP64 residual, so
+                            one inner solve refines at every restart), BiCGSTAB/CGS 1e-4.  A step's
+                            tolerance is at least rtol * ||b|| / ||r|| (no step over-solves) */
   int32_t max_refine;    /* FP32_REFINE: cap on refinement steps */
   double* resid_hist;    /* optional host array: relative residual estimate per iteration */
   int32_t hist_cap;      /* its capacity */
@@ -363,7 +366,8 @@ typedef struct {
 } rt_solve_info;
 
 /* Fill opts with defaults: restart 30, maxit 10000, Jacobi, x0 = 0, MGS,
-   FP64, rtol 1e-8, inner_rtol 1e-4, max_refine 20, no history, omega 1. */
+   FP64, rtol 1e-8, inner_rtol 0 (per solver, above), max_refine 20, no
+   history, omega 1. */
 void rt_solver_opts_default(rt_solver_opts* opts);
 
 /* Right-preconditioned restarted GMRES(m) (Sect. 2.1; Saad & Schultz 1986),

@@ -348,12 +348,14 @@ class Problem:
     # --------------------------------------------------------------- solvers
     def solve(self, b: torch.Tensor, method: str = "gmres", x: Optional[torch.Tensor] = None, *,
               restart: int = 30, maxit: int = 10000, precond: str = "jacobi", rtol: float = 1e-8,
-              x0=False, precision: str = "fp64", inner_rtol: float = 1e-4, max_refine: int = 20,
+              x0=False, precision: str = "fp64", inner_rtol: float = 0.0, max_refine: int = 20,
               hist_cap: int = 0, omega: float = 1.0, raise_on_error: bool = True, stream=None):
         """Solve A x = b; returns (x, SolveResult).  ``x0=True`` uses ``x`` as initial guess,
         ``x0="paper"`` the paper's (sigma = [1, 0, 1, 0, ...], lifted to the I-form).
         ``precond``: "none", "jacobi", "local_lambda", "jacobi_left" (GMRES), and for the
-        sigma-form "sor", "ssor", "sor_left", "ssor_left" (GMRES) with relaxation ``omega``."""
+        sigma-form "sor", "ssor", "sor_left", "ssor_left" (GMRES) with relaxation ``omega``.
+        ``inner_rtol`` (precision "fp32_refine"): 0 takes the library's default, rtol for
+        GMRES and 1e-4 for BiCGSTAB/CGS."""
         b = self._vec(b)
         x = self._vec(x) if x is not None else torch.zeros(self.N, dtype=torch.float64, device=self.device)
         o = N.SolverOpts()

@@ -1425,6 +1425,11 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
   } else {
     // FP32 operator inside FP64 iterative refinement:
     //   r = b - A64 x (FP64);  solve A32 d = r to inner_rtol;  x += d
+    // Every restart cycle of the inner GMRES starts from its own FP64
+    // residual, so the inner solve refines at each restart by itself; its
+    // default tolerance is the outer one (one inner solve normally suffices).
+    // No step asks for more than the outer tolerance still needs.
+    const double inner0 = o->inner_rtol > 0 ? o->inner_rtol : o->rtol;
     double* xb = wk(P, 7);   // the outer iterate
     RT_TRY_CUDA(cudaMemcpyAsync(xb, wk(P, 0), bytes, cudaMemcpyDeviceToDevice, st));
     double* bsave = wk(P, 8);
@@ -1440,7 +1445,7 @@ static rt_status solve_gmres(Problem* P, const rt_solver_opts* o, const double* 
       // inner solve: b <- r, x <- 0
       RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), wk(P, 2), bytes, cudaMemcpyDeviceToDevice, st));
       RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
-      RT_TRY(gmres_core(P, o, 1, o->inner_rtol > 0 ? o->inner_rtol : 1e-4, o->maxit - iters, true, &hs, &cycles, st));
+      RT_TRY(gmres_core(P, o, 1, std::max(inner0, o->rtol / rel), o->maxit - iters, true, &hs, &cycles, st));
       if (hs.iters > 0) est = hs.est * rel;   // relative to the inner b = r, which is rel * ||b||
       iters += hs.iters;
       applies += hs.iters + cycles;
@@ -1744,6 +1749,10 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
   } else {
     // FP32 operator inside FP64 iterative refinement, as for GMRES:
     //   r = b - A64 x (FP64);  solve A32 d = r to inner_rtol;  x += d
+    // The inner iteration never forms the FP64 residual, so its default
+    // tolerance is 1e-4; no step asks for more than the outer tolerance
+    // still needs.
+    const double inner0 = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
     double* xb = P->V + 3 * (size_t)N;    // the outer iterate
     double* bsave = P->V + 4 * (size_t)N;
     if (o->x0_kind == RT_X0_ZERO) RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
@@ -1758,8 +1767,8 @@ static rt_status solve_bicg(Problem* P, int method, const rt_solver_opts* o, con
       if (rel < o->rtol) { s = RT_OK; break; }
       RT_NVTX("refinement step");
       RT_TRY_CUDA(cudaMemcpyAsync(wk(P, 1), wk(P, 2), bytes, cudaMemcpyDeviceToDevice, st));
-      RT_TRY(bicg_core(P, method, o, 1, o->inner_rtol > 0 ? o->inner_rtol : 1e-4, o->maxit - iters, true, &hs,
-                       &applies, &zero_b, st));
+      RT_TRY(bicg_core(P, method, o, 1, std::max(inner0, o->rtol / rel), o->maxit - iters, true, &hs, &applies,
+                       &zero_b, st));
       iters += hs.iters;
       refine_steps += 1;
       const rt_status inner = bicg_status(hs);
@@ -1818,7 +1827,7 @@ void rt_solver_opts_default(rt_solver_opts* o) {
   o->ortho = RT_ORTHO_MGS;
   o->precision = RT_PRECISION_FP64;
   o->rtol = 1e-8;
-  o->inner_rtol = 1e-4;
+  o->inner_rtol = 0.0;   // per solver: GMRES rtol, BiCGSTAB/CGS 1e-4
   o->max_refine = 20;
   o->omega = 1.0;
 }

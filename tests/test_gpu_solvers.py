@@ -130,6 +130,29 @@ def test_mixed_precision_refinement_slab70(slab70):
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-6
 
 
+@pytest.mark.parametrize("prec", ["jacobi", "local_lambda"])
+def test_fp32_refine_default_refines_at_every_restart(slab70, prec):
+    """The default inner tolerance of FP32-refine GMRES is the outer one:
+    every restart cycle of the inner solve starts from its FP64 residual, so
+    the one inner solve is the refinement.  It meets the stopping rule with
+    the oracle's FP64 operator, in one outer step, with an Arnoldi step count
+    close to the FP64 solver's; and a smaller explicit inner tolerance stops
+    where the outer one is met instead of over-solving."""
+    at, P, tr, b, xs = slab70
+    _, i64 = P.solve(to_dev(b), "gmres", precond=prec, rtol=1e-8)
+    xg, info = P.solve(to_dev(b), "gmres", precond=prec, rtol=1e-8, precision="fp32_refine")
+    assert info.ok and info.refine_steps == 1, info
+    assert info.iters <= 1.3 * i64.iters + 10, (info.iters, i64.iters)
+    x = to_host(xg)
+    assert _true_rel(tr, b, x) < 1e-8
+    if prec == "local_lambda":   # well conditioned: the residual bounds the error
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-6
+    _, i6 = P.solve(to_dev(b), "gmres", precond=prec, rtol=1e-8, precision="fp32_refine", inner_rtol=1e-6)
+    # a second step asks only for what the outer tolerance still needs (about
+    # 1e-2), not 1e-6 again (which took the residual to about 1e-12)
+    assert i6.ok and i6.refine_steps <= 2 and i6.rel_resid > 1e-11, i6
+
+
 def test_user_initial_guess_and_zero_rhs(slab70):
     at, P, tr, b, xs = slab70
     # the exact solution as initial guess: converged before any iteration
