@@ -140,11 +140,17 @@ def test_null_arguments_are_rejected(lib):
     o = N.SolverOpts()
     lib.rt_solver_opts_default(C.byref(o))
     assert (o.restart, o.maxit, o.precond, o.rtol, o.omega) == (30, 10000, N.RT_PREC_JACOBI, 1e-8, 1.0)
+    # the documented rest: x0 = 0, MGS, FP64, inner_rtol 0 (per solver), max_refine 20, no history, no deadline
+    assert (o.x0_kind, o.ortho, o.precision, o.inner_rtol, o.max_refine) == (N.RT_X0_ZERO, N.RT_ORTHO_MGS,
+                                                                            N.RT_PRECISION_FP64, 0.0, 20)
+    assert not o.resid_hist and o.hist_cap == 0 and o.deadline_ms == 0.0
     info = N.SolveInfo()
     assert lib.rt_solve_gmres(None, C.byref(o), None, None, C.byref(info), None) == N.RT_EINVAL
     so = N.ServerOpts()
     lib.rt_server_opts_default(C.byref(so))
     assert so.max_slots == 64 and so.restart == 30
+    assert (so.mem_budget_bytes, so.precond, so.precision, so.autotune, so.graphs) == (
+        8 << 30, N.RT_PREC_LOCAL_LAMBDA, N.RT_PRECISION_FP64, 1, 1)
     so.max_slots = 0
     h = C.c_void_p()
     assert lib.rt_server_create(C.byref(so), C.byref(h)) == N.RT_EINVAL and not h.value
