@@ -816,7 +816,9 @@ __global__ void __launch_bounds__(kVecThreads) k_mul(const double* __restrict__ 
 // check kernel lowers (and flags in kdone) once the iteration has stopped.
 constexpr int kRichSteps = 8;
 
-__global__ void k_rich_begin(GmresDev* gm) { gm->kstop = kRichSteps; }
+// arms the launch's steps, unless an earlier launch stopped (kdone): then the
+// launch changes nothing
+__global__ void k_rich_begin(GmresDev* gm) { gm->kstop = gm->kdone ? 0 : kRichSteps; }
 
 // x += d * z (Jacobi) or x += z
 __global__ void __launch_bounds__(kVecThreads) k_rich_update(double* __restrict__ x, const double* __restrict__ z,
@@ -1605,12 +1607,10 @@ static rt_status solve_richardson(Problem* P, const rt_solver_opts* o, const dou
       const int prec = o->precond;
       RT_TRY(capture_graph(gc, [&](cudaStream_t cs) { return enqueue_rich(P, prec, cs); }, &ex));
     }
-    for (;;) {
-      RT_TRY(launch_graph(gc, ex, st));
-      RT_TRY_CUDA(cudaMemcpyAsync(&hs, P->gm, kGmresHeader, cudaMemcpyDeviceToHost, st));
-      RT_TRY_CUDA(cudaStreamSynchronize(st));
-      if (hs.kdone) break;   // stopped inside this launch
-    }
+    RT_NVTX("Richardson iterations (graphs)");
+    int launches = 0;
+    RT_TRY(launch_until(gc, ex, P->gm, &hs, kGmresHeader, st, &launches,
+                        [](const GmresDev& h) { return h.kdone != 0; }));   // stopped inside this launch
   } else if (hs.bnorm == 0.0) {
     RT_TRY_CUDA(cudaMemsetAsync(wk(P, 0), 0, bytes, st));
     hs.rel = 0.0;
