@@ -374,7 +374,10 @@ void rt_solver_opts_default(rt_solver_opts* opts);
    left-preconditioned with RT_PREC_JACOBI_LEFT, RT_PREC_SOR_LEFT or
    RT_PREC_SSOR_LEFT (then FP64 only; rel_resid is the preconditioned
    residual).  A cycle with m >= the steps needed is the
-   paper's unrestarted GMRES.  b_dev, x_dev: N doubles.  Returns RT_OK when
+   paper's unrestarted GMRES.  With RT_PRECISION_FP32_REFINE the Arnoldi
+   steps apply the FP32 operator and every restart cycle starts from the FP64
+   residual b - A x; outer refinement steps (x += d, d from an inner solve to
+   inner_rtol) wrap that.  b_dev, x_dev: N doubles.  Returns RT_OK when
    converged, RT_ENOTCONV at maxit, RT_EBREAKDOWN, RT_ENUMERIC; in each case
    x_dev holds the iterate. */
 rt_status rt_solve_gmres(rt_problem* prob, const rt_solver_opts* opts, const double* b_dev,
